@@ -1,0 +1,360 @@
+"""Benchmark of the GB300 cut-cell multigrid solve (one JSON line on rank 0).
+
+Workload: the unit square minus the disk of radius 0.2 at (0.5, 0.5),
+a u_xx + b u_xy + c u_yy = f with (a, b, c) = (1, 0.5, 2), Dirichlet data on
+the box and Neumann data on the circle, manufactured u = exp(x) cos(2y), on
+1024 x 1024 cells (the finest grid of the disk refinement sweep).  A step is
+one whole solve through the C ABI: assembly of b = f - N g, then FP32 W(3,3)
+cycles inside FP64 iterative refinement until ||b - A u||_inf / ||b||_inf <
+1e-10, from u = 0.  Setup (cut cells, fits, factorisations) runs once before
+timing, as it does for a cached hierarchy.
+
+Timing: CUDA events around every step on the solve stream; an L2 flush (a
+512 MB write) runs between steps outside the events.  `value` is the solved
+DOF/s of the whole job (all ranks).  `e2e` is the same metric through
+cc_solve_host from pinned host memory, copies included.
+
+--impl reference times the FP64 CPU oracle (the method as a plain numpy /
+scipy program) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 1024
+TOL = 1e-10
+MIN_COARSE = 16
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    """Rank, world size and a max-over-ranks reducer (torchrun or single)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world == 1:
+        return rank, world, local, (lambda x: x), (lambda: None)
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    dev = torch.device("cuda", local) if backend == "nccl" else torch.device("cpu")
+
+    def red_max(x: float) -> float:
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return rank, world, local, red_max, dist.barrier
+
+
+def aggregate(dof_per_rank: float, ms_per_step_max: float, world: int) -> float:
+    """Whole-job DOF/s: every rank solves its own problem per step."""
+    return dof_per_rank * world / (ms_per_step_max / 1e3)
+
+
+def _problem():
+    from paper_2601_02975_gb300 import workloads as W
+    return W.problem_disk()
+
+
+# ---------------------------------------------------------------------------
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from paper_2601_02975_gb300 import inputs as I
+
+    rank, world, local, red_max, barrier = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    barrier()
+    __graft_entry__.build()
+    P = _problem()
+    n = a.n
+    opts = default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1, max_cycles=60)
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n, opts)
+    f, g, ue = I.problem_inputs(H, P)
+    present = H.cell_types()[0] != 0
+    dof = int(H.info.n_dof)
+    ft = torch.tensor(f.ravel(), dtype=torch.float64, device=dev)
+    gt = torch.tensor(g, dtype=torch.float64, device=dev)
+    u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        u.zero_()
+        r = H.solve(ft, gt, u, TOL, stream)
+        if r.status != 0:
+            raise RuntimeError(f"solve failed: status {r.status}, rel_res {r.rel_res}")
+        return r
+
+    for _ in range(a.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    err = float(np.abs(u.cpu().numpy().reshape(n, n) - ue)[present].max())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    cycles, kernels = [], 0
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(a.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            r = step()
+            ev[k][1].record(stream)
+            cycles.append(r.cycles)
+            kernels += r.kernels
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    ms = red_max(sum(step_ms) / a.steps)
+    value = aggregate(dof, ms, world)
+
+    # end to end: pinned host buffers through cc_solve_host
+    hf = torch.tensor(f.ravel(), dtype=torch.float64).pin_memory().numpy()
+    hg = torch.tensor(g, dtype=torch.float64).pin_memory().numpy()
+    hu = torch.zeros(n * n, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(max(1, a.warmup)):
+        hu[:] = 0
+        H.solve_host(hf, hg, hu, TOL, stream)
+    e2e_ms = []
+    for _ in range(a.steps):
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        hu[:] = 0
+        t = time.perf_counter()
+        r = H.solve_host(hf, hg, hu, TOL, stream)
+        e2e_ms.append((time.perf_counter() - t) * 1e3)
+        assert r.status == 0
+    e2e = aggregate(dof, red_max(sum(e2e_ms) / len(e2e_ms)), world)
+
+    # roofline of the finest-level FP32 smoothing sweep (events on its stream)
+    H.kernel_timing(True)
+    for _ in range(2):
+        flush.fill_(3.0)
+        step()
+    launches, tot_ms, bytes_per = H.kernel_timing_read()
+    H.kernel_timing(False)
+    peaks, src = _peaks()
+    achieved = bytes_per / (tot_ms / launches) / 1e6 if launches else None   # GB/s
+    peak = float(peaks["hbm_gbs"])
+    roof = {"kernel": "k_sweep<float> (finest level)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": None, "peak_source": src,
+            "launches_timed": launches, "bytes_per_launch": bytes_per,
+            "note": "FP32 working set of a 1024^2 level is L2-resident within a solve"}
+
+    # plain FP64 solve of the same problem, for comparison
+    H64 = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=0,
+                                                max_cycles=60))
+    u64 = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    H64.solve(ft, gt, u64, TOL, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(4.0)
+    u64.zero_()
+    e0.record(stream)
+    r64 = H64.solve(ft, gt, u64, TOL, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    err64 = float(np.abs(u64.cpu().numpy().reshape(n, n) - ue)[present].max())
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline()
+    out = {
+        "metric": "solved DOF/s at discretization-error accuracy (rel. residual < 1e-10)",
+        "value": value, "unit": "DOF/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 cycles + f64 refinement",
+        "data": "synthetic (manufactured solution exp(x)cos(2y), seeded geometry)",
+        "config": {"workload": f"disk domain, (a,b,c)=(1,0.5,2), Dirichlet box + Neumann circle, "
+                               f"{n}x{n} cells", "n": n, "dof_per_gpu": dof,
+                   "cycle": "W(3,3)", "levels": [H.info.level_n[l] for l in range(H.info.n_levels)],
+                   "precision": "mixed", "tol": TOL, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}", "cycles_per_solve": cycles[-1]},
+        "e2e": {"value": e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * (2 * n * n + H.info.n_g),
+                "d2h_bytes_per_step": 8 * n * n},
+        "gpu_launches": kernels,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "max_error_vs_exact": err,
+        "fp64_solve": {"ms": fp64_ms, "dof_per_s": dof / (fp64_ms / 1e3), "cycles": r64.cycles,
+                       "max_error_vs_exact": err64},
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def _oracle_sample(n: int):
+    """Oracle solve of the same disk problem on an n x n grid (setup excluded)."""
+    import numpy as np
+    from oracle import discretize as D
+    from oracle import multigrid as M
+    P = _problem()
+    H = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=MIN_COARSE)
+    d = H.levels[0]
+    b = D.rhs(d, D.cell_averages(d.lev, P.f), D.boundary_data(d, P.u))
+    dof = int(d.lev.present.sum())
+
+    def solve():
+        return M.solve(H, b, tol=TOL, gamma=2)
+    return solve, dof
+
+
+def cpu_baseline():
+    n = 256
+    solve, dof = _oracle_sample(n)
+    t = time.perf_counter()
+    r = solve()
+    dt = time.perf_counter() - t
+    return {"value": dof / dt, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"one FP64 oracle W(3,3) solve of the same disk problem at {n}x{n} "
+                      f"({len(r.history)} cycles, {dt:.1f} s; setup excluded); "
+                      f"BLAS threads pinned to 1"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = 128
+    solve, dof = _oracle_sample(n)
+    for _ in range(a.warmup):
+        solve()
+    ts = []
+    for _ in range(a.steps):
+        t = time.perf_counter()
+        solve()
+        ts.append(time.perf_counter() - t)
+    ms = 1e3 * sum(ts) / len(ts)
+    value = dof / (ms / 1e3)
+    out = {"impl": "reference",
+           "metric": "solved DOF/s at discretization-error accuracy (rel. residual < 1e-10)",
+           "value": value, "unit": "DOF/s", "n_gpus": a.gpus, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"disk domain, (a,b,c)=(1,0.5,2), sample at {n}x{n} cells "
+                                  f"of the {N_GRID}x{N_GRID} workload", "n": n},
+           "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                            "sample": f"FP64 oracle W(3,3) solves at {n}x{n}, setup excluded"},
+           "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    # the oracle's numpy/scipy work runs on one thread
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    main()

@@ -1,0 +1,256 @@
+/*
+ * ccmg.h - C ABI of the GB300 cut-cell multigrid library.
+ *
+ * The library solves  a u_xx + b u_xy + c u_yy = f  (b^2 < 4ac) on a square
+ * box minus a union of elliptic holes, with Dirichlet, Neumann or Robin data
+ * N u = g on every boundary curve (Sec. 1, Eq. 1.1-1.2), by the fourth-order
+ * cut-cell finite-volume discretisation (Sec. 3-4) and the cut-cell geometric
+ * multigrid solver (Sec. 5).  The unknowns are cell averages <u>_i over the
+ * cut cells of an N x N Cartesian grid (Eq. 4.1).
+ *
+ * Conventions shared by every entry point
+ *  - Grid vectors are N x N row-major arrays of doubles, index j*N + i, i the
+ *    x index (fastest), j the y index; cell (i,j) covers
+ *    [x0 + i h, x0 + (i+1) h] x [y0 + j h, y0 + (j+1) h], h = (x1 - x0)/N.
+ *    Entries of empty control volumes (outside the domain or merged into a
+ *    neighbour by Alg. 1) are ignored on input and written as 0.
+ *  - The boundary-data vector g has 4 N + n_bd entries: the face averages of
+ *    N u on the south (y = y0, by i), east (x = x1, by j), north (y = y1, by
+ *    i) and west (x = x0, by j) box faces, then one boundary average
+ *    <<N u>>_i (Eq. 4.2) per cut cell that touches a hole, in row-major cell
+ *    order (cc_query reports n_bd; cc_quadrature_nodes gives their rules in
+ *    that order).  Entries of
+ *    faces that are not used by the discretisation are ignored.
+ *  - Pointers named d_* are device pointers on the device that was current
+ *    at cc_setup; h_* are host pointers.  The caller owns every array passed
+ *    in; the library owns the handle and everything it allocates.
+ *  - Every call returns a cc_status; no call throws or aborts.  A call that
+ *    fails leaves its outputs unspecified and the handle usable.
+ *  - Device work is issued on the stream argument (0 = legacy default) and
+ *    is stream-ordered; calls that return host data synchronise that stream.
+ *  - A handle may be used from one host thread at a time, except
+ *    cc_submit / cc_poll, which are thread-safe.
+ */
+#ifndef CCMG_H
+#define CCMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_hierarchy* cc_handle;
+typedef void* cc_stream;            /* a cudaStream_t */
+
+typedef enum {
+  CC_OK = 0,
+  CC_ERR_ARG = 1,             /* invalid argument (null pointer, bad size, b^2 >= 4ac, ...) */
+  CC_ERR_GEOMETRY = 2,        /* the finest grid does not resolve the domain (Alg. 1 precondition) */
+  CC_ERR_SINGULAR = 3,        /* a PLG fit, a block factorisation or the bottom matrix is singular */
+  CC_ERR_NO_MEMORY = 4,       /* a device or host allocation failed */
+  CC_ERR_NOT_CONVERGED = 5,   /* max_cycles reached above the tolerance */
+  CC_ERR_DIVERGED = 6,        /* the residual grew by more than 1e3 or became non-finite */
+  CC_ERR_TIMEOUT = 7,         /* a bounded wait expired */
+  CC_ERR_CUDA = 8,            /* a CUDA runtime call failed */
+  CC_ERR_BUSY = 9             /* the request is still in flight (cc_poll) */
+} cc_status;
+
+enum { CC_HOLE_ELLIPSE = 0 };
+enum { CC_BC_DIRICHLET = 0, CC_BC_NEUMANN = 1, CC_BC_ROBIN = 2 };
+enum { CC_CYCLE_V = 1, CC_CYCLE_W = 2, CC_CYCLE_FMG = 3 };
+enum { CC_PREC_FP64 = 0, CC_PREC_MIXED = 1 };
+
+/* An elliptic hole: centre (cx, cy), semi-axes r1, r2, rotation theta (rad). */
+typedef struct { int kind; double cx, cy, r1, r2, theta; } cc_hole;
+
+/* The domain: the square [x0,x1] x [y0,y1] minus the union of the holes.
+ * Holes may overlap one another but must stay inside the box. */
+typedef struct { double x0, y0, x1, y1; int n_holes; const cc_hole* holes; } cc_domain;
+
+/* A boundary condition N u = g: Dirichlet (u), Neumann (du/dn, n the outward
+ * normal of the domain) or Robin (alpha1 u + alpha2 du/dn). */
+typedef struct { int type; double alpha1, alpha2; } cc_bc;
+
+/* Options; cc_default_options fills the defaults noted below. */
+typedef struct {
+  double eps;          /* Alg. 1 volume-fraction threshold (0.1) */
+  int nu1, nu2;        /* pre/post smoothing sweeps (3, 3) */
+  double omega;        /* Jacobi weight of the block smoother (0.5) */
+  int cycle;           /* CC_CYCLE_V / W / FMG (CC_CYCLE_V) */
+  int min_coarse_n;    /* coarsest level: smallest N >= this reached by halving while
+                          every hole stays two cells across (4) */
+  int precision;       /* CC_PREC_FP64 or CC_PREC_MIXED (FP64) */
+  int max_cycles;      /* cycle limit of cc_solve (100) */
+  int use_graphs;      /* capture one cycle in a CUDA graph and replay it (1) */
+  int host_only;       /* build the tables on the host only, no device work (0);
+                          such a handle answers cc_query, cc_cell_types,
+                          cc_quadrature_nodes and cc_level_tables only */
+} cc_options;
+
+/* Sizes of a hierarchy. */
+typedef struct {
+  int n;               /* cells per side on the finest level */
+  int n_levels;        /* levels, finest first */
+  int64_t n_dof;       /* non-empty cells on the finest level */
+  int n_bd;            /* boundary cells (tail of g) */
+  int n_g;             /* 4 n + n_bd */
+  int n_plg;           /* PLG cells on the finest level */
+  int n_block;         /* cells solved exactly by the block smoother, finest level */
+  int64_t device_bytes;/* device memory held by the handle */
+  int level_n[32];     /* cells per side of each level */
+  double block_error;  /* largest normwise backward error of the exact block solves, measured
+                          at setup on a fixed vector: |A x - t|_inf / (|A|_inf |x|_inf) */
+  double bottom_error; /* the same for the coarsest-level solve */
+} cc_info;
+
+/* Outcome of a solve. */
+typedef struct {
+  cc_status status;
+  int cycles;          /* cycles (or refinement steps) performed */
+  double rel_res;      /* final ||b - A u||_inf / ||b||_inf, FP64 */
+  double t_submit, t_start, t_done;   /* seconds, cc_submit/cc_poll only */
+  int64_t kernels;     /* CUDA kernels the call launched (graph nodes count once per replay) */
+} cc_result;
+
+/* Fill *opt with the defaults. */
+void cc_default_options(cc_options* opt);
+
+/* Human-readable name of a status. */
+const char* cc_status_string(cc_status s);
+
+/*
+ * cc_setup: build the multigrid hierarchy (Sec. 3-5, Eq. 5.9) in FP64 on the
+ * host and upload its per-level tables to the current device.
+ *   dom      domain; the box must be square and is divided into n x n cells
+ *   a, b, c  operator coefficients, b^2 < 4ac
+ *   bc       n_bc conditions: bc[0..3] for the south, east, north, west box
+ *            sides, bc[4 + k] for hole k (overlapping holes should share one)
+ *   n        cells per side of the finest level (even down to the coarsest)
+ *   opt      options or NULL for the defaults
+ *   stream   stream for the uploads
+ *   out      receives the handle; release it with cc_destroy
+ * Errors: CC_ERR_ARG, CC_ERR_GEOMETRY (finest level unresolved),
+ * CC_ERR_SINGULAR (no poised lattice or a singular block), CC_ERR_NO_MEMORY,
+ * CC_ERR_CUDA.  On error *out is NULL.
+ */
+cc_status cc_setup(const cc_domain* dom, double a, double b, double c,
+                   const cc_bc* bc, int n_bc, int n, const cc_options* opt,
+                   cc_stream stream, cc_handle* out);
+
+/* Sizes of the hierarchy (host call, no device work). */
+cc_status cc_query(cc_handle h, cc_info* out);
+
+/* Release a handle and all its device memory (synchronises the device). */
+cc_status cc_destroy(cc_handle h);
+
+/*
+ * cc_cell_types: copy the finest-level cell classification to host memory.
+ *   h_type[N*N]: 0 empty, 1 full (regular) cell, 2 cut (irregular) cell.
+ *   h_kind[N*N] (may be NULL): 0 empty, 1 SFV cell, 2 PLG cell (Def. 4.1).
+ *   h_vol[N*N] (may be NULL): cell volumes.
+ */
+cc_status cc_cell_types(cc_handle h, uint8_t* h_type, uint8_t* h_kind, double* h_vol);
+
+/*
+ * cc_quadrature_nodes: quadrature rules on the finest level's cut cells, so
+ * that a caller can form the inputs f (Eq. 4.1) and g (Eq. 4.2) there.
+ * Call once with NULL arrays to get the counts, then with arrays that size.
+ *   n_cut     number of cut cells; h_cell[n_cut] their row-major indices
+ *   h_vptr[n_cut+1], h_vnode[3*nv]: volume rule of cell k is nodes
+ *             vptr[k] .. vptr[k+1]-1 with (x, y, w), sum of w = 1
+ *   h_bptr[n_bd+1], h_bnode[5*nb], h_bbc[nb]: boundary rule of boundary cell
+ *             r (same order as the tail of g): (x, y, nx, ny, w) with the
+ *             outward normal of the domain, sum of w = 1, and the index of the
+ *             condition (into the bc array of cc_setup) that applies there.
+ */
+cc_status cc_quadrature_nodes(cc_handle h, int* n_cut, int64_t* nv, int64_t* nb,
+                              int* h_cell, int64_t* h_vptr, double* h_vnode,
+                              int64_t* h_bptr, double* h_bnode, int* h_bbc);
+
+/*
+ * cc_solve: solve A u = f - N g (Eq. 4.20) to ||b - A u||_inf / ||b||_inf
+ * < tol (FP64 residual), with the method chosen at setup: repeated cycles of
+ * Alg. 2 (V or W) or Alg. 3 (FMG) on u in FP64, or, in the mixed precision
+ * mode, FP32 cycles on the residual equation inside an FP64 refinement loop.
+ *   d_f[N*N]  cell averages of f;  d_g[n_g] boundary data;  d_u[N*N] the
+ *   initial guess on input, the solution on output.  All device pointers.
+ *   out (may be NULL) receives cycles and the final relative residual.
+ * Errors: CC_ERR_ARG, CC_ERR_NOT_CONVERGED, CC_ERR_DIVERGED, CC_ERR_CUDA.
+ */
+cc_status cc_solve(cc_handle h, const double* d_f, const double* d_g, double* d_u,
+                   double tol, cc_stream stream, cc_result* out);
+
+/*
+ * cc_solve_host: cc_solve with host arrays h_f, h_g, h_u (same layouts).  The
+ * library copies them to and from device buffers that the handle owns; the
+ * call returns after the solution is back in h_u.
+ */
+cc_status cc_solve_host(cc_handle h, const double* h_f, const double* h_g, double* h_u,
+                        double tol, cc_stream stream, cc_result* out);
+
+/*
+ * cc_submit / cc_poll: streamed requests.  cc_submit queues a solve of
+ * (d_f, d_g) into d_u on the handle's own worker and returns at once with a
+ * request id; the arrays must stay valid until cc_poll reports completion.
+ * cc_poll returns CC_ERR_BUSY while the request is queued or running, else
+ * the request's final status with its result in *out (timestamps are seconds
+ * on a monotonic host clock).  A finished request is forgotten after the
+ * first poll that reports it.
+ */
+cc_status cc_submit(cc_handle h, const double* d_f, const double* d_g, double* d_u,
+                    double tol, uint64_t* req_id);
+cc_status cc_poll(uint64_t req_id, cc_result* out);
+
+/* ---- operator-level entry points (one step of the method each) ------------
+ * All take FP64 device arrays of the named level's size N_l x N_l and run on
+ * `stream`.  They exist so that each step can be checked on its own.
+ */
+
+/* b = f - N g on the finest level (Eq. 4.20). */
+cc_status cc_assemble_rhs(cc_handle h, const double* d_f, const double* d_g, double* d_b,
+                          cc_stream stream);
+/* r = b - A u on level l (Eq. 4.23), every non-empty cell. */
+cc_status cc_residual(cc_handle h, int level, const double* d_u, const double* d_b,
+                      double* d_r, cc_stream stream);
+/* One sweep of the block smoother T_omega (Def. 5.6) on level l, u in place. */
+cc_status cc_smooth(cc_handle h, int level, double* d_u, const double* d_b, cc_stream stream);
+/* r_c = restriction (Eq. 5.10) of b - A u from level l to level l+1, with the
+ * residual of the exactly solved cells taken as 0. */
+cc_status cc_restrict_residual(cc_handle h, int level, const double* d_u, const double* d_b,
+                               double* d_rc, cc_stream stream);
+/* u += interpolation (Eq. 5.11) of e_c from level l+1 to level l. */
+cc_status cc_prolong_add(cc_handle h, int level, const double* d_ec, double* d_u,
+                         cc_stream stream);
+/* One cycle of Alg. 2 (or its W form, as set up) on the finest level in FP64,
+ * u in place. */
+cc_status cc_cycle(cc_handle h, double* d_u, const double* d_b, cc_stream stream);
+
+/*
+ * cc_level_tables: copy level l's discretisation to host memory for
+ * inspection.  Any pointer may be NULL.
+ *   h_kind[N_l^2]     0 empty, 1 SFV, 2 PLG
+ *   h_lattice[15*m]   the poised lattice (row-major cell indices) of each
+ *                     PLG cell, PLG cells in row-major order (m = n_plg)
+ *   h_beta[16*m]      beta_1..beta_15 and beta_b (0 for regular PLG cells)
+ *   *n_plg            m
+ */
+cc_status cc_level_tables(cc_handle h, int level, uint8_t* h_kind, int* h_lattice,
+                          double* h_beta, int* n_plg);
+
+/*
+ * cc_kernel_timing: when enabled, the library records CUDA events around
+ * every launch of the finest-level smoothing sweep kernel and accumulates
+ * their durations; cc_kernel_timing_read returns the launch count, the total
+ * milliseconds and the algorithmic bytes one launch moves (reads of u and b
+ * plus the write of u, at the cycle's precision).
+ */
+cc_status cc_kernel_timing(cc_handle h, int enable);
+cc_status cc_kernel_timing_read(cc_handle h, int64_t* launches, double* total_ms,
+                                double* bytes_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCMG_H */

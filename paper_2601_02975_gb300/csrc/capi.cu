@@ -1,0 +1,1305 @@
+// C ABI of the cut-cell multigrid library: hierarchy construction (host,
+// FP64), device tables, the multigrid cycle (Alg. 2) and the solve loops.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ccmg.h"
+#include "kernels.cuh"
+#include "setup.h"
+
+using namespace ccmg;
+
+namespace {
+
+// kernels launched by the current host thread (read around each solve)
+thread_local int64_t t_launches = 0;
+#define LAUNCH ++t_launches,
+
+struct CudaError {
+  cudaError_t e;
+};
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) throw CudaError{e_}; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// dense helpers (host, FP64)
+// in-place inverse by Gauss-Jordan with partial pivoting; false if singular
+bool invert(std::vector<double>& A, int n) {
+  std::vector<int> piv(n);
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  double amax = 0;
+  for (double v : A) amax = std::max(amax, std::fabs(v));
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)p * n + c])) p = r;
+    if (!(std::fabs(A[(size_t)p * n + c]) > 1e-14 * amax)) return false;
+    if (p != c) {
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)p * n + k], A[(size_t)c * n + k]);
+        std::swap(I[(size_t)p * n + k], I[(size_t)c * n + k]);
+      }
+    }
+    double d = 1.0 / A[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[(size_t)c * n + k] *= d;
+      I[(size_t)c * n + k] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double l = A[(size_t)r * n + c];
+      if (l == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[(size_t)r * n + k] -= l * A[(size_t)c * n + k];
+        I[(size_t)r * n + k] -= l * I[(size_t)c * n + k];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// row-major n x m -> column-major
+std::vector<double> to_cm(const std::vector<double>& A, int rows, int cols) {
+  std::vector<double> B((size_t)rows * cols);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) B[(size_t)c * rows + r] = A[(size_t)r * cols + c];
+  return B;
+}
+
+// ---------------------------------------------------------------------------
+// exact block solve plan (host)
+struct BlockPlan {
+  int m = 0, nch = 0, ns = 0;
+  std::vector<int> cell;
+  std::vector<int64_t> gptr{0};
+  std::vector<int> gcol;
+  std::vector<double> gval;
+  std::vector<int> cstart, iptr{0}, ipos;
+  std::vector<int64_t> aoff;
+  std::vector<double> ainv;
+  std::vector<int> spos;
+  std::vector<int64_t> asi_ptr{0};
+  std::vector<int> asi_col;
+  std::vector<double> asi_val;
+  std::vector<double> sinv;
+  std::vector<int> wptr{0}, widx;
+  std::vector<int64_t> woff;
+  std::vector<double> wmat;
+  size_t smem_chunk = 0, smem_back = 0;
+  double error = 0;   // backward error of the scheme on a fixed vector (FP64, host)
+};
+
+// Apply the chunked scheme to a fixed vector in FP64 exactly as the device
+// does and return |A x - t|_inf / (|A|_inf |x|_inf).
+double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, double>>& Abb) {
+  const int m = B.m;
+  std::vector<double> t(m), z(m, 0.0), x(m, 0.0), xs(B.ns, 0.0);
+  for (int p = 0; p < m; ++p) t[p] = std::sin(1.0 + 0.7 * p) + 0.25 * std::cos(3.1 * p);
+  for (int c = 0; c < B.nch; ++c) {
+    const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
+    const double* A = &B.ainv[B.aoff[c]];
+    for (int r = 0; r < ni; ++r) {
+      double acc = 0;
+      for (int k = 0; k < ni; ++k) acc += A[(size_t)k * ni + r] * t[B.ipos[i0 + k]];
+      z[B.ipos[i0 + r]] = acc;
+    }
+  }
+  std::vector<double> ts(B.ns);
+  for (int q = 0; q < B.ns; ++q) {
+    double acc = t[B.spos[q]];
+    for (int64_t e = B.asi_ptr[q]; e < B.asi_ptr[q + 1]; ++e) acc -= B.asi_val[e] * z[B.asi_col[e]];
+    ts[q] = acc;
+  }
+  for (int r = 0; r < B.ns; ++r) {
+    double acc = 0;
+    for (int k = 0; k < B.ns; ++k) acc += B.sinv[(size_t)k * B.ns + r] * ts[k];
+    xs[r] = acc;
+    x[B.spos[r]] = acc;
+  }
+  for (int c = 0; c < B.nch; ++c) {
+    const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
+    const int w0 = B.wptr[c], nw = B.wptr[c + 1] - w0;
+    const double* W = &B.wmat[B.woff[c]];
+    for (int r = 0; r < ni; ++r) {
+      double acc = 0;
+      for (int k = 0; k < nw; ++k) acc += W[(size_t)k * ni + r] * xs[B.widx[w0 + k]];
+      x[B.ipos[i0 + r]] = z[B.ipos[i0 + r]] - acc;
+    }
+  }
+  double rmax = 0, amax = 0, xmax = 0;
+  for (int p = 0; p < m; ++p) {
+    double acc = -t[p], arow = 0;
+    for (auto& kv : Abb[p]) { acc += kv.second * x[kv.first]; arow += std::fabs(kv.second); }
+    rmax = std::max(rmax, std::fabs(acc));
+    amax = std::max(amax, arow);
+    xmax = std::max(xmax, std::fabs(x[p]));
+  }
+  return rmax / (amax * xmax);
+}
+
+BlockPlan plan_block(const LevelDisc& D) {
+  BlockPlan B;
+  const int m = (int)D.block.size();
+  B.m = m;
+  if (m == 0) return B;
+  B.cell = D.block;
+  std::unordered_map<int, int> pos;
+  for (int p = 0; p < m; ++p) pos[D.block[p]] = p;
+  std::vector<std::map<int, double>> Abb(m);
+  for (int p = 0; p < m; ++p) {
+    for (int64_t q = D.block_rows.ptr[p]; q < D.block_rows.ptr[p + 1]; ++q) {
+      int c = D.block_rows.col[q];
+      double v = D.block_rows.val[q];
+      auto it = pos.find(c);
+      if (it != pos.end()) Abb[p][it->second] += v;
+      else { B.gcol.push_back(c); B.gval.push_back(v); }
+    }
+    B.gptr.push_back((int64_t)B.gcol.size());
+  }
+  // choose the chunk size with the least dense storage
+  auto build = [&](int s, bool commit, double& storage) {
+    int nch = (m + s - 1) / s;
+    std::vector<char> iface(m, 0);
+    if (nch > 1)
+      for (int r = 0; r < m; ++r)
+        for (auto& kv : Abb[r]) {
+          int c = kv.first;
+          int cr = r / s, cc = c / s;
+          if (cr == cc) continue;
+          iface[cr < cc ? r : c] = 1;
+        }
+    std::vector<int> S;
+    std::vector<int> sidx(m, -1);
+    for (int p = 0; p < m; ++p)
+      if (iface[p]) { sidx[p] = (int)S.size(); S.push_back(p); }
+    const int ns = (int)S.size();
+    storage = (double)ns * ns;
+    std::vector<std::vector<int>> I(nch);
+    for (int p = 0; p < m; ++p)
+      if (!iface[p]) I[p / s].push_back(p);
+    std::vector<std::vector<int>> Sc(nch);
+    for (int c = 0; c < nch; ++c) {
+      std::vector<char> used(ns, 0);
+      for (int p : I[c])
+        for (auto& kv : Abb[p])
+          if (sidx[kv.first] >= 0) used[sidx[kv.first]] = 1;
+      for (int q = 0; q < ns; ++q)
+        if (used[q]) Sc[c].push_back(q);
+      storage += (double)I[c].size() * I[c].size() + (double)I[c].size() * Sc[c].size();
+    }
+    if (!commit) return true;
+    B.iptr.assign(1, 0);
+    B.ipos.clear();
+    B.aoff.clear();
+    B.ainv.clear();
+    B.asi_ptr.assign(1, 0);
+    B.asi_col.clear();
+    B.asi_val.clear();
+    B.wptr.assign(1, 0);
+    B.widx.clear();
+    B.woff.clear();
+    B.wmat.clear();
+    B.nch = nch;
+    B.ns = ns;
+    B.spos = S;
+    B.cstart.clear();
+    for (int c = 0; c <= nch; ++c) B.cstart.push_back(std::min(m, c * s));
+    std::vector<double> Sm((size_t)ns * ns, 0.0);
+    for (int q = 0; q < ns; ++q)
+      for (auto& kv : Abb[S[q]])
+        if (sidx[kv.first] >= 0) Sm[(size_t)q * ns + sidx[kv.first]] += kv.second;
+    for (int c = 0; c < nch; ++c) {
+      const auto& Ic = I[c];
+      const int ni = (int)Ic.size();
+      std::unordered_map<int, int> lpos;
+      for (int q = 0; q < ni; ++q) lpos[Ic[q]] = q;
+      std::vector<double> A((size_t)ni * ni, 0.0);
+      for (int q = 0; q < ni; ++q)
+        for (auto& kv : Abb[Ic[q]]) {
+          auto it = lpos.find(kv.first);
+          if (it != lpos.end()) A[(size_t)q * ni + it->second] += kv.second;
+        }
+      if (ni && !invert(A, ni)) throw SetupError(3, "singular interior block of the smoother");
+      for (int q = 0; q < ni; ++q) B.ipos.push_back(Ic[q]);
+      B.iptr.push_back((int)B.ipos.size());
+      B.aoff.push_back((int64_t)B.ainv.size());
+      auto Acm = to_cm(A, ni, ni);
+      B.ainv.insert(B.ainv.end(), Acm.begin(), Acm.end());
+      // W_c = inv(A_cc) A_c,S restricted to the interface columns Sc
+      const auto& sc = Sc[c];
+      const int nw = (int)sc.size();
+      std::unordered_map<int, int> wcol;
+      for (int q = 0; q < nw; ++q) wcol[sc[q]] = q;
+      std::vector<double> AcS((size_t)ni * nw, 0.0);
+      for (int q = 0; q < ni; ++q)
+        for (auto& kv : Abb[Ic[q]])
+          if (sidx[kv.first] >= 0) AcS[(size_t)q * nw + wcol[sidx[kv.first]]] += kv.second;
+      std::vector<double> Wc((size_t)ni * nw, 0.0);
+      for (int r = 0; r < ni; ++r)
+        for (int k = 0; k < ni; ++k) {
+          double a = A[(size_t)r * ni + k];
+          if (a == 0.0) continue;
+          for (int q = 0; q < nw; ++q) Wc[(size_t)r * nw + q] += a * AcS[(size_t)k * nw + q];
+        }
+      for (int q = 0; q < nw; ++q) B.widx.push_back(sc[q]);
+      B.wptr.push_back((int)B.widx.size());
+      B.woff.push_back((int64_t)B.wmat.size());
+      auto Wcm = to_cm(Wc, ni, nw);
+      B.wmat.insert(B.wmat.end(), Wcm.begin(), Wcm.end());
+      // Schur: S -= A_S,c W_c
+      for (int q = 0; q < ns; ++q)
+        for (auto& kv : Abb[S[q]]) {
+          auto it = lpos.find(kv.first);
+          if (it == lpos.end()) continue;
+          double a = kv.second;
+          int r = it->second;
+          for (int w = 0; w < nw; ++w) Sm[(size_t)q * ns + sc[w]] -= a * Wc[(size_t)r * nw + w];
+        }
+    }
+    // A_S,I rows for the runtime
+    for (int q = 0; q < ns; ++q) {
+      for (auto& kv : Abb[S[q]])
+        if (sidx[kv.first] < 0) { B.asi_col.push_back(kv.first); B.asi_val.push_back(kv.second); }
+      B.asi_ptr.push_back((int64_t)B.asi_col.size());
+    }
+    if (ns && !invert(Sm, ns)) throw SetupError(3, "singular interface Schur complement");
+    B.sinv = to_cm(Sm, ns, ns);
+    return true;
+  };
+  // candidate chunk sizes by dense storage; keep the cheapest whose
+  // backward error on a fixed vector is at the level of rounding
+  std::vector<std::pair<double, int>> cands;
+  {
+    double st;
+    build(m, false, st);
+    cands.push_back({st, m});
+    for (int s : {64, 96, 128, 192, 256, 384, 512}) {
+      if (s >= m) break;
+      build(s, false, st);
+      cands.push_back({st, s});
+    }
+  }
+  std::sort(cands.begin(), cands.end());
+  BlockPlan best_plan;
+  bool have = false;
+  for (auto& cs : cands) {
+    BlockPlan keep = B;
+    double st;
+    try {
+      build(cs.second, true, st);
+    } catch (SetupError&) {
+      B = keep;
+      continue;
+    }
+    B.error = block_plan_error(B, Abb);
+    if (!have || B.error < best_plan.error) { best_plan = B; have = true; }
+    if (B.error < 1e-13) break;
+    B = keep;
+  }
+  if (!have) throw SetupError(3, "singular block of the smoother");
+  B = best_plan;
+  int maxni = 0, maxnw = 0;
+  for (int c = 0; c < B.nch; ++c) {
+    maxni = std::max(maxni, B.iptr[c + 1] - B.iptr[c]);
+    maxnw = std::max(maxnw, B.wptr[c + 1] - B.wptr[c]);
+  }
+  B.smem_chunk = (size_t)(((maxni + 31) & ~31) + 256 + maxni);
+  B.smem_back = (size_t)(((maxnw + 31) & ~31) + 256 + maxni);
+  return B;
+}
+
+// ---------------------------------------------------------------------------
+// device memory
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Pool {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  template <class T>
+  T* alloc(size_t n) {
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) throw CudaError{e};
+    ptrs.push_back(p);
+    bytes += (int64_t)(n * sizeof(T));
+    return static_cast<T*>(p);
+  }
+  template <class T>
+  T* upload(const std::vector<T>& v, cudaStream_t s) {
+    T* d = alloc<T>(v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return d;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+template <class T>
+std::vector<T> cast_vec(const std::vector<double>& v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+struct BlockDevSet {
+  BlockDev d64, d32;
+};
+
+struct Level {
+  int n = 0;
+  int64_t nn = 0;
+  StencilParams sp;
+  uint8_t* cls = nullptr;
+  double* u64[2] = {nullptr, nullptr};
+  double* b64 = nullptr;
+  float* u32[2] = {nullptr, nullptr};
+  float* b32 = nullptr;
+  BlockPlan plan;
+  BlockDevSet blk;
+  // full block rows (FP64) for residuals
+  int* brow_cell = nullptr;
+  int64_t* brow_ptr = nullptr;
+  int* brow_col = nullptr;
+  double* brow_val = nullptr;
+  // owner fix-up list: merged-away control volumes of this level
+  int nfix = 0;
+  int* fix_dst = nullptr;
+  int* fix_src = nullptr;
+  LevelDisc disc;
+};
+
+}  // namespace
+
+struct cc_hierarchy {
+  Problem P;
+  cc_options opt;
+  int device = 0;
+  std::vector<std::unique_ptr<Level>> lv;
+  Pool pool;
+  double* bottom_inv = nullptr;   // column-major FP64
+  double bottom_error = 0;
+  int nc_bottom = 0;
+  // finest-level extras
+  double* f_rhs = nullptr;        // b of the finest level (FP64)
+  double* r64 = nullptr;          // FP64 residual
+  double* h_u_dev = nullptr;      // staging for cc_solve_host
+  double* h_f_dev = nullptr;
+  double* h_g_dev = nullptr;
+  int* nrow_cell = nullptr;
+  int64_t* nrow_ptr = nullptr;
+  int* nrow_col = nullptr;
+  double* nrow_val = nullptr;
+  int n_nrows = 0;
+  unsigned long long* d_norm = nullptr;   // [2]
+  unsigned long long* h_norm = nullptr;   // pinned
+  int n_g = 0, n_bd = 0;
+  int64_t n_dof = 0;
+  // kernel timing
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t ev_used = 0;
+  int64_t timed_launches = 0;
+  double timed_ms = 0;
+  // level-0 FP64 buffer that holds u during a cycle
+  int cur64 = 0;
+  // submit/poll worker
+  std::mutex qmu;
+  std::condition_variable qcv;
+  std::deque<uint64_t> queue;
+  std::thread worker;
+  bool stop = false;
+  cudaStream_t wstream = nullptr;
+  // cuda graphs of one solve iteration
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int64_t gexec_launches[2] = {0, 0};   // kernels in one replay of each graph
+  cudaStream_t gstream = nullptr;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// request registry for cc_submit / cc_poll
+struct Request {
+  cc_hierarchy* h;
+  const double* f;
+  const double* g;
+  double* u;
+  double tol;
+  cc_result res;
+  bool done = false;
+};
+std::mutex g_reqmu;
+std::unordered_map<uint64_t, Request> g_req;
+std::atomic<uint64_t> g_next_id{1};
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+cc_status from_setup(int code) {
+  switch (code) {
+    case 1: return CC_ERR_ARG;
+    case 2: return CC_ERR_GEOMETRY;
+    case 3: return CC_ERR_SINGULAR;
+    default: return CC_ERR_ARG;
+  }
+}
+
+StencilParams make_stencil(const LevelDisc& D, double omega) {
+  StencilParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.n = D.n;
+  P.cross = D.b != 0.0;
+  const double lap[5] = {-1, 16, -30, 16, -1}, grad[5] = {1, -8, 0, 8, -1};
+  const double h2 = D.h * D.h;
+  for (int m = -2; m <= 2; ++m) {
+    P.w[2 * 5 + (m + 2)] += D.a * lap[m + 2] / (12.0 * h2);
+    P.w[(m + 2) * 5 + 2] += D.c * lap[m + 2] / (12.0 * h2);
+  }
+  if (P.cross)
+    for (int m1 = -2; m1 <= 2; ++m1)
+      for (int m2 = -2; m2 <= 2; ++m2)
+        if (m1 && m2) P.w[(m2 + 2) * 5 + (m1 + 2)] += D.b * grad[m1 + 2] * grad[m2 + 2] / (144.0 * h2);
+  for (int w = 0; w < 4; ++w)
+    for (int d = 0; d < 2; ++d)
+      for (int q = 0; q < 4; ++q) P.gh[w][d][q] = D.gc[w][d][q];
+  P.omega_over_diag = omega / D.diag;
+  return P;
+}
+
+template <class T>
+BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
+  BlockDev d;
+  std::memset(&d, 0, sizeof(d));
+  d.m = B.m;
+  d.nch = B.nch;
+  d.ns = B.ns;
+  if (B.m == 0) return d;
+  d.cell = pool.upload(B.cell, s);
+  d.gptr = pool.upload(B.gptr, s);
+  d.gcol = pool.upload(B.gcol, s);
+  d.gval = pool.upload(cast_vec<T>(B.gval), s);
+  d.cstart = pool.upload(B.cstart, s);
+  d.iptr = pool.upload(B.iptr, s);
+  d.ipos = pool.upload(B.ipos, s);
+  d.aoff = pool.upload(B.aoff, s);
+  d.ainv = pool.upload(cast_vec<T>(B.ainv), s);
+  d.spos = pool.upload(B.spos, s);
+  d.asi_ptr = pool.upload(B.asi_ptr, s);
+  d.asi_col = pool.upload(B.asi_col, s);
+  d.asi_val = pool.upload(cast_vec<T>(B.asi_val), s);
+  d.sinv = pool.upload(cast_vec<T>(B.sinv), s);
+  d.wptr = pool.upload(B.wptr, s);
+  d.widx = pool.upload(B.widx, s);
+  d.woff = pool.upload(B.woff, s);
+  d.wmat = pool.upload(cast_vec<T>(B.wmat), s);
+  d.tblk = pool.alloc<T>(B.m);
+  d.zblk = pool.alloc<T>(B.m);
+  d.xs = pool.alloc<T>(std::max(1, B.ns));
+  return d;
+}
+
+inline dim3 tiles(int n) { return dim3((n + TX - 1) / TX, (n + TY - 1) / TY); }
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// the cycle
+template <class T> T* ubuf(Level& L, int i);
+template <> double* ubuf<double>(Level& L, int i) { return L.u64[i]; }
+template <> float* ubuf<float>(Level& L, int i) { return L.u32[i]; }
+template <class T> T* bbuf(Level& L);
+template <> double* bbuf<double>(Level& L) { return L.b64; }
+template <> float* bbuf<float>(Level& L) { return L.b32; }
+template <class T> const BlockDev& bdev(Level& L);
+template <> const BlockDev& bdev<double>(Level& L) { return L.blk.d64; }
+template <> const BlockDev& bdev<float>(Level& L) { return L.blk.d32; }
+
+template <class T>
+void block_solve(Level& L, T* u, const T* b, cudaStream_t s) {
+  const BlockDev& B = bdev<T>(L);
+  if (B.m == 0) return;
+  const BlockPlan& P = L.plan;
+  LAUNCH k_block_chunk<T><<<P.nch, 256, P.smem_chunk * sizeof(T), s>>>(B, b, u);
+  if (P.ns > 0) {
+    size_t sm = (size_t)(((P.ns + 31) & ~31) + 256 + 32) * sizeof(T);
+    LAUNCH k_block_schur<T><<<(P.ns + 31) / 32, 256, sm, s>>>(B, u);
+    LAUNCH k_block_back<T><<<P.nch, 256, P.smem_back * sizeof(T), s>>>(B, u);
+  }
+}
+
+template <class T>
+void sweep(cc_hierarchy* H, int l, int& cur, bool zero, const T* ec, cudaStream_t s) {
+  Level& L = *H->lv[l];
+  T* in = ubuf<T>(L, cur);
+  T* out = ubuf<T>(L, 1 - cur);
+  bool timed = H->timing && l == 0;
+  if (timed) {
+    if (H->ev_used == H->ev.size()) {
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b));
+      H->ev.push_back({a, b});
+    }
+    CK(cudaEventRecord(H->ev[H->ev_used].first, s));
+  }
+  if (L.sp.cross)
+    LAUNCH k_sweep<T, true><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, L.sp, zero);
+  else
+    LAUNCH k_sweep<T, false><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, L.sp, zero);
+  if (timed) {
+    CK(cudaEventRecord(H->ev[H->ev_used].second, s));
+    ++H->ev_used;
+  }
+  block_solve<T>(L, out, bbuf<T>(L), s);
+  cur = 1 - cur;
+}
+
+template <class T>
+void bottom(cc_hierarchy* H, int l, int cur, cudaStream_t s) {
+  Level& L = *H->lv[l];
+  int nc = H->nc_bottom;
+  size_t sm = (size_t)(((nc + 31) & ~31) + 256 + 32) * sizeof(double);
+  LAUNCH k_bottom<T><<<(nc + 31) / 32, 256, sm, s>>>(H->bottom_inv, nc, bbuf<T>(L), ubuf<T>(L, cur));
+}
+
+// Alg. 2 (gamma = 1) or its W form (gamma = 2) on level l; cur[l] tracks the
+// buffer that holds u.
+template <class T>
+void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaStream_t s) {
+  const int nl = (int)H->lv.size();
+  Level& L = *H->lv[l];
+  if (l == nl - 1) {
+    bottom<T>(H, l, cur[l], s);
+    return;
+  }
+  const int nu1 = H->opt.nu1, nu2 = H->opt.nu2;
+  const int gamma = H->opt.cycle == CC_CYCLE_W ? 2 : 1;
+  bool z = zero;
+  for (int k = 0; k < nu1; ++k) {
+    sweep<T>(H, l, cur[l], z, (const T*)nullptr, s);
+    z = false;
+  }
+  if (z) {   // nu1 == 0 on a zero initial guess: materialise u = 0
+    CK(cudaMemsetAsync(ubuf<T>(L, cur[l]), 0, L.nn * sizeof(T), s));
+  }
+  Level& C = *H->lv[l + 1];
+  if (L.sp.cross)
+    LAUNCH k_resid_restrict<T, true><<<tiles(L.n), TX * TY, 0, s>>>(ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
+                                                              C.cls, bbuf<T>(C), L.sp);
+  else
+    LAUNCH k_resid_restrict<T, false><<<tiles(L.n), TX * TY, 0, s>>>(ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
+                                                               C.cls, bbuf<T>(C), L.sp);
+  for (int g = 0; g < gamma; ++g) cycle_level<T>(H, l + 1, cur, g == 0, s);
+  T* ec = ubuf<T>(C, cur[l + 1]);
+  if (C.nfix) LAUNCH k_owner_fix<T><<<nblk(C.nfix), 256, 0, s>>>(C.nfix, C.fix_dst, C.fix_src, ec);
+  if (nu2 == 0) {
+    LAUNCH k_prolong_add<T><<<nblk(L.nn), 256, 0, s>>>(ubuf<T>(L, cur[l]), ec, L.cls, L.n);
+    return;
+  }
+  for (int k = 0; k < nu2; ++k) sweep<T>(H, l, cur[l], false, k == 0 ? ec : (const T*)nullptr, s);
+}
+
+// FP64 residual r = b - A u on the finest level, max |r| into d_norm[0]
+template <class Tout>
+void residual64(cc_hierarchy* H, const double* u, const double* b, Tout* r, cudaStream_t s) {
+  Level& L = *H->lv[0];
+  if (L.sp.cross)
+    LAUNCH k_resid<double, Tout, true><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, r, L.sp, H->d_norm);
+  else
+    LAUNCH k_resid<double, Tout, false><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, r, L.sp, H->d_norm);
+  if (L.plan.m)
+    LAUNCH k_block_resid<Tout><<<nblk(L.plan.m), 256, 0, s>>>(L.plan.m, L.brow_cell, L.brow_ptr, L.brow_col,
+                                                       L.brow_val, u, b, r, H->d_norm);
+}
+
+void assemble_rhs(cc_hierarchy* H, const double* f, const double* g, double* b, cudaStream_t s) {
+  Level& L = *H->lv[0];
+  LAUNCH k_rhs_copy<<<nblk(L.nn), 256, 0, s>>>(f, L.cls, b, L.nn);
+  if (H->n_nrows)
+    LAUNCH k_rhs_n<<<nblk(H->n_nrows), 256, 0, s>>>(H->n_nrows, H->nrow_cell, H->nrow_ptr, H->nrow_col,
+                                             H->nrow_val, g, b);
+}
+
+double read_norm(cc_hierarchy* H, cudaStream_t s) {
+  CK(cudaMemcpyAsync(H->h_norm, H->d_norm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  unsigned long long v = H->h_norm[0];
+  double d;
+  std::memcpy(&d, &v, sizeof(d));
+  return d;
+}
+
+// one iteration of the solve loop, recorded for graph capture or launched
+// directly: FP64 mode: cycle on (u, b) then r = b - A u; mixed mode:
+// r = b - A u (FP64, written as the FP32 cycle right-hand side), FP32 cycle
+// from 0, u += e.
+void iteration(cc_hierarchy* H, bool mixed, cudaStream_t s) {
+  Level& L = *H->lv[0];
+  std::vector<int> cur(H->lv.size(), 0);
+  CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
+  if (!mixed) {
+    cur[0] = H->cur64;
+    cycle_level<double>(H, 0, cur, false, s);
+    if (cur[0] != H->cur64)
+      CK(cudaMemcpyAsync(L.u64[H->cur64], L.u64[cur[0]], L.nn * sizeof(double),
+                         cudaMemcpyDeviceToDevice, s));
+    residual64<double>(H, L.u64[H->cur64], L.b64, H->r64, s);
+  } else {
+    cycle_level<float>(H, 0, cur, true, s);
+    LAUNCH k_update<float><<<nblk(L.nn), 256, 0, s>>>(L.u64[H->cur64], L.u32[cur[0]], L.cls, L.nn);
+    residual64<float>(H, L.u64[H->cur64], L.b64, L.b32, s);
+  }
+}
+
+cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* u, double tol,
+                     cudaStream_t s, cc_result* out) {
+  Level& L = *H->lv[0];
+  const bool mixed = H->opt.precision == CC_PREC_MIXED;
+  const int64_t launches0 = t_launches;
+  H->cur64 = 0;
+  assemble_rhs(H, f, g, L.b64, s);
+  CK(cudaMemcpyAsync(L.u64[0], u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
+  LAUNCH k_absmax<<<152 * 4, 256, 0, s>>>(L.b64, L.nn, H->d_norm);
+  double bn = read_norm(H, s);
+  if (bn == 0.0) bn = 1.0;
+  cc_result res{};
+  res.status = CC_ERR_NOT_CONVERGED;
+  double rel = 0, first = -1;
+  // residual of the initial guess (in the mixed mode it is also the first
+  // FP32 right-hand side)
+  CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
+  if (mixed) residual64<float>(H, L.u64[0], L.b64, L.b32, s);
+  else residual64<double>(H, L.u64[0], L.b64, H->r64, s);
+  rel = read_norm(H, s) / bn;
+  first = rel;
+  if (rel < tol) res.status = CC_OK;
+  int it = 0;
+  const int gi = mixed ? 1 : 0;
+  bool use_graph = H->opt.use_graphs && !H->timing;
+  for (; res.status != CC_OK && it < H->opt.max_cycles; ++it) {
+    if (use_graph) {
+      if (!H->gexec[gi]) {
+        cudaGraph_t gr;
+        int64_t before = t_launches;
+        CK(cudaStreamBeginCapture(H->gstream, cudaStreamCaptureModeThreadLocal));
+        iteration(H, mixed, H->gstream);
+        CK(cudaStreamEndCapture(H->gstream, &gr));
+        CK(cudaGraphInstantiate(&H->gexec[gi], gr, 0));
+        CK(cudaGraphDestroy(gr));
+        H->gexec_launches[gi] = t_launches - before;
+        t_launches = before;
+      }
+      CK(cudaGraphLaunch(H->gexec[gi], s));
+      t_launches += H->gexec_launches[gi];
+    } else {
+      iteration(H, mixed, s);
+    }
+    rel = read_norm(H, s) / bn;
+    if (rel < tol) {
+      res.status = CC_OK;
+      ++it;
+      break;
+    }
+    if (!std::isfinite(rel) || (first > 0 && rel > 1e3 * first)) {
+      res.status = CC_ERR_DIVERGED;
+      ++it;
+      break;
+    }
+  }
+  CK(cudaMemcpyAsync(u, L.u64[H->cur64], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  res.cycles = it;
+  res.rel_res = rel;
+  res.kernels = t_launches - launches0;
+  if (out) *out = res;
+  return res.status;
+}
+
+void worker_loop(cc_hierarchy* H) {
+  CK(cudaSetDevice(H->device));
+  for (;;) {
+    uint64_t id;
+    {
+      std::unique_lock<std::mutex> lk(H->qmu);
+      H->qcv.wait(lk, [&] { return H->stop || !H->queue.empty(); });
+      if (H->stop && H->queue.empty()) return;
+      id = H->queue.front();
+      H->queue.pop_front();
+    }
+    Request rq;
+    {
+      std::lock_guard<std::mutex> lk(g_reqmu);
+      rq = g_req[id];
+    }
+    cc_result res{};
+    const double t_start = now_s();
+    cc_status st;
+    try {
+      st = solve_impl(H, rq.f, rq.g, rq.u, rq.tol, H->wstream, &res);
+    } catch (CudaError&) {
+      st = CC_ERR_CUDA;
+    }
+    res.status = st;
+    res.t_submit = rq.res.t_submit;
+    res.t_start = t_start;
+    res.t_done = now_s();
+    std::lock_guard<std::mutex> lk(g_reqmu);
+    auto it = g_req.find(id);
+    if (it != g_req.end()) {
+      it->second.res = res;
+      it->second.done = true;
+    }
+  }
+}
+
+void destroy_hierarchy(cc_hierarchy* H) {
+  if (!H) return;
+  if (H->worker.joinable()) {
+    {
+      std::lock_guard<std::mutex> lk(H->qmu);
+      H->stop = true;
+    }
+    H->qcv.notify_all();
+    H->worker.join();
+  }
+  if (!H->opt.host_only) cudaDeviceSynchronize();
+  for (auto& g : H->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto& e : H->ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (H->wstream) cudaStreamDestroy(H->wstream);
+  if (H->gstream) cudaStreamDestroy(H->gstream);
+  if (H->h_norm) cudaFreeHost(H->h_norm);
+  H->pool.release();
+  delete H;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void cc_default_options(cc_options* o) {
+  if (!o) return;
+  o->eps = 0.1;
+  o->nu1 = 3;
+  o->nu2 = 3;
+  o->omega = 0.5;
+  o->cycle = CC_CYCLE_V;
+  o->min_coarse_n = 4;
+  o->precision = CC_PREC_FP64;
+  o->max_cycles = 100;
+  o->use_graphs = 1;
+  o->host_only = 0;
+}
+
+const char* cc_status_string(cc_status s) {
+  switch (s) {
+    case CC_OK: return "ok";
+    case CC_ERR_ARG: return "invalid argument";
+    case CC_ERR_GEOMETRY: return "domain not resolved by the grid";
+    case CC_ERR_SINGULAR: return "singular fit or factorisation";
+    case CC_ERR_NO_MEMORY: return "out of memory";
+    case CC_ERR_NOT_CONVERGED: return "not converged";
+    case CC_ERR_DIVERGED: return "diverged";
+    case CC_ERR_TIMEOUT: return "timeout";
+    case CC_ERR_CUDA: return "CUDA error";
+    case CC_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_bc* bc, int n_bc,
+                   int n, const cc_options* opt, cc_stream stream, cc_handle* out) {
+  if (!out) return CC_ERR_ARG;
+  *out = nullptr;
+  if (!dom || !bc || n < 4 || (dom->n_holes > 0 && !dom->holes)) return CC_ERR_ARG;
+  if (!(b * b < 4 * a * c) || !(a > 0)) return CC_ERR_ARG;
+  if (n_bc != 4 + dom->n_holes) return CC_ERR_ARG;
+  cc_options o;
+  cc_default_options(&o);
+  if (opt) o = *opt;
+  if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 == 0 || o.min_coarse_n < 4 || o.max_cycles < 1 ||
+      !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3))
+    return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cc_hierarchy* H = new cc_hierarchy();
+  H->opt = o;
+  Problem& P = H->P;
+  P.x0 = dom->x0; P.y0 = dom->y0; P.x1 = dom->x1; P.y1 = dom->y1;
+  P.a = a; P.b = b; P.c = c; P.eps = o.eps;
+  for (int k = 0; k < dom->n_holes; ++k) {
+    const cc_hole& hh = dom->holes[k];
+    if (!(hh.r1 > 0 && hh.r2 > 0)) { delete H; return CC_ERR_ARG; }
+    Hole e{hh.cx, hh.cy, hh.r1, hh.r2, hh.theta, std::cos(hh.theta), std::sin(hh.theta)};
+    P.holes.push_back(e);
+  }
+  for (int k = 0; k < n_bc; ++k) {
+    if (bc[k].type < 0 || bc[k].type > 2) { delete H; return CC_ERR_ARG; }
+    P.bc.push_back({bc[k].type, bc[k].alpha1, bc[k].alpha2});
+  }
+  const bool dev = !o.host_only;
+  try {
+    if (dev) CK(cudaGetDevice(&H->device));
+    // levels: halve while the level is resolved and discretisable (Eq. 5.9)
+    int nl = n;
+    while (true) {
+      // a coarse level must resolve every hole: two cells across its smaller
+      // semi-axis (the precondition of Alg. 1, made concrete)
+      if (!H->lv.empty()) {
+        double hl = (P.x1 - P.x0) / nl;
+        bool fine_enough = true;
+        for (const Hole& e : P.holes) fine_enough = fine_enough && std::min(e.r1, e.r2) >= 2.0 * hl;
+        if (!fine_enough) break;
+      }
+      LevelDisc D;
+      try {
+        D = discretize(P, nl);
+        if (!D.geom.resolved) throw SetupError(2, D.geom.reason);
+      } catch (SetupError& e) {
+        if (H->lv.empty()) throw;
+        break;
+      }
+      auto L = std::make_unique<Level>();
+      L->disc = std::move(D);
+      L->n = nl;
+      L->nn = (int64_t)nl * nl;
+      H->lv.push_back(std::move(L));
+      if (nl % 2 || nl / 2 < o.min_coarse_n || H->lv.size() >= 30) break;
+      nl /= 2;
+    }
+    // every level but the finest must keep the box walls extendable in the
+    // same rows: nothing else is required for the cycle.
+    for (size_t l = 0; l < H->lv.size(); ++l) {
+      Level& L = *H->lv[l];
+      const LevelDisc& D = L.disc;
+      L.disc.P = &H->P;
+      L.sp = make_stencil(D, o.omega);
+      L.plan = plan_block(D);
+      if (!dev) continue;
+      std::vector<uint8_t> cls(L.nn, C_EMPTY);
+      for (int64_t k = 0; k < L.nn; ++k)
+        if (D.kind[k] != K_EMPTY) cls[k] = C_STENCIL;
+      for (int k : D.block) cls[k] = C_BLOCK;
+      L.cls = H->pool.upload(cls, s);
+      for (int i = 0; i < 2; ++i) {
+        L.u64[i] = H->pool.alloc<double>(L.nn);
+        L.u32[i] = H->pool.alloc<float>(L.nn);
+        CK(cudaMemsetAsync(L.u64[i], 0, L.nn * sizeof(double), s));
+        CK(cudaMemsetAsync(L.u32[i], 0, L.nn * sizeof(float), s));
+      }
+      L.b64 = H->pool.alloc<double>(L.nn);
+      L.b32 = H->pool.alloc<float>(L.nn);
+      CK(cudaMemsetAsync(L.b64, 0, L.nn * sizeof(double), s));
+      CK(cudaMemsetAsync(L.b32, 0, L.nn * sizeof(float), s));
+      if (l + 1 < H->lv.size()) {
+        L.blk.d64 = upload_block<double>(H->pool, L.plan, s);
+        L.blk.d32 = upload_block<float>(H->pool, L.plan, s);
+      }
+      if (!D.block.empty()) {
+        L.brow_cell = H->pool.upload(D.block, s);
+        L.brow_ptr = H->pool.upload(D.block_rows.ptr, s);
+        L.brow_col = H->pool.upload(D.block_rows.col, s);
+        L.brow_val = H->pool.upload(D.block_rows.val, s);
+      }
+      std::vector<int> fd, fs;
+      for (int64_t k = 0; k < L.nn; ++k)
+        if (D.geom.type[k] == CT_EMPTY && D.geom.owner[k] >= 0 && D.geom.owner[k] != k) {
+          fd.push_back((int)k);
+          fs.push_back(D.geom.owner[k]);
+        }
+      L.nfix = (int)fd.size();
+      if (L.nfix) {
+        L.fix_dst = H->pool.upload(fd, s);
+        L.fix_src = H->pool.upload(fs, s);
+      }
+    }
+    // bottom: dense inverse of the coarsest level's matrix
+    if (dev) {
+      Level& L = *H->lv.back();
+      const int nc = (int)L.nn;
+      if (nc > 4096) throw SetupError(1, "coarsest level too large for the dense bottom solve");
+      std::vector<double> A((size_t)nc * nc, 0.0);
+      std::map<int, double> ar;
+      for (int k = 0; k < nc; ++k) {
+        L.disc.row(k, ar, nullptr);
+        for (auto& kv : ar) A[(size_t)k * nc + kv.first] += kv.second;
+      }
+      std::vector<double> A0(A);
+      if (!invert(A, nc)) throw SetupError(3, "singular coarsest-level matrix");
+      {
+        std::vector<double> t(nc), x(nc, 0.0);
+        for (int k = 0; k < nc; ++k) t[k] = std::sin(1.0 + 0.7 * k) + 0.25 * std::cos(3.1 * k);
+        for (int r = 0; r < nc; ++r) {
+          double acc = 0;
+          for (int k = 0; k < nc; ++k) acc += A[(size_t)r * nc + k] * t[k];
+          x[r] = acc;
+        }
+        double rmax = 0, amax = 0, xmax = 0;
+        for (int r = 0; r < nc; ++r) {
+          double acc = -t[r], arow = 0;
+          for (int k = 0; k < nc; ++k) { acc += A0[(size_t)r * nc + k] * x[k]; arow += std::fabs(A0[(size_t)r * nc + k]); }
+          rmax = std::max(rmax, std::fabs(acc));
+          amax = std::max(amax, arow);
+          xmax = std::max(xmax, std::fabs(x[r]));
+        }
+        H->bottom_error = rmax / (amax * xmax);
+      }
+      if (dev) H->bottom_inv = H->pool.upload(to_cm(A, nc, nc), s);
+      H->nc_bottom = nc;
+    }
+    // finest level: N rows, residual buffers, norms
+    {
+      Level& L = *H->lv[0];
+      const LevelDisc& D = L.disc;
+      H->n_bd = (int)D.bd_cells.size();
+      H->n_g = 4 * n + H->n_bd;
+      H->n_nrows = D.nrows.rows();
+      int64_t dof = 0;
+      for (int64_t k = 0; k < L.nn; ++k) dof += D.kind[k] != K_EMPTY;
+      H->n_dof = dof;
+      if (!dev) goto done;
+      if (H->n_nrows) {
+        H->nrow_cell = H->pool.upload(D.nrow_cell, s);
+        H->nrow_ptr = H->pool.upload(D.nrows.ptr, s);
+        H->nrow_col = H->pool.upload(D.nrows.col, s);
+        H->nrow_val = H->pool.upload(D.nrows.val, s);
+      }
+      H->r64 = H->pool.alloc<double>(L.nn);
+      CK(cudaMemsetAsync(H->r64, 0, L.nn * sizeof(double), s));
+      H->d_norm = H->pool.alloc<unsigned long long>(2);
+      CK(cudaMallocHost(&H->h_norm, 2 * sizeof(unsigned long long)));
+    }
+    CK(cudaStreamCreateWithFlags(&H->gstream, cudaStreamNonBlocking));
+    CK(cudaStreamSynchronize(s));
+  done:;
+  } catch (SetupError& e) {
+    cc_status st = from_setup(e.code);
+    destroy_hierarchy(H);
+    return st;
+  } catch (CudaError& e) {
+    destroy_hierarchy(H);
+    return e.e == cudaErrorMemoryAllocation ? CC_ERR_NO_MEMORY : CC_ERR_CUDA;
+  } catch (std::bad_alloc&) {
+    destroy_hierarchy(H);
+    return CC_ERR_NO_MEMORY;
+  }
+  *out = H;
+  return CC_OK;
+}
+
+cc_status cc_query(cc_handle H, cc_info* out) {
+  if (!H || !out) return CC_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->n = H->lv[0]->n;
+  out->n_levels = (int)H->lv.size();
+  out->n_dof = H->n_dof;
+  out->n_bd = H->n_bd;
+  out->n_g = H->n_g;
+  out->n_plg = (int)H->lv[0]->disc.plg.size();
+  out->n_block = (int)H->lv[0]->disc.block.size();
+  out->device_bytes = H->pool.bytes;
+  for (size_t l = 0; l < H->lv.size() && l < 32; ++l) {
+    out->level_n[l] = H->lv[l]->n;
+    out->block_error = std::max(out->block_error, H->lv[l]->plan.error);
+  }
+  out->bottom_error = H->bottom_error;
+  return CC_OK;
+}
+
+cc_status cc_destroy(cc_handle H) {
+  if (!H) return CC_ERR_ARG;
+  destroy_hierarchy(H);
+  return CC_OK;
+}
+
+cc_status cc_cell_types(cc_handle H, uint8_t* h_type, uint8_t* h_kind, double* h_vol) {
+  if (!H || !h_type) return CC_ERR_ARG;
+  const LevelDisc& D = H->lv[0]->disc;
+  std::copy(D.geom.type.begin(), D.geom.type.end(), h_type);
+  if (h_kind) std::copy(D.kind.begin(), D.kind.end(), h_kind);
+  if (h_vol) std::copy(D.geom.vol.begin(), D.geom.vol.end(), h_vol);
+  return CC_OK;
+}
+
+cc_status cc_quadrature_nodes(cc_handle H, int* n_cut, int64_t* nv, int64_t* nb, int* h_cell,
+                              int64_t* h_vptr, double* h_vnode, int64_t* h_bptr, double* h_bnode,
+                              int* h_bbc) {
+  if (!H || !n_cut || !nv || !nb) return CC_ERR_ARG;
+  const LevelDisc& D = H->lv[0]->disc;
+  const LevelGeom& G = D.geom;
+  int nc = 0;
+  int64_t v = 0, bcount = 0;
+  for (auto& kv : G.cut) {
+    auto vn = volume_nodes(H->P, G, kv.first);
+    if (h_cell) {
+      h_cell[nc] = kv.first;
+      h_vptr[nc] = v;
+      for (size_t q = 0; q < vn.size(); ++q)
+        for (int t = 0; t < 3; ++t) h_vnode[3 * (v + (int64_t)q) + t] = vn[q][t];
+    }
+    v += (int64_t)vn.size();
+    ++nc;
+  }
+  if (h_cell && h_vptr) h_vptr[nc] = v;
+  for (size_t r = 0; r < D.bd_cells.size(); ++r) {
+    auto bn = boundary_nodes(H->P, G, D.bd_cells[r]);
+    double ws = 0;
+    for (auto& x : bn) ws += x.w;
+    if (h_bptr) {
+      h_bptr[r] = bcount;
+      for (size_t q = 0; q < bn.size(); ++q) {
+        double* o = h_bnode + 5 * (bcount + (int64_t)q);
+        o[0] = bn[q].x; o[1] = bn[q].y; o[2] = bn[q].nx; o[3] = bn[q].ny; o[4] = bn[q].w / ws;
+        h_bbc[bcount + (int64_t)q] = bn[q].bc;
+      }
+    }
+    bcount += (int64_t)bn.size();
+  }
+  if (h_bptr) h_bptr[D.bd_cells.size()] = bcount;
+  *n_cut = nc;
+  *nv = v;
+  *nb = bcount;
+  return CC_OK;
+}
+
+cc_status cc_solve(cc_handle H, const double* f, const double* g, double* u, double tol,
+                   cc_stream stream, cc_result* out) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || !f || !u || (H->n_g && !g) || !(tol > 0)) return CC_ERR_ARG;
+  try {
+    return solve_impl(H, f, g, u, tol, (cudaStream_t)stream, out);
+  } catch (CudaError&) {
+    return CC_ERR_CUDA;
+  }
+}
+
+cc_status cc_solve_host(cc_handle H, const double* hf, const double* hg, double* hu, double tol,
+                        cc_stream stream, cc_result* out) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || !hf || !hu || (H->n_g && !hg) || !(tol > 0)) return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    Level& L = *H->lv[0];
+    if (!H->h_u_dev) {
+      H->h_u_dev = H->pool.alloc<double>(L.nn);
+      H->h_f_dev = H->pool.alloc<double>(L.nn);
+      H->h_g_dev = H->pool.alloc<double>(std::max(1, H->n_g));
+    }
+    CK(cudaMemcpyAsync(H->h_f_dev, hf, L.nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (H->n_g) CK(cudaMemcpyAsync(H->h_g_dev, hg, H->n_g * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(H->h_u_dev, hu, L.nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    cc_status st = solve_impl(H, H->h_f_dev, H->h_g_dev, H->h_u_dev, tol, s, out);
+    CK(cudaMemcpyAsync(hu, H->h_u_dev, L.nn * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+  } catch (CudaError& e) {
+    return e.e == cudaErrorMemoryAllocation ? CC_ERR_NO_MEMORY : CC_ERR_CUDA;
+  }
+}
+
+cc_status cc_submit(cc_handle H, const double* f, const double* g, double* u, double tol,
+                    uint64_t* req_id) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || !f || !u || !req_id || (H->n_g && !g) || !(tol > 0)) return CC_ERR_ARG;
+  try {
+    if (!H->worker.joinable()) {
+      CK(cudaStreamCreateWithFlags(&H->wstream, cudaStreamNonBlocking));
+      H->worker = std::thread(worker_loop, H);
+    }
+  } catch (CudaError&) {
+    return CC_ERR_CUDA;
+  }
+  uint64_t id = g_next_id++;
+  Request rq{H, f, g, u, tol, cc_result{}, false};
+  rq.res.t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lk(g_reqmu);
+    g_req[id] = rq;
+  }
+  {
+    std::lock_guard<std::mutex> lk(H->qmu);
+    H->queue.push_back(id);
+  }
+  H->qcv.notify_one();
+  *req_id = id;
+  return CC_OK;
+}
+
+cc_status cc_poll(uint64_t id, cc_result* out) {
+  std::lock_guard<std::mutex> lk(g_reqmu);
+  auto it = g_req.find(id);
+  if (it == g_req.end()) return CC_ERR_ARG;
+  if (!it->second.done) return CC_ERR_BUSY;
+  if (out) *out = it->second.res;
+  cc_status st = it->second.res.status;
+  g_req.erase(it);
+  return st;
+}
+
+// ---- operator-level entry points -------------------------------------------
+cc_status cc_assemble_rhs(cc_handle H, const double* f, const double* g, double* b, cc_stream st) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || !f || !b || (H->n_g && !g)) return CC_ERR_ARG;
+  try {
+    assemble_rhs(H, f, g, b, (cudaStream_t)st);
+    CK(cudaGetLastError());
+  } catch (CudaError&) { return CC_ERR_CUDA; }
+  return CC_OK;
+}
+
+cc_status cc_residual(cc_handle H, int l, const double* u, const double* b, double* r, cc_stream st) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || l < 0 || l >= (int)H->lv.size() || !u || !b || !r) return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)st;
+  try {
+    Level& L = *H->lv[l];
+    if (L.sp.cross)
+      LAUNCH k_resid<double, double, true><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, r, L.sp, nullptr);
+    else
+      LAUNCH k_resid<double, double, false><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, r, L.sp, nullptr);
+    if (!L.disc.block.empty())
+      LAUNCH k_block_resid<double><<<nblk((int64_t)L.disc.block.size()), 256, 0, s>>>(
+          (int)L.disc.block.size(), L.brow_cell, L.brow_ptr, L.brow_col, L.brow_val, u, b, r, nullptr);
+    CK(cudaGetLastError());
+  } catch (CudaError&) { return CC_ERR_CUDA; }
+  return CC_OK;
+}
+
+cc_status cc_smooth(cc_handle H, int l, double* u, const double* b, cc_stream st) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || l < 0 || l + 1 >= (int)H->lv.size() || !u || !b) return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)st;
+  try {
+    Level& L = *H->lv[l];
+    CK(cudaMemcpyAsync(L.u64[0], u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(L.u64[1], u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(L.b64, b, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    int cur = 0;
+    sweep<double>(H, l, cur, false, (const double*)nullptr, s);
+    CK(cudaMemcpyAsync(u, L.u64[cur], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+  } catch (CudaError&) { return CC_ERR_CUDA; }
+  return CC_OK;
+}
+
+cc_status cc_restrict_residual(cc_handle H, int l, const double* u, const double* b, double* rc,
+                               cc_stream st) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || l < 0 || l + 1 >= (int)H->lv.size() || !u || !b || !rc) return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)st;
+  try {
+    Level& L = *H->lv[l];
+    Level& C = *H->lv[l + 1];
+    if (L.sp.cross)
+      LAUNCH k_resid_restrict<double, true><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, C.cls, rc, L.sp);
+    else
+      LAUNCH k_resid_restrict<double, false><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, C.cls, rc, L.sp);
+    CK(cudaGetLastError());
+  } catch (CudaError&) { return CC_ERR_CUDA; }
+  return CC_OK;
+}
+
+cc_status cc_prolong_add(cc_handle H, int l, const double* ec, double* u, cc_stream st) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || l < 0 || l + 1 >= (int)H->lv.size() || !ec || !u) return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)st;
+  try {
+    Level& L = *H->lv[l];
+    Level& C = *H->lv[l + 1];
+    double* tmp = C.u64[1];
+    CK(cudaMemcpyAsync(tmp, ec, C.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (C.nfix) LAUNCH k_owner_fix<double><<<nblk(C.nfix), 256, 0, s>>>(C.nfix, C.fix_dst, C.fix_src, tmp);
+    LAUNCH k_prolong_add<double><<<nblk(L.nn), 256, 0, s>>>(u, tmp, L.cls, L.n);
+    CK(cudaGetLastError());
+  } catch (CudaError&) { return CC_ERR_CUDA; }
+  return CC_OK;
+}
+
+cc_status cc_cycle(cc_handle H, double* u, const double* b, cc_stream st) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H || !u || !b) return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)st;
+  try {
+    Level& L = *H->lv[0];
+    CK(cudaMemcpyAsync(L.u64[0], u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(L.b64, b, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    std::vector<int> cur(H->lv.size(), 0);
+    cycle_level<double>(H, 0, cur, false, s);
+    CK(cudaMemcpyAsync(u, L.u64[cur[0]], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+  } catch (CudaError&) { return CC_ERR_CUDA; }
+  return CC_OK;
+}
+
+cc_status cc_level_tables(cc_handle H, int l, uint8_t* h_kind, int* h_lattice, double* h_beta,
+                          int* n_plg) {
+  if (!H || l < 0 || l >= (int)H->lv.size()) return CC_ERR_ARG;
+  const LevelDisc& D = H->lv[l]->disc;
+  if (h_kind) std::copy(D.kind.begin(), D.kind.end(), h_kind);
+  for (size_t r = 0; r < D.plg.size(); ++r) {
+    if (h_lattice) std::copy(D.lattice[r].begin(), D.lattice[r].end(), h_lattice + 15 * r);
+    if (h_beta) std::copy(D.beta[r].begin(), D.beta[r].end(), h_beta + 16 * r);
+  }
+  if (n_plg) *n_plg = (int)D.plg.size();
+  return CC_OK;
+}
+
+cc_status cc_kernel_timing(cc_handle H, int enable) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H) return CC_ERR_ARG;
+  H->timing = enable != 0;
+  H->ev_used = 0;
+  H->timed_launches = 0;
+  H->timed_ms = 0;
+  return CC_OK;
+}
+
+cc_status cc_kernel_timing_read(cc_handle H, int64_t* launches, double* total_ms,
+                                double* bytes_per_launch) {
+  if (H && H->opt.host_only) return CC_ERR_ARG;
+  if (!H) return CC_ERR_ARG;
+  try {
+    CK(cudaDeviceSynchronize());
+    for (size_t i = 0; i < H->ev_used; ++i) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, H->ev[i].first, H->ev[i].second));
+      H->timed_ms += ms;
+      ++H->timed_launches;
+    }
+    H->ev_used = 0;
+  } catch (CudaError&) { return CC_ERR_CUDA; }
+  const int64_t nn = H->lv[0]->nn;
+  const double w = H->opt.precision == CC_PREC_MIXED ? 4.0 : 8.0;
+  if (launches) *launches = H->timed_launches;
+  if (total_ms) *total_ms = H->timed_ms;
+  if (bytes_per_launch) *bytes_per_launch = 3.0 * w * (double)nn;
+  return CC_OK;
+}
+
+}  // extern "C"

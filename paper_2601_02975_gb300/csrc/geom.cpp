@@ -1,0 +1,519 @@
+// Cut cells of a box minus a union of ellipses (Sec. 3.1) and the merging of
+// small cells (Alg. 1, lines 8-11), in FP64 on the host.
+//
+// A cut cell is described by its oriented boundary pieces: the parts of its
+// four faces that lie in the domain (counter-clockwise) and the arcs of hole
+// boundaries inside it (clockwise around the hole), so the cell is on the
+// left of every piece.  Area integrals then follow from Green's theorem,
+//   integral_C X^p Y^q dA = contour integral X^(p+1) Y^q / (p+1) dY,
+// in the scaled coordinates X = (x - px)/h, Y = (y - py)/h about the centre
+// of the control volume (Sec. 4.2, quadrature paragraph).  Faces are
+// integrated by 5-point Gauss-Legendre (exact for these polynomials), arcs by
+// 10-point Gauss-Legendre on sub-arcs of at most 0.25 rad.
+//
+// Alg. 1 lines 8-11 are applied once in row-major order (y index outer) with
+// the current volumes; the merge target is a present neighbour reached
+// through a shared face piece of positive length (following the chain of
+// earlier merges), minimising |vol + vol' - h^2|, ties to the first of the
+// neighbours in the order -x, +x, -y, +y.  A level whose cut cells have more
+// than one connected component violates the precondition of Alg. 1 and is
+// marked unresolved.
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <map>
+#include <set>
+
+#include "setup.h"
+
+namespace ccmg {
+
+void Hole::at(double t, double& x, double& y) const {
+  double ct = std::cos(t), st = std::sin(t);
+  x = cx + co * r1 * ct - si * r2 * st;
+  y = cy + si * r1 * ct + co * r2 * st;
+}
+void Hole::dat(double t, double& dx, double& dy) const {
+  double ct = std::cos(t), st = std::sin(t);
+  dx = -co * r1 * st - si * r2 * ct;
+  dy = -si * r1 * st + co * r2 * ct;
+}
+double Hole::level(double x, double y) const {
+  double dx = x - cx, dy = y - cy;
+  double u = co * dx + si * dy, v = -si * dx + co * dy;
+  return (u / r1) * (u / r1) + (v / r2) * (v / r2) - 1.0;
+}
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+namespace {
+
+const double kTwoPi = 6.283185307179586476925286766559;
+
+struct Rules {
+  std::vector<double> sx, sw, ax, aw, ix, iw;
+  Rules() {
+    gauss_legendre(5, sx, sw);
+    gauss_legendre(10, ax, aw);
+    gauss_legendre(6, ix, iw);
+  }
+};
+const Rules& rules() {
+  static Rules r;
+  return r;
+}
+
+// Quadrature points along a piece: position and the vector weight (dx, dy).
+template <class F>
+void walk(const Problem& P, const Piece& pc, F&& fn) {
+  const Rules& R = rules();
+  if (!pc.arc) {
+    for (size_t q = 0; q < R.sx.size(); ++q) {
+      double tau = 0.5 * (R.sx[q] + 1.0), wt = 0.5 * R.sw[q];
+      fn(pc.xa + tau * (pc.xb - pc.xa), pc.ya + tau * (pc.yb - pc.ya), (pc.xb - pc.xa) * wt,
+         (pc.yb - pc.ya) * wt);
+    }
+    return;
+  }
+  const Hole& H = P.holes[pc.hole];
+  int nsub = std::max(1, (int)std::ceil(std::fabs(pc.tb - pc.ta) / 0.25));
+  for (int s = 0; s < nsub; ++s) {
+    double s0 = pc.ta + (pc.tb - pc.ta) * s / nsub, s1 = pc.ta + (pc.tb - pc.ta) * (s + 1) / nsub;
+    for (size_t q = 0; q < R.ax.size(); ++q) {
+      double t = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * R.ax[q];
+      double wt = 0.5 * (s1 - s0) * R.aw[q];
+      double x, y, dx, dy;
+      H.at(t, x, y);
+      H.dat(t, dx, dy);
+      fn(x, y, dx * wt, dy * wt);
+    }
+  }
+}
+
+void piece_moments(const Problem& P, const Piece& pc, double px, double py, double h,
+                   double m[kMoments]) {
+  walk(P, pc, [&](double x, double y, double, double dy) {
+    double X = (x - px) / h, Y = (y - py) / h, dY = dy / h;
+    double xp[8], yq[7];
+    xp[0] = 1;
+    yq[0] = 1;
+    for (int k = 1; k < 8; ++k) xp[k] = xp[k - 1] * X;
+    for (int k = 1; k < 7; ++k) yq[k] = yq[k - 1] * Y;
+    for (int d = 0; d <= 6; ++d)
+      for (int q = 0; q <= d; ++q) {
+        int p = d - q;
+        m[midx(p, q)] += xp[p + 1] * yq[q] * dY / (p + 1);
+      }
+  });
+}
+
+// parameters t in [0, 2pi) with A cos t + B sin t = C
+void trig_roots(double A, double B, double C, std::vector<double>& out) {
+  double R = std::hypot(A, B);
+  if (std::fabs(C) >= R) return;
+  double phi = std::atan2(B, A), d = std::acos(C / R);
+  for (double t : {phi + d, phi - d}) {
+    t = std::fmod(t, kTwoPi);
+    if (t < 0) t += kTwoPi;
+    out.push_back(t);
+  }
+}
+
+// crossings of hole i with hole j: bracket sign changes of j's level function
+// along i, then refine with the Illinois variant of regula falsi
+void hole_crossings(const Hole& hi, const Hole& hj, std::vector<double>& out) {
+  const int ns = 3000;
+  auto f = [&](double t) {
+    double x, y;
+    hi.at(t, x, y);
+    return hj.level(x, y);
+  };
+  double ta = 0, fa = f(0);
+  for (int s = 1; s <= ns; ++s) {
+    double tb = kTwoPi * s / ns, fb = f(tb);
+    if (fa == 0.0) {
+      out.push_back(ta);
+    } else if ((fa < 0) != (fb < 0) && fb != 0.0) {
+      double a = ta, b = tb, ya = fa, yb = fb;
+      int side = 0;
+      for (int it = 0; it < 200 && b - a > 1e-16; ++it) {
+        double m = (a * yb - b * ya) / (yb - ya);
+        if (!(m > a && m < b)) m = 0.5 * (a + b);
+        double ym = f(m);
+        if (ym == 0.0) { a = b = m; break; }
+        if ((ym < 0) == (ya < 0)) {
+          a = m; ya = ym;
+          if (side == -1) yb *= 0.5;
+          side = -1;
+        } else {
+          b = m; yb = ym;
+          if (side == 1) ya *= 0.5;
+          side = 1;
+        }
+      }
+      out.push_back(0.5 * (a + b));
+    }
+    ta = tb;
+    fa = fb;
+  }
+}
+
+bool outside_all(const Problem& P, double x, double y, int skip = -1) {
+  for (size_t k = 0; k < P.holes.size(); ++k)
+    if ((int)k != skip && P.holes[k].level(x, y) <= 0.0) return false;
+  return true;
+}
+
+// number of closed loops with positive / negative area
+void count_loops(const Problem& P, const std::vector<Piece>& pcs, double px, double py, double h,
+                 int& n_out, int& n_in) {
+  n_out = n_in = 0;
+  std::vector<char> used(pcs.size(), 0);
+  const double tol = 1e-10 * h;
+  for (size_t s = 0; s < pcs.size(); ++s) {
+    if (used[s]) continue;
+    used[s] = 1;
+    double area = 0, m[kMoments];
+    std::fill(m, m + kMoments, 0.0);
+    piece_moments(P, pcs[s], px, py, h, m);
+    double ex = pcs[s].xb, ey = pcs[s].yb;
+    int guard = 0;
+    while (std::hypot(ex - pcs[s].xa, ey - pcs[s].ya) > tol) {
+      int nxt = -1;
+      for (size_t q = 0; q < pcs.size(); ++q)
+        if (!used[q] && std::hypot(pcs[q].xa - ex, pcs[q].ya - ey) <= tol) {
+          nxt = (int)q;
+          break;
+        }
+      if (nxt < 0 || ++guard > 100000)
+        throw SetupError(2, "cut-cell boundary pieces do not close");
+      used[nxt] = 1;
+      piece_moments(P, pcs[nxt], px, py, h, m);
+      ex = pcs[nxt].xb;
+      ey = pcs[nxt].yb;
+    }
+    area = m[0];
+    if (area > 0) ++n_out; else ++n_in;
+  }
+}
+
+}  // namespace
+
+void shift_moments(const double in[kMoments], double dx, double dy, double out[kMoments]) {
+  static double C[7][7];
+  static bool init = false;
+  if (!init) {
+    for (int n = 0; n < 7; ++n) {
+      C[n][0] = C[n][n] = 1;
+      for (int k = 1; k < n; ++k) C[n][k] = C[n - 1][k - 1] + C[n - 1][k];
+    }
+    init = true;
+  }
+  double px[7], py[7];
+  px[0] = py[0] = 1;
+  for (int k = 1; k < 7; ++k) { px[k] = px[k - 1] * dx; py[k] = py[k - 1] * dy; }
+  for (int d = 0; d <= 6; ++d)
+    for (int q = 0; q <= d; ++q) {
+      int p = d - q;
+      double s = 0;
+      for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= q; ++b) s += C[p][a] * C[q][b] * px[p - a] * py[q - b] * in[midx(a, b)];
+      out[midx(p, q)] = s;
+    }
+}
+
+void LevelGeom::moments(int k, double out[kMoments]) const {
+  auto it = cut.find(k);
+  if (it != cut.end()) {
+    std::copy(it->second.mom, it->second.mom + kMoments, out);
+    return;
+  }
+  // full unit cell about its centre: (1/(p+1)) (1/2)^p for even p, 0 odd
+  for (int d = 0; d <= 6; ++d)
+    for (int q = 0; q <= d; ++q) {
+      int p = d - q;
+      double mp = (p % 2) ? 0.0 : std::pow(0.5, p) / (p + 1);
+      double mq = (q % 2) ? 0.0 : std::pow(0.5, q) / (q + 1);
+      out[midx(p, q)] = mp * mq;
+    }
+}
+
+static std::vector<Piece> full_faces(const LevelGeom& G, int i, int j) {
+  int n = G.n;
+  double xl = G.x0 + i * G.h, xr = xl + G.h, yb = G.y0 + j * G.h, yt = yb + G.h;
+  std::vector<Piece> v;
+  v.push_back({false, xl, yb, xr, yb, -1, 0, 0, j == 0 ? 0 : -1});
+  v.push_back({false, xr, yb, xr, yt, -1, 0, 0, i == n - 1 ? 1 : -1});
+  v.push_back({false, xr, yt, xl, yt, -1, 0, 0, j == n - 1 ? 2 : -1});
+  v.push_back({false, xl, yt, xl, yb, -1, 0, 0, i == 0 ? 3 : -1});
+  return v;
+}
+
+LevelGeom build_geometry(const Problem& P, int n) {
+  LevelGeom G;
+  G.n = n;
+  G.x0 = P.x0;
+  G.y0 = P.y0;
+  G.h = (P.x1 - P.x0) / n;
+  const double h = G.h;
+  if (std::fabs((P.y1 - P.y0) - h * n) > 1e-12 * std::max(1.0, P.y1 - P.y0))
+    throw SetupError(1, "the box must be square");
+  const int nh = (int)P.holes.size();
+  std::map<int, std::vector<Piece>> arcs;      // cell -> arcs
+  std::map<int, std::vector<double>> vline;    // vertical line i -> y of crossings
+  std::map<int, std::vector<double>> hline;    // horizontal line j -> x of crossings
+  for (int e = 0; e < nh; ++e) {
+    const Hole& H = P.holes[e];
+    double hx = std::hypot(H.r1 * H.co, H.r2 * H.si), hy = std::hypot(H.r1 * H.si, H.r2 * H.co);
+    std::vector<double> ts;
+    int i0 = std::max(0, (int)std::floor((H.cx - hx - P.x0) / h));
+    int i1 = std::min(n, (int)std::ceil((H.cx + hx - P.x0) / h));
+    for (int i = i0; i <= i1; ++i) {
+      std::vector<double> r;
+      trig_roots(H.co * H.r1, -H.si * H.r2, P.x0 + i * h - H.cx, r);
+      for (double t : r) {
+        double x, y;
+        H.at(t, x, y);
+        ts.push_back(t);
+        vline[i].push_back(y);
+      }
+    }
+    int j0 = std::max(0, (int)std::floor((H.cy - hy - P.y0) / h));
+    int j1 = std::min(n, (int)std::ceil((H.cy + hy - P.y0) / h));
+    for (int j = j0; j <= j1; ++j) {
+      std::vector<double> r;
+      trig_roots(H.si * H.r1, H.co * H.r2, P.y0 + j * h - H.cy, r);
+      for (double t : r) {
+        double x, y;
+        H.at(t, x, y);
+        ts.push_back(t);
+        hline[j].push_back(x);
+      }
+    }
+    for (int f = 0; f < nh; ++f)
+      if (f != e) hole_crossings(H, P.holes[f], ts);
+    std::sort(ts.begin(), ts.end());
+    ts.erase(std::unique(ts.begin(), ts.end()), ts.end());
+    std::vector<std::pair<double, double>> segs;   // (from, to), from > to
+    if (ts.empty()) {
+      segs.push_back({kTwoPi, 0.0});
+    } else {
+      for (size_t k = 0; k < ts.size(); ++k) {
+        double lo = ts[k], hi = (k + 1 < ts.size()) ? ts[k + 1] : ts[0] + kTwoPi;
+        segs.push_back({hi, lo});
+      }
+    }
+    for (auto& sg : segs) {
+      double tm = 0.5 * (sg.first + sg.second), xm, ym;
+      H.at(tm, xm, ym);
+      if (!outside_all(P, xm, ym, e)) continue;
+      int ii = (int)std::floor((xm - P.x0) / h), jj = (int)std::floor((ym - P.y0) / h);
+      if (ii < 0 || jj < 0 || ii >= n || jj >= n) throw SetupError(2, "a hole leaves the box");
+      Piece pc;
+      pc.arc = true;
+      pc.hole = e;
+      pc.ta = sg.first;
+      pc.tb = sg.second;
+      H.at(pc.ta, pc.xa, pc.ya);
+      H.at(pc.tb, pc.xb, pc.yb);
+      pc.bc = 4 + e;
+      arcs[jj * n + ii].push_back(pc);
+    }
+  }
+
+  G.type.assign((size_t)n * n, CT_EMPTY);
+  G.vol.assign((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      int k = j * n + i;
+      if (arcs.count(k)) continue;
+      double xc = P.x0 + (i + 0.5) * h, yc = P.y0 + (j + 0.5) * h;
+      if (outside_all(P, xc, yc)) {
+        G.type[k] = CT_FULL;
+        G.vol[k] = h * h;
+      }
+    }
+  for (auto& kv : arcs) {
+    int k = kv.first, j = k / n, i = k % n;
+    double xl = P.x0 + i * h, xr = xl + h, yb = P.y0 + j * h, yt = yb + h;
+    double px = xl + 0.5 * h, py = yb + 0.5 * h;
+    Cut C;
+    C.pieces = kv.second;
+    for (int f = 0; f < 4; ++f) C.face[f] = false;
+    // faces counter-clockwise: bottom, right, top, left
+    struct E { double ax, ay, bx, by; bool horiz; const std::vector<double>* cr; int bc; };
+    static const std::vector<double> none;
+    auto crs = [&](std::map<int, std::vector<double>>& m, int key) -> const std::vector<double>* {
+      auto it = m.find(key);
+      return it == m.end() ? &none : &it->second;
+    };
+    E edges[4] = {{xl, yb, xr, yb, true, crs(hline, j), j == 0 ? 0 : -1},
+                  {xr, yb, xr, yt, false, crs(vline, i + 1), i == n - 1 ? 1 : -1},
+                  {xr, yt, xl, yt, true, crs(hline, j + 1), j == n - 1 ? 2 : -1},
+                  {xl, yt, xl, yb, false, crs(vline, i), i == 0 ? 3 : -1}};
+    for (int f = 0; f < 4; ++f) {
+      const E& ed = edges[f];
+      double ca = ed.horiz ? ed.ax : ed.ay, cb = ed.horiz ? ed.bx : ed.by;
+      double lo = std::min(ca, cb), hi = std::max(ca, cb);
+      std::vector<double> pts{lo};
+      for (double v : *ed.cr)
+        if (v > lo && v < hi) pts.push_back(v);
+      pts.push_back(hi);
+      std::sort(pts.begin(), pts.end());
+      if (ca > cb) std::reverse(pts.begin(), pts.end());
+      for (size_t s = 0; s + 1 < pts.size(); ++s) {
+        Piece pc;
+        pc.arc = false;
+        pc.hole = -1;
+        pc.ta = pc.tb = 0;
+        if (ed.horiz) { pc.xa = pts[s]; pc.xb = pts[s + 1]; pc.ya = pc.yb = ed.ay; }
+        else { pc.ya = pts[s]; pc.yb = pts[s + 1]; pc.xa = pc.xb = ed.ax; }
+        if (!outside_all(P, 0.5 * (pc.xa + pc.xb), 0.5 * (pc.ya + pc.yb))) continue;
+        pc.bc = ed.bc;
+        C.pieces.push_back(pc);
+        C.face[f] = true;
+      }
+    }
+    int n_out, n_in;
+    count_loops(P, C.pieces, px, py, h, n_out, n_in);
+    if (n_out != 1) {
+      G.resolved = false;
+      G.reason = "cell (" + std::to_string(i) + "," + std::to_string(j) + ") has " +
+                 std::to_string(n_out) + " components";
+    }
+    std::fill(C.mom, C.mom + kMoments, 0.0);
+    for (auto& pc : C.pieces) piece_moments(P, pc, px, py, h, C.mom);
+    if (C.mom[0] <= 0) continue;   // empty
+    G.type[k] = CT_CUT;
+    G.vol[k] = C.mom[0] * h * h;
+    G.cut[k] = C;
+  }
+
+  // ---- Alg. 1, lines 8-11 ------------------------------------------------
+  G.owner.assign((size_t)n * n, -1);
+  for (int k = 0; k < n * n; ++k)
+    if (G.type[k] != CT_EMPTY) G.owner[k] = k;
+  std::function<int(int)> root = [&](int k) {
+    while (G.owner[k] != k) k = G.owner[k];
+    return k;
+  };
+  const double h2 = h * h;
+  for (int k = 0; k < n * n; ++k) {
+    if (G.type[k] == CT_EMPTY || G.vol[k] >= P.eps * h2) continue;
+    int i = k % n, j = k / n;
+    const bool* face = G.cut.count(k) ? G.cut[k].face : nullptr;
+    static const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1}, fidx[4] = {3, 1, 0, 2};
+    std::vector<int> cand;
+    for (int q = 0; q < 4; ++q) {
+      if (face && !face[fidx[q]]) continue;
+      int ii = i + di[q], jj = j + dj[q];
+      if (ii < 0 || jj < 0 || ii >= n || jj >= n) continue;
+      int kk = jj * n + ii;
+      if (G.owner[kk] < 0) continue;
+      int t = root(kk);
+      if (t != k && std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
+    }
+    if (cand.empty()) throw SetupError(2, "a small cut cell has no neighbour to merge into");
+    int best = cand[0];
+    double bv = std::fabs(G.vol[best] + G.vol[k] - h2);
+    for (size_t q = 1; q < cand.size(); ++q) {
+      double v = std::fabs(G.vol[cand[q]] + G.vol[k] - h2);
+      if (v < bv) { bv = v; best = cand[q]; }
+    }
+    int bi = best % n, bj = best / n;
+    double mk[kMoments], mt[kMoments], sh[kMoments];
+    G.moments(k, mk);
+    G.moments(best, mt);
+    shift_moments(mk, i - bi, j - bj, sh);
+    if (!G.cut.count(best)) {
+      Cut T;
+      T.pieces = full_faces(G, bi, bj);
+      for (int f = 0; f < 4; ++f) T.face[f] = true;
+      std::copy(mt, mt + kMoments, T.mom);
+      G.cut[best] = T;
+    }
+    Cut& T = G.cut[best];
+    for (int q = 0; q < kMoments; ++q) T.mom[q] = mt[q] + sh[q];
+    auto it = G.cut.find(k);
+    if (it != G.cut.end()) {
+      T.pieces.insert(T.pieces.end(), it->second.pieces.begin(), it->second.pieces.end());
+      G.cut.erase(it);
+    }
+    G.vol[best] += G.vol[k];
+    G.vol[k] = 0;
+    G.type[k] = CT_EMPTY;
+    G.type[best] = CT_CUT;
+    G.owner[k] = best;
+  }
+  for (int k = 0; k < n * n; ++k)
+    if (G.owner[k] >= 0) G.owner[k] = root(k);
+  return G;
+}
+
+std::vector<BNode> boundary_nodes(const Problem& P, const LevelGeom& G, int k) {
+  std::vector<BNode> out;
+  auto it = G.cut.find(k);
+  if (it == G.cut.end()) return out;
+  for (const Piece& pc : it->second.pieces) {
+    if (pc.bc < 0) continue;
+    walk(P, pc, [&](double x, double y, double dx, double dy) {
+      double ds = std::hypot(dx, dy);
+      // the cell is on the left: the outward normal is the right-hand normal
+      out.push_back({x, y, dy / ds, -dx / ds, ds, pc.bc});
+    });
+  }
+  return out;
+}
+
+std::vector<std::array<double, 3>> volume_nodes(const Problem& P, const LevelGeom& G, int k) {
+  std::vector<std::array<double, 3>> out;
+  auto it = G.cut.find(k);
+  if (it == G.cut.end()) return out;
+  int i = k % G.n;
+  double px = G.x0 + (i + 0.5) * G.h;
+  const Rules& R = rules();
+  double vol = G.vol[k];
+  for (const Piece& pc : it->second.pieces) {
+    walk(P, pc, [&](double x, double y, double, double dy) {
+      if (dy == 0.0) return;
+      double half = 0.5 * (x - px);
+      for (size_t q = 0; q < R.ix.size(); ++q)
+        out.push_back({px + half * (1.0 + R.ix[q]), y, dy * half * R.iw[q] / vol});
+    });
+  }
+  return out;
+}
+
+}  // namespace ccmg

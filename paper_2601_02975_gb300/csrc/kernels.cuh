@@ -1,0 +1,430 @@
+// Device kernels of the cut-cell multigrid cycle (Sec. 5), templated on the
+// cycle precision T (float or double).  Level vectors are N x N row-major.
+//
+// Cell classes on the device: 0 empty, 1 stencil cell (an SFV cell relaxed
+// by weighted Jacobi, Eq. 5.7), 2 block cell (solved exactly by the block
+// smoother, Eq. 5.8: the PLG cells, plus the 4 x 4 box corners when b != 0).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ccmg {
+
+constexpr int TX = 32;   // tile width (cells) of the stencil kernels
+constexpr int TY = 8;    // tile height
+constexpr int HALO = 2;  // stencil radius
+constexpr int SX = TX + 2 * HALO;
+constexpr int SY = TY + 2 * HALO;
+
+enum : uint8_t { C_EMPTY = 0, C_STENCIL = 1, C_BLOCK = 2 };
+
+// Constant per-level stencil data: weights of the 5 x 5 SFV stencil (Eq.
+// 4.7a,b) and the homogeneous ghost coefficients of each wall.
+struct StencilParams {
+  int n;
+  int cross;               // b != 0
+  double w[25];            // (dj + 2) * 5 + (di + 2)
+  double gh[4][2][4];      // wall (S, E, N, W), depth - 1, inward cell q
+  double omega_over_diag;  // omega / D (D the centre weight)
+};
+
+// ---- tile loader: u (+ prolonged e) with ghosts beyond the box walls --------
+template <class T>
+__device__ __forceinline__ T cell_value(const T* __restrict__ u, const T* __restrict__ ec,
+                                        int n, int gx, int gy, bool zero) {
+  T v = zero ? T(0) : u[(size_t)gy * n + gx];
+  if (ec) v += ec[(size_t)(gy >> 1) * (n >> 1) + (gx >> 1)];
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ void load_tile(T (*s)[SX], const T* __restrict__ u,
+                                          const T* __restrict__ ec, const StencilParams& P,
+                                          int x0, int y0, bool zero) {
+  const int n = P.n;
+  for (int idx = threadIdx.x; idx < SX * SY; idx += blockDim.x) {
+    int ly = idx / SX, lx = idx % SX;
+    int gx = x0 + lx - HALO, gy = y0 + ly - HALO;
+    bool ox = gx < 0 || gx >= n, oy = gy < 0 || gy >= n;
+    T v = T(0);
+    if (!ox && !oy) {
+      v = cell_value(u, ec, n, gx, gy, zero);
+    } else if (ox != oy) {
+      // ghost beyond one wall: homogeneous part of the wall formula
+      int w, t, m;
+      if (gx >= n) { w = 1; t = gy; m = gx - n; }
+      else if (gx < 0) { w = 3; t = gy; m = -gx - 1; }
+      else if (gy >= n) { w = 2; t = gx; m = gy - n; }
+      else { w = 0; t = gx; m = -gy - 1; }
+      double acc = 0.0;
+      if (n >= 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int cx, cy;
+          switch (w) {
+            case 0: cx = t; cy = q; break;
+            case 1: cx = n - 1 - q; cy = t; break;
+            case 2: cx = t; cy = n - 1 - q; break;
+            default: cx = q; cy = t; break;
+          }
+          acc += P.gh[w][m][q] * (double)cell_value(u, ec, n, cx, cy, zero);
+        }
+      }
+      v = (T)acc;
+    }
+    s[ly][lx] = v;
+  }
+}
+
+template <class T, bool CROSS>
+__device__ __forceinline__ T apply_A(const T (*s)[SX], const double* w, int lx, int ly) {
+  // lx, ly: tile-interior coordinates (0-based)
+  const int cx = lx + HALO, cy = ly + HALO;
+  T acc = (T)w[2 * 5 + 0] * s[cy][cx - 2] + (T)w[2 * 5 + 1] * s[cy][cx - 1] +
+        (T)w[2 * 5 + 2] * s[cy][cx] + (T)w[2 * 5 + 3] * s[cy][cx + 1] + (T)w[2 * 5 + 4] * s[cy][cx + 2];
+  acc += (T)w[0 * 5 + 2] * s[cy - 2][cx] + (T)w[1 * 5 + 2] * s[cy - 1][cx] +
+         (T)w[3 * 5 + 2] * s[cy + 1][cx] + (T)w[4 * 5 + 2] * s[cy + 2][cx];
+  if (CROSS) {
+#pragma unroll
+    for (int dj = -2; dj <= 2; ++dj) {
+      if (dj == 0) continue;
+#pragma unroll
+      for (int di = -2; di <= 2; ++di) {
+        if (di == 0) continue;
+        acc += (T)w[(dj + 2) * 5 + (di + 2)] * s[cy + dj][cx + di];
+      }
+    }
+  }
+  return acc;
+}
+
+// ---- a1: weighted Jacobi sweep on stencil cells (Eq. 5.7) --------------------
+// u_out = u + omega/D (b - A u) on stencil cells; other cells are left as
+// they are in u_out (block cells are written by the block solve).  With ec,
+// the sweep reads u + I(ec) (Eq. 5.11) instead of u (the first post-sweep,
+// fused with the prolongation); with zero it reads 0 (a coarse level's first
+// sweep, whose initial guess is 0, Alg. 2).
+template <class T, bool CROSS>
+__global__ void __launch_bounds__(TX * TY)
+k_sweep(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ b,
+        const uint8_t* __restrict__ cls, const T* __restrict__ ec, StencilParams P, int zero) {
+  __shared__ T s[SY][SX];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  load_tile<T>(s, u_in, ec, P, x0, y0, zero != 0);
+  __syncthreads();
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const int gx = x0 + lx, gy = y0 + ly, n = P.n;
+  if (gx >= n || gy >= n) return;
+  const size_t k = (size_t)gy * n + gx;
+  if (cls[k] != C_STENCIL) return;
+  T Au = apply_A<T, CROSS>(s, P.w, lx, ly);
+  T uc = s[ly + HALO][lx + HALO];
+  u_out[k] = uc + (T)P.omega_over_diag * (b[k] - Au);
+}
+
+// ---- a4: residual and restriction (Eq. 5.10) ---------------------------------
+// r = b - A u on stencil cells, 0 on block and empty cells (the block residual
+// is zero after a block-smoother sweep); rc = average of the 4 children,
+// 0 on empty coarse cells.
+template <class T, bool CROSS>
+__global__ void __launch_bounds__(TX * TY)
+k_resid_restrict(const T* __restrict__ u, const T* __restrict__ b, const uint8_t* __restrict__ cls,
+                 const uint8_t* __restrict__ cls_c, T* __restrict__ rc, StencilParams P) {
+  __shared__ T s[SY][SX];
+  __shared__ T r[TY][TX];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  load_tile<T>(s, u, nullptr, P, x0, y0, false);
+  __syncthreads();
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const int gx = x0 + lx, gy = y0 + ly, n = P.n;
+  T rv = T(0);
+  if (gx < n && gy < n) {
+    const size_t k = (size_t)gy * n + gx;
+    if (cls[k] == C_STENCIL) rv = b[k] - apply_A<T, CROSS>(s, P.w, lx, ly);
+  }
+  r[ly][lx] = rv;
+  __syncthreads();
+  if (threadIdx.x < (TX / 2) * (TY / 2)) {
+    const int cx = threadIdx.x % (TX / 2), cy = threadIdx.x / (TX / 2);
+    const int nc = n >> 1;
+    const int gcx = (x0 >> 1) + cx, gcy = (y0 >> 1) + cy;
+    if (gcx < nc && gcy < nc) {
+      const size_t kc = (size_t)gcy * nc + gcx;
+      T v = T(0.25) * (r[2 * cy][2 * cx] + r[2 * cy][2 * cx + 1] + r[2 * cy + 1][2 * cx] +
+                       r[2 * cy + 1][2 * cx + 1]);
+      rc[kc] = cls_c[kc] == C_EMPTY ? T(0) : v;
+    }
+  }
+}
+
+// ---- a8 / Eq. 4.23: residual on stencil cells, max-norm ----------------------
+// r = b - A u on stencil cells (Tin arithmetic), 0 on empty cells; block cells
+// are left to k_block_resid.  |r| is folded into *rmax (as ordered bits).
+__device__ __forceinline__ void atomic_max_abs(unsigned long long* p, double v) {
+  atomicMax(p, (unsigned long long)__double_as_longlong(fabs(v)));
+}
+
+template <class Tin, class Tout, bool CROSS>
+__global__ void __launch_bounds__(TX * TY)
+k_resid(const Tin* __restrict__ u, const Tin* __restrict__ b, const uint8_t* __restrict__ cls,
+        Tout* __restrict__ r, StencilParams P, unsigned long long* rmax) {
+  __shared__ Tin s[SY][SX];
+  __shared__ double red[TX * TY / 32];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  load_tile<Tin>(s, u, nullptr, P, x0, y0, false);
+  __syncthreads();
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const int gx = x0 + lx, gy = y0 + ly, n = P.n;
+  double av = 0.0;
+  if (gx < n && gy < n) {
+    const size_t k = (size_t)gy * n + gx;
+    uint8_t c = cls[k];
+    if (c == C_STENCIL) {
+      Tin rv = b[k] - apply_A<Tin, CROSS>(s, P.w, lx, ly);
+      r[k] = (Tout)rv;
+      av = fabs((double)rv);
+    } else if (c == C_EMPTY) {
+      r[k] = Tout(0);
+    }
+  }
+  if (rmax) {
+    for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = av;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int q = 0; q < TX * TY / 32; ++q) m = fmax(m, red[q]);
+      atomic_max_abs(rmax, m);
+    }
+  }
+}
+
+// residual of block rows from their full sparse rows (FP64)
+template <class Tout>
+__global__ void k_block_resid(int m, const int* __restrict__ cell, const int64_t* __restrict__ ptr,
+                              const int* __restrict__ col, const double* __restrict__ val,
+                              const double* __restrict__ u, const double* __restrict__ b,
+                              Tout* __restrict__ r, unsigned long long* rmax) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double av = 0.0;
+  if (i < m) {
+    double acc = 0.0;
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) acc += val[q] * u[col[q]];
+    double rv = b[cell[i]] - acc;
+    r[cell[i]] = (Tout)rv;
+    av = fabs(rv);
+  }
+  if (rmax) {
+    for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_abs(rmax, av);
+  }
+}
+
+// ---- a3: exact solve on the block (Eq. 5.8), two-level Schur scheme ---------
+// The block unknowns (in curve order) are split into chunks; interface
+// unknowns couple chunks, interior unknowns only their own chunk and the
+// interfaces.  Precomputed in FP64 on the host: the inverse of each chunk's
+// interior block (column-major), the inverse of the interface Schur
+// complement (column-major), W_c = inv(A_cc) A_c,S on each chunk's interface
+// columns, and A_S,I.
+struct BlockDev {
+  int m, nch, ns;
+  const int* cell;          // [m] grid cell of block position
+  const int64_t* gptr;      // [m+1] gather rows: non-block columns
+  const int* gcol;
+  const void* gval;         // T
+  const int* cstart;        // [nch+1] block positions of each chunk
+  const int* iptr;          // [nch+1] interior list ptr
+  const int* ipos;          // interior block positions
+  const int64_t* aoff;      // [nch] offset of chunk inverse
+  const void* ainv;         // T, column-major per chunk
+  const int* spos;          // [ns] block positions of interfaces
+  const int64_t* asi_ptr;   // [ns+1] A_S,I rows
+  const int* asi_col;       // interior block positions
+  const void* asi_val;      // T
+  const void* sinv;         // T, ns x ns column-major
+  const int* wptr;          // [nch+1] interface columns of W_c
+  const int* widx;          // interface indices (into 0..ns-1)
+  const int64_t* woff;      // [nch] offset of W_c (column-major, rows = interior)
+  const void* wmat;         // T
+  void* tblk;               // T scratch [m]: gathered right-hand side
+  void* zblk;               // T scratch [m]: interior solutions
+  void* xs;                 // T scratch [ns]
+};
+
+// y[0..rows) = M x, M column-major (rows x cols), x in shared memory; the CTA
+// cooperates: lanes run over rows, warps split the columns.
+template <class T>
+__device__ void cta_matvec_cm(const T* __restrict__ M, int rows, int ld, int cols,
+                              const T* __restrict__ x, T* __restrict__ partial, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r0 = 0; r0 < rows; r0 += 32) {
+    int r = r0 + lane;
+    T acc = T(0);
+    if (r < rows)
+      for (int c = warp; c < cols; c += nw) acc += M[(size_t)c * ld + r] * x[c];
+    partial[warp * 32 + lane] = acc;
+    __syncthreads();
+    if (warp == 0 && r < rows) {
+      T s = T(0);
+      for (int q = 0; q < nw; ++q) s += partial[q * 32 + lane];
+      y[r] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// K_a: gather t = b - A(block, rest) u for the chunk, z = inv(A_cc) t_I;
+// interface rows' t go to tblk.  With no interfaces z is the solution.
+template <class T>
+__global__ void k_block_chunk(BlockDev B, const T* __restrict__ b, T* __restrict__ u) {
+  extern __shared__ unsigned char smem_raw[];
+  T* tI = reinterpret_cast<T*>(smem_raw);
+  const int c = blockIdx.x;
+  const int p0 = B.cstart[c], p1 = B.cstart[c + 1];
+  const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
+  T* partial = tI + ((ni + 31) & ~31);
+  T* zI = partial + blockDim.x;
+  const T* gval = static_cast<const T*>(B.gval);
+  T* tblk = static_cast<T*>(B.tblk);
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    T acc = b[B.cell[p]];
+    for (int64_t q = B.gptr[p]; q < B.gptr[p + 1]; ++q) acc -= gval[q] * u[B.gcol[q]];
+    tblk[p] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < ni; q += blockDim.x) tI[q] = tblk[B.ipos[i0 + q]];
+  __syncthreads();
+  const T* A = static_cast<const T*>(B.ainv) + B.aoff[c];
+  cta_matvec_cm<T>(A, ni, ni, ni, tI, partial, zI);
+  T* zblk = static_cast<T*>(B.zblk);
+  for (int q = threadIdx.x; q < ni; q += blockDim.x) {
+    int p = B.ipos[i0 + q];
+    zblk[p] = zI[q];
+    if (B.ns == 0) u[B.cell[p]] = zI[q];
+  }
+}
+
+// K_b: x_S = inv(S) (t_S - A_S,I z) for 32 interface rows per CTA.
+template <class T>
+__global__ void k_block_schur(BlockDev B, T* __restrict__ u) {
+  extern __shared__ unsigned char smem_raw[];
+  T* tS = reinterpret_cast<T*>(smem_raw);
+  T* partial = tS + ((B.ns + 31) & ~31);
+  T* y = partial + blockDim.x;
+  const T* tblk = static_cast<const T*>(B.tblk);
+  const T* zblk = static_cast<const T*>(B.zblk);
+  const T* av = static_cast<const T*>(B.asi_val);
+  for (int i = threadIdx.x; i < B.ns; i += blockDim.x) {
+    T acc = tblk[B.spos[i]];
+    for (int64_t q = B.asi_ptr[i]; q < B.asi_ptr[i + 1]; ++q) acc -= av[q] * zblk[B.asi_col[q]];
+    tS[i] = acc;
+  }
+  __syncthreads();
+  const int r0 = blockIdx.x * 32;
+  const int rows = min(32, B.ns - r0);
+  const T* S = static_cast<const T*>(B.sinv) + r0;
+  cta_matvec_cm<T>(S, rows, B.ns, B.ns, tS, partial, y);
+  T* xs = static_cast<T*>(B.xs);
+  for (int q = threadIdx.x; q < rows; q += blockDim.x) {
+    xs[r0 + q] = y[q];
+    u[B.cell[B.spos[r0 + q]]] = y[q];
+  }
+}
+
+// K_c: x_I = z - W_c x_S for the chunk's interior unknowns.
+template <class T>
+__global__ void k_block_back(BlockDev B, T* __restrict__ u) {
+  extern __shared__ unsigned char smem_raw[];
+  T* xl = reinterpret_cast<T*>(smem_raw);
+  const int c = blockIdx.x;
+  const int w0 = B.wptr[c], nw_ = B.wptr[c + 1] - w0;
+  T* partial = xl + ((nw_ + 31) & ~31);
+  const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
+  T* y = partial + blockDim.x;
+  const T* xs = static_cast<const T*>(B.xs);
+  for (int q = threadIdx.x; q < nw_; q += blockDim.x) xl[q] = xs[B.widx[w0 + q]];
+  __syncthreads();
+  const T* W = static_cast<const T*>(B.wmat) + B.woff[c];
+  cta_matvec_cm<T>(W, ni, ni, nw_, xl, partial, y);
+  const T* zblk = static_cast<const T*>(B.zblk);
+  for (int q = threadIdx.x; q < ni; q += blockDim.x) {
+    int p = B.ipos[i0 + q];
+    u[B.cell[p]] = zblk[p] - y[q];
+  }
+}
+
+// ---- a7: bottom solve, u = inv(A_c) b (FP64 matrix) --------------------------
+template <class T>
+__global__ void k_bottom(const double* __restrict__ Ainv_cm, int nc, const T* __restrict__ b,
+                         T* __restrict__ u) {
+  extern __shared__ unsigned char smem_raw[];
+  double* x = reinterpret_cast<double*>(smem_raw);
+  double* partial = x + ((nc + 31) & ~31);
+  double* y = partial + blockDim.x;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) x[i] = (double)b[i];
+  __syncthreads();
+  const int r0 = blockIdx.x * 32;
+  const int rows = min(32, nc - r0);
+  cta_matvec_cm<double>(Ainv_cm + r0, rows, nc, nc, x, partial, y);
+  for (int q = threadIdx.x; q < rows; q += blockDim.x) u[r0 + q] = (T)y[q];
+}
+
+// ---- a0: b = f - N g -----------------------------------------------------------
+__global__ void k_rhs_copy(const double* __restrict__ f, const uint8_t* __restrict__ cls,
+                           double* __restrict__ b, int64_t nn) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nn) b[k] = cls[k] == C_EMPTY ? 0.0 : f[k];
+}
+__global__ void k_rhs_n(int rows, const int* __restrict__ cell, const int64_t* __restrict__ ptr,
+                        const int* __restrict__ col, const double* __restrict__ val,
+                        const double* __restrict__ g, double* __restrict__ b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  double acc = 0.0;
+  for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) acc += val[q] * g[col[q]];
+  b[cell[i]] -= acc;
+}
+
+// ---- small helpers ---------------------------------------------------------------
+template <class T>
+__global__ void k_owner_fix(int cnt, const int* __restrict__ dst, const int* __restrict__ src,
+                            T* __restrict__ e) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) e[dst[i]] = e[src[i]];
+}
+
+template <class T>
+__global__ void k_prolong_add(T* __restrict__ u, const T* __restrict__ ec,
+                              const uint8_t* __restrict__ cls, int n) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)n * n) return;
+  if (cls[k] == C_EMPTY) return;
+  int gx = (int)(k % n), gy = (int)(k / n);
+  u[k] += ec[(size_t)(gy >> 1) * (n >> 1) + (gx >> 1)];
+}
+
+// u64 += e (non-empty cells)
+template <class T>
+__global__ void k_update(double* __restrict__ u, const T* __restrict__ e,
+                         const uint8_t* __restrict__ cls, int64_t nn) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nn && cls[k] != C_EMPTY) u[k] += (double)e[k];
+}
+
+template <class A, class B>
+__global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, int64_t nn) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nn) y[k] = (B)x[k];
+}
+
+__global__ void k_absmax(const double* __restrict__ x, int64_t nn, unsigned long long* out) {
+  double av = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nn;
+       k += (int64_t)gridDim.x * blockDim.x)
+    av = fmax(av, fabs(x[k]));
+  for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_abs(out, av);
+}
+
+}  // namespace ccmg

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Each side builds its own hierarchy and its own inputs from the seeded
+workload functions (the library through its exported quadrature rules, the
+oracle through its own), so the comparison covers the whole path.  The bar
+for the FP64 path is 1e-11 relative max-norm per cycle; each step is also
+compared on its own with random inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import __graft_entry__  # noqa: E402
+from oracle import discretize as D  # noqa: E402
+from oracle import multigrid as M  # noqa: E402
+from paper_2601_02975_gb300 import Hierarchy, default_options  # noqa: E402
+from paper_2601_02975_gb300 import inputs as I  # noqa: E402
+from paper_2601_02975_gb300 import workloads as W  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+
+
+def _problem(name):
+    if name == "poisson":
+        return W.problem_poisson_square()
+    if name == "table3":
+        return W.problem_table3()
+    if name == "disk":
+        return W.problem_disk()
+    if name.startswith("ellipses"):
+        return W.problem_ellipses(int(name[len("ellipses"):]))
+    if name == "box_cross":
+        u = W.u_expcos()
+        dom = W.Domain(box_bc=(W.BC(), W.BC(W.NEUMANN, 0, 1), W.BC(), W.BC(W.ROBIN, 1.0, 0.5)))
+        return W.Problem("box_cross", dom, 1.0, 0.5, 2.0, u, W.apply_L(u, 1.0, 0.5, 2.0))
+    raise KeyError(name)
+
+
+def _pair(name, n, mc, **opt):
+    P = _problem(name)
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n, default_options(min_coarse_n=mc, **opt))
+    O = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=mc)
+    assert H.info.n_levels == O.nl
+    return P, H, O
+
+
+def _t(x):
+    return torch.tensor(np.ascontiguousarray(x).ravel(), dtype=torch.float64, device=DEV)
+
+
+def _np(t, n):
+    return t.cpu().numpy().reshape(n, n)
+
+
+def _gpu_rhs(H, P):
+    f, g, ue = I.problem_inputs(H, P)
+    b = torch.zeros(H.info.n * H.info.n, dtype=torch.float64, device=DEV)
+    H.assemble_rhs(_t(f), _t(g), b)
+    return f, g, ue, b
+
+
+def _oracle_rhs(O, P):
+    d = O.levels[0]
+    return D.rhs(d, D.cell_averages(d.lev, P.f), D.boundary_data(d, P.u))
+
+
+CASES = [("poisson", 64, 4), ("table3", 48, 6), ("box_cross", 40, 5), ("disk", 32, 16),
+         ("disk", 64, 16), ("ellipses0", 64, 16)]
+
+
+@pytest.mark.parametrize("name,n,mc", CASES)
+def test_rhs_parity(name, n, mc):
+    P, H, O = _pair(name, n, mc)
+    _, _, _, b = _gpu_rhs(H, P)
+    bo = _oracle_rhs(O, P)
+    got = _np(b, n)
+    assert np.abs(got - bo).max() <= 1e-12 * np.abs(bo).max()
+
+
+@pytest.mark.parametrize("name,n,mc", CASES)
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_cycle_parity_fp64(name, n, mc, gamma):
+    """FP64 iterates of Alg. 2 (V) and its W form match the oracle to 1e-11
+    relative max-norm after every cycle."""
+    cyc = 1 if gamma == 1 else 2
+    P, H, O = _pair(name, n, mc, cycle=cyc)
+    _, _, _, b = _gpu_rhs(H, P)
+    bo = _oracle_rhs(O, P)
+    u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    uo = np.zeros((n, n))
+    for k in range(5):
+        H.cycle(u, b)
+        uo = M.cycle(O, 0, uo, bo, 3, 3, gamma)
+        err = np.abs(_np(u, n) - uo).max() / np.abs(uo).max()
+        assert err < 1e-11, (k, err)
+
+
+def _random_state(O, l, seed):
+    d = O.levels[l]
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((d.n, d.n)) * d.lev.present
+    b = rng.standard_normal((d.n, d.n)) * d.lev.present
+    return u, b
+
+
+@pytest.mark.parametrize("name,n,mc", [("table3", 48, 6), ("box_cross", 40, 5), ("disk", 64, 16),
+                                       ("ellipses0", 64, 16)])
+def test_step_parity(name, n, mc):
+    """Each step on its own, every level but the coarsest, random inputs:
+    residual (Eq. 4.23), one block-smoother sweep (Def. 5.6), restriction
+    (Eq. 5.10) and interpolation (Eq. 5.11)."""
+    P, H, O = _pair(name, n, mc)
+    for l in range(O.nl - 1):
+        d = O.levels[l]
+        nl = d.n
+        u, b = _random_state(O, l, 10 + l)
+        scale = np.abs(u).max() / d.h ** 2
+        r = torch.zeros(nl * nl, dtype=torch.float64, device=DEV)
+        H.residual(l, _t(u), _t(b), r)
+        ro = M.residual(d, u, b)
+        assert np.abs(_np(r, nl) - ro).max() < 1e-12 * scale
+        ut = _t(u)
+        H.smooth(l, ut, _t(b))
+        uo = M.smooth(O, l, u, b)
+        assert np.abs(_np(ut, nl) - uo).max() < 1e-12 * np.abs(uo).max() * 10
+        rc = torch.zeros((nl // 2) ** 2, dtype=torch.float64, device=DEV)
+        H.restrict_residual(l, _t(u), _t(b), rc)
+        rco = M.restrict(O, l, M.residual(d, u, b))
+        assert np.abs(_np(rc, nl // 2) - rco).max() < 1e-12 * scale
+        ec = np.random.default_rng(5).standard_normal((nl // 2, nl // 2)) * O.levels[l + 1].lev.present
+        ut = _t(u)
+        H.prolong_add(l, _t(ec), ut)
+        np.testing.assert_array_equal(_np(ut, nl), u + M.interpolate(O, l, ec))
+
+
+def test_block_residual_zero_after_sweep():
+    """Sec. 5.2: the block smoother leaves a zero residual on the exactly
+    solved cells (the PLG cells) after every sweep."""
+    P, H, O = _pair("ellipses0", 64, 16)
+    u, b = _random_state(O, 0, 3)
+    ut, bt = _t(u), _t(b)
+    H.smooth(0, ut, bt)
+    r = torch.zeros(64 * 64, dtype=torch.float64, device=DEV)
+    H.residual(0, ut, bt, r)
+    rn = _np(r, 64).ravel()
+    blk = O.lus[0].order
+    assert np.abs(rn[blk]).max() < 1e-11 * np.abs(rn).max()
+
+
+@pytest.mark.parametrize("name,n,mc,cyc", [("poisson", 64, 4, 1), ("disk", 64, 16, 2),
+                                           ("ellipses0", 128, 16, 2)])
+def test_solve_fp64_and_mixed(name, n, mc, cyc):
+    """cc_solve in FP64 and in the mixed mode (FP32 cycles in FP64
+    refinement) reach 1e-10 relative residual; the mixed solution's error
+    against the exact cell averages is within 1.1x of the oracle's."""
+    P, H, O = _pair(name, n, mc, cycle=cyc)
+    f, g, ue, b = _gpu_rhs(H, P)
+    bo = _oracle_rhs(O, P)
+    ro = M.solve(O, bo, tol=1e-10, gamma=cyc)
+    d = O.levels[0]
+    err_o = np.abs(ro.u - D.cell_averages(d.lev, P.u))[d.lev.present].max()
+    u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    r = H.solve(_t(f), _t(g), u, 1e-10)
+    assert r.status == 0 and r.rel_res < 1e-10
+    assert abs(r.cycles - len(ro.history)) <= 1
+    present = d.lev.present
+    err64 = np.abs(_np(u, n) - ue)[present].max()
+    assert err64 <= 1.1 * err_o + 1e-14
+    Hm = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                               default_options(min_coarse_n=mc, cycle=cyc, precision=1))
+    um = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    rm = Hm.solve(_t(f), _t(g), um, 1e-10)
+    assert rm.status == 0 and rm.rel_res < 1e-10
+    errm = np.abs(_np(um, n) - ue)[present].max()
+    assert errm <= 1.1 * err_o + 1e-14, (errm, err_o)
+
+
+def test_solve_host_and_submit_match_device_solve():
+    P, H, O = _pair("disk", 64, 16, cycle=2, precision=1)
+    f, g, ue, _ = _gpu_rhs(H, P)
+    n = 64
+    u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    r = H.solve(_t(f), _t(g), u, 1e-10)
+    uh = np.zeros(n * n)
+    rh = H.solve_host(np.ascontiguousarray(f.ravel()), np.ascontiguousarray(g), uh, 1e-10)
+    assert rh.status == 0 and rh.cycles == r.cycles
+    np.testing.assert_array_equal(uh, u.cpu().numpy())
+    us = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    ft, gt = _t(f), _t(g)
+    torch.cuda.synchronize()
+    rid = H.submit(ft, gt, us, 1e-10)
+    import time
+    t0 = time.time()
+    while True:
+        st, res = H.poll(rid)
+        if st != 9:
+            break
+        assert time.time() - t0 < 60
+        time.sleep(0.001)
+    assert st == 0 and res.t_done >= res.t_start >= res.t_submit
+    np.testing.assert_array_equal(us.cpu().numpy(), u.cpu().numpy())

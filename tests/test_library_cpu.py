@@ -1,0 +1,111 @@
+"""Library checks that need no GPU: the shared library loads and exports every
+entry point of include/ccmg.h, and its host-side setup (geometry, Alg. 1,
+Def. 4.1, PLG fits) agrees with the oracle's tables."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from oracle import discretize as D
+from oracle import geometry as G
+from paper_2601_02975_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    from paper_2601_02975_gb300 import _lib
+    return _lib
+
+
+def test_exports_every_declared_symbol(lib):
+    text = open(os.path.join(ROOT, "include", "ccmg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(cc_[a-z_0-9]+)\s*\(", text))
+    assert len(names) >= 20
+    L = lib.lib()
+    for name in sorted(names):
+        assert hasattr(L, name), name
+    assert names == set(lib._SIGS), names ^ set(lib._SIGS)
+
+
+def _host(P, n, **kw):
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    return Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n, default_options(host_only=1, **kw))
+
+
+@pytest.mark.parametrize("name,n", [("disk", 32), ("disk", 64), ("ellipses0", 64),
+                                    ("ellipses3", 96), ("box_cross", 24)])
+def test_setup_tables_match_oracle(lib, name, n):
+    if name == "disk":
+        P = W.problem_disk()
+    elif name.startswith("ellipses"):
+        P = W.problem_ellipses(int(name[-1]))
+    else:
+        P = W.Problem("box_cross", W.Domain(box_bc=(W.BC(), W.BC(W.NEUMANN, 0, 1), W.BC(),
+                                                     W.BC(W.ROBIN, 1.0, 0.5))),
+                      1.0, 0.5, 2.0, W.u_expcos(), W.apply_L(W.u_expcos(), 1.0, 0.5, 2.0))
+    H = _host(P, n, min_coarse_n=n)
+    lev = G.build_level(P.dom, n, 0.1)
+    d = D.discretize(lev, P.a, P.b, P.c)
+    typ, kind, vol = H.cell_types()
+    np.testing.assert_array_equal(kind, d.kind)
+    np.testing.assert_array_equal(typ, lev.ctype)
+    assert np.abs(vol - lev.vol).max() < 1e-15
+    _, lat, beta = H.level_tables(0)
+    plg = sorted(d.lattices)
+    assert len(plg) == len(lat)
+    for r, k in enumerate(plg):
+        np.testing.assert_array_equal(lat[r], d.lattices[k])
+        want = np.array(list(d.betas[k]))
+        scale = np.abs(want).max()
+        assert np.abs(beta[r, :15] - want).max() < 1e-11 * scale
+        if k in d.bd_cells:
+            bb = d.Nmat[k, 4 * n + d.bd_cells.index(k)]
+            assert abs(beta[r, 15] - bb) < 1e-11 * max(1.0, abs(bb))
+    assert H.info.n_bd == len(d.bd_cells)
+    H.close()
+
+
+def test_quadrature_rules(lib):
+    """The exported rules integrate polynomials like the oracle's geometry."""
+    P = W.problem_ellipses(0)
+    n = 64
+    H = _host(P, n, min_coarse_n=n)
+    q = H.quadrature_nodes()
+    lev = G.build_level(P.dom, n, 0.1)
+    w = np.add.reduceat(q["vnode"][:, 2], q["vptr"][:-1])
+    np.testing.assert_allclose(w, 1.0, atol=1e-12)
+    poly = lambda x, y: (x - 0.3) ** 4 - 2 * (x - 0.5) * (y - 0.4) ** 3 + y
+    want = D.cell_averages(lev, poly)
+    vn = q["vnode"]
+    got = np.add.reduceat(poly(vn[:, 0], vn[:, 1]) * vn[:, 2], q["vptr"][:-1])
+    assert np.abs(got - want.ravel()[q["cell"]]).max() < 1e-12
+    bw = np.add.reduceat(q["bnode"][:, 4], q["bptr"][:-1])
+    np.testing.assert_allclose(bw, 1.0, atol=1e-12)
+    H.close()
+
+
+@pytest.mark.parametrize("case", ["not_elliptic", "too_small", "hole_outside", "bad_bc_count"])
+def test_setup_rejects_bad_arguments(lib, case):
+    from paper_2601_02975_gb300 import CCError, Hierarchy, default_options
+    P = W.problem_disk()
+    a, b, c, n = P.a, P.b, P.c, 32
+    dom = P.dom
+    bcs = list(dom.box_bc) + list(dom.hole_bc)
+    if case == "not_elliptic":
+        b = 3.0
+    elif case == "too_small":
+        n = 2
+    elif case == "hole_outside":
+        dom = W.Domain(holes=[W.Ellipse(0.95, 0.5, 0.2, 0.2)], hole_bc=[W.BC()])
+        bcs = list(dom.box_bc) + list(dom.hole_bc)
+    else:
+        bcs = bcs[:3]
+    with pytest.raises(CCError) as ei:
+        Hierarchy(dom, a, b, c, bcs, n, default_options(host_only=1))
+    assert ei.value.status in (1, 2)
