@@ -35,6 +35,7 @@ EMPTY, SFV, PLG = 0, 1, 2
 GRAD = {-2: 1.0, -1: -8.0, 0: 0.0, 1: 8.0, 2: -1.0}          # x 1/(12 h)
 LAP = {-2: -1.0, -1: 16.0, 0: -30.0, 1: 16.0, 2: -1.0}      # x 1/(12 h^2)
 PLG_RADIUS = 4
+PLG_RADIUS_MAX = 6    # larger boxes are searched only when the 9 x 9 box has no lattice
 EXT = extrapolation_coefficients()
 
 
@@ -211,16 +212,16 @@ def _boundary_column(lev: G.Level, ki: int) -> np.ndarray:
 
 
 ROW_COUNTS = (5, 4, 3, 2, 1)
+CUT_PENALTY = 2      # cost of a cut cell (other than the cell itself) in a lattice
 
 
-def _best_rows(avail: Dict[int, List[int]], radius: int):
+def _best_rows(avail: Dict[int, List[int]], cost: Dict[Tuple[int, int], int], radius: int):
     """Choose 5 distinct lines v and assign them the counts 5,4,3,2,1 so that
-    the chosen cells (the c nearest of each line) minimise the sum of squared
-    offsets.  Ties: lexicographically larger count vector (c_-R, ..., c_R).
+    the chosen cells (the c cheapest of each line) minimise the total cost.
+    Ties: lexicographically larger count vector (c_-R, ..., c_R).
     Returns (cost, key, {v: c}) or None."""
     vs = list(range(-radius, radius + 1))
     full = (1 << len(ROW_COUNTS)) - 1
-    INF = (float("inf"), ())
     nxt = {full: (0, (), {})}
     for v in reversed(vs):
         cur = {}
@@ -237,7 +238,7 @@ def _best_rows(avail: Dict[int, List[int]], radius: int):
                 if m2 not in nxt:
                     continue
                 c1, k1, a1 = nxt[m2]
-                rc = sum(u * u + v * v for u in us[:cnt])
+                rc = sum(cost[(u, v)] for u in us[:cnt])
                 a = dict(a1)
                 a[v] = cnt
                 opts.append((c1 + rc, (-cnt,) + k1, a))
@@ -252,28 +253,44 @@ def choose_lattice(lev: G.Level, ki: int) -> List[int]:
 
     The lattice is made of 5 distinct grid lines (rows, or else columns)
     holding 5, 4, 3, 2 and 1 present cells of the 9 x 9 box centred on the
-    cell; such a set is poised in Pi_4 for point values (a line with 5
+    cell (11 x 11, then 13 x 13, where the 9 x 9 box holds none, as in thin
+    wedges at the kinks of a union of holes); such a set is poised in Pi_4 for point values (a line with 5
     distinct points fixes a quartic on it, and the rest recurses on Pi_3),
-    and hence for cell averages, which are an invertible map of Pi_4.  On each
-    line the cells nearest the centre are used (|u| ascending, negative u
-    first); among all such lattices the one with the least sum of squared
-    offsets is taken, rows before columns on a tie.
+    and hence for cell averages, which are an invertible map of Pi_4.  A
+    cell at offset (u, v) costs u^2 + v^2, plus CUT_PENALTY if it is a cut
+    cell other than the cell itself (a cut cell's centroid is off its grid
+    point; without the penalty a few lattices ended in a far sliver and gave
+    rows with a positive diagonal).  On each line the cheapest cells are
+    used (negative u first on a tie); among all such lattices the one of
+    least total cost is taken, rows before columns on a tie.
     """
+    for radius in range(PLG_RADIUS, PLG_RADIUS_MAX + 1):
+        lat = _lattice_in_box(lev, ki, radius)
+        if lat is not None:
+            return lat
+    n = lev.n
+    raise FitError(f"no poised lattice for cell {divmod(ki, n)[::-1]}")
+
+
+def _lattice_in_box(lev: G.Level, ki: int, radius: int):
     n = lev.n
     j0, i0 = divmod(ki, n)
     best = None
     for orient in (0, 1):             # 0: lines of constant dj; 1: of constant di
         avail: Dict[int, List[int]] = {}
-        for v in range(-PLG_RADIUS, PLG_RADIUS + 1):
+        cost: Dict[Tuple[int, int], int] = {}
+        for v in range(-radius, radius + 1):
             us = []
-            for u in range(-PLG_RADIUS, PLG_RADIUS + 1):
+            for u in range(-radius, radius + 1):
                 di, dj = (u, v) if orient == 0 else (v, u)
                 i, j = i0 + di, j0 + dj
                 if 0 <= i < n and 0 <= j < n and lev.present[j, i]:
                     us.append(u)
-            us.sort(key=lambda u: (u * u, u))
+                    cut = lev.ctype[j, i] != G.REGULAR and (di, dj) != (0, 0)
+                    cost[(u, v)] = u * u + v * v + (CUT_PENALTY if cut else 0)
+            us.sort(key=lambda u: (cost[(u, v)], u))
             avail[v] = us
-        r = _best_rows(avail, PLG_RADIUS)
+        r = _best_rows(avail, cost, radius)
         if r is None:
             continue
         cand = (r[0], orient, r[1])
@@ -284,9 +301,7 @@ def choose_lattice(lev: G.Level, ki: int) -> List[int]:
                     di, dj = (u, v) if orient == 0 else (v, u)
                     cells.append((j0 + dj) * n + (i0 + di))
             best = (cand, sorted(cells))
-    if best is None:
-        raise FitError(f"no poised lattice for cell {divmod(ki, n)[::-1]}")
-    return best[1]
+    return None if best is None else best[1]
 
 
 def fit_beta(lev: G.Level, ki: int, lattice: List[int], a, b, c, with_boundary: bool):

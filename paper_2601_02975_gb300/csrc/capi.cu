@@ -370,7 +370,8 @@ struct BlockDevSet {
 struct Level {
   int n = 0;
   int64_t nn = 0;
-  StencilParams sp;
+  StencilParams sp;          // FP64 stencil data
+  StencilP<float> spf;       // the same in FP32
   uint8_t* cls = nullptr;
   double* u64[2] = {nullptr, nullptr};
   double* b64 = nullptr;
@@ -536,6 +537,10 @@ template <class T> const BlockDev& bdev(Level& L);
 template <> const BlockDev& bdev<double>(Level& L) { return L.blk.d64; }
 template <> const BlockDev& bdev<float>(Level& L) { return L.blk.d32; }
 
+template <class T> const StencilP<T>& sparams(Level& L);
+template <> const StencilP<double>& sparams<double>(Level& L) { return L.sp; }
+template <> const StencilP<float>& sparams<float>(Level& L) { return L.spf; }
+
 template <class T>
 void block_solve(Level& L, T* u, const T* b, cudaStream_t s) {
   const BlockDev& B = bdev<T>(L);
@@ -565,9 +570,9 @@ void sweep(cc_hierarchy* H, int l, int& cur, bool zero, const T* ec, cudaStream_
     CK(cudaEventRecord(H->ev[H->ev_used].first, s));
   }
   if (L.sp.cross)
-    LAUNCH k_sweep<T, true><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, L.sp, zero);
+    LAUNCH k_sweep<T, true><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, sparams<T>(L), zero);
   else
-    LAUNCH k_sweep<T, false><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, L.sp, zero);
+    LAUNCH k_sweep<T, false><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, sparams<T>(L), zero);
   if (timed) {
     CK(cudaEventRecord(H->ev[H->ev_used].second, s));
     ++H->ev_used;
@@ -607,10 +612,10 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
   Level& C = *H->lv[l + 1];
   if (L.sp.cross)
     LAUNCH k_resid_restrict<T, true><<<tiles(L.n), TX * TY, 0, s>>>(ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
-                                                              C.cls, bbuf<T>(C), L.sp);
+                                                              C.cls, bbuf<T>(C), sparams<T>(L));
   else
     LAUNCH k_resid_restrict<T, false><<<tiles(L.n), TX * TY, 0, s>>>(ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
-                                                               C.cls, bbuf<T>(C), L.sp);
+                                                               C.cls, bbuf<T>(C), sparams<T>(L));
   for (int g = 0; g < gamma; ++g) cycle_level<T>(H, l + 1, cur, g == 0, s);
   T* ec = ubuf<T>(C, cur[l + 1]);
   if (C.nfix) LAUNCH k_owner_fix<T><<<nblk(C.nfix), 256, 0, s>>>(C.nfix, C.fix_dst, C.fix_src, ec);
@@ -900,6 +905,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       const LevelDisc& D = L.disc;
       L.disc.P = &H->P;
       L.sp = make_stencil(D, o.omega);
+      L.spf = stencil_as<float>(L.sp);
       L.plan = plan_block(D);
       if (!dev) continue;
       std::vector<uint8_t> cls(L.nn, C_EMPTY);

@@ -23,10 +23,13 @@
 //
 // PLG lattice.  The paper cites its poised-lattice search without stating it.
 // The lattice here is made of five grid lines (rows, or else columns) holding
-// 5, 4, 3, 2 and 1 present cells of the 9 x 9 box around the cell, the cells
-// nearest the centre on each line, choosing the lines and counts that
-// minimise the sum of squared offsets (ties: larger counts on lower lines
-// first, rows before columns).  A set of points on five parallel lines with
+// 5, 4, 3, 2 and 1 present cells of the 9 x 9 box around the cell (11 x 11,
+// then 13 x 13, where that box holds none, as in the thin wedges at the kinks
+// of a union of holes).  A cell at
+// offset (u, v) costs u^2 + v^2, plus 2 if it is a cut cell other than the
+// cell itself (its centroid lies off the grid line); each line takes its
+// cheapest cells and the lines and counts minimise the total cost (ties:
+// larger counts on lower lines first, rows before columns).  A set of points on five parallel lines with
 // 5, 4, 3, 2, 1 points each is poised for quartics, and so are the averages
 // of cells at those points.
 #include <algorithm>
@@ -44,7 +47,9 @@ namespace {
 const double kLap[5] = {-1, 16, -30, 16, -1};
 const double kGrad[5] = {1, -8, 0, 8, -1};
 const double kExt[2][5] = {{5, -10, 10, -5, 1}, {15, -40, 45, -24, 5}};
-const int kRadius = 4;
+const int kRadius = 6;       // largest search box (13 x 13)
+const int kRadiusFirst = 4;  // first search box (9 x 9)
+const int kCutPenalty = 2;
 
 void ghost_coefs(const Bc& bc, double h, double out[2][5]) {
   double a1 = 1.0, a2 = 0.0;
@@ -276,17 +281,27 @@ LevelDisc discretize(const Problem& P, int n) {
     // lattice: dynamic programme over lines
     struct Cand { int cost; int orient; std::vector<int> key; std::vector<int> cells; bool ok = false; };
     Cand best;
+    for (int R = kRadiusFirst; R <= kRadius && !best.ok; ++R)
     for (int orient = 0; orient < 2; ++orient) {
       std::vector<std::vector<int>> avail(2 * kRadius + 1);
-      for (int v = -kRadius; v <= kRadius; ++v) {
+      // cost of the cell at offset (u, v): u^2 + v^2, plus kCutPenalty for a
+      // cut cell other than the cell itself (its centroid is off the line)
+      int cost[2 * kRadius + 1][2 * kRadius + 1];
+      for (int v = -R; v <= R; ++v) {
         auto& us = avail[v + kRadius];
-        for (int u = -kRadius; u <= kRadius; ++u) {
+        for (int u = -R; u <= R; ++u) {
           int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
           int ii = i0 + di, jj = j0 + dj;
-          if (ii >= 0 && jj >= 0 && ii < n && jj < n && G.type[jj * n + ii] != CT_EMPTY) us.push_back(u);
+          if (ii >= 0 && jj >= 0 && ii < n && jj < n && G.type[jj * n + ii] != CT_EMPTY) {
+            us.push_back(u);
+            bool cut = G.type[jj * n + ii] == CT_CUT && (di != 0 || dj != 0);
+            cost[v + kRadius][u + kRadius] = u * u + v * v + (cut ? kCutPenalty : 0);
+          }
         }
-        std::sort(us.begin(), us.end(), [](int x, int y) {
-          return x * x != y * y ? x * x < y * y : x < y;
+        const int* cv = cost[v + kRadius];
+        std::sort(us.begin(), us.end(), [&](int x, int y) {
+          int cx = cv[x + kRadius], cy = cv[y + kRadius];
+          return cx != cy ? cx < cy : x < y;
         });
       }
       const int counts[5] = {5, 4, 3, 2, 1};
@@ -294,7 +309,7 @@ LevelDisc discretize(const Problem& P, int n) {
       std::vector<St> nxt(32), cur(32);
       nxt[31].have = true;
       nxt[31].asg.assign(2 * kRadius + 1, 0);
-      for (int v = kRadius; v >= -kRadius; --v) {
+      for (int v = R; v >= -R; --v) {
         const auto& us = avail[v + kRadius];
         for (int mask = 0; mask < 32; ++mask) {
           St bestS;
@@ -317,7 +332,7 @@ LevelDisc discretize(const Problem& P, int n) {
             int m2 = mask | (1 << bit);
             if (!nxt[m2].have) continue;
             int rc = 0;
-            for (int q = 0; q < cnt; ++q) rc += us[q] * us[q] + v * v;
+            for (int q = 0; q < cnt; ++q) rc += cost[v + kRadius][us[q] + kRadius];
             std::vector<int> key{-cnt};
             key.insert(key.end(), nxt[m2].key.begin(), nxt[m2].key.end());
             std::vector<int> asg = nxt[m2].asg;
@@ -334,7 +349,7 @@ LevelDisc discretize(const Problem& P, int n) {
         best.cost = nxt[0].cost;
         best.orient = orient;
         best.cells.clear();
-        for (int v = -kRadius; v <= kRadius; ++v) {
+        for (int v = -R; v <= R; ++v) {
           int cnt = nxt[0].asg[v + kRadius];
           for (int q = 0; q < cnt; ++q) {
             int u = avail[v + kRadius][q];

@@ -19,14 +19,30 @@ constexpr int SY = TY + 2 * HALO;
 enum : uint8_t { C_EMPTY = 0, C_STENCIL = 1, C_BLOCK = 2 };
 
 // Constant per-level stencil data: weights of the 5 x 5 SFV stencil (Eq.
-// 4.7a,b) and the homogeneous ghost coefficients of each wall.
-struct StencilParams {
+// 4.7a,b) and the homogeneous ghost coefficients of each wall, in the
+// arithmetic type of the kernel (FP32 kernels must not touch the FP64 pipe).
+template <class T>
+struct StencilP {
   int n;
   int cross;               // b != 0
-  double w[25];            // (dj + 2) * 5 + (di + 2)
-  double gh[4][2][4];      // wall (S, E, N, W), depth - 1, inward cell q
-  double omega_over_diag;  // omega / D (D the centre weight)
+  T w[25];                 // (dj + 2) * 5 + (di + 2)
+  T gh[4][2][4];           // wall (S, E, N, W), depth - 1, inward cell q
+  T omega_over_diag;       // omega / D (D the centre weight)
 };
+using StencilParams = StencilP<double>;
+
+template <class T>
+StencilP<T> stencil_as(const StencilParams& d) {
+  StencilP<T> o;
+  o.n = d.n;
+  o.cross = d.cross;
+  for (int k = 0; k < 25; ++k) o.w[k] = (T)d.w[k];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int c = 0; c < 4; ++c) o.gh[a][b][c] = (T)d.gh[a][b][c];
+  o.omega_over_diag = (T)d.omega_over_diag;
+  return o;
+}
 
 // ---- tile loader: u (+ prolonged e) with ghosts beyond the box walls --------
 template <class T>
@@ -39,7 +55,7 @@ __device__ __forceinline__ T cell_value(const T* __restrict__ u, const T* __rest
 
 template <class T>
 __device__ __forceinline__ void load_tile(T (*s)[SX], const T* __restrict__ u,
-                                          const T* __restrict__ ec, const StencilParams& P,
+                                          const T* __restrict__ ec, const StencilP<T>& P,
                                           int x0, int y0, bool zero) {
   const int n = P.n;
   for (int idx = threadIdx.x; idx < SX * SY; idx += blockDim.x) {
@@ -56,7 +72,7 @@ __device__ __forceinline__ void load_tile(T (*s)[SX], const T* __restrict__ u,
       else if (gx < 0) { w = 3; t = gy; m = -gx - 1; }
       else if (gy >= n) { w = 2; t = gx; m = gy - n; }
       else { w = 0; t = gx; m = -gy - 1; }
-      double acc = 0.0;
+      T acc = T(0);
       if (n >= 4) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -67,23 +83,23 @@ __device__ __forceinline__ void load_tile(T (*s)[SX], const T* __restrict__ u,
             case 2: cx = t; cy = n - 1 - q; break;
             default: cx = q; cy = t; break;
           }
-          acc += P.gh[w][m][q] * (double)cell_value(u, ec, n, cx, cy, zero);
+          acc += P.gh[w][m][q] * cell_value(u, ec, n, cx, cy, zero);
         }
       }
-      v = (T)acc;
+      v = acc;
     }
     s[ly][lx] = v;
   }
 }
 
 template <class T, bool CROSS>
-__device__ __forceinline__ T apply_A(const T (*s)[SX], const double* w, int lx, int ly) {
+__device__ __forceinline__ T apply_A(const T (*s)[SX], const T* w, int lx, int ly) {
   // lx, ly: tile-interior coordinates (0-based)
   const int cx = lx + HALO, cy = ly + HALO;
-  T acc = (T)w[2 * 5 + 0] * s[cy][cx - 2] + (T)w[2 * 5 + 1] * s[cy][cx - 1] +
-        (T)w[2 * 5 + 2] * s[cy][cx] + (T)w[2 * 5 + 3] * s[cy][cx + 1] + (T)w[2 * 5 + 4] * s[cy][cx + 2];
-  acc += (T)w[0 * 5 + 2] * s[cy - 2][cx] + (T)w[1 * 5 + 2] * s[cy - 1][cx] +
-         (T)w[3 * 5 + 2] * s[cy + 1][cx] + (T)w[4 * 5 + 2] * s[cy + 2][cx];
+  T acc = w[2 * 5 + 0] * s[cy][cx - 2] + w[2 * 5 + 1] * s[cy][cx - 1] +
+        w[2 * 5 + 2] * s[cy][cx] + w[2 * 5 + 3] * s[cy][cx + 1] + w[2 * 5 + 4] * s[cy][cx + 2];
+  acc += w[0 * 5 + 2] * s[cy - 2][cx] + w[1 * 5 + 2] * s[cy - 1][cx] +
+         w[3 * 5 + 2] * s[cy + 1][cx] + w[4 * 5 + 2] * s[cy + 2][cx];
   if (CROSS) {
 #pragma unroll
     for (int dj = -2; dj <= 2; ++dj) {
@@ -91,7 +107,7 @@ __device__ __forceinline__ T apply_A(const T (*s)[SX], const double* w, int lx, 
 #pragma unroll
       for (int di = -2; di <= 2; ++di) {
         if (di == 0) continue;
-        acc += (T)w[(dj + 2) * 5 + (di + 2)] * s[cy + dj][cx + di];
+        acc += w[(dj + 2) * 5 + (di + 2)] * s[cy + dj][cx + di];
       }
     }
   }
@@ -107,7 +123,7 @@ __device__ __forceinline__ T apply_A(const T (*s)[SX], const double* w, int lx, 
 template <class T, bool CROSS>
 __global__ void __launch_bounds__(TX * TY)
 k_sweep(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ b,
-        const uint8_t* __restrict__ cls, const T* __restrict__ ec, StencilParams P, int zero) {
+        const uint8_t* __restrict__ cls, const T* __restrict__ ec, StencilP<T> P, int zero) {
   __shared__ T s[SY][SX];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   load_tile<T>(s, u_in, ec, P, x0, y0, zero != 0);
@@ -119,7 +135,7 @@ k_sweep(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__
   if (cls[k] != C_STENCIL) return;
   T Au = apply_A<T, CROSS>(s, P.w, lx, ly);
   T uc = s[ly + HALO][lx + HALO];
-  u_out[k] = uc + (T)P.omega_over_diag * (b[k] - Au);
+  u_out[k] = uc + P.omega_over_diag * (b[k] - Au);
 }
 
 // ---- a4: residual and restriction (Eq. 5.10) ---------------------------------
@@ -129,7 +145,7 @@ k_sweep(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__
 template <class T, bool CROSS>
 __global__ void __launch_bounds__(TX * TY)
 k_resid_restrict(const T* __restrict__ u, const T* __restrict__ b, const uint8_t* __restrict__ cls,
-                 const uint8_t* __restrict__ cls_c, T* __restrict__ rc, StencilParams P) {
+                 const uint8_t* __restrict__ cls_c, T* __restrict__ rc, StencilP<T> P) {
   __shared__ T s[SY][SX];
   __shared__ T r[TY][TX];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -167,7 +183,7 @@ __device__ __forceinline__ void atomic_max_abs(unsigned long long* p, double v) 
 template <class Tin, class Tout, bool CROSS>
 __global__ void __launch_bounds__(TX * TY)
 k_resid(const Tin* __restrict__ u, const Tin* __restrict__ b, const uint8_t* __restrict__ cls,
-        Tout* __restrict__ r, StencilParams P, unsigned long long* rmax) {
+        Tout* __restrict__ r, StencilP<Tin> P, unsigned long long* rmax) {
   __shared__ Tin s[SY][SX];
   __shared__ double red[TX * TY / 32];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;

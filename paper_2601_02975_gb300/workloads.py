@@ -307,10 +307,18 @@ def problem_disk() -> Problem:
     return Problem("disk", dom, 1.0, 0.5, 2.0, u, apply_L(u, 1.0, 0.5, 2.0))
 
 
+def _boundary_points(e: Ellipse, m: int = 720):
+    t = np.linspace(0, 2 * math.pi, m, endpoint=False)
+    c, s = math.cos(e.theta), math.sin(e.theta)
+    return (e.cx + c * e.r1 * np.cos(t) - s * e.r2 * np.sin(t),
+            e.cy + s * e.r1 * np.cos(t) + c * e.r2 * np.sin(t))
+
+
 def _ellipse_union(rng) -> List[Ellipse]:
     """3-6 ellipses, centres U[0.3,0.7]^2, semi-axes U[0.06,0.16],
-    rotation U[0,pi); accepted when at least one pair overlaps and every
-    ellipse keeps 0.05 from the box (bounding-circle test)."""
+    rotation U[0,pi); accepted when at least one pair overlaps, every
+    ellipse keeps 0.05 from the box (bounding-circle test), and every pair
+    that does not overlap keeps 0.05 apart (no narrow channels)."""
     while True:
         k = int(rng.integers(3, 7))
         es = []
@@ -324,17 +332,18 @@ def _ellipse_union(rng) -> List[Ellipse]:
         if not ok_box:
             continue
         overl = False
+        narrow = False
+        pts = [_boundary_points(e) for e in es]
         for i in range(k):
             for j in range(i + 1, k):
                 # overlap if some point of ellipse i lies inside ellipse j
-                t = np.linspace(0, 2 * math.pi, 256, endpoint=False)
-                ei = es[i]
-                c, s = math.cos(ei.theta), math.sin(ei.theta)
-                px = ei.cx + c * ei.r1 * np.cos(t) - s * ei.r2 * np.sin(t)
-                py = ei.cy + s * ei.r1 * np.cos(t) + c * ei.r2 * np.sin(t)
-                if np.any(es[j].inside(px, py)):
+                if np.any(es[j].inside(*pts[i])) or np.any(es[i].inside(*pts[j])):
                     overl = True
-        if overl:
+                else:
+                    d = np.hypot(pts[i][0][:, None] - pts[j][0][None, :],
+                                 pts[i][1][:, None] - pts[j][1][None, :]).min()
+                    narrow = narrow or d < 0.05
+        if overl and not narrow:
             return es
 
 

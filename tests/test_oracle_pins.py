@@ -433,7 +433,7 @@ def test_plg_rows_exact_on_quartics():
 def test_disk_fourth_order_convergence():
     P = W.problem_disk()
     errs = []
-    for n in (32, 64, 128):
+    for n in (64, 128, 256):
         lev = G.build_level(P.dom, n, 0.1)
         d = D.discretize(lev, P.a, P.b, P.c)
         b = D.rhs(d, D.cell_averages(lev, P.f), D.boundary_data(d, P.u))
