@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 N_GRID = 1024
 TOL = 1e-10
-MIN_COARSE = 16
+MIN_COARSE = 32
 
 
 def _args():
@@ -44,7 +44,39 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="warm up, then run one solve inside the NVTX range 'solve' and exit "
+                         "(for ncu --nvtx --nvtx-include solve/)")
     return ap.parse_args()
+
+
+def run_profile(a):
+    import torch
+
+    import __graft_entry__
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from paper_2601_02975_gb300 import inputs as I
+    __graft_entry__.build()
+    P = _problem()
+    n = a.n
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                              default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1,
+                                              max_cycles=60))
+    f, g, _ = I.problem_inputs(H, P)
+    ft = torch.tensor(f.ravel(), dtype=torch.float64, device="cuda")
+    gt = torch.tensor(g, dtype=torch.float64, device="cuda")
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    for _ in range(max(1, a.warmup)):
+        u.zero_()
+        H.solve(ft, gt, u, TOL)
+    torch.cuda.synchronize()
+    u.zero_()
+    torch.cuda.nvtx.range_push("solve")
+    r = H.solve(ft, gt, u, TOL)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile": "one solve", "n": n, "status": r.status, "cycles": r.cycles,
+                      "kernels": r.kernels, "rel_res": r.rel_res}))
 
 
 def _peaks():
@@ -347,7 +379,9 @@ def run_reference(a):
 
 def main():
     a = _args()
-    if a.impl == "reference":
+    if a.profile:
+        run_profile(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -120,6 +120,10 @@ void cc_default_options(cc_options* opt);
 /* Human-readable name of a status. */
 const char* cc_status_string(cc_status s);
 
+/* Text of the last CUDA error that made a call from this host thread return
+ * CC_ERR_CUDA or CC_ERR_NO_MEMORY ("" if none); valid until the next call. */
+const char* cc_last_error_string(void);
+
 /*
  * cc_setup: build the multigrid hierarchy (Sec. 3-5, Eq. 5.9) in FP64 on the
  * host and upload its per-level tables to the current device.

@@ -67,6 +67,7 @@ _P = C.c_void_p
 _SIGS = {
     "cc_default_options": (None, [C.POINTER(cc_options)]),
     "cc_status_string": (C.c_char_p, [C.c_int]),
+    "cc_last_error_string": (C.c_char_p, []),
     "cc_setup": (C.c_int, [C.POINTER(cc_domain), C.c_double, C.c_double, C.c_double,
                            C.POINTER(cc_bc), C.c_int, C.c_int, C.POINTER(cc_options), _P,
                            C.POINTER(_P)]),
@@ -114,6 +115,8 @@ def status_string(s: int) -> str:
 
 def _check(st: int, what: str):
     if st != CC_OK:
+        if st in (CC_ERR_CUDA, CC_ERR_NO_MEMORY):
+            what = what + " [" + lib().cc_last_error_string().decode() + "]"
         raise CCError(st, what)
 
 

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -31,10 +32,19 @@ thread_local int64_t t_launches = 0;
 struct CudaError {
   cudaError_t e;
 };
+// text of the last CUDA error seen by a call from this host thread
+thread_local char t_last_error[256] = "";
+inline void note_error(cudaError_t e, const char* what) {
+  snprintf(t_last_error, sizeof(t_last_error), "%s: %s (%s)", what, cudaGetErrorString(e),
+           cudaGetErrorName(e));
+}
 #define CK(x)                                   \
   do {                                          \
     cudaError_t e_ = (x);                       \
-    if (e_ != cudaSuccess) throw CudaError{e_}; \
+    if (e_ != cudaSuccess) {                    \
+      note_error(e_, #x);                       \
+      throw CudaError{e_};                      \
+    }                                           \
   } while (0)
 
 // ---------------------------------------------------------------------------
@@ -92,6 +102,12 @@ struct BlockPlan {
   std::vector<int64_t> gptr{0};
   std::vector<int> gcol;
   std::vector<double> gval;
+  int gk = 0;                          // ELL width of the gather
+  std::vector<int> ell_col;            // [gk * m] term-major
+  std::vector<double> ell_val;
+  int sk = 0;                          // ELL width of A_S,I
+  std::vector<int> asi_ell_col;        // [sk * ns]
+  std::vector<double> asi_ell_val;
   std::vector<int> cstart, iptr{0}, ipos;
   std::vector<int64_t> aoff;
   std::vector<double> ainv;
@@ -105,7 +121,11 @@ struct BlockPlan {
   std::vector<double> wmat;
   size_t smem_chunk = 0, smem_back = 0;
   double error = 0;   // backward error of the scheme on a fixed vector (FP64, host)
+  bool dense = false; // one chunk holding the whole block (its inverse in ainv)
+  std::vector<int> alias_ptr{0}, alias_cell;
 };
+
+const int kDenseMax = 1024;   // blocks up to this size use one dense inverse
 
 // Apply the chunked scheme to a fixed vector in FP64 exactly as the device
 // does and return |A x - t|_inf / (|A|_inf |x|_inf).
@@ -155,7 +175,47 @@ double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, doub
   return rmax / (amax * xmax);
 }
 
+// padded term-major (ELL) copies of the gather rows and of A_S,I
+void make_ell(BlockPlan& B) {
+  const int m = B.m;
+  B.gk = 0;
+  for (int p = 0; p < m; ++p) B.gk = std::max<int>(B.gk, (int)(B.gptr[p + 1] - B.gptr[p]));
+  B.ell_col.assign((size_t)B.gk * m, 0);
+  B.ell_val.assign((size_t)B.gk * m, 0.0);
+  for (int p = 0; p < m; ++p) {
+    int q = 0;
+    for (int64_t e = B.gptr[p]; e < B.gptr[p + 1]; ++e, ++q) {
+      B.ell_col[(size_t)q * m + p] = B.gcol[e];
+      B.ell_val[(size_t)q * m + p] = B.gval[e];
+    }
+    for (; q < B.gk; ++q) B.ell_col[(size_t)q * m + p] = B.cell[p];   // value 0
+  }
+  const int ns = B.ns;
+  B.sk = 0;
+  for (int i = 0; i < ns; ++i) B.sk = std::max<int>(B.sk, (int)(B.asi_ptr[i + 1] - B.asi_ptr[i]));
+  B.asi_ell_col.assign((size_t)B.sk * ns, 0);
+  B.asi_ell_val.assign((size_t)B.sk * ns, 0.0);
+  for (int i = 0; i < ns; ++i) {
+    int q = 0;
+    for (int64_t e = B.asi_ptr[i]; e < B.asi_ptr[i + 1]; ++e, ++q) {
+      B.asi_ell_col[(size_t)q * ns + i] = B.asi_col[e];
+      B.asi_ell_val[(size_t)q * ns + i] = B.asi_val[e];
+    }
+  }
+}
+
+BlockPlan plan_block_impl(const LevelDisc& D);
+
 BlockPlan plan_block(const LevelDisc& D) {
+  BlockPlan B = plan_block_impl(D);
+  if (B.m) {
+    if (B.dense) B.ainv = to_cm(B.ainv, B.m, B.m);   // column-major -> row-major (square)
+    make_ell(B);
+  }
+  return B;
+}
+
+BlockPlan plan_block_impl(const LevelDisc& D) {
   BlockPlan B;
   const int m = (int)D.block.size();
   B.m = m;
@@ -284,6 +344,15 @@ BlockPlan plan_block(const LevelDisc& D) {
     B.sinv = to_cm(Sm, ns, ns);
     return true;
   };
+  // small blocks: one chunk, dense inverse of the whole block
+  if (m <= kDenseMax) {
+    double st;
+    build(m, true, st);
+    B.error = block_plan_error(B, Abb);
+    B.dense = true;
+    B.smem_chunk = (size_t)((m + 31) & ~31);
+    return B;
+  }
   // candidate chunk sizes by dense storage; keep the cheapest whose
   // backward error on a fixed vector is at the level of rounding
   std::vector<std::pair<double, int>> cands;
@@ -433,8 +502,9 @@ struct cc_hierarchy {
   bool stop = false;
   cudaStream_t wstream = nullptr;
   // cuda graphs of one solve iteration
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  int64_t gexec_launches[2] = {0, 0};   // kernels in one replay of each graph
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};   // [timing][mixed]
+  int64_t gexec_launches[4] = {0, 0, 0, 0};   // kernels in one replay of each graph
+  size_t gexec_events[4] = {0, 0, 0, 0};      // timing event pairs in each graph
   cudaStream_t gstream = nullptr;
 };
 
@@ -499,18 +569,18 @@ BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
   d.ns = B.ns;
   if (B.m == 0) return d;
   d.cell = pool.upload(B.cell, s);
-  d.gptr = pool.upload(B.gptr, s);
-  d.gcol = pool.upload(B.gcol, s);
-  d.gval = pool.upload(cast_vec<T>(B.gval), s);
+  d.gk = B.gk;
+  d.gcol = pool.upload(B.ell_col, s);
+  d.gval = pool.upload(cast_vec<T>(B.ell_val), s);
   d.cstart = pool.upload(B.cstart, s);
   d.iptr = pool.upload(B.iptr, s);
   d.ipos = pool.upload(B.ipos, s);
   d.aoff = pool.upload(B.aoff, s);
   d.ainv = pool.upload(cast_vec<T>(B.ainv), s);
   d.spos = pool.upload(B.spos, s);
-  d.asi_ptr = pool.upload(B.asi_ptr, s);
-  d.asi_col = pool.upload(B.asi_col, s);
-  d.asi_val = pool.upload(cast_vec<T>(B.asi_val), s);
+  d.sk = B.sk;
+  d.asi_col = pool.upload(B.asi_ell_col, s);
+  d.asi_val = pool.upload(cast_vec<T>(B.asi_ell_val), s);
   d.sinv = pool.upload(cast_vec<T>(B.sinv), s);
   d.wptr = pool.upload(B.wptr, s);
   d.widx = pool.upload(B.widx, s);
@@ -519,6 +589,9 @@ BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
   d.tblk = pool.alloc<T>(B.m);
   d.zblk = pool.alloc<T>(B.m);
   d.xs = pool.alloc<T>(std::max(1, B.ns));
+  d.dense = B.dense ? 1 : 0;
+  d.alias_ptr = pool.upload(B.alias_ptr, s);
+  d.alias_cell = pool.upload(B.alias_cell, s);
   return d;
 }
 
@@ -546,6 +619,11 @@ void block_solve(Level& L, T* u, const T* b, cudaStream_t s) {
   const BlockDev& B = bdev<T>(L);
   if (B.m == 0) return;
   const BlockPlan& P = L.plan;
+  if (P.dense) {
+    LAUNCH k_block_gather<T><<<nblk(P.m), 256, 0, s>>>(B, b, u);
+    LAUNCH k_block_gemv<T><<<(P.m + 7) / 8, 256, P.smem_chunk * sizeof(T), s>>>(B, u);
+    return;
+  }
   LAUNCH k_block_chunk<T><<<P.nch, 256, P.smem_chunk * sizeof(T), s>>>(B, b, u);
   if (P.ns > 0) {
     size_t sm = (size_t)(((P.ns + 31) & ~31) + 256 + 32) * sizeof(T);
@@ -567,14 +645,14 @@ void sweep(cc_hierarchy* H, int l, int& cur, bool zero, const T* ec, cudaStream_
       CK(cudaEventCreate(&b));
       H->ev.push_back({a, b});
     }
-    CK(cudaEventRecord(H->ev[H->ev_used].first, s));
+    CK(cudaEventRecordWithFlags(H->ev[H->ev_used].first, s, cudaEventRecordExternal));
   }
   if (L.sp.cross)
     LAUNCH k_sweep<T, true><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, sparams<T>(L), zero);
   else
     LAUNCH k_sweep<T, false><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, sparams<T>(L), zero);
   if (timed) {
-    CK(cudaEventRecord(H->ev[H->ev_used].second, s));
+    CK(cudaEventRecordWithFlags(H->ev[H->ev_used].second, s, cudaEventRecordExternal));
     ++H->ev_used;
   }
   block_solve<T>(L, out, bbuf<T>(L), s);
@@ -585,8 +663,7 @@ template <class T>
 void bottom(cc_hierarchy* H, int l, int cur, cudaStream_t s) {
   Level& L = *H->lv[l];
   int nc = H->nc_bottom;
-  size_t sm = (size_t)(((nc + 31) & ~31) + 256 + 32) * sizeof(double);
-  LAUNCH k_bottom<T><<<(nc + 31) / 32, 256, sm, s>>>(H->bottom_inv, nc, bbuf<T>(L), ubuf<T>(L, cur));
+  LAUNCH k_bottom<T><<<(nc + 7) / 8, 256, 0, s>>>(H->bottom_inv, nc, bbuf<T>(L), ubuf<T>(L, cur));
 }
 
 // Alg. 2 (gamma = 1) or its W form (gamma = 2) on level l; cur[l] tracks the
@@ -617,8 +694,9 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
     LAUNCH k_resid_restrict<T, false><<<tiles(L.n), TX * TY, 0, s>>>(ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
                                                                C.cls, bbuf<T>(C), sparams<T>(L));
   for (int g = 0; g < gamma; ++g) cycle_level<T>(H, l + 1, cur, g == 0, s);
+  // merged-away coarse cells already hold their owner's value (written by
+  // the block solve, or by the alias rows of the bottom matrix)
   T* ec = ubuf<T>(C, cur[l + 1]);
-  if (C.nfix) LAUNCH k_owner_fix<T><<<nblk(C.nfix), 256, 0, s>>>(C.nfix, C.fix_dst, C.fix_src, ec);
   if (nu2 == 0) {
     LAUNCH k_prolong_add<T><<<nblk(L.nn), 256, 0, s>>>(ubuf<T>(L, cur[l]), ec, L.cls, L.n);
     return;
@@ -702,27 +780,42 @@ cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* 
   first = rel;
   if (rel < tol) res.status = CC_OK;
   int it = 0;
-  const int gi = mixed ? 1 : 0;
-  bool use_graph = H->opt.use_graphs && !H->timing;
+  const int gi = (mixed ? 1 : 0) + (H->timing ? 2 : 0);
+  bool use_graph = H->opt.use_graphs != 0;
   for (; res.status != CC_OK && it < H->opt.max_cycles; ++it) {
     if (use_graph) {
       if (!H->gexec[gi]) {
         cudaGraph_t gr;
         int64_t before = t_launches;
+        H->ev_used = 0;
         CK(cudaStreamBeginCapture(H->gstream, cudaStreamCaptureModeThreadLocal));
         iteration(H, mixed, H->gstream);
         CK(cudaStreamEndCapture(H->gstream, &gr));
         CK(cudaGraphInstantiate(&H->gexec[gi], gr, 0));
         CK(cudaGraphDestroy(gr));
         H->gexec_launches[gi] = t_launches - before;
+        H->gexec_events[gi] = H->ev_used;
         t_launches = before;
       }
       CK(cudaGraphLaunch(H->gexec[gi], s));
       t_launches += H->gexec_launches[gi];
     } else {
+      H->ev_used = 0;
       iteration(H, mixed, s);
     }
     rel = read_norm(H, s) / bn;
+    if (H->timing) {
+      // the timed sweeps of this iteration (their events live in the graph
+      // when graphs are used, so host launch gaps are not measured)
+      size_t ne = use_graph ? H->gexec_events[gi] : H->ev_used;
+      for (size_t i = 0; i < ne; ++i) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, H->ev[i].first, H->ev[i].second));
+        H->timed_ms += ms;
+        ++H->timed_launches;
+      }
+      if (!use_graph) H->ev_used = 0;
+    }
     if (rel < tol) {
       res.status = CC_OK;
       ++it;
@@ -823,6 +916,8 @@ void cc_default_options(cc_options* o) {
   o->host_only = 0;
 }
 
+const char* cc_last_error_string(void) { return t_last_error; }
+
 const char* cc_status_string(cc_status s) {
   switch (s) {
     case CC_OK: return "ok";
@@ -907,6 +1002,24 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       L.sp = make_stencil(D, o.omega);
       L.spf = stencil_as<float>(L.sp);
       L.plan = plan_block(D);
+      {
+        // merged-away control volumes take their owner's value (Eq. 5.11)
+        std::unordered_map<int, int> pos;
+        for (int p = 0; p < L.plan.m; ++p) pos[L.plan.cell[p]] = p;
+        std::vector<std::vector<int>> al(L.plan.m);
+        for (int64_t k = 0; l > 0 && k < L.nn; ++k)
+          if (D.geom.type[k] == CT_EMPTY && D.geom.owner[k] >= 0 && D.geom.owner[k] != k) {
+            auto it = pos.find(D.geom.owner[k]);
+            if (it == pos.end()) throw SetupError(3, "a merged cell is not in the exact block");
+            al[it->second].push_back((int)k);
+          }
+        L.plan.alias_ptr.assign(1, 0);
+        L.plan.alias_cell.clear();
+        for (auto& v : al) {
+          L.plan.alias_cell.insert(L.plan.alias_cell.end(), v.begin(), v.end());
+          L.plan.alias_ptr.push_back((int)L.plan.alias_cell.size());
+        }
+      }
       if (!dev) continue;
       std::vector<uint8_t> cls(L.nn, C_EMPTY);
       for (int64_t k = 0; k < L.nn; ++k)
@@ -955,6 +1068,10 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       for (int k = 0; k < nc; ++k) {
         L.disc.row(k, ar, nullptr);
         for (auto& kv : ar) A[(size_t)k * nc + kv.first] += kv.second;
+        // a merged-away control volume repeats its owner's value (Eq. 5.11)
+        int own = L.disc.geom.owner[k];
+        if (H->lv.size() > 1 && L.disc.kind[k] == K_EMPTY && own >= 0 && own != k)
+          A[(size_t)k * nc + own] = -1.0;
       }
       std::vector<double> A0(A);
       if (!invert(A, nc)) throw SetupError(3, "singular coarsest-level matrix");
@@ -976,7 +1093,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
         }
         H->bottom_error = rmax / (amax * xmax);
       }
-      if (dev) H->bottom_inv = H->pool.upload(to_cm(A, nc, nc), s);
+      if (dev) H->bottom_inv = H->pool.upload(A, s);   // row-major
       H->nc_bottom = nc;
     }
     // finest level: N rows, residual buffers, norms
@@ -1208,7 +1325,7 @@ cc_status cc_smooth(cc_handle H, int l, double* u, const double* b, cc_stream st
     CK(cudaMemcpyAsync(L.b64, b, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
     int cur = 0;
     sweep<double>(H, l, cur, false, (const double*)nullptr, s);
-    CK(cudaMemcpyAsync(u, L.u64[cur], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    LAUNCH k_rhs_copy<<<nblk(L.nn), 256, 0, s>>>(L.u64[cur], L.cls, u, L.nn);
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
@@ -1283,6 +1400,17 @@ cc_status cc_kernel_timing(cc_handle H, int enable) {
   H->ev_used = 0;
   H->timed_launches = 0;
   H->timed_ms = 0;
+  try {
+    // one event pair per finest-level sweep of a cycle, created up front so
+    // that none is created during graph capture
+    int per = H->opt.nu1 + H->opt.nu2;
+    while (H->timing && (int)H->ev.size() < per) {
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b));
+      H->ev.push_back({a, b});
+    }
+  } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
 }
 
@@ -1292,13 +1420,6 @@ cc_status cc_kernel_timing_read(cc_handle H, int64_t* launches, double* total_ms
   if (!H) return CC_ERR_ARG;
   try {
     CK(cudaDeviceSynchronize());
-    for (size_t i = 0; i < H->ev_used; ++i) {
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, H->ev[i].first, H->ev[i].second));
-      H->timed_ms += ms;
-      ++H->timed_launches;
-    }
-    H->ev_used = 0;
   } catch (CudaError&) { return CC_ERR_CUDA; }
   const int64_t nn = H->lv[0]->nn;
   const double w = H->opt.precision == CC_PREC_MIXED ? 4.0 : 8.0;

@@ -246,18 +246,18 @@ __global__ void k_block_resid(int m, const int* __restrict__ cell, const int64_t
 struct BlockDev {
   int m, nch, ns;
   const int* cell;          // [m] grid cell of block position
-  const int64_t* gptr;      // [m+1] gather rows: non-block columns
-  const int* gcol;
-  const void* gval;         // T
+  int gk;                   // gather width: terms per row (padded)
+  const int* gcol;          // [gk * m] term-major: entry q of row p at q * m + p
+  const void* gval;         // T, padded terms have value 0
   const int* cstart;        // [nch+1] block positions of each chunk
   const int* iptr;          // [nch+1] interior list ptr
   const int* ipos;          // interior block positions
   const int64_t* aoff;      // [nch] offset of chunk inverse
   const void* ainv;         // T, column-major per chunk
   const int* spos;          // [ns] block positions of interfaces
-  const int64_t* asi_ptr;   // [ns+1] A_S,I rows
-  const int* asi_col;       // interior block positions
-  const void* asi_val;      // T
+  int sk;                   // A_S,I width (padded)
+  const int* asi_col;       // [sk * ns] term-major, interior block positions
+  const void* asi_val;      // T, padded terms have value 0
   const void* sinv;         // T, ns x ns column-major
   const int* wptr;          // [nch+1] interface columns of W_c
   const int* widx;          // interface indices (into 0..ns-1)
@@ -266,7 +266,32 @@ struct BlockDev {
   void* tblk;               // T scratch [m]: gathered right-hand side
   void* zblk;               // T scratch [m]: interior solutions
   void* xs;                 // T scratch [ns]
+  int dense;                // 1: one chunk, inverse of the whole block in ainv
+  const int* alias_ptr;     // [m+1] merged-away control volumes owned by each block cell
+  const int* alias_cell;    //       (they carry the owner's value for Eq. 5.11)
 };
+
+template <class T>
+__device__ __forceinline__ void block_write(const BlockDev& B, T* u, int p, T v) {
+  u[B.cell[p]] = v;
+  for (int q = B.alias_ptr[p]; q < B.alias_ptr[p + 1]; ++q) u[B.alias_cell[q]] = v;
+}
+
+// t = b - A(block, rest) u for block row p: the padded terms are laid out
+// term-major, so the loads of consecutive rows are coalesced and the loads of
+// one row are independent of one another.
+template <class T>
+__device__ __forceinline__ T block_rhs(const BlockDev& B, const T* __restrict__ b,
+                                       const T* __restrict__ u, int p) {
+  const T* gval = static_cast<const T*>(B.gval);
+  T acc = b[B.cell[p]];
+#pragma unroll 8
+  for (int q = 0; q < B.gk; ++q) {
+    size_t e = (size_t)q * B.m + p;
+    acc -= gval[e] * u[B.gcol[e]];
+  }
+  return acc;
+}
 
 // y[0..rows) = M x, M column-major (rows x cols), x in shared memory; the CTA
 // cooperates: lanes run over rows, warps split the columns.
@@ -301,13 +326,8 @@ __global__ void k_block_chunk(BlockDev B, const T* __restrict__ b, T* __restrict
   const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
   T* partial = tI + ((ni + 31) & ~31);
   T* zI = partial + blockDim.x;
-  const T* gval = static_cast<const T*>(B.gval);
   T* tblk = static_cast<T*>(B.tblk);
-  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    T acc = b[B.cell[p]];
-    for (int64_t q = B.gptr[p]; q < B.gptr[p + 1]; ++q) acc -= gval[q] * u[B.gcol[q]];
-    tblk[p] = acc;
-  }
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) tblk[p] = block_rhs(B, b, u, p);
   __syncthreads();
   for (int q = threadIdx.x; q < ni; q += blockDim.x) tI[q] = tblk[B.ipos[i0 + q]];
   __syncthreads();
@@ -317,7 +337,7 @@ __global__ void k_block_chunk(BlockDev B, const T* __restrict__ b, T* __restrict
   for (int q = threadIdx.x; q < ni; q += blockDim.x) {
     int p = B.ipos[i0 + q];
     zblk[p] = zI[q];
-    if (B.ns == 0) u[B.cell[p]] = zI[q];
+    if (B.ns == 0) block_write(B, u, p, zI[q]);
   }
 }
 
@@ -333,7 +353,11 @@ __global__ void k_block_schur(BlockDev B, T* __restrict__ u) {
   const T* av = static_cast<const T*>(B.asi_val);
   for (int i = threadIdx.x; i < B.ns; i += blockDim.x) {
     T acc = tblk[B.spos[i]];
-    for (int64_t q = B.asi_ptr[i]; q < B.asi_ptr[i + 1]; ++q) acc -= av[q] * zblk[B.asi_col[q]];
+#pragma unroll 8
+    for (int q = 0; q < B.sk; ++q) {
+      size_t e = (size_t)q * B.ns + i;
+      acc -= av[e] * zblk[B.asi_col[e]];
+    }
     tS[i] = acc;
   }
   __syncthreads();
@@ -344,7 +368,7 @@ __global__ void k_block_schur(BlockDev B, T* __restrict__ u) {
   T* xs = static_cast<T*>(B.xs);
   for (int q = threadIdx.x; q < rows; q += blockDim.x) {
     xs[r0 + q] = y[q];
-    u[B.cell[B.spos[r0 + q]]] = y[q];
+    block_write(B, u, B.spos[r0 + q], y[q]);
   }
 }
 
@@ -366,24 +390,52 @@ __global__ void k_block_back(BlockDev B, T* __restrict__ u) {
   const T* zblk = static_cast<const T*>(B.zblk);
   for (int q = threadIdx.x; q < ni; q += blockDim.x) {
     int p = B.ipos[i0 + q];
-    u[B.cell[p]] = zblk[p] - y[q];
+    block_write(B, u, p, zblk[p] - y[q]);
   }
 }
 
-// ---- a7: bottom solve, u = inv(A_c) b (FP64 matrix) --------------------------
+// Dense blocks (a few thousand unknowns at most) are solved with the dense
+// inverse: one kernel gathers t = b - A(block, rest) u for every block row,
+// the next applies inv(A) row-major, one warp per row.
 template <class T>
-__global__ void k_bottom(const double* __restrict__ Ainv_cm, int nc, const T* __restrict__ b,
-                         T* __restrict__ u) {
+__global__ void k_block_gather(BlockDev B, const T* __restrict__ b, const T* __restrict__ u) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < B.m) static_cast<T*>(B.tblk)[p] = block_rhs(B, b, u, p);
+}
+
+template <class T>
+__global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
   extern __shared__ unsigned char smem_raw[];
-  double* x = reinterpret_cast<double*>(smem_raw);
-  double* partial = x + ((nc + 31) & ~31);
-  double* y = partial + blockDim.x;
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) x[i] = (double)b[i];
+  T* t = reinterpret_cast<T*>(smem_raw);
+  const T* tg = static_cast<const T*>(B.tblk);
+  for (int c = threadIdx.x; c < B.m; c += blockDim.x) t[c] = tg[c];
   __syncthreads();
-  const int r0 = blockIdx.x * 32;
-  const int rows = min(32, nc - r0);
-  cta_matvec_cm<double>(Ainv_cm + r0, rows, nc, nc, x, partial, y);
-  for (int q = threadIdx.x; q < rows; q += blockDim.x) u[r0 + q] = (T)y[q];
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= B.m) return;
+  const T* A = static_cast<const T*>(B.ainv) + (size_t)r * B.m;
+  T acc = T(0);
+#pragma unroll 4
+  for (int c = lane; c < B.m; c += 32) acc += A[c] * t[c];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) block_write(B, u, r, acc);
+}
+
+// ---- a7: bottom solve, u = inv(A_c) b (FP64 matrix, row-major) --------------
+// One warp per row; the FP64 products keep the coarsest-level solve exact to
+// rounding whatever the cycle precision.
+template <class T>
+__global__ void k_bottom(const double* __restrict__ Ainv, int nc, const T* __restrict__ b,
+                         T* __restrict__ u) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= nc) return;
+  const double* A = Ainv + (size_t)r * nc;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int c = lane; c < nc; c += 32) acc += A[c] * (double)b[c];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) u[r] = (T)acc;
 }
 
 // ---- a0: b = f - N g -----------------------------------------------------------
