@@ -120,8 +120,10 @@ void cc_default_options(cc_options* opt);
 /* Human-readable name of a status. */
 const char* cc_status_string(cc_status s);
 
-/* Text of the last CUDA error that made a call from this host thread return
- * CC_ERR_CUDA or CC_ERR_NO_MEMORY ("" if none); valid until the next call. */
+/* Text of the last error that made a call from this host thread return
+ * CC_ERR_CUDA or CC_ERR_NO_MEMORY, or of a size limit that made
+ * cc_smooth_noalloc return CC_ERR_ARG ("" if none); valid until the next
+ * call. */
 const char* cc_last_error_string(void);
 
 /*
@@ -230,6 +232,43 @@ cc_status cc_prolong_add(cc_handle h, int level, const double* d_ec, double* d_u
 /* One cycle of Alg. 2 (or its W form, as set up) on the finest level in FP64,
  * u in place. */
 cc_status cc_cycle(cc_handle h, double* d_u, const double* d_b, cc_stream stream);
+
+/*
+ * cc_smooth_noalloc: the same block-smoother sweep as cc_smooth, for callers
+ * that must not allocate device memory when they call it.  Such callers
+ * include code running while a stream is being captured (cudaMalloc is not
+ * allowed there), real-time loops that cannot afford an allocation's
+ * latency or its implicit synchronisation, and hosts whose device memory is
+ * owned by another allocator.  The paper has no counterpart: this only
+ * changes where the sweep keeps its temporaries.
+ *
+ * The call allocates nothing and writes none of the handle's level buffers.
+ * The Jacobi output and the exact block solve's temporaries (gathered
+ * right-hand sides, chunk and interface solutions) live in one file-scope
+ * device array of CC_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB) in the
+ * library.  Every GPU that loads the library's device code holds that array
+ * until the process exits.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current.
+ * Make that first call before any stream capture.
+ *
+ * All calls share the one array, and it keeps the last call's contents.
+ * Each call writes every entry it reads before reading it, so nothing needs
+ * clearing between calls.  Calls that overlap on the GPU (on different
+ * streams or different handles of one device) race on the array, so
+ * serialise them.
+ *
+ *   level   0 .. n_levels - 2 (as for cc_smooth)
+ *   d_u     N_l^2 FP64 values; input, and output of one sweep (empty cells 0)
+ *   d_b     N_l^2 FP64 right-hand side
+ * Errors: CC_ERR_ARG for a bad argument, a device other than the handle's,
+ * or a level that needs more than CC_NOALLOC_SCRATCH_DOUBLES doubles
+ * (N_l^2 plus twice the block size plus the interface count;
+ * cc_last_error_string() gives the numbers).  CC_ERR_CUDA if the
+ * address lookup or a launch fails.
+ */
+#define CC_NOALLOC_SCRATCH_DOUBLES (1 << 20)
+cc_status cc_smooth_noalloc(cc_handle h, int level, double* d_u, const double* d_b,
+                            cc_stream stream);
 
 /*
  * cc_level_tables: copy level l's discretisation to host memory for

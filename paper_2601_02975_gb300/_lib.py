@@ -83,6 +83,7 @@ _SIGS = {
     "cc_assemble_rhs": (C.c_int, [_P, _P, _P, _P, _P]),
     "cc_residual": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     "cc_smooth": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "cc_smooth_noalloc": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "cc_restrict_residual": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     "cc_prolong_add": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "cc_cycle": (C.c_int, [_P, _P, _P, _P]),
@@ -115,8 +116,9 @@ def status_string(s: int) -> str:
 
 def _check(st: int, what: str):
     if st != CC_OK:
-        if st in (CC_ERR_CUDA, CC_ERR_NO_MEMORY):
-            what = what + " [" + lib().cc_last_error_string().decode() + "]"
+        msg = lib().cc_last_error_string().decode()
+        if msg and st in (CC_ERR_ARG, CC_ERR_CUDA, CC_ERR_NO_MEMORY):
+            what = what + " [" + msg + "]"
         raise CCError(st, what)
 
 
@@ -269,6 +271,12 @@ class Hierarchy:
 
     def smooth(self, level, u, b, stream=None):
         _check(lib().cc_smooth(self.h, level, _ptr(u), _ptr(b), _stream(stream)), "cc_smooth")
+
+    def smooth_noalloc(self, level, u, b, stream=None):
+        """cc_smooth_noalloc: the sweep of `smooth` with no device allocation;
+        its temporaries live in one library-wide device array (see ccmg.h)."""
+        _check(lib().cc_smooth_noalloc(self.h, level, _ptr(u), _ptr(b), _stream(stream)),
+               "cc_smooth_noalloc")
 
     def restrict_residual(self, level, u, b, rc, stream=None):
         _check(lib().cc_restrict_residual(self.h, level, _ptr(u), _ptr(b), _ptr(rc),

@@ -1380,6 +1380,82 @@ cc_status cc_cycle(cc_handle H, double* u, const double* b, cc_stream st) {
   return CC_OK;
 }
 
+}  // extern "C"
+
+// ---- allocation-free sweep ---------------------------------------------------
+// Scratch of cc_smooth_noalloc: one file-scope device array per device.  Host
+// code cannot use the symbol's host-side address; the device address is
+// looked up once per device (with that device current) and cached.
+static __device__ __align__(256) double g_noalloc_scratch[CC_NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mu;
+std::unordered_map<int, double*> g_noalloc_ptr;   // device -> address of the array
+
+double* noalloc_scratch(int device) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  auto it = g_noalloc_ptr.find(device);
+  if (it != g_noalloc_ptr.end()) return it->second;
+  void* p = nullptr;
+  CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  g_noalloc_ptr[device] = static_cast<double*>(p);
+  return static_cast<double*>(p);
+}
+}  // namespace
+
+extern "C" {
+
+cc_status cc_smooth_noalloc(cc_handle H, int l, double* u, const double* b, cc_stream st) {
+  t_last_error[0] = '\0';
+  if (!H || H->opt.host_only || l < 0 || l + 1 >= (int)H->lv.size() || !u || !b) return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)st;
+  try {
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != H->device) {
+      snprintf(t_last_error, sizeof(t_last_error),
+               "cc_smooth_noalloc: current device %d is not the handle's device %d", dev, H->device);
+      return CC_ERR_ARG;
+    }
+    Level& L = *H->lv[l];
+    const BlockPlan& P = L.plan;
+    const int64_t need = L.nn + 2 * (int64_t)P.m + P.ns;
+    if (need > CC_NOALLOC_SCRATCH_DOUBLES) {
+      snprintf(t_last_error, sizeof(t_last_error),
+               "cc_smooth_noalloc: level %d needs %lld doubles of scratch, more than the %d "
+               "available", l, (long long)need, CC_NOALLOC_SCRATCH_DOUBLES);
+      return CC_ERR_ARG;
+    }
+    double* scr = noalloc_scratch(dev);
+    double* out = scr;                      // [0, nn): Jacobi output
+    BlockDev B = L.blk.d64;                 // the handle's tables, temporaries in scratch
+    B.tblk = scr + L.nn;                    // [nn, nn + m)
+    B.zblk = scr + L.nn + P.m;              // [nn + m, nn + 2m)
+    B.xs = scr + L.nn + 2 * P.m;            // [nn + 2m, nn + 2m + ns)
+    if (L.sp.cross)
+      LAUNCH k_sweep<double, true><<<tiles(L.n), TX * TY, 0, s>>>(u, out, b, L.cls, nullptr, L.sp, 0);
+    else
+      LAUNCH k_sweep<double, false><<<tiles(L.n), TX * TY, 0, s>>>(u, out, b, L.cls, nullptr, L.sp, 0);
+    if (P.m) {
+      if (P.dense) {
+        LAUNCH k_block_gather<double><<<nblk(P.m), 256, 0, s>>>(B, b, out);
+        LAUNCH k_block_gemv<double><<<(P.m + 7) / 8, 256, P.smem_chunk * sizeof(double), s>>>(B, out);
+      } else {
+        LAUNCH k_block_chunk<double><<<P.nch, 256, P.smem_chunk * sizeof(double), s>>>(B, b, out);
+        if (P.ns > 0) {
+          size_t sm = (size_t)(((P.ns + 31) & ~31) + 256 + 32) * sizeof(double);
+          LAUNCH k_block_schur<double><<<(P.ns + 31) / 32, 256, sm, s>>>(B, out);
+          LAUNCH k_block_back<double><<<P.nch, 256, P.smem_back * sizeof(double), s>>>(B, out);
+        }
+      }
+    }
+    // every non-empty cell of `out` was written above; empty cells go out as 0
+    LAUNCH k_rhs_copy<<<nblk(L.nn), 256, 0, s>>>(out, L.cls, u, L.nn);
+    CK(cudaGetLastError());
+  } catch (CudaError&) { return CC_ERR_CUDA; }
+  return CC_OK;
+}
+
 cc_status cc_level_tables(cc_handle H, int l, uint8_t* h_kind, int* h_lattice, double* h_beta,
                           int* n_plg) {
   if (!H || l < 0 || l >= (int)H->lv.size()) return CC_ERR_ARG;
