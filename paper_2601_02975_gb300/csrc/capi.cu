@@ -8,6 +8,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -27,7 +28,6 @@ namespace {
 
 // kernels launched by the current host thread (read around each solve)
 thread_local int64_t t_launches = 0;
-#define LAUNCH ++t_launches,
 
 struct CudaError {
   cudaError_t e;
@@ -46,6 +46,43 @@ inline void note_error(cudaError_t e, const char* what) {
       throw CudaError{e_};                      \
     }                                           \
   } while (0)
+
+// Launch with the programmatic-stream-serialisation attribute (PDL); the
+// kernels call pdl_enter() first.  CCMG_NO_PDL=1 in the environment turns the
+// attribute off.
+// CCMG_PDL: 0 off, 1 on with dependents released at kernel entry, 2 on with
+// release at exit, 3 on without explicit release.
+int pdl_mode() {
+  static const int mode = [] {
+    const char* e = getenv("CCMG_PDL");
+    return e ? atoi(e) : 0;
+  }();
+  return mode;
+}
+bool pdl_enabled() { return pdl_mode() != 0; }
+
+// publish the trigger placement to the device (once per device)
+void pdl_setup_device() {
+  int trig = pdl_mode() == 1 ? 1 : pdl_mode() == 2 ? 2 : 0;
+  CK(cudaMemcpyToSymbol(g_pdl_trigger, &trig, sizeof(int)));
+}
+
+template <typename... KArgs, typename... Args>
+void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args... args) {
+  ++t_launches;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
 
 // ---------------------------------------------------------------------------
 // dense helpers (host, FP64)
@@ -105,6 +142,8 @@ struct BlockPlan {
   int gk = 0;                          // ELL width of the gather
   std::vector<int> ell_col;            // [gk * m] term-major
   std::vector<double> ell_val;
+  std::vector<int> tail_ptr{0}, tail_col;   // terms beyond the width
+  std::vector<double> tail_val;
   int sk = 0;                          // ELL width of A_S,I
   std::vector<int> asi_ell_col;        // [sk * ns]
   std::vector<double> asi_ell_val;
@@ -125,14 +164,14 @@ struct BlockPlan {
   std::vector<int> alias_ptr{0}, alias_cell;
 };
 
-const int kDenseMax = 1024;   // blocks up to this size use one dense inverse
+const int kDenseDirect = 1024;  // blocks up to this size: dense inverse by Gauss-Jordan
+const int kDenseMax = 2560;     // up to this size: dense inverse from the chunked plan
 
-// Apply the chunked scheme to a fixed vector in FP64 exactly as the device
-// does and return |A x - t|_inf / (|A|_inf |x|_inf).
-double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, double>>& Abb) {
+// Apply the chunked scheme to t in FP64 exactly as the device does.
+void apply_plan(const BlockPlan& B, const std::vector<double>& t, std::vector<double>& x) {
   const int m = B.m;
-  std::vector<double> t(m), z(m, 0.0), x(m, 0.0), xs(B.ns, 0.0);
-  for (int p = 0; p < m; ++p) t[p] = std::sin(1.0 + 0.7 * p) + 0.25 * std::cos(3.1 * p);
+  std::vector<double> z(m, 0.0), xs(B.ns, 0.0);
+  x.assign(m, 0.0);
   for (int c = 0; c < B.nch; ++c) {
     const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
     const double* A = &B.ainv[B.aoff[c]];
@@ -164,6 +203,15 @@ double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, doub
       x[B.ipos[i0 + r]] = z[B.ipos[i0 + r]] - acc;
     }
   }
+}
+
+// Apply the scheme to a fixed vector and return the normwise backward error
+// |A x - t|_inf / (|A|_inf |x|_inf).
+double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, double>>& Abb) {
+  const int m = B.m;
+  std::vector<double> t(m), x;
+  for (int p = 0; p < m; ++p) t[p] = std::sin(1.0 + 0.7 * p) + 0.25 * std::cos(3.1 * p);
+  apply_plan(B, t, x);
   double rmax = 0, amax = 0, xmax = 0;
   for (int p = 0; p < m; ++p) {
     double acc = -t[p], arow = 0;
@@ -178,17 +226,30 @@ double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, doub
 // padded term-major (ELL) copies of the gather rows and of A_S,I
 void make_ell(BlockPlan& B) {
   const int m = B.m;
+  // width: the longest PLG row (at most 15 terms) rounded up; the few
+  // longer rows (box-corner rows with ghost expansions) spill into a tail
+  const int kMaxWidth = 16;
   B.gk = 0;
   for (int p = 0; p < m; ++p) B.gk = std::max<int>(B.gk, (int)(B.gptr[p + 1] - B.gptr[p]));
+  B.gk = std::min(B.gk, kMaxWidth);
   B.ell_col.assign((size_t)B.gk * m, 0);
   B.ell_val.assign((size_t)B.gk * m, 0.0);
+  B.tail_ptr.assign(1, 0);
+  B.tail_col.clear();
+  B.tail_val.clear();
   for (int p = 0; p < m; ++p) {
     int q = 0;
     for (int64_t e = B.gptr[p]; e < B.gptr[p + 1]; ++e, ++q) {
-      B.ell_col[(size_t)q * m + p] = B.gcol[e];
-      B.ell_val[(size_t)q * m + p] = B.gval[e];
+      if (q < B.gk) {
+        B.ell_col[(size_t)q * m + p] = B.gcol[e];
+        B.ell_val[(size_t)q * m + p] = B.gval[e];
+      } else {
+        B.tail_col.push_back(B.gcol[e]);
+        B.tail_val.push_back(B.gval[e]);
+      }
     }
     for (; q < B.gk; ++q) B.ell_col[(size_t)q * m + p] = B.cell[p];   // value 0
+    B.tail_ptr.push_back((int)B.tail_col.size());
   }
   const int ns = B.ns;
   B.sk = 0;
@@ -345,7 +406,7 @@ BlockPlan plan_block_impl(const LevelDisc& D) {
     return true;
   };
   // small blocks: one chunk, dense inverse of the whole block
-  if (m <= kDenseMax) {
+  if (m <= kDenseDirect) {
     double st;
     build(m, true, st);
     B.error = block_plan_error(B, Abb);
@@ -385,6 +446,40 @@ BlockPlan plan_block_impl(const LevelDisc& D) {
   }
   if (!have) throw SetupError(3, "singular block of the smoother");
   B = best_plan;
+  if (m <= kDenseMax) {
+    // mid-sized blocks: the dense inverse, column by column from the plan
+    std::vector<double> inv((size_t)m * m), e(m, 0.0), x;
+    for (int c = 0; c < m; ++c) {
+      e[c] = 1.0;
+      apply_plan(B, e, x);
+      e[c] = 0.0;
+      for (int r = 0; r < m; ++r) inv[(size_t)c * m + r] = x[r];   // column-major
+    }
+    BlockPlan D = B;
+    D.nch = 1;
+    D.ns = 0;
+    D.cstart = {0, m};
+    D.iptr = {0, m};
+    D.ipos.resize(m);
+    for (int p = 0; p < m; ++p) D.ipos[p] = p;
+    D.aoff = {0};
+    D.ainv.swap(inv);
+    D.spos.clear();
+    D.asi_ptr = {0};
+    D.asi_col.clear();
+    D.asi_val.clear();
+    D.sinv.clear();
+    D.wptr = {0, 0};
+    D.widx.clear();
+    D.woff = {0};
+    D.wmat.clear();
+    D.error = block_plan_error(D, Abb);
+    if (D.error < 1e-13) {
+      D.dense = true;
+      D.smem_chunk = (size_t)((m + 31) & ~31);
+      return D;
+    }
+  }
   int maxni = 0, maxnw = 0;
   for (int c = 0; c < B.nch; ++c) {
     maxni = std::max(maxni, B.iptr[c + 1] - B.iptr[c]);
@@ -557,6 +652,9 @@ StencilParams make_stencil(const LevelDisc& D, double omega) {
     for (int d = 0; d < 2; ++d)
       for (int q = 0; q < 4; ++q) P.gh[w][d][q] = D.gc[w][d][q];
   P.omega_over_diag = omega / D.diag;
+  P.sx = D.a / (12.0 * h2);
+  P.sy = D.c / (12.0 * h2);
+  P.sxy = D.b / (144.0 * h2);
   return P;
 }
 
@@ -572,6 +670,9 @@ BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
   d.gk = B.gk;
   d.gcol = pool.upload(B.ell_col, s);
   d.gval = pool.upload(cast_vec<T>(B.ell_val), s);
+  d.tptr = pool.upload(B.tail_ptr, s);
+  d.tcol = pool.upload(B.tail_col, s);
+  d.tval = pool.upload(cast_vec<T>(B.tail_val), s);
   d.cstart = pool.upload(B.cstart, s);
   d.iptr = pool.upload(B.iptr, s);
   d.ipos = pool.upload(B.ipos, s);
@@ -614,21 +715,37 @@ template <class T> const StencilP<T>& sparams(Level& L);
 template <> const StencilP<double>& sparams<double>(Level& L) { return L.sp; }
 template <> const StencilP<float>& sparams<float>(Level& L) { return L.spf; }
 
+// Jacobi sweep on level L: 32 x 32 tiles (4 rows per thread) on large grids,
+// 32 x 8 tiles on small ones, where more CTAs matter more than fewer loads.
+template <class T>
+void launch_sweep(Level& L, const T* in, T* out, const T* b, const T* ec, bool zero,
+                  cudaStream_t s) {
+  const auto& P = sparams<T>(L);
+  if (L.n >= 256) {
+    dim3 g((L.n + TX - 1) / TX, (L.n + WY - 1) / WY);
+    if (L.sp.cross) pdl_launch(k_sweep_w<T, true>, g, TX * TY, 0, s, in, out, b, L.cls, ec, P, zero);
+    else pdl_launch(k_sweep_w<T, false>, g, TX * TY, 0, s, in, out, b, L.cls, ec, P, zero);
+  } else {
+    if (L.sp.cross) pdl_launch(k_sweep<T, true, 1>, tiles(L.n), TX * TY, 0, s, in, out, b, L.cls, ec, P, zero);
+    else pdl_launch(k_sweep<T, false, 1>, tiles(L.n), TX * TY, 0, s, in, out, b, L.cls, ec, P, zero);
+  }
+}
+
 template <class T>
 void block_solve(Level& L, T* u, const T* b, cudaStream_t s) {
   const BlockDev& B = bdev<T>(L);
   if (B.m == 0) return;
   const BlockPlan& P = L.plan;
   if (P.dense) {
-    LAUNCH k_block_gather<T><<<nblk(P.m), 256, 0, s>>>(B, b, u);
-    LAUNCH k_block_gemv<T><<<(P.m + 7) / 8, 256, P.smem_chunk * sizeof(T), s>>>(B, u);
+    pdl_launch(k_block_gather<T>, nblk(P.m), 256, 0, s, B, b, u);
+    pdl_launch(k_block_gemv<T>, (P.m + 7) / 8, 256, P.smem_chunk * sizeof(T), s, B, u);
     return;
   }
-  LAUNCH k_block_chunk<T><<<P.nch, 256, P.smem_chunk * sizeof(T), s>>>(B, b, u);
+  pdl_launch(k_block_chunk<T>, P.nch, 256, P.smem_chunk * sizeof(T), s, B, b, u);
   if (P.ns > 0) {
     size_t sm = (size_t)(((P.ns + 31) & ~31) + 256 + 32) * sizeof(T);
-    LAUNCH k_block_schur<T><<<(P.ns + 31) / 32, 256, sm, s>>>(B, u);
-    LAUNCH k_block_back<T><<<P.nch, 256, P.smem_back * sizeof(T), s>>>(B, u);
+    pdl_launch(k_block_schur<T>, (P.ns + 31) / 32, 256, sm, s, B, u);
+    pdl_launch(k_block_back<T>, P.nch, 256, P.smem_back * sizeof(T), s, B, u);
   }
 }
 
@@ -647,10 +764,7 @@ void sweep(cc_hierarchy* H, int l, int& cur, bool zero, const T* ec, cudaStream_
     }
     CK(cudaEventRecordWithFlags(H->ev[H->ev_used].first, s, cudaEventRecordExternal));
   }
-  if (L.sp.cross)
-    LAUNCH k_sweep<T, true><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, sparams<T>(L), zero);
-  else
-    LAUNCH k_sweep<T, false><<<tiles(L.n), TX * TY, 0, s>>>(in, out, bbuf<T>(L), L.cls, ec, sparams<T>(L), zero);
+  launch_sweep<T>(L, in, out, bbuf<T>(L), ec, zero, s);
   if (timed) {
     CK(cudaEventRecordWithFlags(H->ev[H->ev_used].second, s, cudaEventRecordExternal));
     ++H->ev_used;
@@ -663,7 +777,7 @@ template <class T>
 void bottom(cc_hierarchy* H, int l, int cur, cudaStream_t s) {
   Level& L = *H->lv[l];
   int nc = H->nc_bottom;
-  LAUNCH k_bottom<T><<<(nc + 7) / 8, 256, 0, s>>>(H->bottom_inv, nc, bbuf<T>(L), ubuf<T>(L, cur));
+  pdl_launch(k_bottom<T>, (nc + 7) / 8, 256, 0, s, H->bottom_inv, nc, bbuf<T>(L), ubuf<T>(L, cur));
 }
 
 // Alg. 2 (gamma = 1) or its W form (gamma = 2) on level l; cur[l] tracks the
@@ -688,17 +802,17 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
   }
   Level& C = *H->lv[l + 1];
   if (L.sp.cross)
-    LAUNCH k_resid_restrict<T, true><<<tiles(L.n), TX * TY, 0, s>>>(ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
+    pdl_launch(k_resid_restrict<T, true>, tiles(L.n), TX * TY, 0, s, ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
                                                               C.cls, bbuf<T>(C), sparams<T>(L));
   else
-    LAUNCH k_resid_restrict<T, false><<<tiles(L.n), TX * TY, 0, s>>>(ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
+    pdl_launch(k_resid_restrict<T, false>, tiles(L.n), TX * TY, 0, s, ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
                                                                C.cls, bbuf<T>(C), sparams<T>(L));
   for (int g = 0; g < gamma; ++g) cycle_level<T>(H, l + 1, cur, g == 0, s);
   // merged-away coarse cells already hold their owner's value (written by
   // the block solve, or by the alias rows of the bottom matrix)
   T* ec = ubuf<T>(C, cur[l + 1]);
   if (nu2 == 0) {
-    LAUNCH k_prolong_add<T><<<nblk(L.nn), 256, 0, s>>>(ubuf<T>(L, cur[l]), ec, L.cls, L.n);
+    pdl_launch(k_prolong_add<T>, nblk(L.nn), 256, 0, s, ubuf<T>(L, cur[l]), ec, L.cls, L.n);
     return;
   }
   for (int k = 0; k < nu2; ++k) sweep<T>(H, l, cur[l], false, k == 0 ? ec : (const T*)nullptr, s);
@@ -709,19 +823,19 @@ template <class Tout>
 void residual64(cc_hierarchy* H, const double* u, const double* b, Tout* r, cudaStream_t s) {
   Level& L = *H->lv[0];
   if (L.sp.cross)
-    LAUNCH k_resid<double, Tout, true><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, r, L.sp, H->d_norm);
+    pdl_launch(k_resid<double, Tout, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm);
   else
-    LAUNCH k_resid<double, Tout, false><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, r, L.sp, H->d_norm);
+    pdl_launch(k_resid<double, Tout, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm);
   if (L.plan.m)
-    LAUNCH k_block_resid<Tout><<<nblk(L.plan.m), 256, 0, s>>>(L.plan.m, L.brow_cell, L.brow_ptr, L.brow_col,
+    pdl_launch(k_block_resid<Tout>, nblk(L.plan.m), 256, 0, s, L.plan.m, L.brow_cell, L.brow_ptr, L.brow_col,
                                                        L.brow_val, u, b, r, H->d_norm);
 }
 
 void assemble_rhs(cc_hierarchy* H, const double* f, const double* g, double* b, cudaStream_t s) {
   Level& L = *H->lv[0];
-  LAUNCH k_rhs_copy<<<nblk(L.nn), 256, 0, s>>>(f, L.cls, b, L.nn);
+  pdl_launch(k_rhs_copy, nblk(L.nn), 256, 0, s, f, L.cls, b, L.nn);
   if (H->n_nrows)
-    LAUNCH k_rhs_n<<<nblk(H->n_nrows), 256, 0, s>>>(H->n_nrows, H->nrow_cell, H->nrow_ptr, H->nrow_col,
+    pdl_launch(k_rhs_n, nblk(H->n_nrows), 256, 0, s, H->n_nrows, H->nrow_cell, H->nrow_ptr, H->nrow_col,
                                              H->nrow_val, g, b);
 }
 
@@ -751,7 +865,7 @@ void iteration(cc_hierarchy* H, bool mixed, cudaStream_t s) {
     residual64<double>(H, L.u64[H->cur64], L.b64, H->r64, s);
   } else {
     cycle_level<float>(H, 0, cur, true, s);
-    LAUNCH k_update<float><<<nblk(L.nn), 256, 0, s>>>(L.u64[H->cur64], L.u32[cur[0]], L.cls, L.nn);
+    pdl_launch(k_update<float>, nblk(L.nn), 256, 0, s, L.u64[H->cur64], L.u32[cur[0]], L.cls, L.nn);
     residual64<float>(H, L.u64[H->cur64], L.b64, L.b32, s);
   }
 }
@@ -765,7 +879,7 @@ cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* 
   assemble_rhs(H, f, g, L.b64, s);
   CK(cudaMemcpyAsync(L.u64[0], u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
-  LAUNCH k_absmax<<<152 * 4, 256, 0, s>>>(L.b64, L.nn, H->d_norm);
+  pdl_launch(k_absmax, 152 * 4, 256, 0, s, L.b64, L.nn, H->d_norm);
   double bn = read_norm(H, s);
   if (bn == 0.0) bn = 1.0;
   cc_result res{};
@@ -965,7 +1079,10 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   }
   const bool dev = !o.host_only;
   try {
-    if (dev) CK(cudaGetDevice(&H->device));
+    if (dev) {
+      CK(cudaGetDevice(&H->device));
+      pdl_setup_device();
+    }
     // levels: halve while the level is resolved and discretisable (Eq. 5.9)
     int nl = n;
     while (true) {
@@ -1303,11 +1420,11 @@ cc_status cc_residual(cc_handle H, int l, const double* u, const double* b, doub
   try {
     Level& L = *H->lv[l];
     if (L.sp.cross)
-      LAUNCH k_resid<double, double, true><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, r, L.sp, nullptr);
+      pdl_launch(k_resid<double, double, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr);
     else
-      LAUNCH k_resid<double, double, false><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, r, L.sp, nullptr);
+      pdl_launch(k_resid<double, double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr);
     if (!L.disc.block.empty())
-      LAUNCH k_block_resid<double><<<nblk((int64_t)L.disc.block.size()), 256, 0, s>>>(
+      pdl_launch(k_block_resid<double>, nblk((int64_t)L.disc.block.size()), 256, 0, s, 
           (int)L.disc.block.size(), L.brow_cell, L.brow_ptr, L.brow_col, L.brow_val, u, b, r, nullptr);
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
@@ -1325,7 +1442,7 @@ cc_status cc_smooth(cc_handle H, int l, double* u, const double* b, cc_stream st
     CK(cudaMemcpyAsync(L.b64, b, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
     int cur = 0;
     sweep<double>(H, l, cur, false, (const double*)nullptr, s);
-    LAUNCH k_rhs_copy<<<nblk(L.nn), 256, 0, s>>>(L.u64[cur], L.cls, u, L.nn);
+    pdl_launch(k_rhs_copy, nblk(L.nn), 256, 0, s, L.u64[cur], L.cls, u, L.nn);
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
@@ -1340,9 +1457,9 @@ cc_status cc_restrict_residual(cc_handle H, int l, const double* u, const double
     Level& L = *H->lv[l];
     Level& C = *H->lv[l + 1];
     if (L.sp.cross)
-      LAUNCH k_resid_restrict<double, true><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, C.cls, rc, L.sp);
+      pdl_launch(k_resid_restrict<double, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, C.cls, rc, L.sp);
     else
-      LAUNCH k_resid_restrict<double, false><<<tiles(L.n), TX * TY, 0, s>>>(u, b, L.cls, C.cls, rc, L.sp);
+      pdl_launch(k_resid_restrict<double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, C.cls, rc, L.sp);
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
@@ -1357,8 +1474,8 @@ cc_status cc_prolong_add(cc_handle H, int l, const double* ec, double* u, cc_str
     Level& C = *H->lv[l + 1];
     double* tmp = C.u64[1];
     CK(cudaMemcpyAsync(tmp, ec, C.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (C.nfix) LAUNCH k_owner_fix<double><<<nblk(C.nfix), 256, 0, s>>>(C.nfix, C.fix_dst, C.fix_src, tmp);
-    LAUNCH k_prolong_add<double><<<nblk(L.nn), 256, 0, s>>>(u, tmp, L.cls, L.n);
+    if (C.nfix) pdl_launch(k_owner_fix<double>, nblk(C.nfix), 256, 0, s, C.nfix, C.fix_dst, C.fix_src, tmp);
+    pdl_launch(k_prolong_add<double>, nblk(L.nn), 256, 0, s, u, tmp, L.cls, L.n);
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
@@ -1432,25 +1549,22 @@ cc_status cc_smooth_noalloc(cc_handle H, int l, double* u, const double* b, cc_s
     B.tblk = scr + L.nn;                    // [nn, nn + m)
     B.zblk = scr + L.nn + P.m;              // [nn + m, nn + 2m)
     B.xs = scr + L.nn + 2 * P.m;            // [nn + 2m, nn + 2m + ns)
-    if (L.sp.cross)
-      LAUNCH k_sweep<double, true><<<tiles(L.n), TX * TY, 0, s>>>(u, out, b, L.cls, nullptr, L.sp, 0);
-    else
-      LAUNCH k_sweep<double, false><<<tiles(L.n), TX * TY, 0, s>>>(u, out, b, L.cls, nullptr, L.sp, 0);
+    launch_sweep<double>(L, u, out, b, (const double*)nullptr, false, s);
     if (P.m) {
       if (P.dense) {
-        LAUNCH k_block_gather<double><<<nblk(P.m), 256, 0, s>>>(B, b, out);
-        LAUNCH k_block_gemv<double><<<(P.m + 7) / 8, 256, P.smem_chunk * sizeof(double), s>>>(B, out);
+        pdl_launch(k_block_gather<double>, nblk(P.m), 256, 0, s, B, b, out);
+        pdl_launch(k_block_gemv<double>, (P.m + 7) / 8, 256, P.smem_chunk * sizeof(double), s, B, out);
       } else {
-        LAUNCH k_block_chunk<double><<<P.nch, 256, P.smem_chunk * sizeof(double), s>>>(B, b, out);
+        pdl_launch(k_block_chunk<double>, P.nch, 256, P.smem_chunk * sizeof(double), s, B, b, out);
         if (P.ns > 0) {
           size_t sm = (size_t)(((P.ns + 31) & ~31) + 256 + 32) * sizeof(double);
-          LAUNCH k_block_schur<double><<<(P.ns + 31) / 32, 256, sm, s>>>(B, out);
-          LAUNCH k_block_back<double><<<P.nch, 256, P.smem_back * sizeof(double), s>>>(B, out);
+          pdl_launch(k_block_schur<double>, (P.ns + 31) / 32, 256, sm, s, B, out);
+          pdl_launch(k_block_back<double>, P.nch, 256, P.smem_back * sizeof(double), s, B, out);
         }
       }
     }
     // every non-empty cell of `out` was written above; empty cells go out as 0
-    LAUNCH k_rhs_copy<<<nblk(L.nn), 256, 0, s>>>(out, L.cls, u, L.nn);
+    pdl_launch(k_rhs_copy, nblk(L.nn), 256, 0, s, out, L.cls, u, L.nn);
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;

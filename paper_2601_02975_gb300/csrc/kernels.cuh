@@ -11,12 +11,35 @@
 namespace ccmg {
 
 constexpr int TX = 32;   // tile width (cells) of the stencil kernels
-constexpr int TY = 8;    // tile height
+constexpr int TY = 8;    // thread rows of a CTA (256 threads = TX x TY)
 constexpr int HALO = 2;  // stencil radius
 constexpr int SX = TX + 2 * HALO;
 constexpr int SY = TY + 2 * HALO;
+// A CTA covers TX x (TY * RPT) cells; each thread computes RPT rows, ly =
+// ty + TY * r, so that a warp always touches one shared-memory row.
+template <int RPT>
+struct Tile {
+  static constexpr int H = TY * RPT;
+  static constexpr int SH = H + 2 * HALO;
+};
 
 enum : uint8_t { C_EMPTY = 0, C_STENCIL = 1, C_BLOCK = 2 };
+
+// Programmatic dependent launch: every kernel lets the next kernel of the
+// stream begin launching at once, then waits until the previous kernel has
+// completed and its writes are visible before it reads anything.  The launch
+// latency of a kernel then overlaps the execution of the one before it.
+// g_pdl_trigger: 1 lets dependents launch at kernel entry, 2 at exit, 0 never
+// (they then launch when the kernel completes).
+__device__ int g_pdl_trigger = 0;
+
+__device__ __forceinline__ void pdl_enter() {
+  if (g_pdl_trigger == 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_exit() {
+  if (g_pdl_trigger == 2) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // Constant per-level stencil data: weights of the 5 x 5 SFV stencil (Eq.
 // 4.7a,b) and the homogeneous ghost coefficients of each wall, in the
@@ -28,6 +51,7 @@ struct StencilP {
   T w[25];                 // (dj + 2) * 5 + (di + 2)
   T gh[4][2][4];           // wall (S, E, N, W), depth - 1, inward cell q
   T omega_over_diag;       // omega / D (D the centre weight)
+  T sx, sy, sxy;           // a / (12 h^2), c / (12 h^2), b / (144 h^2)
 };
 using StencilParams = StencilP<double>;
 
@@ -41,6 +65,9 @@ StencilP<T> stencil_as(const StencilParams& d) {
     for (int b = 0; b < 2; ++b)
       for (int c = 0; c < 4; ++c) o.gh[a][b][c] = (T)d.gh[a][b][c];
   o.omega_over_diag = (T)d.omega_over_diag;
+  o.sx = (T)d.sx;
+  o.sy = (T)d.sy;
+  o.sxy = (T)d.sxy;
   return o;
 }
 
@@ -53,12 +80,13 @@ __device__ __forceinline__ T cell_value(const T* __restrict__ u, const T* __rest
   return v;
 }
 
-template <class T>
+template <class T, int SHT = SY>
 __device__ __forceinline__ void load_tile(T (*s)[SX], const T* __restrict__ u,
                                           const T* __restrict__ ec, const StencilP<T>& P,
                                           int x0, int y0, bool zero) {
   const int n = P.n;
-  for (int idx = threadIdx.x; idx < SX * SY; idx += blockDim.x) {
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < SX * SHT; idx += blockDim.x) {
     int ly = idx / SX, lx = idx % SX;
     int gx = x0 + lx - HALO, gy = y0 + ly - HALO;
     bool ox = gx < 0 || gx >= n, oy = gy < 0 || gy >= n;
@@ -120,22 +148,116 @@ __device__ __forceinline__ T apply_A(const T (*s)[SX], const T* w, int lx, int l
 // the sweep reads u + I(ec) (Eq. 5.11) instead of u (the first post-sweep,
 // fused with the prolongation); with zero it reads 0 (a coarse level's first
 // sweep, whose initial guess is 0, Alg. 2).
-template <class T, bool CROSS>
+template <class T, bool CROSS, int RPT = 1>
 __global__ void __launch_bounds__(TX * TY)
 k_sweep(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ b,
         const uint8_t* __restrict__ cls, const T* __restrict__ ec, StencilP<T> P, int zero) {
-  __shared__ T s[SY][SX];
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  load_tile<T>(s, u_in, ec, P, x0, y0, zero != 0);
+  pdl_enter();
+  constexpr int TH = Tile<RPT>::H;
+  __shared__ T s[Tile<RPT>::SH][SX];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TH;
+  const int n = P.n;
+  const int lx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int gx = x0 + lx;
+  // issue the loads of b and of the class map before the tile barrier
+  T bv[RPT];
+  uint8_t cv[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int gy = y0 + ty + TY * r;
+    const bool in = gx < n && gy < n;
+    const size_t k = (size_t)gy * n + gx;
+    cv[r] = in ? cls[k] : (uint8_t)C_EMPTY;
+    bv[r] = in ? b[k] : T(0);
+  }
+  load_tile<T, Tile<RPT>::SH>(s, u_in, ec, P, x0, y0, zero != 0);
   __syncthreads();
-  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-  const int gx = x0 + lx, gy = y0 + ly, n = P.n;
-  if (gx >= n || gy >= n) return;
-  const size_t k = (size_t)gy * n + gx;
-  if (cls[k] != C_STENCIL) return;
-  T Au = apply_A<T, CROSS>(s, P.w, lx, ly);
-  T uc = s[ly + HALO][lx + HALO];
-  u_out[k] = uc + P.omega_over_diag * (b[k] - Au);
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int ly = ty + TY * r, gy = y0 + ly;
+    if (cv[r] != C_STENCIL) continue;
+    T Au = apply_A<T, CROSS>(s, P.w, lx, ly);
+    T uc = s[ly + HALO][lx + HALO];
+    u_out[(size_t)gy * n + gx] = uc + P.omega_over_diag * (bv[r] - Au);
+  }
+  pdl_exit();
+}
+
+// ---- a1 on large grids: 32 x 32 tiles, 4 consecutive rows per thread ---------
+// The stencil is a dxx + c dyy + b dx(dy) with the one-dimensional formulas of
+// Eq. 4.7a,b.  Each thread reads the 5 values of each row of its 8-row window
+// once, forms the row's second difference and gradient in x, and combines
+// them along y for its 4 outputs; the loader walks the halo tile in 2-D.
+constexpr int WY = 32;          // tile height of the windowed sweep
+constexpr int WSH = WY + 2 * HALO;
+
+template <class T>
+__device__ __forceinline__ void load_tile_2d(T (*s)[SX], const T* __restrict__ u,
+                                             const T* __restrict__ ec, const StencilP<T>& P,
+                                             int x0, int y0, bool zero) {
+  const int n = P.n;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const bool interior = x0 >= HALO && y0 >= HALO && x0 + SX - HALO <= n && y0 + WSH - HALO <= n;
+  if (interior) {
+#pragma unroll
+    for (int ly = ty; ly < WSH; ly += TY) {
+      const size_t row = (size_t)(y0 + ly - HALO) * n + (x0 - HALO);
+      s[ly][tx] = zero ? T(0) : u[row + tx];
+      if (tx < SX - TX) s[ly][tx + TX] = zero ? T(0) : u[row + tx + TX];
+      if (ec) {
+        const int gy = y0 + ly - HALO;
+        const size_t crow = (size_t)(gy >> 1) * (n >> 1);
+        s[ly][tx] += ec[crow + ((x0 - HALO + tx) >> 1)];
+        if (tx < SX - TX) s[ly][tx + TX] += ec[crow + ((x0 - HALO + tx + TX) >> 1)];
+      }
+    }
+  } else {
+    load_tile<T, WSH>(s, u, ec, P, x0, y0, zero);
+  }
+}
+
+template <class T, bool CROSS>
+__global__ void __launch_bounds__(TX * TY)
+k_sweep_w(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ b,
+          const uint8_t* __restrict__ cls, const T* __restrict__ ec, StencilP<T> P, int zero) {
+  pdl_enter();
+  __shared__ T s[WSH][SX];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * WY;
+  const int n = P.n;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int gx = x0 + tx, gy0 = y0 + 4 * ty;
+  T bv[4];
+  uint8_t cv[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gy = gy0 + r;
+    const bool in = gx < n && gy < n;
+    const size_t k = (size_t)gy * n + gx;
+    cv[r] = in ? cls[k] : (uint8_t)C_EMPTY;
+    bv[r] = in ? b[k] : T(0);
+  }
+  load_tile_2d<T>(s, u_in, ec, P, x0, y0, zero != 0);
+  __syncthreads();
+  // rows 4 ty - 2 .. 4 ty + 5 of the window (tile rows 4 ty .. 4 ty + 7)
+  T lx[8], gxr[8], cc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const T* row = &s[4 * ty + k][tx];
+    const T v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3], v4 = row[4];
+    lx[k] = T(16) * (v1 + v3) - T(30) * v2 - (v0 + v4);
+    gxr[k] = T(8) * (v3 - v1) + (v0 - v4);
+    cc[k] = v2;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if (cv[r] != C_STENCIL) continue;
+    const int j = r + 2;
+    const T ly = T(16) * (cc[j - 1] + cc[j + 1]) - T(30) * cc[j] - (cc[j - 2] + cc[j + 2]);
+    T Au = P.sx * lx[j] + P.sy * ly;
+    if (CROSS) Au += P.sxy * (T(8) * (gxr[j + 1] - gxr[j - 1]) + (gxr[j - 2] - gxr[j + 2]));
+    u_out[(size_t)(gy0 + r) * n + gx] = cc[j] + P.omega_over_diag * (bv[r] - Au);
+  }
+  pdl_exit();
 }
 
 // ---- a4: residual and restriction (Eq. 5.10) ---------------------------------
@@ -146,6 +268,7 @@ template <class T, bool CROSS>
 __global__ void __launch_bounds__(TX * TY)
 k_resid_restrict(const T* __restrict__ u, const T* __restrict__ b, const uint8_t* __restrict__ cls,
                  const uint8_t* __restrict__ cls_c, T* __restrict__ rc, StencilP<T> P) {
+  pdl_enter();
   __shared__ T s[SY][SX];
   __shared__ T r[TY][TX];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -171,6 +294,7 @@ k_resid_restrict(const T* __restrict__ u, const T* __restrict__ b, const uint8_t
       rc[kc] = cls_c[kc] == C_EMPTY ? T(0) : v;
     }
   }
+  pdl_exit();
 }
 
 // ---- a8 / Eq. 4.23: residual on stencil cells, max-norm ----------------------
@@ -184,6 +308,7 @@ template <class Tin, class Tout, bool CROSS>
 __global__ void __launch_bounds__(TX * TY)
 k_resid(const Tin* __restrict__ u, const Tin* __restrict__ b, const uint8_t* __restrict__ cls,
         Tout* __restrict__ r, StencilP<Tin> P, unsigned long long* rmax) {
+  pdl_enter();
   __shared__ Tin s[SY][SX];
   __shared__ double red[TX * TY / 32];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -221,6 +346,7 @@ __global__ void k_block_resid(int m, const int* __restrict__ cell, const int64_t
                               const int* __restrict__ col, const double* __restrict__ val,
                               const double* __restrict__ u, const double* __restrict__ b,
                               Tout* __restrict__ r, unsigned long long* rmax) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double av = 0.0;
   if (i < m) {
@@ -249,6 +375,9 @@ struct BlockDev {
   int gk;                   // gather width: terms per row (padded)
   const int* gcol;          // [gk * m] term-major: entry q of row p at q * m + p
   const void* gval;         // T, padded terms have value 0
+  const int* tptr;          // [m+1] terms beyond gk (rows longer than the width)
+  const int* tcol;
+  const void* tval;         // T
   const int* cstart;        // [nch+1] block positions of each chunk
   const int* iptr;          // [nch+1] interior list ptr
   const int* ipos;          // interior block positions
@@ -290,6 +419,8 @@ __device__ __forceinline__ T block_rhs(const BlockDev& B, const T* __restrict__ 
     size_t e = (size_t)q * B.m + p;
     acc -= gval[e] * u[B.gcol[e]];
   }
+  const T* tval = static_cast<const T*>(B.tval);
+  for (int q = B.tptr[p]; q < B.tptr[p + 1]; ++q) acc -= tval[q] * u[B.tcol[q]];
   return acc;
 }
 
@@ -319,6 +450,7 @@ __device__ void cta_matvec_cm(const T* __restrict__ M, int rows, int ld, int col
 // interface rows' t go to tblk.  With no interfaces z is the solution.
 template <class T>
 __global__ void k_block_chunk(BlockDev B, const T* __restrict__ b, T* __restrict__ u) {
+  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* tI = reinterpret_cast<T*>(smem_raw);
   const int c = blockIdx.x;
@@ -344,6 +476,7 @@ __global__ void k_block_chunk(BlockDev B, const T* __restrict__ b, T* __restrict
 // K_b: x_S = inv(S) (t_S - A_S,I z) for 32 interface rows per CTA.
 template <class T>
 __global__ void k_block_schur(BlockDev B, T* __restrict__ u) {
+  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* tS = reinterpret_cast<T*>(smem_raw);
   T* partial = tS + ((B.ns + 31) & ~31);
@@ -375,6 +508,7 @@ __global__ void k_block_schur(BlockDev B, T* __restrict__ u) {
 // K_c: x_I = z - W_c x_S for the chunk's interior unknowns.
 template <class T>
 __global__ void k_block_back(BlockDev B, T* __restrict__ u) {
+  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* xl = reinterpret_cast<T*>(smem_raw);
   const int c = blockIdx.x;
@@ -399,12 +533,15 @@ __global__ void k_block_back(BlockDev B, T* __restrict__ u) {
 // the next applies inv(A) row-major, one warp per row.
 template <class T>
 __global__ void k_block_gather(BlockDev B, const T* __restrict__ b, const T* __restrict__ u) {
+  pdl_enter();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < B.m) static_cast<T*>(B.tblk)[p] = block_rhs(B, b, u, p);
+  pdl_exit();
 }
 
 template <class T>
 __global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
+  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* t = reinterpret_cast<T*>(smem_raw);
   const T* tg = static_cast<const T*>(B.tblk);
@@ -412,13 +549,14 @@ __global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= B.m) return;
+  if (r >= B.m) { pdl_exit(); return; }
   const T* A = static_cast<const T*>(B.ainv) + (size_t)r * B.m;
   T acc = T(0);
 #pragma unroll 4
   for (int c = lane; c < B.m; c += 32) acc += A[c] * t[c];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) block_write(B, u, r, acc);
+  pdl_exit();
 }
 
 // ---- a7: bottom solve, u = inv(A_c) b (FP64 matrix, row-major) --------------
@@ -427,26 +565,30 @@ __global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
 template <class T>
 __global__ void k_bottom(const double* __restrict__ Ainv, int nc, const T* __restrict__ b,
                          T* __restrict__ u) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= nc) return;
+  if (r >= nc) { pdl_exit(); return; }
   const double* A = Ainv + (size_t)r * nc;
   double acc = 0.0;
 #pragma unroll 4
   for (int c = lane; c < nc; c += 32) acc += A[c] * (double)b[c];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) u[r] = (T)acc;
+  pdl_exit();
 }
 
 // ---- a0: b = f - N g -----------------------------------------------------------
 __global__ void k_rhs_copy(const double* __restrict__ f, const uint8_t* __restrict__ cls,
                            double* __restrict__ b, int64_t nn) {
+  pdl_enter();
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < nn) b[k] = cls[k] == C_EMPTY ? 0.0 : f[k];
 }
 __global__ void k_rhs_n(int rows, const int* __restrict__ cell, const int64_t* __restrict__ ptr,
                         const int* __restrict__ col, const double* __restrict__ val,
                         const double* __restrict__ g, double* __restrict__ b) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   double acc = 0.0;
@@ -458,6 +600,7 @@ __global__ void k_rhs_n(int rows, const int* __restrict__ cell, const int64_t* _
 template <class T>
 __global__ void k_owner_fix(int cnt, const int* __restrict__ dst, const int* __restrict__ src,
                             T* __restrict__ e) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < cnt) e[dst[i]] = e[src[i]];
 }
@@ -465,6 +608,7 @@ __global__ void k_owner_fix(int cnt, const int* __restrict__ dst, const int* __r
 template <class T>
 __global__ void k_prolong_add(T* __restrict__ u, const T* __restrict__ ec,
                               const uint8_t* __restrict__ cls, int n) {
+  pdl_enter();
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= (int64_t)n * n) return;
   if (cls[k] == C_EMPTY) return;
@@ -476,17 +620,20 @@ __global__ void k_prolong_add(T* __restrict__ u, const T* __restrict__ ec,
 template <class T>
 __global__ void k_update(double* __restrict__ u, const T* __restrict__ e,
                          const uint8_t* __restrict__ cls, int64_t nn) {
+  pdl_enter();
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < nn && cls[k] != C_EMPTY) u[k] += (double)e[k];
 }
 
 template <class A, class B>
 __global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, int64_t nn) {
+  pdl_enter();
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < nn) y[k] = (B)x[k];
 }
 
 __global__ void k_absmax(const double* __restrict__ x, int64_t nn, unsigned long long* out) {
+  pdl_enter();
   double av = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nn;
        k += (int64_t)gridDim.x * blockDim.x)

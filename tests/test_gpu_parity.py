@@ -210,3 +210,29 @@ def test_solve_host_and_submit_match_device_solve():
         time.sleep(0.001)
     assert st == 0 and res.t_done >= res.t_start >= res.t_submit
     np.testing.assert_array_equal(us.cpu().numpy(), u.cpu().numpy())
+
+
+@pytest.mark.slow
+def test_step_parity_large_grid():
+    """Grids of 256^2 and more take the windowed sweep kernel and chunked
+    block solves: one sweep and the residual restriction on the 256^2 disk
+    level against the oracle."""
+    P, H, O = _pair("disk", 256, 64)
+    d = O.levels[0]
+    n = d.n
+    u, b = _random_state(O, 0, 77)
+    ut = _t(u)
+    H.smooth(0, ut, _t(b))
+    uo = M.smooth(O, 0, u, b)
+    assert np.abs(_np(ut, n) - uo).max() < 1e-11 * np.abs(uo).max()
+    rc = torch.zeros((n // 2) ** 2, dtype=torch.float64, device=DEV)
+    H.restrict_residual(0, _t(u), _t(b), rc)
+    rco = M.restrict(O, 0, M.residual(d, u, b))
+    assert np.abs(_np(rc, n // 2) - rco).max() < 1e-12 * np.abs(u).max() / d.h ** 2
+    # a prolongation-fused sweep through a whole cycle: compare one cycle
+    bo = _oracle_rhs(O, P)
+    _, _, _, bg = _gpu_rhs(H, P)
+    ug = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    H.cycle(ug, bg)
+    uc = M.cycle(O, 0, np.zeros((n, n)), bo, 3, 3, 1)
+    assert np.abs(_np(ug, n) - uc).max() < 1e-11 * np.abs(uc).max()
