@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--min-coarse", type=int, default=MIN_COARSE,
+                    help="cells a side of the coarsest level")
     ap.add_argument("--profile", action="store_true",
                     help="warm up, then run one solve inside the NVTX range 'solve' and exit "
                          "(for ncu --nvtx --nvtx-include solve/)")
@@ -60,7 +62,7 @@ def run_profile(a):
     P = _problem()
     n = a.n
     H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
-                              default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1,
+                              default_options(min_coarse_n=a.min_coarse, cycle=2, precision=1,
                                               max_cycles=60))
     f, g, _ = I.problem_inputs(H, P)
     ft = torch.tensor(f.ravel(), dtype=torch.float64, device="cuda")
@@ -194,7 +196,7 @@ def run_ours(a):
     __graft_entry__.build()
     P = _problem()
     n = a.n
-    opts = default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1, max_cycles=60)
+    opts = default_options(min_coarse_n=a.min_coarse, cycle=2, precision=1, max_cycles=60)
     H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n, opts)
     f, g, ue = I.problem_inputs(H, P)
     present = H.cell_types()[0] != 0
@@ -275,7 +277,7 @@ def run_ours(a):
 
     # plain FP64 solve of the same problem, for comparison
     H64 = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
-                                default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=0,
+                                default_options(min_coarse_n=a.min_coarse, cycle=2, precision=0,
                                                 max_cycles=60))
     u64 = torch.zeros(n * n, dtype=torch.float64, device=dev)
     H64.solve(ft, gt, u64, TOL, stream)

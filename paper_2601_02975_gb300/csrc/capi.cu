@@ -48,14 +48,14 @@ inline void note_error(cudaError_t e, const char* what) {
   } while (0)
 
 // Launch with the programmatic-stream-serialisation attribute (PDL); the
-// kernels call pdl_enter() first.  CCMG_NO_PDL=1 in the environment turns the
-// attribute off.
-// CCMG_PDL: 0 off, 1 on with dependents released at kernel entry, 2 on with
-// release at exit, 3 on without explicit release.
+// kernels call pdl_enter() first, which waits for the previous kernel's
+// completion and memory flush, so only the launch latency overlaps.
+// CCMG_PDL in the environment: 0 off, 1 on with dependents released at kernel
+// entry, 2 (default) on with release at exit, 3 on without explicit release.
 int pdl_mode() {
   static const int mode = [] {
     const char* e = getenv("CCMG_PDL");
-    return e ? atoi(e) : 0;
+    return e ? atoi(e) : 2;
   }();
   return mode;
 }
@@ -165,6 +165,7 @@ struct BlockPlan {
 };
 
 const int kDenseDirect = 1024;  // blocks up to this size: dense inverse by Gauss-Jordan
+const int kBlockOneLaunch = 1024;  // dense blocks up to this size: gather and solve in one launch
 const int kDenseMax = 2560;     // up to this size: dense inverse from the chunked plan
 
 // Apply the chunked scheme to t in FP64 exactly as the device does.
@@ -548,6 +549,11 @@ struct Level {
   int64_t* brow_ptr = nullptr;
   int* brow_col = nullptr;
   double* brow_val = nullptr;
+  // one-launch block-smoother sweeps (k_smooth), for dense blocks
+  bool fused = false;
+  int fuse_nb = 0;                     // block-solving CTAs
+  size_t fuse_smem[2] = {0, 0};        // their shared memory, [FP64, FP32]
+  FrontierDev fr64{}, fr32{};
   // owner fix-up list: merged-away control volumes of this level
   int nfix = 0;
   int* fix_dst = nullptr;
@@ -696,6 +702,45 @@ BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
   return d;
 }
 
+// The stencil cells that the block rows couple to (the frontier) and the
+// gather rows over them, in the term order of the gather; false if a coupled
+// cell is not a stencil cell (its new value would then not be the sweep's).
+bool build_frontier(const BlockPlan& B, const std::vector<uint8_t>& cls, std::vector<int>& qcell,
+                    std::vector<int>& fptr, std::vector<int>& fidx, std::vector<double>& fval) {
+  std::map<int, int> pos;
+  for (int64_t e = 0; e < B.gptr[B.m]; ++e) pos[B.gcol[e]] = 0;
+  qcell.clear();
+  for (auto& kv : pos) {
+    if (cls[kv.first] != C_STENCIL) return false;
+    kv.second = (int)qcell.size();
+    qcell.push_back(kv.first);
+  }
+  fptr.assign(1, 0);
+  fidx.clear();
+  fval.clear();
+  for (int p = 0; p < B.m; ++p) {
+    for (int64_t e = B.gptr[p]; e < B.gptr[p + 1]; ++e) {
+      fidx.push_back(pos[B.gcol[e]]);
+      fval.push_back(B.gval[e]);
+    }
+    fptr.push_back((int)fidx.size());
+  }
+  return true;
+}
+
+template <class T>
+FrontierDev upload_frontier(Pool& pool, const std::vector<int>& qcell, const std::vector<int>& fptr,
+                            const std::vector<int>& fidx, const std::vector<double>& fval,
+                            cudaStream_t s) {
+  FrontierDev f{};
+  f.nq = (int)qcell.size();
+  f.qcell = pool.upload(qcell, s);
+  f.fptr = pool.upload(fptr, s);
+  f.fidx = pool.upload(fidx, s);
+  f.fval = pool.upload(cast_vec<T>(fval), s);
+  return f;
+}
+
 inline dim3 tiles(int n) { return dim3((n + TX - 1) / TX, (n + TY - 1) / TY); }
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -710,6 +755,10 @@ template <> float* bbuf<float>(Level& L) { return L.b32; }
 template <class T> const BlockDev& bdev(Level& L);
 template <> const BlockDev& bdev<double>(Level& L) { return L.blk.d64; }
 template <> const BlockDev& bdev<float>(Level& L) { return L.blk.d32; }
+
+template <class T> const FrontierDev& fdev(Level& L);
+template <> const FrontierDev& fdev<double>(Level& L) { return L.fr64; }
+template <> const FrontierDev& fdev<float>(Level& L) { return L.fr32; }
 
 template <class T> const StencilP<T>& sparams(Level& L);
 template <> const StencilP<double>& sparams<double>(Level& L) { return L.sp; }
@@ -731,14 +780,61 @@ void launch_sweep(Level& L, const T* in, T* out, const T* b, const T* ec, bool z
   }
 }
 
+// Largest dense block whose sweeps run as one k_smooth launch; CCMG_FUSE in
+// the environment sets it (0, the default, keeps sweep and block solve as
+// separate launches: the redundant frontier work of k_smooth costs more than
+// the launch it saves on the grids measured so far).
+int fuse_max_m() {
+  static const int v = [] {
+    const char* e = getenv("CCMG_FUSE");
+    return e ? atoi(e) : 0;
+  }();
+  return v;
+}
+
+// Raise the dynamic shared memory limit of k_smooth to at least `bytes` (the
+// limit is per function and process-wide, so it only grows).
+void smooth_smem_limit(int bytes) {
+  static std::mutex mu;
+  static int limit = 48 * 1024;
+  std::lock_guard<std::mutex> lock(mu);
+  if (bytes <= limit) return;
+  CK(cudaFuncSetAttribute(k_smooth<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_smooth<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_smooth<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_smooth<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  limit = bytes;
+}
+
+// one block-smoother sweep of a level with a dense block: one launch
+template <class T>
+void launch_smooth(Level& L, const T* in, T* out, const T* b, const T* ec, bool zero,
+                   cudaStream_t s) {
+  const int pi = sizeof(T) == sizeof(float) ? 1 : 0;
+  const int ntiles = (int)(((L.n + TX - 1) / TX) * ((L.n + TY - 1) / TY));
+  const dim3 grid(ntiles + L.fuse_nb);
+  if (L.sp.cross)
+    pdl_launch(k_smooth<T, true>, grid, TX * TY, L.fuse_smem[pi], s, in, out, b, L.cls, ec,
+               sparams<T>(L), (int)zero, bdev<T>(L), fdev<T>(L), ntiles);
+  else
+    pdl_launch(k_smooth<T, false>, grid, TX * TY, L.fuse_smem[pi], s, in, out, b, L.cls, ec,
+               sparams<T>(L), (int)zero, bdev<T>(L), fdev<T>(L), ntiles);
+}
+
 template <class T>
 void block_solve(Level& L, T* u, const T* b, cudaStream_t s) {
   const BlockDev& B = bdev<T>(L);
   if (B.m == 0) return;
   const BlockPlan& P = L.plan;
+  if (P.dense && P.m <= kBlockOneLaunch) {
+    // 1024-thread CTAs: every thread gathers at most one row, every warp
+    // applies one row of the inverse
+    pdl_launch(k_block_dense<T>, (unsigned)((P.m + 31) / 32), 1024, (size_t)P.m * sizeof(T), s, B, b, u);
+    return;
+  }
   if (P.dense) {
     pdl_launch(k_block_gather<T>, nblk(P.m), 256, 0, s, B, b, u);
-    pdl_launch(k_block_gemv<T>, (P.m + 7) / 8, 256, P.smem_chunk * sizeof(T), s, B, u);
+    pdl_launch(k_block_gemv<T>, (P.m + 7) / 8, 256, (size_t)P.m * sizeof(T), s, B, u);
     return;
   }
   pdl_launch(k_block_chunk<T>, P.nch, 256, P.smem_chunk * sizeof(T), s, B, b, u);
@@ -755,6 +851,11 @@ void sweep(cc_hierarchy* H, int l, int& cur, bool zero, const T* ec, cudaStream_
   T* in = ubuf<T>(L, cur);
   T* out = ubuf<T>(L, 1 - cur);
   bool timed = H->timing && l == 0;
+  if (L.fused && !timed) {
+    launch_smooth<T>(L, in, out, bbuf<T>(L), ec, zero, s);
+    cur = 1 - cur;
+    return;
+  }
   if (timed) {
     if (H->ev_used == H->ev.size()) {
       cudaEvent_t a, b;
@@ -782,8 +883,13 @@ void bottom(cc_hierarchy* H, int l, int cur, cudaStream_t s) {
 
 // Alg. 2 (gamma = 1) or its W form (gamma = 2) on level l; cur[l] tracks the
 // buffer that holds u.
+// With pre, the stencil cells of the first pre-sweep from the zero initial
+// guess were written by the kernel that made this level's right-hand side
+// (the restriction, or the FP64 residual of the refinement loop); only its
+// block solve is left.
 template <class T>
-void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaStream_t s) {
+void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaStream_t s,
+                 bool pre = false) {
   const int nl = (int)H->lv.size();
   Level& L = *H->lv[l];
   if (l == nl - 1) {
@@ -794,20 +900,30 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
   const int gamma = H->opt.cycle == CC_CYCLE_W ? 2 : 1;
   bool z = zero;
   for (int k = 0; k < nu1; ++k) {
-    sweep<T>(H, l, cur[l], z, (const T*)nullptr, s);
+    if (k == 0 && pre) {
+      block_solve<T>(L, ubuf<T>(L, 1 - cur[l]), bbuf<T>(L), s);
+      cur[l] = 1 - cur[l];
+    } else {
+      sweep<T>(H, l, cur[l], z, (const T*)nullptr, s);
+    }
     z = false;
   }
   if (z) {   // nu1 == 0 on a zero initial guess: materialise u = 0
     CK(cudaMemsetAsync(ubuf<T>(L, cur[l]), 0, L.nn * sizeof(T), s));
   }
   Level& C = *H->lv[l + 1];
+  // the coarse level's first visit starts from zero: its first sweep is
+  // written by the restriction kernel (not on the bottom level, which has none)
+  const bool fuse_c = l + 1 < nl - 1 && nu1 > 0;
+  T* uc = fuse_c ? ubuf<T>(C, 1 - cur[l + 1]) : nullptr;
+  const T wd_c = sparams<T>(C).omega_over_diag;
   if (L.sp.cross)
     pdl_launch(k_resid_restrict<T, true>, tiles(L.n), TX * TY, 0, s, ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
-                                                              C.cls, bbuf<T>(C), sparams<T>(L));
+               C.cls, bbuf<T>(C), sparams<T>(L), uc, wd_c);
   else
     pdl_launch(k_resid_restrict<T, false>, tiles(L.n), TX * TY, 0, s, ubuf<T>(L, cur[l]), bbuf<T>(L), L.cls,
-                                                               C.cls, bbuf<T>(C), sparams<T>(L));
-  for (int g = 0; g < gamma; ++g) cycle_level<T>(H, l + 1, cur, g == 0, s);
+               C.cls, bbuf<T>(C), sparams<T>(L), uc, wd_c);
+  for (int g = 0; g < gamma; ++g) cycle_level<T>(H, l + 1, cur, g == 0, s, g == 0 && fuse_c);
   // merged-away coarse cells already hold their owner's value (written by
   // the block solve, or by the alias rows of the bottom matrix)
   T* ec = ubuf<T>(C, cur[l + 1]);
@@ -818,14 +934,19 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
   for (int k = 0; k < nu2; ++k) sweep<T>(H, l, cur[l], false, k == 0 ? ec : (const T*)nullptr, s);
 }
 
-// FP64 residual r = b - A u on the finest level, max |r| into d_norm[0]
+// FP64 residual r = b - A u on the finest level, max |r| into d_norm[0]; with
+// e0, also the stencil-cell part of the first sweep of the next cycle on
+// A e = r from e = 0 (wd = omega / D in Tout)
 template <class Tout>
-void residual64(cc_hierarchy* H, const double* u, const double* b, Tout* r, cudaStream_t s) {
+void residual64(cc_hierarchy* H, const double* u, const double* b, Tout* r, cudaStream_t s,
+                Tout* e0 = nullptr, Tout wd = Tout(0)) {
   Level& L = *H->lv[0];
   if (L.sp.cross)
-    pdl_launch(k_resid<double, Tout, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm);
+    pdl_launch(k_resid<double, Tout, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm,
+               e0, wd);
   else
-    pdl_launch(k_resid<double, Tout, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm);
+    pdl_launch(k_resid<double, Tout, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm,
+               e0, wd);
   if (L.plan.m)
     pdl_launch(k_block_resid<Tout>, nblk(L.plan.m), 256, 0, s, L.plan.m, L.brow_cell, L.brow_ptr, L.brow_col,
                                                        L.brow_val, u, b, r, H->d_norm);
@@ -848,6 +969,12 @@ double read_norm(cc_hierarchy* H, cudaStream_t s) {
   return d;
 }
 
+// Mixed mode: the FP64 residual kernel also writes the stencil cells of the
+// next FP32 cycle's first sweep (into u32[1], its output buffer; the cycle
+// starts in buffer 0) when that cycle has a pre-sweep on the finest level.
+bool mixed_pre(cc_hierarchy* H) { return H->opt.nu1 > 0 && H->lv.size() > 1; }
+float* mixed_e0(cc_hierarchy* H) { return mixed_pre(H) ? H->lv[0]->u32[1] : nullptr; }
+
 // one iteration of the solve loop, recorded for graph capture or launched
 // directly: FP64 mode: cycle on (u, b) then r = b - A u; mixed mode:
 // r = b - A u (FP64, written as the FP32 cycle right-hand side), FP32 cycle
@@ -864,9 +991,9 @@ void iteration(cc_hierarchy* H, bool mixed, cudaStream_t s) {
                          cudaMemcpyDeviceToDevice, s));
     residual64<double>(H, L.u64[H->cur64], L.b64, H->r64, s);
   } else {
-    cycle_level<float>(H, 0, cur, true, s);
+    cycle_level<float>(H, 0, cur, true, s, mixed_pre(H));
     pdl_launch(k_update<float>, nblk(L.nn), 256, 0, s, L.u64[H->cur64], L.u32[cur[0]], L.cls, L.nn);
-    residual64<float>(H, L.u64[H->cur64], L.b64, L.b32, s);
+    residual64<float>(H, L.u64[H->cur64], L.b64, L.b32, s, mixed_e0(H), L.spf.omega_over_diag);
   }
 }
 
@@ -888,7 +1015,7 @@ cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* 
   // residual of the initial guess (in the mixed mode it is also the first
   // FP32 right-hand side)
   CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
-  if (mixed) residual64<float>(H, L.u64[0], L.b64, L.b32, s);
+  if (mixed) residual64<float>(H, L.u64[0], L.b64, L.b32, s, mixed_e0(H), L.spf.omega_over_diag);
   else residual64<double>(H, L.u64[0], L.b64, H->r64, s);
   rel = read_norm(H, s) / bn;
   first = rel;
@@ -1156,6 +1283,23 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       if (l + 1 < H->lv.size()) {
         L.blk.d64 = upload_block<double>(H->pool, L.plan, s);
         L.blk.d32 = upload_block<float>(H->pool, L.plan, s);
+        // sweep and dense block solve in one launch (k_smooth) on the grids
+        // that the 32 x 8 tile sweep serves
+        std::vector<int> qcell, fptr, fidx;
+        std::vector<double> fval;
+        if (fuse_max_m() > 0 && L.plan.m > 0 && L.plan.m <= fuse_max_m() && L.plan.dense &&
+            L.n < 512 && build_frontier(L.plan, cls, qcell, fptr, fidx, fval)) {
+          const size_t words = qcell.size() + (size_t)L.plan.m;
+          if (words * sizeof(double) <= 96 * 1024) {
+            L.fr64 = upload_frontier<double>(H->pool, qcell, fptr, fidx, fval, s);
+            L.fr32 = upload_frontier<float>(H->pool, qcell, fptr, fidx, fval, s);
+            L.fuse_smem[0] = words * sizeof(double);
+            L.fuse_smem[1] = words * sizeof(float);
+            L.fuse_nb = std::min(128, std::max(1, (L.plan.m + 15) / 16));
+            smooth_smem_limit((int)L.fuse_smem[0]);
+            L.fused = true;
+          }
+        }
       }
       if (!D.block.empty()) {
         L.brow_cell = H->pool.upload(D.block, s);
@@ -1420,9 +1564,11 @@ cc_status cc_residual(cc_handle H, int l, const double* u, const double* b, doub
   try {
     Level& L = *H->lv[l];
     if (L.sp.cross)
-      pdl_launch(k_resid<double, double, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr);
+      pdl_launch(k_resid<double, double, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr,
+                 (double*)nullptr, 0.0);
     else
-      pdl_launch(k_resid<double, double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr);
+      pdl_launch(k_resid<double, double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr,
+                 (double*)nullptr, 0.0);
     if (!L.disc.block.empty())
       pdl_launch(k_block_resid<double>, nblk((int64_t)L.disc.block.size()), 256, 0, s, 
           (int)L.disc.block.size(), L.brow_cell, L.brow_ptr, L.brow_col, L.brow_val, u, b, r, nullptr);
@@ -1457,9 +1603,11 @@ cc_status cc_restrict_residual(cc_handle H, int l, const double* u, const double
     Level& L = *H->lv[l];
     Level& C = *H->lv[l + 1];
     if (L.sp.cross)
-      pdl_launch(k_resid_restrict<double, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, C.cls, rc, L.sp);
+      pdl_launch(k_resid_restrict<double, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, C.cls, rc, L.sp,
+                 (double*)nullptr, 0.0);
     else
-      pdl_launch(k_resid_restrict<double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, C.cls, rc, L.sp);
+      pdl_launch(k_resid_restrict<double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, C.cls, rc, L.sp,
+                 (double*)nullptr, 0.0);
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;

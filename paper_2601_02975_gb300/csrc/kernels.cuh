@@ -80,54 +80,59 @@ __device__ __forceinline__ T cell_value(const T* __restrict__ u, const T* __rest
   return v;
 }
 
+// Value at (gx, gy) of the extended grid: a cell of u (+ I(ec)), or, beyond
+// one box wall, the homogeneous part of that wall's ghost formula; 0 beyond
+// two walls (no stencil cell reaches there: b != 0 puts the box-corner cells
+// in the exactly solved block).
+template <class T>
+__device__ __forceinline__ T halo_value(const T* __restrict__ u, const T* __restrict__ ec,
+                                        const StencilP<T>& P, int gx, int gy, bool zero) {
+  const int n = P.n;
+  const bool ox = gx < 0 || gx >= n, oy = gy < 0 || gy >= n;
+  if (!ox && !oy) return cell_value(u, ec, n, gx, gy, zero);
+  T acc = T(0);
+  if (ox != oy && n >= 4) {
+    int w, t, m;
+    if (gx >= n) { w = 1; t = gy; m = gx - n; }
+    else if (gx < 0) { w = 3; t = gy; m = -gx - 1; }
+    else if (gy >= n) { w = 2; t = gx; m = gy - n; }
+    else { w = 0; t = gx; m = -gy - 1; }
+    if (m > 1) return T(0);   // beyond the two ghost layers (tile padding only)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int cx, cy;
+      switch (w) {
+        case 0: cx = t; cy = q; break;
+        case 1: cx = n - 1 - q; cy = t; break;
+        case 2: cx = t; cy = n - 1 - q; break;
+        default: cx = q; cy = t; break;
+      }
+      acc += P.gh[w][m][q] * cell_value(u, ec, n, cx, cy, zero);
+    }
+  }
+  return acc;
+}
+
 template <class T, int SHT = SY>
 __device__ __forceinline__ void load_tile(T (*s)[SX], const T* __restrict__ u,
                                           const T* __restrict__ ec, const StencilP<T>& P,
                                           int x0, int y0, bool zero) {
-  const int n = P.n;
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < SX * SHT; idx += blockDim.x) {
     int ly = idx / SX, lx = idx % SX;
-    int gx = x0 + lx - HALO, gy = y0 + ly - HALO;
-    bool ox = gx < 0 || gx >= n, oy = gy < 0 || gy >= n;
-    T v = T(0);
-    if (!ox && !oy) {
-      v = cell_value(u, ec, n, gx, gy, zero);
-    } else if (ox != oy) {
-      // ghost beyond one wall: homogeneous part of the wall formula
-      int w, t, m;
-      if (gx >= n) { w = 1; t = gy; m = gx - n; }
-      else if (gx < 0) { w = 3; t = gy; m = -gx - 1; }
-      else if (gy >= n) { w = 2; t = gx; m = gy - n; }
-      else { w = 0; t = gx; m = -gy - 1; }
-      T acc = T(0);
-      if (n >= 4) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int cx, cy;
-          switch (w) {
-            case 0: cx = t; cy = q; break;
-            case 1: cx = n - 1 - q; cy = t; break;
-            case 2: cx = t; cy = n - 1 - q; break;
-            default: cx = q; cy = t; break;
-          }
-          acc += P.gh[w][m][q] * cell_value(u, ec, n, cx, cy, zero);
-        }
-      }
-      v = acc;
-    }
-    s[ly][lx] = v;
+    s[ly][lx] = halo_value(u, ec, P, x0 + lx - HALO, y0 + ly - HALO, zero);
   }
 }
 
-template <class T, bool CROSS>
-__device__ __forceinline__ T apply_A(const T (*s)[SX], const T* w, int lx, int ly) {
-  // lx, ly: tile-interior coordinates (0-based)
-  const int cx = lx + HALO, cy = ly + HALO;
-  T acc = w[2 * 5 + 0] * s[cy][cx - 2] + w[2 * 5 + 1] * s[cy][cx - 1] +
-        w[2 * 5 + 2] * s[cy][cx] + w[2 * 5 + 3] * s[cy][cx + 1] + w[2 * 5 + 4] * s[cy][cx + 2];
-  acc += w[0 * 5 + 2] * s[cy - 2][cx] + w[1 * 5 + 2] * s[cy - 1][cx] +
-         w[3 * 5 + 2] * s[cy + 1][cx] + w[4 * 5 + 2] * s[cy + 2][cx];
+// (A u) at one cell from the values v(di, dj) of its 5 x 5 neighbourhood, in
+// one fixed order of the terms, so that the tile kernels and the point
+// evaluation below give the same bits.
+template <class T, bool CROSS, class V>
+__device__ __forceinline__ T apply_A_by(const T* w, V v) {
+  T acc = w[2 * 5 + 0] * v(-2, 0) + w[2 * 5 + 1] * v(-1, 0) + w[2 * 5 + 2] * v(0, 0) +
+          w[2 * 5 + 3] * v(1, 0) + w[2 * 5 + 4] * v(2, 0);
+  acc += w[0 * 5 + 2] * v(0, -2) + w[1 * 5 + 2] * v(0, -1) + w[3 * 5 + 2] * v(0, 1) +
+         w[4 * 5 + 2] * v(0, 2);
   if (CROSS) {
 #pragma unroll
     for (int dj = -2; dj <= 2; ++dj) {
@@ -135,11 +140,31 @@ __device__ __forceinline__ T apply_A(const T (*s)[SX], const T* w, int lx, int l
 #pragma unroll
       for (int di = -2; di <= 2; ++di) {
         if (di == 0) continue;
-        acc += w[(dj + 2) * 5 + (di + 2)] * s[cy + dj][cx + di];
+        acc += w[(dj + 2) * 5 + (di + 2)] * v(di, dj);
       }
     }
   }
   return acc;
+}
+
+template <class T, bool CROSS>
+__device__ __forceinline__ T apply_A(const T (*s)[SX], const T* w, int lx, int ly) {
+  // lx, ly: tile-interior coordinates (0-based)
+  const int cx = lx + HALO, cy = ly + HALO;
+  return apply_A_by<T, CROSS>(w, [&](int di, int dj) { return s[cy + dj][cx + di]; });
+}
+
+// One Jacobi update (Eq. 5.7) of the stencil cell (gx, gy) evaluated straight
+// from global memory: what the tile sweep writes there.
+template <class T, bool CROSS>
+__device__ __forceinline__ T sweep_point(const T* __restrict__ u, const T* __restrict__ ec,
+                                         const T* __restrict__ b, const StencilP<T>& P, int gx,
+                                         int gy, bool zero) {
+  T Au = apply_A_by<T, CROSS>(P.w, [&](int di, int dj) {
+    return halo_value(u, ec, P, gx + di, gy + dj, zero);
+  });
+  T uc = cell_value(u, ec, P.n, gx, gy, zero);
+  return uc + P.omega_over_diag * (b[(size_t)gy * P.n + gx] - Au);
 }
 
 // ---- a1: weighted Jacobi sweep on stencil cells (Eq. 5.7) --------------------
@@ -263,11 +288,13 @@ k_sweep_w(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict
 // ---- a4: residual and restriction (Eq. 5.10) ---------------------------------
 // r = b - A u on stencil cells, 0 on block and empty cells (the block residual
 // is zero after a block-smoother sweep); rc = average of the 4 children,
-// 0 on empty coarse cells.
+// 0 on empty coarse cells.  With uc, also the stencil-cell part of the coarse
+// level's first sweep (wd_c = omega / D of the coarse level).
 template <class T, bool CROSS>
 __global__ void __launch_bounds__(TX * TY)
 k_resid_restrict(const T* __restrict__ u, const T* __restrict__ b, const uint8_t* __restrict__ cls,
-                 const uint8_t* __restrict__ cls_c, T* __restrict__ rc, StencilP<T> P) {
+                 const uint8_t* __restrict__ cls_c, T* __restrict__ rc, StencilP<T> P,
+                 T* __restrict__ uc, T wd_c) {
   pdl_enter();
   __shared__ T s[SY][SX];
   __shared__ T r[TY][TX];
@@ -291,7 +318,11 @@ k_resid_restrict(const T* __restrict__ u, const T* __restrict__ b, const uint8_t
       const size_t kc = (size_t)gcy * nc + gcx;
       T v = T(0.25) * (r[2 * cy][2 * cx] + r[2 * cy][2 * cx + 1] + r[2 * cy + 1][2 * cx] +
                        r[2 * cy + 1][2 * cx + 1]);
-      rc[kc] = cls_c[kc] == C_EMPTY ? T(0) : v;
+      const uint8_t cc = cls_c[kc];
+      rc[kc] = cc == C_EMPTY ? T(0) : v;
+      // the coarse level's first sweep from a zero initial guess is pointwise,
+      // u_c = omega / D_c * b_c (Eq. 5.7 with u = 0): written here with it
+      if (uc && cc == C_STENCIL) uc[kc] = wd_c * v;
     }
   }
   pdl_exit();
@@ -300,6 +331,8 @@ k_resid_restrict(const T* __restrict__ u, const T* __restrict__ b, const uint8_t
 // ---- a8 / Eq. 4.23: residual on stencil cells, max-norm ----------------------
 // r = b - A u on stencil cells (Tin arithmetic), 0 on empty cells; block cells
 // are left to k_block_resid.  |r| is folded into *rmax (as ordered bits).
+// With e0, also the stencil-cell part of the first sweep of a cycle on the
+// residual equation A e = r from e = 0: e0 = wd r (wd = omega / D).
 __device__ __forceinline__ void atomic_max_abs(unsigned long long* p, double v) {
   atomicMax(p, (unsigned long long)__double_as_longlong(fabs(v)));
 }
@@ -307,7 +340,8 @@ __device__ __forceinline__ void atomic_max_abs(unsigned long long* p, double v) 
 template <class Tin, class Tout, bool CROSS>
 __global__ void __launch_bounds__(TX * TY)
 k_resid(const Tin* __restrict__ u, const Tin* __restrict__ b, const uint8_t* __restrict__ cls,
-        Tout* __restrict__ r, StencilP<Tin> P, unsigned long long* rmax) {
+        Tout* __restrict__ r, StencilP<Tin> P, unsigned long long* rmax, Tout* __restrict__ e0,
+        Tout wd) {
   pdl_enter();
   __shared__ Tin s[SY][SX];
   __shared__ double red[TX * TY / 32];
@@ -323,6 +357,7 @@ k_resid(const Tin* __restrict__ u, const Tin* __restrict__ b, const uint8_t* __r
     if (c == C_STENCIL) {
       Tin rv = b[k] - apply_A<Tin, CROSS>(s, P.w, lx, ly);
       r[k] = (Tout)rv;
+      if (e0) e0[k] = wd * (Tout)rv;
       av = fabs((double)rv);
     } else if (c == C_EMPTY) {
       r[k] = Tout(0);
@@ -556,6 +591,119 @@ __global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
   for (int c = lane; c < B.m; c += 32) acc += A[c] * t[c];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) block_write(B, u, r, acc);
+  pdl_exit();
+}
+
+// ---- a1 + a3 fused: one block-smoother sweep (Def. 5.6) in one launch -------
+// For a block small enough to hold its dense inverse.  The first ntiles CTAs
+// run the Jacobi sweep on 32 x 8 tiles (as k_sweep).  The remaining CTAs solve
+// the block exactly: the block rows couple to a few stencil cells (the
+// frontier) whose new values the sweep is writing at the same time, so each
+// of these CTAs evaluates the Jacobi update of every frontier cell from u_in
+// itself (sweep_point, the same arithmetic), gathers t = b - A(block, rest)
+// u_new in shared memory and applies its share of the rows of inv(A_block).
+// No CTA reads what another writes, so the sweep and the block solve need no
+// grid-wide ordering between them.
+struct FrontierDev {
+  int nq;
+  const int* qcell;        // [nq] grid cell of each frontier cell
+  const int* fptr;         // [m+1] gather rows over frontier indices (CSR, the
+  const int* fidx;         //       term order of block_rhs)
+  const void* fval;        // T
+};
+
+template <class T, bool CROSS>
+__global__ void __launch_bounds__(TX * TY)
+k_smooth(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ b,
+         const uint8_t* __restrict__ cls, const T* __restrict__ ec, StencilP<T> P, int zero,
+         BlockDev B, FrontierDev F, int ntiles) {
+  pdl_enter();
+  const int n = P.n;
+  if ((int)blockIdx.x < ntiles) {
+    __shared__ T s[SY][SX];
+    const int tpr = (n + TX - 1) / TX;
+    const int x0 = (blockIdx.x % tpr) * TX, y0 = (blockIdx.x / tpr) * TY;
+    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+    const int gx = x0 + lx, gy = y0 + ly;
+    const bool in = gx < n && gy < n;
+    const size_t k = (size_t)gy * n + gx;
+    const uint8_t c = in ? cls[k] : (uint8_t)C_EMPTY;
+    const T bv = in ? b[k] : T(0);
+    load_tile<T>(s, u_in, ec, P, x0, y0, zero != 0);
+    __syncthreads();
+    if (c == C_STENCIL) {
+      T Au = apply_A<T, CROSS>(s, P.w, lx, ly);
+      u_out[k] = s[ly + HALO][lx + HALO] + P.omega_over_diag * (bv - Au);
+    }
+    pdl_exit();
+    return;
+  }
+  extern __shared__ unsigned char smem_raw[];
+  T* ut = reinterpret_cast<T*>(smem_raw);   // [nq] new frontier values
+  T* t = ut + F.nq;                         // [m]  gathered right-hand side
+  for (int q = threadIdx.x; q < F.nq; q += blockDim.x) {
+    const int kq = F.qcell[q];
+    ut[q] = sweep_point<T, CROSS>(u_in, ec, b, P, kq % n, kq / n, zero != 0);
+  }
+  __syncthreads();
+  const T* fval = static_cast<const T*>(F.fval);
+  for (int p = threadIdx.x; p < B.m; p += blockDim.x) {
+    T acc = b[B.cell[p]];
+    for (int e = F.fptr[p]; e < F.fptr[p + 1]; ++e) acc -= fval[e] * ut[F.fidx[e]];
+    t[p] = acc;
+  }
+  __syncthreads();
+  const int j = blockIdx.x - ntiles, nb = gridDim.x - ntiles;
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int r = j * wpb + (threadIdx.x >> 5); r < B.m; r += nb * wpb) {
+    const T* A = static_cast<const T*>(B.ainv) + (size_t)r * B.m;
+    T acc = T(0);
+#pragma unroll 4
+    for (int c = lane; c < B.m; c += 32) acc += A[c] * t[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) block_write(B, u_out, r, acc);
+  }
+  pdl_exit();
+}
+
+// Dense block solve in one launch: every CTA gathers the whole right-hand
+// side t = b - A(block, rest) u into its shared memory (the gather reads no
+// block cell, so rows written meanwhile by other CTAs do not disturb it), then
+// applies its share of the rows of inv(A_block), one warp per row.  Each warp
+// loads the first PF entries per lane of its row of the inverse into
+// registers before the gather, so those loads overlap it.
+template <class T>
+__global__ void __launch_bounds__(1024) k_block_dense(BlockDev B, const T* __restrict__ b,
+                                                      T* __restrict__ u) {
+  constexpr int PF = 64 / (int)sizeof(T);   // 16 floats or 8 doubles per lane
+  pdl_enter();
+  extern __shared__ unsigned char smem_raw[];
+  T* t = reinterpret_cast<T*>(smem_raw);
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  const int r0 = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const T* A = static_cast<const T*>(B.ainv) + (size_t)r0 * B.m;
+  T a[PF];
+#pragma unroll
+  for (int j = 0; j < PF; ++j) {
+    const int c = lane + 32 * j;
+    a[j] = r0 < B.m && c < B.m ? A[c] : T(0);
+  }
+  for (int p = threadIdx.x; p < B.m; p += blockDim.x) t[p] = block_rhs(B, b, u, p);
+  __syncthreads();
+  for (int r = r0; r < B.m; r += gridDim.x * wpb) {
+    const T* Ar = static_cast<const T*>(B.ainv) + (size_t)r * B.m;
+    T acc = T(0);
+    if (r == r0) {
+#pragma unroll
+      for (int j = 0; j < PF; ++j) acc += a[j] * t[min(lane + 32 * j, B.m - 1)];
+      for (int c = lane + 32 * PF; c < B.m; c += 32) acc += Ar[c] * t[c];
+    } else {
+#pragma unroll 8
+      for (int c = lane; c < B.m; c += 32) acc += Ar[c] * t[c];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) block_write(B, u, r, acc);
+  }
   pdl_exit();
 }
 
