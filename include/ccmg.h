@@ -87,6 +87,8 @@ typedef struct {
   int host_only;       /* build the tables on the host only, no device work (0);
                           such a handle answers cc_query, cc_cell_types,
                           cc_quadrature_nodes and cc_level_tables only */
+  int fmg_cycle;       /* with cycle = CC_CYCLE_FMG: the cycle Alg. 3 runs on each
+                          level, CC_CYCLE_V (the paper's, default) or CC_CYCLE_W */
 } cc_options;
 
 /* Sizes of a hierarchy. */

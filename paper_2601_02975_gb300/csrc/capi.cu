@@ -887,9 +887,19 @@ void bottom(cc_hierarchy* H, int l, int cur, cudaStream_t s) {
 // guess were written by the kernel that made this level's right-hand side
 // (the restriction, or the FP64 residual of the refinement loop); only its
 // block solve is left.
+// The cycle Alg. 2 repeats: gamma = 1 (V) or 2 (W); Alg. 3 runs the cycle
+// that fmg_cycle names.
+int cycle_gamma(const cc_options& o) {
+  const int c = o.cycle == CC_CYCLE_FMG ? o.fmg_cycle : o.cycle;
+  return c == CC_CYCLE_W ? 2 : 1;
+}
+
+// With ec0, the initial guess is u + I(ec0) (0 + I(ec0) with zero), the
+// interpolated coarse solution of Alg. 3; the interpolation is fused into the
+// first pre-sweep.
 template <class T>
 void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaStream_t s,
-                 bool pre = false) {
+                 bool pre = false, const T* ec0 = nullptr) {
   const int nl = (int)H->lv.size();
   Level& L = *H->lv[l];
   if (l == nl - 1) {
@@ -897,20 +907,22 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
     return;
   }
   const int nu1 = H->opt.nu1, nu2 = H->opt.nu2;
-  const int gamma = H->opt.cycle == CC_CYCLE_W ? 2 : 1;
+  const int gamma = cycle_gamma(H->opt);
   bool z = zero;
   for (int k = 0; k < nu1; ++k) {
     if (k == 0 && pre) {
       block_solve<T>(L, ubuf<T>(L, 1 - cur[l]), bbuf<T>(L), s);
       cur[l] = 1 - cur[l];
     } else {
-      sweep<T>(H, l, cur[l], z, (const T*)nullptr, s);
+      sweep<T>(H, l, cur[l], z, k == 0 ? ec0 : (const T*)nullptr, s);
     }
     z = false;
   }
   if (z) {   // nu1 == 0 on a zero initial guess: materialise u = 0
     CK(cudaMemsetAsync(ubuf<T>(L, cur[l]), 0, L.nn * sizeof(T), s));
   }
+  if (nu1 == 0 && ec0)
+    pdl_launch(k_prolong_add<T>, nblk(L.nn), 256, 0, s, ubuf<T>(L, cur[l]), ec0, L.cls, L.n);
   Level& C = *H->lv[l + 1];
   // the coarse level's first visit starts from zero: its first sweep is
   // written by the restriction kernel (not on the bottom level, which has none)
@@ -933,6 +945,18 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
   }
   for (int k = 0; k < nu2; ++k) sweep<T>(H, l, cur[l], false, k == 0 ? ec : (const T*)nullptr, s);
 }
+
+// b of level l + 1 = restriction of r (a right-hand side of level l, Alg. 3)
+template <class Tin, class Tout>
+void restrict_rhs(cc_hierarchy* H, int l, const Tin* r, cudaStream_t s) {
+  Level& L = *H->lv[l];
+  Level& C = *H->lv[l + 1];
+  pdl_launch(k_restrict_rhs<Tin, Tout>, nblk(C.nn), 256, 0, s, r, L.cls, C.cls, bbuf<Tout>(C), L.n);
+}
+
+// the solution buffer of level 1
+template <class T>
+T* L1u(cc_hierarchy* H, const std::vector<int>& cur) { return ubuf<T>(*H->lv[1], cur[1]); }
 
 // FP64 residual r = b - A u on the finest level, max |r| into d_norm[0]; with
 // e0, also the stencil-cell part of the first sweep of the next cycle on
@@ -969,10 +993,26 @@ double read_norm(cc_hierarchy* H, cudaStream_t s) {
   return d;
 }
 
+// Alg. 3 below level l0, whose right-hand side is in place: restrict it down
+// to the coarsest level, solve there, and climb back with one cycle per level
+// from the interpolated coarse solution.  The solution of level l0 + 1 is
+// left in its buffer cur[l0 + 1].
+template <class T>
+void fmg_below(cc_hierarchy* H, int l0, std::vector<int>& cur, cudaStream_t s) {
+  const int nl = (int)H->lv.size();
+  for (int l = l0 + 1; l + 1 < nl; ++l) restrict_rhs<T, T>(H, l, bbuf<T>(*H->lv[l]), s);
+  bottom<T>(H, nl - 1, cur[nl - 1], s);
+  for (int l = nl - 2; l > l0; --l)
+    cycle_level<T>(H, l, cur, true, s, false, (const T*)ubuf<T>(*H->lv[l + 1], cur[l + 1]));
+}
+
 // Mixed mode: the FP64 residual kernel also writes the stencil cells of the
 // next FP32 cycle's first sweep (into u32[1], its output buffer; the cycle
-// starts in buffer 0) when that cycle has a pre-sweep on the finest level.
-bool mixed_pre(cc_hierarchy* H) { return H->opt.nu1 > 0 && H->lv.size() > 1; }
+// starts in buffer 0) when that cycle has a pre-sweep on the finest level
+// from a zero initial guess (not in Alg. 3, which starts it from I(e)).
+bool mixed_pre(cc_hierarchy* H) {
+  return H->opt.nu1 > 0 && H->lv.size() > 1 && H->opt.cycle != CC_CYCLE_FMG;
+}
 float* mixed_e0(cc_hierarchy* H) { return mixed_pre(H) ? H->lv[0]->u32[1] : nullptr; }
 
 // one iteration of the solve loop, recorded for graph capture or launched
@@ -983,15 +1023,31 @@ void iteration(cc_hierarchy* H, bool mixed, cudaStream_t s) {
   Level& L = *H->lv[0];
   std::vector<int> cur(H->lv.size(), 0);
   CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
+  const bool fmg = H->opt.cycle == CC_CYCLE_FMG && H->lv.size() > 1;
   if (!mixed) {
     cur[0] = H->cur64;
-    cycle_level<double>(H, 0, cur, false, s);
+    if (fmg) {
+      // u + FMG(r): the finest-level cycle of Alg. 3 on the residual
+      // equation from I(e_1) equals the same cycle on A u = b from
+      // u + I(e_1) (the cycle is affine with error propagator I - N A)
+      restrict_rhs<double, double>(H, 0, H->r64, s);
+      fmg_below<double>(H, 0, cur, s);
+      cycle_level<double>(H, 0, cur, false, s, false, (const double*)L1u<double>(H, cur));
+    } else {
+      cycle_level<double>(H, 0, cur, false, s);
+    }
     if (cur[0] != H->cur64)
       CK(cudaMemcpyAsync(L.u64[H->cur64], L.u64[cur[0]], L.nn * sizeof(double),
                          cudaMemcpyDeviceToDevice, s));
     residual64<double>(H, L.u64[H->cur64], L.b64, H->r64, s);
   } else {
-    cycle_level<float>(H, 0, cur, true, s, mixed_pre(H));
+    if (fmg) {
+      restrict_rhs<float, float>(H, 0, L.b32, s);
+      fmg_below<float>(H, 0, cur, s);
+      cycle_level<float>(H, 0, cur, true, s, false, (const float*)L1u<float>(H, cur));
+    } else {
+      cycle_level<float>(H, 0, cur, true, s, mixed_pre(H));
+    }
     pdl_launch(k_update<float>, nblk(L.nn), 256, 0, s, L.u64[H->cur64], L.u32[cur[0]], L.cls, L.nn);
     residual64<float>(H, L.u64[H->cur64], L.b64, L.b32, s, mixed_e0(H), L.spf.omega_over_diag);
   }
@@ -1155,6 +1211,7 @@ void cc_default_options(cc_options* o) {
   o->max_cycles = 100;
   o->use_graphs = 1;
   o->host_only = 0;
+  o->fmg_cycle = CC_CYCLE_V;
 }
 
 const char* cc_last_error_string(void) { return t_last_error; }
@@ -1186,7 +1243,8 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   cc_default_options(&o);
   if (opt) o = *opt;
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 == 0 || o.min_coarse_n < 4 || o.max_cycles < 1 ||
-      !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3))
+      !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3) ||
+      (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W))
     return CC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   cc_hierarchy* H = new cc_hierarchy();

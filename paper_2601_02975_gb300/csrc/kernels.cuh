@@ -328,6 +328,24 @@ k_resid_restrict(const T* __restrict__ u, const T* __restrict__ b, const uint8_t
   pdl_exit();
 }
 
+// ---- Alg. 3 descent: restriction of a right-hand side (Eq. 5.10) -------------
+// rc = average of the 4 children (empty children count 0), 0 on empty coarse
+// cells.  Unlike the cycle's restriction, block cells keep their value: the
+// FMG cycle restricts the residual of the iterate as it is.
+template <class Tin, class Tout>
+__global__ void k_restrict_rhs(const Tin* __restrict__ r, const uint8_t* __restrict__ cls,
+                               const uint8_t* __restrict__ cls_c, Tout* __restrict__ rc, int n) {
+  pdl_enter();
+  const int nc = n >> 1;
+  const int64_t kc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kc >= (int64_t)nc * nc) return;
+  const int cx = (int)(kc % nc), cy = (int)(kc / nc);
+  const size_t k00 = (size_t)(2 * cy) * n + 2 * cx, k10 = k00 + n;
+  auto v = [&](size_t k) { return cls[k] == C_EMPTY ? Tin(0) : r[k]; };
+  const Tin s = Tin(0.25) * (v(k00) + v(k10) + v(k00 + 1) + v(k10 + 1));
+  rc[kc] = cls_c[kc] == C_EMPTY ? Tout(0) : (Tout)s;
+}
+
 // ---- a8 / Eq. 4.23: residual on stencil cells, max-norm ----------------------
 // r = b - A u on stencil cells (Tin arithmetic), 0 on empty cells; block cells
 // are left to k_block_resid.  |r| is folded into *rmax (as ordered bits).

@@ -186,6 +186,51 @@ def test_solve_fp64_and_mixed(name, n, mc, cyc):
     assert errm <= 1.1 * err_o + 1e-14, (errm, err_o)
 
 
+@pytest.mark.parametrize("name,n,mc", [("poisson", 64, 4), ("disk", 64, 16), ("ellipses0", 64, 16)])
+@pytest.mark.parametrize("inner", [1, 2])
+def test_fmg_parity_fp64(name, n, mc, inner):
+    """Alg. 3 iterated as u <- u + FMG(b - A u), in FP64, with V (the paper's)
+    or W cycles inside: the GPU iterate after one and after three iterations
+    matches the oracle's to 1e-11 relative max-norm."""
+    P = _problem(name)
+    bo = None
+    for k in (1, 3):
+        H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                  default_options(min_coarse_n=mc, cycle=3, fmg_cycle=inner,
+                                                  max_cycles=k))
+        if bo is None:
+            O = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=mc)
+            assert H.info.n_levels == O.nl
+            bo = _oracle_rhs(O, P)
+            ro = M.solve(O, bo, tol=0.0, gamma=inner, method="fmg", max_cycles=3, keep_iterates=True)
+        f, g, _, _ = _gpu_rhs(H, P)
+        u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+        r = H.solve(_t(f), _t(g), u, 1e-300)
+        assert r.cycles == k
+        want = ro.iterates[k - 1]
+        err = np.abs(_np(u, n) - want).max() / np.abs(want).max()
+        assert err < 1e-11, (k, err)
+
+
+@pytest.mark.parametrize("name,n,mc", [("disk", 64, 16), ("ellipses0", 128, 16)])
+def test_fmg_solve_mixed(name, n, mc):
+    """The mixed-precision FMG solve (FP32 Alg. 3 inside FP64 refinement, W
+    cycles inside) reaches 1e-10 relative residual with an error against the
+    exact cell averages within 1.1x of the oracle's FMG solve."""
+    P, H, O = _pair(name, n, mc, cycle=3, fmg_cycle=2, precision=1)
+    f, g, ue, _ = _gpu_rhs(H, P)
+    bo = _oracle_rhs(O, P)
+    ro = M.solve(O, bo, tol=1e-10, gamma=2, method="fmg")
+    d = O.levels[0]
+    err_o = np.abs(ro.u - D.cell_averages(d.lev, P.u))[d.lev.present].max()
+    u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    r = H.solve(_t(f), _t(g), u, 1e-10)
+    assert r.status == 0 and r.rel_res < 1e-10
+    assert abs(r.cycles - len(ro.history)) <= 1
+    err = np.abs(_np(u, n) - ue)[d.lev.present].max()
+    assert err <= 1.1 * err_o + 1e-14, (err, err_o)
+
+
 def test_solve_host_and_submit_match_device_solve():
     P, H, O = _pair("disk", 64, 16, cycle=2, precision=1)
     f, g, ue, _ = _gpu_rhs(H, P)
