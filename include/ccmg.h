@@ -284,14 +284,23 @@ cc_status cc_smooth_noalloc(cc_handle h, int level, double* d_u, const double* d
 cc_status cc_level_tables(cc_handle h, int level, uint8_t* h_kind, int* h_lattice,
                           double* h_beta, int* n_plg);
 
+/* Kernels that cc_kernel_timing can time. */
+enum { CC_TIME_OFF = 0, CC_TIME_FINE_SWEEP = 1, CC_TIME_BLOCK_DENSE = 2 };
+
 /*
- * cc_kernel_timing: when enabled, the library records CUDA events around
- * every launch of the finest-level smoothing sweep kernel and accumulates
- * their durations; cc_kernel_timing_read returns the launch count, the total
- * milliseconds and the algorithmic bytes one launch moves (reads of u and b
- * plus the write of u, at the cycle's precision).
+ * cc_kernel_timing: with which = CC_TIME_FINE_SWEEP the library records CUDA
+ * events around every launch of the finest-level Jacobi sweep kernel (Eq.
+ * 5.7); with CC_TIME_BLOCK_DENSE around every one-launch dense block solve
+ * (Eq. 5.8, blocks of up to 1024 cells, any level); CC_TIME_OFF stops.  The
+ * events are recorded on the solve's stream, inside its CUDA graph, so host
+ * launch gaps are not measured, but each interval includes the launch latency
+ * of the kernel it brackets.  cc_kernel_timing_read returns the launch count,
+ * the total milliseconds and the average algorithmic bytes of one launch
+ * (sweep: reads of u and b plus the write of u; block solve: the inverse, the
+ * gather terms, b and the writes; at the cycle's precision).  Enabling resets
+ * the counters.  Errors: CC_ERR_ARG for an unknown kernel.
  */
-cc_status cc_kernel_timing(cc_handle h, int enable);
+cc_status cc_kernel_timing(cc_handle h, int which);
 cc_status cc_kernel_timing_read(cc_handle h, int64_t* launches, double* total_ms,
                                 double* bytes_per_launch);
 

@@ -290,8 +290,9 @@ class Hierarchy:
     def cycle(self, u, b, stream=None):
         _check(lib().cc_cycle(self.h, _ptr(u), _ptr(b), _stream(stream)), "cc_cycle")
 
-    def kernel_timing(self, enable: bool):
-        _check(lib().cc_kernel_timing(self.h, int(enable)), "cc_kernel_timing")
+    def kernel_timing(self, which: int):
+        """0 off, 1 finest-level sweeps, 2 one-launch dense block solves."""
+        _check(lib().cc_kernel_timing(self.h, int(which)), "cc_kernel_timing")
 
     def kernel_timing_read(self):
         n, ms, by = C.c_int64(), C.c_double(), C.c_double()

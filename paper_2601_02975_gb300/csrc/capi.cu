@@ -587,12 +587,15 @@ struct cc_hierarchy {
   unsigned long long* h_norm = nullptr;   // pinned
   int n_g = 0, n_bd = 0;
   int64_t n_dof = 0;
-  // kernel timing
-  bool timing = false;
+  // kernel timing (cc_kernel_timing): which kernel, its event pairs and the
+  // algorithmic bytes of the launch each pair brackets
+  int timing = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  std::vector<double> ev_bytes;
   size_t ev_used = 0;
   int64_t timed_launches = 0;
   double timed_ms = 0;
+  double timed_bytes = 0;
   // level-0 FP64 buffer that holds u during a cycle
   int cur64 = 0;
   // submit/poll worker
@@ -603,9 +606,9 @@ struct cc_hierarchy {
   bool stop = false;
   cudaStream_t wstream = nullptr;
   // cuda graphs of one solve iteration
-  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};   // [timing][mixed]
-  int64_t gexec_launches[4] = {0, 0, 0, 0};   // kernels in one replay of each graph
-  size_t gexec_events[4] = {0, 0, 0, 0};      // timing event pairs in each graph
+  cudaGraphExec_t gexec[6] = {};             // [timed kernel][mixed]
+  int64_t gexec_launches[6] = {};            // kernels in one replay of each graph
+  size_t gexec_events[6] = {};               // timing event pairs in each graph
   cudaStream_t gstream = nullptr;
 };
 
@@ -806,6 +809,27 @@ void smooth_smem_limit(int bytes) {
   limit = bytes;
 }
 
+// event pair around one timed launch (the pairs are created up front by
+// cc_kernel_timing, so none is created while a graph is being captured)
+bool time_begin(cc_hierarchy* H, cudaStream_t s) {
+  if (H->ev_used >= H->ev.size()) return false;
+  CK(cudaEventRecordWithFlags(H->ev[H->ev_used].first, s, cudaEventRecordExternal));
+  return true;
+}
+void time_end(cc_hierarchy* H, cudaStream_t s, double bytes) {
+  CK(cudaEventRecordWithFlags(H->ev[H->ev_used].second, s, cudaEventRecordExternal));
+  H->ev_bytes[H->ev_used] = bytes;
+  ++H->ev_used;
+}
+
+// algorithmic bytes of one one-launch dense block solve: the inverse, the
+// gather terms (column, coefficient, gathered value), b and the cell index of
+// every row, the writes of the block and alias cells
+double dense_block_bytes(const BlockPlan& P, int w) {
+  const double m = P.m, nnz = (double)P.gptr[P.m], na = (double)P.alias_cell.size();
+  return m * m * w + nnz * (4 + 2 * w) + m * (4 + w) + m * w + (m + 1) * 4 + na * (4 + w);
+}
+
 // one block-smoother sweep of a level with a dense block: one launch
 template <class T>
 void launch_smooth(Level& L, const T* in, T* out, const T* b, const T* ec, bool zero,
@@ -822,14 +846,16 @@ void launch_smooth(Level& L, const T* in, T* out, const T* b, const T* ec, bool 
 }
 
 template <class T>
-void block_solve(Level& L, T* u, const T* b, cudaStream_t s) {
+void block_solve(cc_hierarchy* H, Level& L, T* u, const T* b, cudaStream_t s) {
   const BlockDev& B = bdev<T>(L);
   if (B.m == 0) return;
   const BlockPlan& P = L.plan;
   if (P.dense && P.m <= kBlockOneLaunch) {
     // 1024-thread CTAs: every thread gathers at most one row, every warp
     // applies one row of the inverse
+    const bool timed = H->timing == CC_TIME_BLOCK_DENSE && time_begin(H, s);
     pdl_launch(k_block_dense<T>, (unsigned)((P.m + 31) / 32), 1024, (size_t)P.m * sizeof(T), s, B, b, u);
+    if (timed) time_end(H, s, dense_block_bytes(P, (int)sizeof(T)));
     return;
   }
   if (P.dense) {
@@ -850,27 +876,16 @@ void sweep(cc_hierarchy* H, int l, int& cur, bool zero, const T* ec, cudaStream_
   Level& L = *H->lv[l];
   T* in = ubuf<T>(L, cur);
   T* out = ubuf<T>(L, 1 - cur);
-  bool timed = H->timing && l == 0;
+  bool timed = H->timing == CC_TIME_FINE_SWEEP && l == 0;
   if (L.fused && !timed) {
     launch_smooth<T>(L, in, out, bbuf<T>(L), ec, zero, s);
     cur = 1 - cur;
     return;
   }
-  if (timed) {
-    if (H->ev_used == H->ev.size()) {
-      cudaEvent_t a, b;
-      CK(cudaEventCreate(&a));
-      CK(cudaEventCreate(&b));
-      H->ev.push_back({a, b});
-    }
-    CK(cudaEventRecordWithFlags(H->ev[H->ev_used].first, s, cudaEventRecordExternal));
-  }
+  timed = timed && time_begin(H, s);
   launch_sweep<T>(L, in, out, bbuf<T>(L), ec, zero, s);
-  if (timed) {
-    CK(cudaEventRecordWithFlags(H->ev[H->ev_used].second, s, cudaEventRecordExternal));
-    ++H->ev_used;
-  }
-  block_solve<T>(L, out, bbuf<T>(L), s);
+  if (timed) time_end(H, s, 3.0 * sizeof(T) * (double)L.nn);
+  block_solve<T>(H, L, out, bbuf<T>(L), s);
   cur = 1 - cur;
 }
 
@@ -911,7 +926,7 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
   bool z = zero;
   for (int k = 0; k < nu1; ++k) {
     if (k == 0 && pre) {
-      block_solve<T>(L, ubuf<T>(L, 1 - cur[l]), bbuf<T>(L), s);
+      block_solve<T>(H, L, ubuf<T>(L, 1 - cur[l]), bbuf<T>(L), s);
       cur[l] = 1 - cur[l];
     } else {
       sweep<T>(H, l, cur[l], z, k == 0 ? ec0 : (const T*)nullptr, s);
@@ -1077,7 +1092,7 @@ cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* 
   first = rel;
   if (rel < tol) res.status = CC_OK;
   int it = 0;
-  const int gi = (mixed ? 1 : 0) + (H->timing ? 2 : 0);
+  const int gi = (mixed ? 1 : 0) + 2 * H->timing;
   bool use_graph = H->opt.use_graphs != 0;
   for (; res.status != CC_OK && it < H->opt.max_cycles; ++it) {
     if (use_graph) {
@@ -1109,6 +1124,7 @@ cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* 
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, H->ev[i].first, H->ev[i].second));
         H->timed_ms += ms;
+        H->timed_bytes += H->ev_bytes[i];
         ++H->timed_launches;
       }
       if (!use_graph) H->ev_used = 0;
@@ -1789,23 +1805,29 @@ cc_status cc_level_tables(cc_handle H, int l, uint8_t* h_kind, int* h_lattice, d
   return CC_OK;
 }
 
-cc_status cc_kernel_timing(cc_handle H, int enable) {
+cc_status cc_kernel_timing(cc_handle H, int which) {
   if (H && H->opt.host_only) return CC_ERR_ARG;
-  if (!H) return CC_ERR_ARG;
-  H->timing = enable != 0;
+  if (!H || which < CC_TIME_OFF || which > CC_TIME_BLOCK_DENSE) return CC_ERR_ARG;
+  H->timing = which;
   H->ev_used = 0;
   H->timed_launches = 0;
   H->timed_ms = 0;
+  H->timed_bytes = 0;
   try {
-    // one event pair per finest-level sweep of a cycle, created up front so
-    // that none is created during graph capture
-    int per = H->opt.nu1 + H->opt.nu2;
-    while (H->timing && (int)H->ev.size() < per) {
+    // event pairs for every timed launch of one solve iteration, created up
+    // front so that none is created during graph capture: a cycle visits
+    // level l at most 2^l times (W; V and FMG fewer), each visit sweeps
+    // nu1 + nu2 times
+    const int nl = (int)H->lv.size();
+    size_t per = (size_t)(H->opt.nu1 + H->opt.nu2) * ((size_t)1 << std::min(nl, 12)) * 2;
+    if (which == CC_TIME_FINE_SWEEP) per = (size_t)(H->opt.nu1 + H->opt.nu2);
+    while (which != CC_TIME_OFF && H->ev.size() < per) {
       cudaEvent_t a, b;
       CK(cudaEventCreate(&a));
       CK(cudaEventCreate(&b));
       H->ev.push_back({a, b});
     }
+    H->ev_bytes.assign(H->ev.size(), 0.0);
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
 }
@@ -1817,11 +1839,10 @@ cc_status cc_kernel_timing_read(cc_handle H, int64_t* launches, double* total_ms
   try {
     CK(cudaDeviceSynchronize());
   } catch (CudaError&) { return CC_ERR_CUDA; }
-  const int64_t nn = H->lv[0]->nn;
-  const double w = H->opt.precision == CC_PREC_MIXED ? 4.0 : 8.0;
   if (launches) *launches = H->timed_launches;
   if (total_ms) *total_ms = H->timed_ms;
-  if (bytes_per_launch) *bytes_per_launch = 3.0 * w * (double)nn;
+  if (bytes_per_launch)
+    *bytes_per_launch = H->timed_launches ? H->timed_bytes / (double)H->timed_launches : 0.0;
   return CC_OK;
 }
 

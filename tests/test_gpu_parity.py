@@ -281,3 +281,28 @@ def test_step_parity_large_grid():
     H.cycle(ug, bg)
     uc = M.cycle(O, 0, np.zeros((n, n)), bo, 3, 3, 1)
     assert np.abs(_np(ug, n) - uc).max() < 1e-11 * np.abs(uc).max()
+
+
+def test_kernel_timing_leaves_the_solve_unchanged():
+    """Timing events inside the solve graph (finest-level sweeps, or the
+    one-launch dense block solves) change no result bit, and count launches
+    with their algorithmic bytes."""
+    P, H, O = _pair("disk", 256, 32, cycle=2, precision=1)
+    f, g, _, _ = _gpu_rhs(H, P)
+    ft, gt = _t(f), _t(g)
+    u0 = torch.zeros(256 * 256, dtype=torch.float64, device=DEV)
+    r0 = H.solve(ft, gt, u0, 1e-12)
+    for which in (1, 2):
+        H.kernel_timing(which)
+        u = torch.zeros_like(u0)
+        r = H.solve(ft, gt, u, 1e-12)
+        launches, ms, bytes_per = H.kernel_timing_read()
+        H.kernel_timing(0)
+        assert r.cycles == r0.cycles
+        assert torch.equal(u, u0)
+        assert launches > 0 and ms > 0 and bytes_per > 0
+        if which == 1:
+            # 3 FP32 arrays of 256^2; the first pre-sweep of each FP32 cycle
+            # is written by the FP64 residual kernel, so 5 per cycle
+            assert bytes_per == 3 * 4 * 256 * 256
+            assert launches == 5 * r.cycles
