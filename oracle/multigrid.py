@@ -249,30 +249,34 @@ def bottom_solve(H: Hierarchy, b: np.ndarray) -> np.ndarray:
 
 
 def cycle(H: Hierarchy, l: int, u: np.ndarray, b: np.ndarray, nu1: int, nu2: int,
-          gamma: int = 1) -> np.ndarray:
-    """Alg. 2 (gamma = 1: V-cycle; gamma = 2: W-cycle)."""
+          gamma: int = 1, w_depth: int = 0) -> np.ndarray:
+    """Alg. 2 (gamma = 1: V-cycle; gamma = 2: W-cycle).  With w_depth > 0
+    only the w_depth finest levels repeat their coarse-grid correction gamma
+    times; coarser levels recurse once (a cycle shape outside the paper)."""
     if l == H.nl - 1:
         return bottom_solve(H, b)
     for _ in range(nu1):
         u = smooth(H, l, u, b)
     rc = restrict(H, l, residual(H.levels[l], u, b))
     ec = np.zeros_like(rc)
-    for _ in range(gamma):
-        ec = cycle(H, l + 1, ec, rc, nu1, nu2, gamma)
+    g = gamma if (w_depth == 0 or l < w_depth) else 1
+    for _ in range(g):
+        ec = cycle(H, l + 1, ec, rc, nu1, nu2, gamma, w_depth)
     u = u + interpolate(H, l, ec)
     for _ in range(nu2):
         u = smooth(H, l, u, b)
     return u
 
 
-def fmg(H: Hierarchy, l: int, r: np.ndarray, nu1: int, nu2: int, gamma: int = 1) -> np.ndarray:
+def fmg(H: Hierarchy, l: int, r: np.ndarray, nu1: int, nu2: int, gamma: int = 1,
+        w_depth: int = 0) -> np.ndarray:
     """Alg. 3: an approximation of (A^h)^-1 r."""
     if l == H.nl - 1:
         return bottom_solve(H, r)
     rc = restrict(H, l, r, zero_plg=False)
-    ec = fmg(H, l + 1, rc, nu1, nu2, gamma)
+    ec = fmg(H, l + 1, rc, nu1, nu2, gamma, w_depth)
     e = interpolate(H, l, ec)
-    return cycle(H, l, e, r, nu1, nu2, gamma)
+    return cycle(H, l, e, r, nu1, nu2, gamma, w_depth)
 
 
 @dataclass
@@ -284,7 +288,7 @@ class SolveResult:
 
 def solve(H: Hierarchy, b: np.ndarray, u0: Optional[np.ndarray] = None, tol: float = 1e-10,
           nu1: int = 3, nu2: int = 3, gamma: int = 1, method: str = "cycle",
-          max_cycles: int = 100, keep_iterates: bool = False) -> SolveResult:
+          max_cycles: int = 100, keep_iterates: bool = False, w_depth: int = 0) -> SolveResult:
     """Repeat cycles (Alg. 2) or the FMG residual iteration (Alg. 3 loop)
     until ||b - A u||_inf / ||b||_inf < tol."""
     d = H.levels[0]
@@ -294,9 +298,9 @@ def solve(H: Hierarchy, b: np.ndarray, u0: Optional[np.ndarray] = None, tol: flo
     for _ in range(max_cycles):
         if method == "fmg":
             r = residual(d, u, b)
-            u = u + fmg(H, 0, r, nu1, nu2, gamma)
+            u = u + fmg(H, 0, r, nu1, nu2, gamma, w_depth)
         else:
-            u = cycle(H, 0, u, b, nu1, nu2, gamma)
+            u = cycle(H, 0, u, b, nu1, nu2, gamma, w_depth)
         rel = np.abs(residual(d, u, b)).max() / bn
         res.history.append(float(rel))
         if keep_iterates:
