@@ -89,6 +89,12 @@ typedef struct {
                           cc_quadrature_nodes and cc_level_tables only */
   int fmg_cycle;       /* with cycle = CC_CYCLE_FMG: the cycle Alg. 3 runs on each
                           level, CC_CYCLE_V (the paper's, default) or CC_CYCLE_W */
+  int w_depth;         /* W cycles: only the w_depth finest levels repeat their
+                          coarse-grid correction; coarser levels recurse once.
+                          0 (default): every level, the plain W-cycle.  With 1
+                          the cycle converges like the W-cycle on the domains
+                          tested while each coarse level is visited twice per
+                          cycle instead of 2^l times */
 } cc_options;
 
 /* Sizes of a hierarchy. */

@@ -39,7 +39,7 @@ class cc_options(C.Structure):
     _fields_ = [("eps", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("cycle", C.c_int), ("min_coarse_n", C.c_int), ("precision", C.c_int),
                 ("max_cycles", C.c_int), ("use_graphs", C.c_int), ("host_only", C.c_int),
-                ("fmg_cycle", C.c_int)]
+                ("fmg_cycle", C.c_int), ("w_depth", C.c_int)]
 
 
 class cc_info(C.Structure):

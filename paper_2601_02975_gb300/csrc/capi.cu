@@ -902,11 +902,17 @@ void bottom(cc_hierarchy* H, int l, int cur, cudaStream_t s) {
 // guess were written by the kernel that made this level's right-hand side
 // (the restriction, or the FP64 residual of the refinement loop); only its
 // block solve is left.
-// The cycle Alg. 2 repeats: gamma = 1 (V) or 2 (W); Alg. 3 runs the cycle
-// that fmg_cycle names.
-int cycle_gamma(const cc_options& o) {
+// Visits of level l + 1 from level l: gamma = 1 (V) or 2 (W) of Alg. 2, W
+// only on the w_depth finest levels when w_depth > 0; Alg. 3 runs the cycle
+// that fmg_cycle names.  A second visit of the bottom level would repeat the
+// same exact solve on the same right-hand side, so it is left out.
+int cycle_gamma(const cc_hierarchy* H, int l) {
+  const cc_options& o = H->opt;
   const int c = o.cycle == CC_CYCLE_FMG ? o.fmg_cycle : o.cycle;
-  return c == CC_CYCLE_W ? 2 : 1;
+  if (c != CC_CYCLE_W) return 1;
+  if (o.w_depth > 0 && l >= o.w_depth) return 1;
+  if (l + 2 == (int)H->lv.size()) return 1;
+  return 2;
 }
 
 // With ec0, the initial guess is u + I(ec0) (0 + I(ec0) with zero), the
@@ -922,7 +928,7 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
     return;
   }
   const int nu1 = H->opt.nu1, nu2 = H->opt.nu2;
-  const int gamma = cycle_gamma(H->opt);
+  const int gamma = cycle_gamma(H, l);
   bool z = zero;
   for (int k = 0; k < nu1; ++k) {
     if (k == 0 && pre) {
@@ -1228,6 +1234,7 @@ void cc_default_options(cc_options* o) {
   o->use_graphs = 1;
   o->host_only = 0;
   o->fmg_cycle = CC_CYCLE_V;
+  o->w_depth = 0;
 }
 
 const char* cc_last_error_string(void) { return t_last_error; }
@@ -1260,7 +1267,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   if (opt) o = *opt;
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 == 0 || o.min_coarse_n < 4 || o.max_cycles < 1 ||
       !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3) ||
-      (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W))
+      (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W) || o.w_depth < 0)
     return CC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   cc_hierarchy* H = new cc_hierarchy();
