@@ -686,7 +686,17 @@ BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
   d.iptr = pool.upload(B.iptr, s);
   d.ipos = pool.upload(B.ipos, s);
   d.aoff = pool.upload(B.aoff, s);
-  d.ainv = pool.upload(cast_vec<T>(B.ainv), s);
+  if (B.dense) {
+    // row-major with 16-byte rows, zero padded, for vector loads
+    const int w = 16 / (int)sizeof(T);
+    d.ld = (B.m + w - 1) / w * w;
+    std::vector<T> a((size_t)d.ld * B.m, T(0));
+    for (int r = 0; r < B.m; ++r)
+      for (int c = 0; c < B.m; ++c) a[(size_t)r * d.ld + c] = (T)B.ainv[(size_t)r * B.m + c];
+    d.ainv = pool.upload(a, s);
+  } else {
+    d.ainv = pool.upload(cast_vec<T>(B.ainv), s);
+  }
   d.spos = pool.upload(B.spos, s);
   d.sk = B.sk;
   d.asi_col = pool.upload(B.asi_ell_col, s);
@@ -854,13 +864,17 @@ void block_solve(cc_hierarchy* H, Level& L, T* u, const T* b, cudaStream_t s) {
     // 1024-thread CTAs: every thread gathers at most one row, every warp
     // applies one row of the inverse
     const bool timed = H->timing == CC_TIME_BLOCK_DENSE && time_begin(H, s);
-    pdl_launch(k_block_dense<T>, (unsigned)((P.m + 31) / 32), 1024, (size_t)P.m * sizeof(T), s, B, b, u);
+    pdl_launch(k_block_dense<T>, (unsigned)((P.m + 31) / 32), 1024, (size_t)B.ld * sizeof(T), s, B, b, u);
     if (timed) time_end(H, s, dense_block_bytes(P, (int)sizeof(T)));
     return;
   }
   if (P.dense) {
+    // the gathered right-hand side goes through global memory: written once,
+    // read once per CTA of the product
+    const bool timed = H->timing == CC_TIME_BLOCK_DENSE && time_begin(H, s);
     pdl_launch(k_block_gather<T>, nblk(P.m), 256, 0, s, B, b, u);
-    pdl_launch(k_block_gemv<T>, (P.m + 7) / 8, 256, (size_t)P.m * sizeof(T), s, B, u);
+    pdl_launch(k_block_gemv<T>, (P.m + 7) / 8, 256, (size_t)B.ld * sizeof(T), s, B, u);
+    if (timed) time_end(H, s, dense_block_bytes(P, (int)sizeof(T)) + 2.0 * P.m * sizeof(T));
     return;
   }
   pdl_launch(k_block_chunk<T>, P.nch, 256, P.smem_chunk * sizeof(T), s, B, b, u);

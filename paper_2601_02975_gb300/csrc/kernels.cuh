@@ -6,6 +6,7 @@
 // smoother, Eq. 5.8: the PLG cells, plus the 4 x 4 box corners when b != 0).
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace ccmg {
@@ -448,7 +449,8 @@ struct BlockDev {
   void* tblk;               // T scratch [m]: gathered right-hand side
   void* zblk;               // T scratch [m]: interior solutions
   void* xs;                 // T scratch [ns]
-  int dense;                // 1: one chunk, inverse of the whole block in ainv
+  int dense;                // 1: one chunk, inverse of the whole block in ainv,
+  int ld;                   //    row-major with row stride ld (16-byte rows, zero padded)
   const int* alias_ptr;     // [m+1] merged-away control volumes owned by each block cell
   const int* alias_cell;    //       (they carry the owner's value for Eq. 5.11)
 };
@@ -592,21 +594,36 @@ __global__ void k_block_gather(BlockDev B, const T* __restrict__ b, const T* __r
   pdl_exit();
 }
 
+// 16-byte vectors for the rows of a dense inverse
+template <class T>
+using vec16_t = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+__device__ __forceinline__ float dot16(const float4& a, const float* t) {
+  const float4 b = *reinterpret_cast<const float4*>(t);
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+__device__ __forceinline__ double dot16(const double2& a, const double* t) {
+  const double2 b = *reinterpret_cast<const double2*>(t);
+  return a.x * b.x + a.y * b.y;
+}
+
 template <class T>
 __global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
   pdl_enter();
-  extern __shared__ unsigned char smem_raw[];
-  T* t = reinterpret_cast<T*>(smem_raw);
+  using V = vec16_t<T>;
+  constexpr int W = 16 / sizeof(T);
+  extern __shared__ float4 smem_f4[];
+  T* t = reinterpret_cast<T*>(smem_f4);
   const T* tg = static_cast<const T*>(B.tblk);
-  for (int c = threadIdx.x; c < B.m; c += blockDim.x) t[c] = tg[c];
+  for (int c = threadIdx.x; c < B.ld; c += blockDim.x) t[c] = c < B.m ? tg[c] : T(0);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= B.m) { pdl_exit(); return; }
-  const T* A = static_cast<const T*>(B.ainv) + (size_t)r * B.m;
+  const V* A = reinterpret_cast<const V*>(static_cast<const T*>(B.ainv) + (size_t)r * B.ld);
+  const int nv = B.ld / W;
   T acc = T(0);
-#pragma unroll 4
-  for (int c = lane; c < B.m; c += 32) acc += A[c] * t[c];
+#pragma unroll 8
+  for (int c = lane; c < nv; c += 32) acc += dot16(A[c], t + c * W);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) block_write(B, u, r, acc);
   pdl_exit();
@@ -674,7 +691,7 @@ k_smooth(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict_
   const int j = blockIdx.x - ntiles, nb = gridDim.x - ntiles;
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   for (int r = j * wpb + (threadIdx.x >> 5); r < B.m; r += nb * wpb) {
-    const T* A = static_cast<const T*>(B.ainv) + (size_t)r * B.m;
+    const T* A = static_cast<const T*>(B.ainv) + (size_t)r * B.ld;
     T acc = T(0);
 #pragma unroll 4
     for (int c = lane; c < B.m; c += 32) acc += A[c] * t[c];
@@ -688,37 +705,45 @@ k_smooth(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict_
 // side t = b - A(block, rest) u into its shared memory (the gather reads no
 // block cell, so rows written meanwhile by other CTAs do not disturb it), then
 // applies its share of the rows of inv(A_block), one warp per row.  Each warp
-// loads the first PF entries per lane of its row of the inverse into
+// loads the first PFV 16-byte vectors per lane of its row of the inverse into
 // registers before the gather, so those loads overlap it.
 template <class T>
 __global__ void __launch_bounds__(1024) k_block_dense(BlockDev B, const T* __restrict__ b,
                                                       T* __restrict__ u) {
-  constexpr int PF = 64 / (int)sizeof(T);   // 16 floats or 8 doubles per lane
+  using V = vec16_t<T>;
+  constexpr int W = 16 / sizeof(T);
+  constexpr int PFV = 6;
   pdl_enter();
-  extern __shared__ unsigned char smem_raw[];
-  T* t = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ float4 smem_f4[];
+  T* t = reinterpret_cast<T*>(smem_f4);
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   const int r0 = blockIdx.x * wpb + (threadIdx.x >> 5);
-  const T* A = static_cast<const T*>(B.ainv) + (size_t)r0 * B.m;
-  T a[PF];
+  const int nv = B.ld / W;
+  const V* A0 = reinterpret_cast<const V*>(static_cast<const T*>(B.ainv) +
+                                           (size_t)min(r0, B.m - 1) * B.ld);
+  V a[PFV];
 #pragma unroll
-  for (int j = 0; j < PF; ++j) {
+  for (int j = 0; j < PFV; ++j) {
     const int c = lane + 32 * j;
-    a[j] = r0 < B.m && c < B.m ? A[c] : T(0);
+    if (c < nv) a[j] = A0[c];
+    else a[j] = V{};
   }
-  for (int p = threadIdx.x; p < B.m; p += blockDim.x) t[p] = block_rhs(B, b, u, p);
+  for (int p = threadIdx.x; p < B.ld; p += blockDim.x) t[p] = p < B.m ? block_rhs(B, b, u, p) : T(0);
   __syncthreads();
   for (int r = r0; r < B.m; r += gridDim.x * wpb) {
-    const T* Ar = static_cast<const T*>(B.ainv) + (size_t)r * B.m;
+    const V* A = reinterpret_cast<const V*>(static_cast<const T*>(B.ainv) + (size_t)r * B.ld);
     T acc = T(0);
+    int c0 = lane;
     if (r == r0) {
 #pragma unroll
-      for (int j = 0; j < PF; ++j) acc += a[j] * t[min(lane + 32 * j, B.m - 1)];
-      for (int c = lane + 32 * PF; c < B.m; c += 32) acc += Ar[c] * t[c];
-    } else {
-#pragma unroll 8
-      for (int c = lane; c < B.m; c += 32) acc += Ar[c] * t[c];
+      for (int j = 0; j < PFV; ++j) {
+        const int c = lane + 32 * j;
+        if (c < nv) acc += dot16(a[j], t + c * W);
+      }
+      c0 = lane + 32 * PFV;
     }
+#pragma unroll 4
+    for (int c = c0; c < nv; c += 32) acc += dot16(A[c], t + c * W);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) block_write(B, u, r, acc);
   }
