@@ -297,7 +297,7 @@ enum { CC_TIME_OFF = 0, CC_TIME_FINE_SWEEP = 1, CC_TIME_BLOCK_DENSE = 2 };
  * cc_kernel_timing: with which = CC_TIME_FINE_SWEEP the library records CUDA
  * events around every launch of the finest-level Jacobi sweep kernel (Eq.
  * 5.7); with CC_TIME_BLOCK_DENSE around every one-launch dense block solve
- * (Eq. 5.8, blocks of up to 1024 cells, any level); CC_TIME_OFF stops.  The
+ * (Eq. 5.8, any level); CC_TIME_OFF stops.  The
  * events are recorded on the solve's stream, inside its CUDA graph, so host
  * launch gaps are not measured, but each interval includes the launch latency
  * of the kernel it brackets.  cc_kernel_timing_read returns the launch count,
