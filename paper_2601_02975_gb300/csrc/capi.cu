@@ -165,7 +165,7 @@ struct BlockPlan {
 };
 
 const int kDenseDirect = 1024;  // blocks up to this size: dense inverse by Gauss-Jordan
-const int kBlockOneLaunch = 1536;  // dense blocks up to this size: gather and solve in one launch
+const int kBlockOneLaunch = 1024;  // dense blocks up to this size: gather and solve in one launch
 const int kDenseMax = 2560;     // up to this size: dense inverse from the chunked plan
 
 // Apply the chunked scheme to t in FP64 exactly as the device does.
