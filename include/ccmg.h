@@ -197,6 +197,38 @@ cc_status cc_solve(cc_handle h, const double* d_f, const double* d_g, double* d_
                    double tol, cc_stream stream, cc_result* out);
 
 /*
+ * cc_clone: a second handle on the hierarchy of src.  It shares every
+ * read-only device table of src (class maps, stencil data, block inverses,
+ * the coarsest-level inverse) and the host-side setup, and owns its work
+ * arrays, CUDA graphs, norm buffer and stream, so that solves on src and on
+ * its clones can run at the same time (cc_solve_batch, or cc_solve from
+ * different host threads).  No setup is repeated: a clone costs the work
+ * arrays only (about 2 x 12 bytes per cell over all levels).  The shared
+ * tables stay allocated until src and all its clones are destroyed; destroy
+ * each with cc_destroy.  The current device must be src's device.
+ * Errors: CC_ERR_ARG (NULL, host-only or wrong device), CC_ERR_NO_MEMORY,
+ * CC_ERR_CUDA.  The paper's method needs no counterpart of this call.
+ */
+cc_status cc_clone(cc_handle src, cc_stream stream, cc_handle* out);
+
+/*
+ * cc_solve_batch: n independent solves at once, solve i as cc_solve on
+ * handle h[i] with d_f[i], d_g[i], d_u[i] and tolerance tol[i].  The handles
+ * must be distinct (clones of one hierarchy are; a handle twice is
+ * CC_ERR_ARG).  Solve i runs on streams[i], or, with streams NULL, on h[i]'s
+ * own stream after a device synchronisation (so inputs written by earlier
+ * work on any stream are visible).  One host thread advances every solve as
+ * soon as its previous step has completed on the GPU, so the solves' kernels
+ * overlap on the device.  Each solve does exactly the arithmetic of cc_solve
+ * on its handle.  out[i] (out may be NULL) receives solve i's result; the
+ * return value is CC_OK if every solve converged, else the first failing
+ * status.  Outputs are complete on return.
+ */
+cc_status cc_solve_batch(int n, const cc_handle* h, const double* const* d_f,
+                         const double* const* d_g, double* const* d_u, const double* tol,
+                         const cc_stream* streams, cc_result* out);
+
+/*
  * cc_solve_host: cc_solve with host arrays h_f, h_g, h_u (same layouts).  The
  * library copies them to and from device buffers that the handle owns; the
  * call returns after the solution is back in h_u.

@@ -78,6 +78,10 @@ _SIGS = {
     "cc_quadrature_nodes": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int64), _P, _P, _P, _P, _P, _P]),
     "cc_solve": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, C.POINTER(cc_result)]),
+    "cc_clone": (C.c_int, [_P, _P, C.POINTER(_P)]),
+    "cc_solve_batch": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                                 C.POINTER(_P), C.POINTER(C.c_double), C.POINTER(_P),
+                                 C.POINTER(cc_result)]),
     "cc_solve_host": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, C.POINTER(cc_result)]),
     "cc_submit": (C.c_int, [_P, _P, _P, _P, C.c_double, C.POINTER(C.c_uint64)]),
     "cc_poll": (C.c_int, [C.c_uint64, C.POINTER(cc_result)]),
@@ -179,6 +183,17 @@ class Hierarchy:
     def from_domain(cls, dom, a, b, c, n, options=None, stream=None):
         """Conditions from a workloads.Domain (box sides then holes)."""
         return cls(dom, a, b, c, list(dom.box_bc) + list(dom.hole_bc), n, options, stream)
+
+    def clone(self, stream=None) -> "Hierarchy":
+        """cc_clone: a handle sharing this hierarchy's tables, with its own
+        work arrays, so that solves on both can run at the same time."""
+        h = C.c_void_p()
+        _check(lib().cc_clone(self.h, _stream(stream), C.byref(h)), "cc_clone")
+        c = object.__new__(Hierarchy)
+        c.h = h
+        c.options = self.options
+        c.info = c.query()
+        return c
 
     def close(self):
         if getattr(self, "h", None):
@@ -299,3 +314,21 @@ class Hierarchy:
         _check(lib().cc_kernel_timing_read(self.h, C.byref(n), C.byref(ms), C.byref(by)),
                "cc_kernel_timing_read")
         return n.value, ms.value, by.value
+
+
+def solve_batch(hs, fs, gs, us, tols, streams=None):
+    """cc_solve_batch: solve i on handle hs[i] (distinct handles), all at once.
+    Returns the list of cc_result; raises on CC_ERR_ARG / CC_ERR_CUDA."""
+    n = len(hs)
+    P = _P * max(1, n)
+    h = P(*[x.h for x in hs])
+    f = P(*[_ptr(x) for x in fs])
+    g = P(*[_ptr(x) for x in gs])
+    u = P(*[_ptr(x) for x in us])
+    t = (C.c_double * max(1, n))(*[float(x) for x in tols])
+    st_arr = P(*[_stream(x) for x in streams]) if streams is not None else None
+    out = (cc_result * max(1, n))()
+    st = lib().cc_solve_batch(n, h, f, g, u, t, st_arr, out)
+    if st not in (CC_OK, CC_ERR_NOT_CONVERGED, CC_ERR_DIVERGED):
+        _check(st, "cc_solve_batch")
+    return [out[i] for i in range(n)]

@@ -521,6 +521,7 @@ struct Pool {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
   }
+  ~Pool() { release(); }
 };
 
 template <class T>
@@ -542,7 +543,10 @@ struct Level {
   double* b64 = nullptr;
   float* u32[2] = {nullptr, nullptr};
   float* b32 = nullptr;
-  BlockPlan plan;
+  // host-side plan and discretisation, shared by the clones of a hierarchy
+  std::shared_ptr<BlockPlan> planp = std::make_shared<BlockPlan>();
+  BlockPlan& plan() { return *planp; }
+  const BlockPlan& plan() const { return *planp; }
   BlockDevSet blk;
   // full block rows (FP64) for residuals
   int* brow_cell = nullptr;
@@ -558,7 +562,9 @@ struct Level {
   int nfix = 0;
   int* fix_dst = nullptr;
   int* fix_src = nullptr;
-  LevelDisc disc;
+  std::shared_ptr<LevelDisc> discp = std::make_shared<LevelDisc>();
+  LevelDisc& disc() { return *discp; }
+  const LevelDisc& disc() const { return *discp; }
 };
 
 }  // namespace
@@ -568,7 +574,8 @@ struct cc_hierarchy {
   cc_options opt;
   int device = 0;
   std::vector<std::unique_ptr<Level>> lv;
-  Pool pool;
+  std::shared_ptr<Pool> pool = std::make_shared<Pool>();   // this handle's device memory
+  std::shared_ptr<Pool> tables;   // a clone: the source's memory, which holds the shared tables
   double* bottom_inv = nullptr;   // column-major FP64
   double bottom_error = 0;
   int nc_bottom = 0;
@@ -585,6 +592,7 @@ struct cc_hierarchy {
   int n_nrows = 0;
   unsigned long long* d_norm = nullptr;   // [2]
   unsigned long long* h_norm = nullptr;   // pinned
+  cudaEvent_t step_ev = nullptr;          // recorded at the end of every solve step
   int n_g = 0, n_bd = 0;
   int64_t n_dof = 0;
   // kernel timing (cc_kernel_timing): which kernel, its event pairs and the
@@ -859,7 +867,7 @@ template <class T>
 void block_solve(cc_hierarchy* H, Level& L, T* u, const T* b, cudaStream_t s) {
   const BlockDev& B = bdev<T>(L);
   if (B.m == 0) return;
-  const BlockPlan& P = L.plan;
+  const BlockPlan& P = L.plan();
   if (P.dense && P.m <= kBlockOneLaunch) {
     // 1024-thread CTAs: every thread gathers at most one row, every warp
     // applies one row of the inverse
@@ -1006,8 +1014,8 @@ void residual64(cc_hierarchy* H, const double* u, const double* b, Tout* r, cuda
   else
     pdl_launch(k_resid<double, Tout, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm,
                e0, wd);
-  if (L.plan.m)
-    pdl_launch(k_block_resid<Tout>, nblk(L.plan.m), 256, 0, s, L.plan.m, L.brow_cell, L.brow_ptr, L.brow_col,
+  if (L.plan().m)
+    pdl_launch(k_block_resid<Tout>, nblk(L.plan().m), 256, 0, s, L.plan().m, L.brow_cell, L.brow_ptr, L.brow_col,
                                                        L.brow_val, u, b, r, H->d_norm);
 }
 
@@ -1088,85 +1096,187 @@ void iteration(cc_hierarchy* H, bool mixed, cudaStream_t s) {
   }
 }
 
-cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* u, double tol,
-                     cudaStream_t s, cc_result* out) {
+// One solve as a sequence of steps that never wait on the GPU: every step
+// enqueues its work and the copy of one norm to pinned memory, then records
+// the handle's step event; the next step runs once that event has completed.
+// A host thread can so drive several solves (on distinct handles) at once.
+struct SolveTask {
+  cc_hierarchy* H = nullptr;
+  const double* f = nullptr;
+  const double* g = nullptr;
+  double* u = nullptr;
+  double tol = 0;
+  cudaStream_t s = nullptr;
+  int phase = 0;   // 0 start, 1 |b| pending, 2 first residual pending, 3 cycle pending,
+                   // 4 result copy pending, 5 done
+  double bn = 1, rel = 0, first = -1;
+  int it = 0;
+  int64_t launches = 0;
+  cc_result res{};
+};
+
+void enqueue_norm(cc_hierarchy* H, cudaStream_t s) {
+  CK(cudaMemcpyAsync(H->h_norm, H->d_norm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(H->step_ev, s));
+}
+
+double host_norm(const cc_hierarchy* H) {
+  unsigned long long v = H->h_norm[0];
+  double d;
+  std::memcpy(&d, &v, sizeof(d));
+  return d;
+}
+
+// one solve iteration (a cycle, the FP64 residual and its norm), replayed
+// from the handle's graph when graphs are on
+void launch_iteration(cc_hierarchy* H, bool mixed, cudaStream_t s) {
+  const int gi = (mixed ? 1 : 0) + 2 * H->timing;
+  if (H->opt.use_graphs) {
+    if (!H->gexec[gi]) {
+      cudaGraph_t gr;
+      int64_t before = t_launches;
+      H->ev_used = 0;
+      CK(cudaStreamBeginCapture(H->gstream, cudaStreamCaptureModeThreadLocal));
+      iteration(H, mixed, H->gstream);
+      CK(cudaStreamEndCapture(H->gstream, &gr));
+      CK(cudaGraphInstantiate(&H->gexec[gi], gr, 0));
+      CK(cudaGraphDestroy(gr));
+      H->gexec_launches[gi] = t_launches - before;
+      H->gexec_events[gi] = H->ev_used;
+      t_launches = before;
+    }
+    CK(cudaGraphLaunch(H->gexec[gi], s));
+    t_launches += H->gexec_launches[gi];
+  } else {
+    H->ev_used = 0;
+    iteration(H, mixed, s);
+  }
+  enqueue_norm(H, s);
+}
+
+// durations of the timed launches of the iteration just completed
+void collect_timing(cc_hierarchy* H, bool mixed) {
+  if (!H->timing) return;
+  const int gi = (mixed ? 1 : 0) + 2 * H->timing;
+  size_t ne = H->opt.use_graphs ? H->gexec_events[gi] : H->ev_used;
+  for (size_t i = 0; i < ne; ++i) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, H->ev[i].first, H->ev[i].second));
+    H->timed_ms += ms;
+    H->timed_bytes += H->ev_bytes[i];
+    ++H->timed_launches;
+  }
+  if (!H->opt.use_graphs) H->ev_used = 0;
+}
+
+void finish_task(SolveTask& T) {
+  Level& L = *T.H->lv[0];
+  CK(cudaMemcpyAsync(T.u, L.u64[T.H->cur64], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, T.s));
+  CK(cudaEventRecord(T.H->step_ev, T.s));
+  T.phase = 4;
+}
+
+// Advance T by one step (its previous step has completed on the GPU); true
+// once the solve is done and its result copied out.
+bool solve_step(SolveTask& T) {
+  cc_hierarchy* H = T.H;
   Level& L = *H->lv[0];
   const bool mixed = H->opt.precision == CC_PREC_MIXED;
-  const int64_t launches0 = t_launches;
-  H->cur64 = 0;
-  assemble_rhs(H, f, g, L.b64, s);
-  CK(cudaMemcpyAsync(L.u64[0], u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
-  pdl_launch(k_absmax, 152 * 4, 256, 0, s, L.b64, L.nn, H->d_norm);
-  double bn = read_norm(H, s);
-  if (bn == 0.0) bn = 1.0;
-  cc_result res{};
-  res.status = CC_ERR_NOT_CONVERGED;
-  double rel = 0, first = -1;
-  // residual of the initial guess (in the mixed mode it is also the first
-  // FP32 right-hand side)
-  CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
-  if (mixed) residual64<float>(H, L.u64[0], L.b64, L.b32, s, mixed_e0(H), L.spf.omega_over_diag);
-  else residual64<double>(H, L.u64[0], L.b64, H->r64, s);
-  rel = read_norm(H, s) / bn;
-  first = rel;
-  if (rel < tol) res.status = CC_OK;
-  int it = 0;
-  const int gi = (mixed ? 1 : 0) + 2 * H->timing;
-  bool use_graph = H->opt.use_graphs != 0;
-  for (; res.status != CC_OK && it < H->opt.max_cycles; ++it) {
-    if (use_graph) {
-      if (!H->gexec[gi]) {
-        cudaGraph_t gr;
-        int64_t before = t_launches;
-        H->ev_used = 0;
-        CK(cudaStreamBeginCapture(H->gstream, cudaStreamCaptureModeThreadLocal));
-        iteration(H, mixed, H->gstream);
-        CK(cudaStreamEndCapture(H->gstream, &gr));
-        CK(cudaGraphInstantiate(&H->gexec[gi], gr, 0));
-        CK(cudaGraphDestroy(gr));
-        H->gexec_launches[gi] = t_launches - before;
-        H->gexec_events[gi] = H->ev_used;
-        t_launches = before;
-      }
-      CK(cudaGraphLaunch(H->gexec[gi], s));
-      t_launches += H->gexec_launches[gi];
-    } else {
-      H->ev_used = 0;
-      iteration(H, mixed, s);
-    }
-    rel = read_norm(H, s) / bn;
-    if (H->timing) {
-      // the timed sweeps of this iteration (their events live in the graph
-      // when graphs are used, so host launch gaps are not measured)
-      size_t ne = use_graph ? H->gexec_events[gi] : H->ev_used;
-      for (size_t i = 0; i < ne; ++i) {
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, H->ev[i].first, H->ev[i].second));
-        H->timed_ms += ms;
-        H->timed_bytes += H->ev_bytes[i];
-        ++H->timed_launches;
-      }
-      if (!use_graph) H->ev_used = 0;
-    }
-    if (rel < tol) {
-      res.status = CC_OK;
-      ++it;
+  const cudaStream_t s = T.s;
+  const int64_t l0 = t_launches;
+  switch (T.phase) {
+    case 0:
+      H->cur64 = 0;
+      T.res.status = CC_ERR_NOT_CONVERGED;
+      assemble_rhs(H, T.f, T.g, L.b64, s);
+      CK(cudaMemcpyAsync(L.u64[0], T.u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
+      pdl_launch(k_absmax, 152 * 4, 256, 0, s, L.b64, L.nn, H->d_norm);
+      enqueue_norm(H, s);
+      T.phase = 1;
       break;
-    }
-    if (!std::isfinite(rel) || (first > 0 && rel > 1e3 * first)) {
-      res.status = CC_ERR_DIVERGED;
-      ++it;
+    case 1:
+      // residual of the initial guess (in the mixed mode it is also the first
+      // FP32 right-hand side)
+      T.bn = host_norm(H);
+      if (T.bn == 0.0) T.bn = 1.0;
+      CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
+      if (mixed) residual64<float>(H, L.u64[0], L.b64, L.b32, s, mixed_e0(H), L.spf.omega_over_diag);
+      else residual64<double>(H, L.u64[0], L.b64, H->r64, s);
+      enqueue_norm(H, s);
+      T.phase = 2;
       break;
-    }
+    case 2:
+      T.rel = T.first = host_norm(H) / T.bn;
+      if (T.rel < T.tol) {
+        T.res.status = CC_OK;
+        finish_task(T);
+      } else if (H->opt.max_cycles <= 0) {
+        finish_task(T);
+      } else {
+        launch_iteration(H, mixed, s);
+        T.phase = 3;
+      }
+      break;
+    case 3:
+      T.rel = host_norm(H) / T.bn;
+      collect_timing(H, mixed);
+      ++T.it;
+      if (T.rel < T.tol) {
+        T.res.status = CC_OK;
+        finish_task(T);
+      } else if (!std::isfinite(T.rel) || (T.first > 0 && T.rel > 1e3 * T.first)) {
+        T.res.status = CC_ERR_DIVERGED;
+        finish_task(T);
+      } else if (T.it >= H->opt.max_cycles) {
+        finish_task(T);
+      } else {
+        launch_iteration(H, mixed, s);
+      }
+      break;
+    case 4:
+      T.res.cycles = T.it;
+      T.res.rel_res = T.rel;
+      T.phase = 5;
+      break;
   }
-  CK(cudaMemcpyAsync(u, L.u64[H->cur64], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(cudaStreamSynchronize(s));
-  res.cycles = it;
-  res.rel_res = rel;
-  res.kernels = t_launches - launches0;
-  if (out) *out = res;
-  return res.status;
+  T.launches += t_launches - l0;
+  T.res.kernels = T.launches;
+  return T.phase == 5;
+}
+
+// Drive every task to completion, advancing each as soon as its last step
+// has completed on the GPU.  The handles must be distinct.
+void run_solves(std::vector<SolveTask>& T) {
+  size_t left = T.size();
+  for (auto& t : T)
+    if (solve_step(t)) --left;
+  while (left) {
+    bool moved = false;
+    for (auto& t : T) {
+      if (t.phase == 5) continue;
+      cudaError_t q = cudaEventQuery(t.H->step_ev);
+      if (q == cudaErrorNotReady) continue;
+      CK(q);
+      if (solve_step(t)) --left;
+      moved = true;
+    }
+    if (!moved) std::this_thread::yield();
+  }
+}
+
+cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* u, double tol,
+                     cudaStream_t s, cc_result* out) {
+  std::vector<SolveTask> T(1);
+  T[0].H = H;
+  T[0].f = f;
+  T[0].g = g;
+  T[0].u = u;
+  T[0].tol = tol;
+  T[0].s = s;
+  run_solves(T);
+  if (out) *out = T[0].res;
+  return T[0].res.status;
 }
 
 void worker_loop(cc_hierarchy* H) {
@@ -1223,10 +1333,12 @@ void destroy_hierarchy(cc_hierarchy* H) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
   }
+  if (H->step_ev) cudaEventDestroy(H->step_ev);
   if (H->wstream) cudaStreamDestroy(H->wstream);
   if (H->gstream) cudaStreamDestroy(H->gstream);
   if (H->h_norm) cudaFreeHost(H->h_norm);
-  H->pool.release();
+  H->pool.reset();
+  H->tables.reset();
   delete H;
 }
 
@@ -1325,7 +1437,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
         break;
       }
       auto L = std::make_unique<Level>();
-      L->disc = std::move(D);
+      L->disc() = std::move(D);
       L->n = nl;
       L->nn = (int64_t)nl * nl;
       H->lv.push_back(std::move(L));
@@ -1336,27 +1448,27 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     // same rows: nothing else is required for the cycle.
     for (size_t l = 0; l < H->lv.size(); ++l) {
       Level& L = *H->lv[l];
-      const LevelDisc& D = L.disc;
-      L.disc.P = &H->P;
+      const LevelDisc& D = L.disc();
+      L.disc().P = &H->P;
       L.sp = make_stencil(D, o.omega);
       L.spf = stencil_as<float>(L.sp);
-      L.plan = plan_block(D);
+      L.plan() = plan_block(D);
       {
         // merged-away control volumes take their owner's value (Eq. 5.11)
         std::unordered_map<int, int> pos;
-        for (int p = 0; p < L.plan.m; ++p) pos[L.plan.cell[p]] = p;
-        std::vector<std::vector<int>> al(L.plan.m);
+        for (int p = 0; p < L.plan().m; ++p) pos[L.plan().cell[p]] = p;
+        std::vector<std::vector<int>> al(L.plan().m);
         for (int64_t k = 0; l > 0 && k < L.nn; ++k)
           if (D.geom.type[k] == CT_EMPTY && D.geom.owner[k] >= 0 && D.geom.owner[k] != k) {
             auto it = pos.find(D.geom.owner[k]);
             if (it == pos.end()) throw SetupError(3, "a merged cell is not in the exact block");
             al[it->second].push_back((int)k);
           }
-        L.plan.alias_ptr.assign(1, 0);
-        L.plan.alias_cell.clear();
+        L.plan().alias_ptr.assign(1, 0);
+        L.plan().alias_cell.clear();
         for (auto& v : al) {
-          L.plan.alias_cell.insert(L.plan.alias_cell.end(), v.begin(), v.end());
-          L.plan.alias_ptr.push_back((int)L.plan.alias_cell.size());
+          L.plan().alias_cell.insert(L.plan().alias_cell.end(), v.begin(), v.end());
+          L.plan().alias_ptr.push_back((int)L.plan().alias_cell.size());
         }
       }
       if (!dev) continue;
@@ -1364,43 +1476,43 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       for (int64_t k = 0; k < L.nn; ++k)
         if (D.kind[k] != K_EMPTY) cls[k] = C_STENCIL;
       for (int k : D.block) cls[k] = C_BLOCK;
-      L.cls = H->pool.upload(cls, s);
+      L.cls = H->pool->upload(cls, s);
       for (int i = 0; i < 2; ++i) {
-        L.u64[i] = H->pool.alloc<double>(L.nn);
-        L.u32[i] = H->pool.alloc<float>(L.nn);
+        L.u64[i] = H->pool->alloc<double>(L.nn);
+        L.u32[i] = H->pool->alloc<float>(L.nn);
         CK(cudaMemsetAsync(L.u64[i], 0, L.nn * sizeof(double), s));
         CK(cudaMemsetAsync(L.u32[i], 0, L.nn * sizeof(float), s));
       }
-      L.b64 = H->pool.alloc<double>(L.nn);
-      L.b32 = H->pool.alloc<float>(L.nn);
+      L.b64 = H->pool->alloc<double>(L.nn);
+      L.b32 = H->pool->alloc<float>(L.nn);
       CK(cudaMemsetAsync(L.b64, 0, L.nn * sizeof(double), s));
       CK(cudaMemsetAsync(L.b32, 0, L.nn * sizeof(float), s));
       if (l + 1 < H->lv.size()) {
-        L.blk.d64 = upload_block<double>(H->pool, L.plan, s);
-        L.blk.d32 = upload_block<float>(H->pool, L.plan, s);
+        L.blk.d64 = upload_block<double>(*H->pool, L.plan(), s);
+        L.blk.d32 = upload_block<float>(*H->pool, L.plan(), s);
         // sweep and dense block solve in one launch (k_smooth) on the grids
         // that the 32 x 8 tile sweep serves
         std::vector<int> qcell, fptr, fidx;
         std::vector<double> fval;
-        if (fuse_max_m() > 0 && L.plan.m > 0 && L.plan.m <= fuse_max_m() && L.plan.dense &&
-            L.n < 512 && build_frontier(L.plan, cls, qcell, fptr, fidx, fval)) {
-          const size_t words = qcell.size() + (size_t)L.plan.m;
+        if (fuse_max_m() > 0 && L.plan().m > 0 && L.plan().m <= fuse_max_m() && L.plan().dense &&
+            L.n < 512 && build_frontier(L.plan(), cls, qcell, fptr, fidx, fval)) {
+          const size_t words = qcell.size() + (size_t)L.plan().m;
           if (words * sizeof(double) <= 96 * 1024) {
-            L.fr64 = upload_frontier<double>(H->pool, qcell, fptr, fidx, fval, s);
-            L.fr32 = upload_frontier<float>(H->pool, qcell, fptr, fidx, fval, s);
+            L.fr64 = upload_frontier<double>(*H->pool, qcell, fptr, fidx, fval, s);
+            L.fr32 = upload_frontier<float>(*H->pool, qcell, fptr, fidx, fval, s);
             L.fuse_smem[0] = words * sizeof(double);
             L.fuse_smem[1] = words * sizeof(float);
-            L.fuse_nb = std::min(128, std::max(1, (L.plan.m + 15) / 16));
+            L.fuse_nb = std::min(128, std::max(1, (L.plan().m + 15) / 16));
             smooth_smem_limit((int)L.fuse_smem[0]);
             L.fused = true;
           }
         }
       }
       if (!D.block.empty()) {
-        L.brow_cell = H->pool.upload(D.block, s);
-        L.brow_ptr = H->pool.upload(D.block_rows.ptr, s);
-        L.brow_col = H->pool.upload(D.block_rows.col, s);
-        L.brow_val = H->pool.upload(D.block_rows.val, s);
+        L.brow_cell = H->pool->upload(D.block, s);
+        L.brow_ptr = H->pool->upload(D.block_rows.ptr, s);
+        L.brow_col = H->pool->upload(D.block_rows.col, s);
+        L.brow_val = H->pool->upload(D.block_rows.val, s);
       }
       std::vector<int> fd, fs;
       for (int64_t k = 0; k < L.nn; ++k)
@@ -1410,8 +1522,8 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
         }
       L.nfix = (int)fd.size();
       if (L.nfix) {
-        L.fix_dst = H->pool.upload(fd, s);
-        L.fix_src = H->pool.upload(fs, s);
+        L.fix_dst = H->pool->upload(fd, s);
+        L.fix_src = H->pool->upload(fs, s);
       }
     }
     // bottom: dense inverse of the coarsest level's matrix
@@ -1422,11 +1534,11 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       std::vector<double> A((size_t)nc * nc, 0.0);
       std::map<int, double> ar;
       for (int k = 0; k < nc; ++k) {
-        L.disc.row(k, ar, nullptr);
+        L.disc().row(k, ar, nullptr);
         for (auto& kv : ar) A[(size_t)k * nc + kv.first] += kv.second;
         // a merged-away control volume repeats its owner's value (Eq. 5.11)
-        int own = L.disc.geom.owner[k];
-        if (H->lv.size() > 1 && L.disc.kind[k] == K_EMPTY && own >= 0 && own != k)
+        int own = L.disc().geom.owner[k];
+        if (H->lv.size() > 1 && L.disc().kind[k] == K_EMPTY && own >= 0 && own != k)
           A[(size_t)k * nc + own] = -1.0;
       }
       std::vector<double> A0(A);
@@ -1449,13 +1561,13 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
         }
         H->bottom_error = rmax / (amax * xmax);
       }
-      if (dev) H->bottom_inv = H->pool.upload(A, s);   // row-major
+      if (dev) H->bottom_inv = H->pool->upload(A, s);   // row-major
       H->nc_bottom = nc;
     }
     // finest level: N rows, residual buffers, norms
     {
       Level& L = *H->lv[0];
-      const LevelDisc& D = L.disc;
+      const LevelDisc& D = L.disc();
       H->n_bd = (int)D.bd_cells.size();
       H->n_g = 4 * n + H->n_bd;
       H->n_nrows = D.nrows.rows();
@@ -1464,15 +1576,16 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       H->n_dof = dof;
       if (!dev) goto done;
       if (H->n_nrows) {
-        H->nrow_cell = H->pool.upload(D.nrow_cell, s);
-        H->nrow_ptr = H->pool.upload(D.nrows.ptr, s);
-        H->nrow_col = H->pool.upload(D.nrows.col, s);
-        H->nrow_val = H->pool.upload(D.nrows.val, s);
+        H->nrow_cell = H->pool->upload(D.nrow_cell, s);
+        H->nrow_ptr = H->pool->upload(D.nrows.ptr, s);
+        H->nrow_col = H->pool->upload(D.nrows.col, s);
+        H->nrow_val = H->pool->upload(D.nrows.val, s);
       }
-      H->r64 = H->pool.alloc<double>(L.nn);
+      H->r64 = H->pool->alloc<double>(L.nn);
       CK(cudaMemsetAsync(H->r64, 0, L.nn * sizeof(double), s));
-      H->d_norm = H->pool.alloc<unsigned long long>(2);
+      H->d_norm = H->pool->alloc<unsigned long long>(2);
       CK(cudaMallocHost(&H->h_norm, 2 * sizeof(unsigned long long)));
+      CK(cudaEventCreateWithFlags(&H->step_ev, cudaEventDisableTiming));
     }
     CK(cudaStreamCreateWithFlags(&H->gstream, cudaStreamNonBlocking));
     CK(cudaStreamSynchronize(s));
@@ -1500,12 +1613,12 @@ cc_status cc_query(cc_handle H, cc_info* out) {
   out->n_dof = H->n_dof;
   out->n_bd = H->n_bd;
   out->n_g = H->n_g;
-  out->n_plg = (int)H->lv[0]->disc.plg.size();
-  out->n_block = (int)H->lv[0]->disc.block.size();
-  out->device_bytes = H->pool.bytes;
+  out->n_plg = (int)H->lv[0]->disc().plg.size();
+  out->n_block = (int)H->lv[0]->disc().block.size();
+  out->device_bytes = H->pool->bytes;
   for (size_t l = 0; l < H->lv.size() && l < 32; ++l) {
     out->level_n[l] = H->lv[l]->n;
-    out->block_error = std::max(out->block_error, H->lv[l]->plan.error);
+    out->block_error = std::max(out->block_error, H->lv[l]->plan().error);
   }
   out->bottom_error = H->bottom_error;
   return CC_OK;
@@ -1519,7 +1632,7 @@ cc_status cc_destroy(cc_handle H) {
 
 cc_status cc_cell_types(cc_handle H, uint8_t* h_type, uint8_t* h_kind, double* h_vol) {
   if (!H || !h_type) return CC_ERR_ARG;
-  const LevelDisc& D = H->lv[0]->disc;
+  const LevelDisc& D = H->lv[0]->disc();
   std::copy(D.geom.type.begin(), D.geom.type.end(), h_type);
   if (h_kind) std::copy(D.kind.begin(), D.kind.end(), h_kind);
   if (h_vol) std::copy(D.geom.vol.begin(), D.geom.vol.end(), h_vol);
@@ -1530,7 +1643,7 @@ cc_status cc_quadrature_nodes(cc_handle H, int* n_cut, int64_t* nv, int64_t* nb,
                               int64_t* h_vptr, double* h_vnode, int64_t* h_bptr, double* h_bnode,
                               int* h_bbc) {
   if (!H || !n_cut || !nv || !nb) return CC_ERR_ARG;
-  const LevelDisc& D = H->lv[0]->disc;
+  const LevelDisc& D = H->lv[0]->disc();
   const LevelGeom& G = D.geom;
   int nc = 0;
   int64_t v = 0, bcount = 0;
@@ -1567,6 +1680,111 @@ cc_status cc_quadrature_nodes(cc_handle H, int* n_cut, int64_t* nv, int64_t* nb,
   return CC_OK;
 }
 
+cc_status cc_clone(cc_handle S, cc_stream stream, cc_handle* out) {
+  if (!out) return CC_ERR_ARG;
+  *out = nullptr;
+  if (!S || S->opt.host_only) return CC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cc_hierarchy* H = nullptr;
+  try {
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != S->device) return CC_ERR_ARG;
+    H = new cc_hierarchy();
+    H->P = S->P;
+    H->opt = S->opt;
+    H->device = S->device;
+    H->tables = S->tables ? S->tables : S->pool;
+    H->bottom_inv = S->bottom_inv;
+    H->bottom_error = S->bottom_error;
+    H->nc_bottom = S->nc_bottom;
+    H->nrow_cell = S->nrow_cell;
+    H->nrow_ptr = S->nrow_ptr;
+    H->nrow_col = S->nrow_col;
+    H->nrow_val = S->nrow_val;
+    H->n_nrows = S->n_nrows;
+    H->n_g = S->n_g;
+    H->n_bd = S->n_bd;
+    H->n_dof = S->n_dof;
+    const size_t nl = S->lv.size();
+    for (size_t l = 0; l < nl; ++l) {
+      // shares the plan, the discretisation and every device table ...
+      auto L = std::make_unique<Level>(*S->lv[l]);
+      // ... and gets its own work arrays
+      for (int i = 0; i < 2; ++i) {
+        L->u64[i] = H->pool->alloc<double>(L->nn);
+        L->u32[i] = H->pool->alloc<float>(L->nn);
+        CK(cudaMemsetAsync(L->u64[i], 0, L->nn * sizeof(double), s));
+        CK(cudaMemsetAsync(L->u32[i], 0, L->nn * sizeof(float), s));
+      }
+      L->b64 = H->pool->alloc<double>(L->nn);
+      L->b32 = H->pool->alloc<float>(L->nn);
+      CK(cudaMemsetAsync(L->b64, 0, L->nn * sizeof(double), s));
+      CK(cudaMemsetAsync(L->b32, 0, L->nn * sizeof(float), s));
+      const BlockPlan& B = L->plan();
+      if (l + 1 < nl && B.m > 0) {
+        L->blk.d64.tblk = H->pool->alloc<double>(B.m);
+        L->blk.d64.zblk = H->pool->alloc<double>(B.m);
+        L->blk.d64.xs = H->pool->alloc<double>(std::max(1, B.ns));
+        L->blk.d32.tblk = H->pool->alloc<float>(B.m);
+        L->blk.d32.zblk = H->pool->alloc<float>(B.m);
+        L->blk.d32.xs = H->pool->alloc<float>(std::max(1, B.ns));
+      }
+      H->lv.push_back(std::move(L));
+    }
+    Level& L0 = *H->lv[0];
+    H->r64 = H->pool->alloc<double>(L0.nn);
+    CK(cudaMemsetAsync(H->r64, 0, L0.nn * sizeof(double), s));
+    H->d_norm = H->pool->alloc<unsigned long long>(2);
+    CK(cudaMallocHost(&H->h_norm, 2 * sizeof(unsigned long long)));
+    CK(cudaEventCreateWithFlags(&H->step_ev, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&H->gstream, cudaStreamNonBlocking));
+    CK(cudaStreamSynchronize(s));
+  } catch (CudaError& e) {
+    if (H) destroy_hierarchy(H);
+    return e.e == cudaErrorMemoryAllocation ? CC_ERR_NO_MEMORY : CC_ERR_CUDA;
+  }
+  *out = H;
+  return CC_OK;
+}
+
+cc_status cc_solve_batch(int n, const cc_handle* h, const double* const* f, const double* const* g,
+                         double* const* u, const double* tol, const cc_stream* streams,
+                         cc_result* out) {
+  t_last_error[0] = '\0';
+  if (n < 0 || (n > 0 && (!h || !f || !u || !tol))) return CC_ERR_ARG;
+  std::vector<SolveTask> T(n);
+  for (int i = 0; i < n; ++i) {
+    cc_hierarchy* H = h[i];
+    if (!H || H->opt.host_only || !f[i] || !u[i] || (H->n_g && (!g || !g[i])) || !(tol[i] > 0))
+      return CC_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (h[j] == H) {
+        snprintf(t_last_error, sizeof(t_last_error),
+                 "cc_solve_batch: handle %d repeats handle %d (use cc_clone)", i, j);
+        return CC_ERR_ARG;
+      }
+    T[i].H = H;
+    T[i].f = f[i];
+    T[i].g = g ? g[i] : nullptr;
+    T[i].u = u[i];
+    T[i].tol = tol[i];
+    T[i].s = streams ? (cudaStream_t)streams[i] : H->gstream;
+  }
+  try {
+    if (!streams) CK(cudaDeviceSynchronize());
+    run_solves(T);
+  } catch (CudaError&) {
+    return CC_ERR_CUDA;
+  }
+  cc_status st = CC_OK;
+  for (int i = 0; i < n; ++i) {
+    if (out) out[i] = T[i].res;
+    if (st == CC_OK && T[i].res.status != CC_OK) st = T[i].res.status;
+  }
+  return st;
+}
+
 cc_status cc_solve(cc_handle H, const double* f, const double* g, double* u, double tol,
                    cc_stream stream, cc_result* out) {
   if (H && H->opt.host_only) return CC_ERR_ARG;
@@ -1586,9 +1804,9 @@ cc_status cc_solve_host(cc_handle H, const double* hf, const double* hg, double*
   try {
     Level& L = *H->lv[0];
     if (!H->h_u_dev) {
-      H->h_u_dev = H->pool.alloc<double>(L.nn);
-      H->h_f_dev = H->pool.alloc<double>(L.nn);
-      H->h_g_dev = H->pool.alloc<double>(std::max(1, H->n_g));
+      H->h_u_dev = H->pool->alloc<double>(L.nn);
+      H->h_f_dev = H->pool->alloc<double>(L.nn);
+      H->h_g_dev = H->pool->alloc<double>(std::max(1, H->n_g));
     }
     CK(cudaMemcpyAsync(H->h_f_dev, hf, L.nn * sizeof(double), cudaMemcpyHostToDevice, s));
     if (H->n_g) CK(cudaMemcpyAsync(H->h_g_dev, hg, H->n_g * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1664,9 +1882,9 @@ cc_status cc_residual(cc_handle H, int l, const double* u, const double* b, doub
     else
       pdl_launch(k_resid<double, double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr,
                  (double*)nullptr, 0.0);
-    if (!L.disc.block.empty())
-      pdl_launch(k_block_resid<double>, nblk((int64_t)L.disc.block.size()), 256, 0, s, 
-          (int)L.disc.block.size(), L.brow_cell, L.brow_ptr, L.brow_col, L.brow_val, u, b, r, nullptr);
+    if (!L.disc().block.empty())
+      pdl_launch(k_block_resid<double>, nblk((int64_t)L.disc().block.size()), 256, 0, s, 
+          (int)L.disc().block.size(), L.brow_cell, L.brow_ptr, L.brow_col, L.brow_val, u, b, r, nullptr);
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
@@ -1778,7 +1996,7 @@ cc_status cc_smooth_noalloc(cc_handle H, int l, double* u, const double* b, cc_s
       return CC_ERR_ARG;
     }
     Level& L = *H->lv[l];
-    const BlockPlan& P = L.plan;
+    const BlockPlan& P = L.plan();
     const int64_t need = L.nn + 2 * (int64_t)P.m + P.ns;
     if (need > CC_NOALLOC_SCRATCH_DOUBLES) {
       snprintf(t_last_error, sizeof(t_last_error),
@@ -1816,7 +2034,7 @@ cc_status cc_smooth_noalloc(cc_handle H, int l, double* u, const double* b, cc_s
 cc_status cc_level_tables(cc_handle H, int l, uint8_t* h_kind, int* h_lattice, double* h_beta,
                           int* n_plg) {
   if (!H || l < 0 || l >= (int)H->lv.size()) return CC_ERR_ARG;
-  const LevelDisc& D = H->lv[l]->disc;
+  const LevelDisc& D = H->lv[l]->disc();
   if (h_kind) std::copy(D.kind.begin(), D.kind.end(), h_kind);
   for (size_t r = 0; r < D.plg.size(); ++r) {
     if (h_lattice) std::copy(D.lattice[r].begin(), D.lattice[r].end(), h_lattice + 15 * r);

@@ -309,3 +309,58 @@ def test_kernel_timing_leaves_the_solve_unchanged():
             # is written by the FP64 residual kernel, so 5 per cycle
             assert bytes_per == 3 * 4 * 256 * 256
             assert launches == 5 * r.cycles
+
+
+def _fourier_f(n, seed):
+    rng = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    f = np.zeros((n, n))
+    for p in range(1, 5):
+        for q in range(1, 5):
+            f += rng.standard_normal() / (p * p + q * q) * np.sin(p * np.pi * X) * np.sin(q * np.pi * Y)
+    return f
+
+
+def test_clone_and_batch_match_single_solves():
+    """cc_clone shares the tables and cc_solve_batch runs several solves at
+    once: every batched result equals, bit for bit, the same solve run alone,
+    for clones of one hierarchy and for hierarchies of different sizes; a
+    clone keeps working after its source is destroyed; a repeated handle is
+    rejected."""
+    from paper_2601_02975_gb300 import CCError, solve_batch
+    P, H, _ = _pair("disk", 128, 16, cycle=2, precision=1, w_depth=2)
+    f, g, _, _ = _gpu_rhs(H, P)
+    clones = [H.clone(), H.clone()]
+    hs = [H] + clones
+    fs = [_t(f + 50.0 * _fourier_f(128, k)) for k in range(3)]
+    gs = [_t(g)] * 3
+    alone = []
+    for k in range(3):
+        u = torch.zeros(128 * 128, dtype=torch.float64, device=DEV)
+        r = H.solve(fs[k], gs[k], u, 1e-12)
+        alone.append((u, r.cycles))
+    us = [torch.zeros(128 * 128, dtype=torch.float64, device=DEV) for _ in range(3)]
+    res = solve_batch(hs, fs, gs, us, [1e-12] * 3)
+    for k in range(3):
+        assert res[k].status == 0 and res[k].cycles == alone[k][1]
+        assert torch.equal(us[k], alone[k][0]), k
+    # different sizes and domains in one batch
+    P2 = _problem("ellipses0")
+    H2 = Hierarchy.from_domain(P2.dom, P2.a, P2.b, P2.c, 64,
+                               default_options(min_coarse_n=16, cycle=2, precision=1))
+    f2, g2, _, _ = _gpu_rhs(H2, P2)
+    u2a = torch.zeros(64 * 64, dtype=torch.float64, device=DEV)
+    H2.solve(_t(f2), _t(g2), u2a, 1e-11)
+    u1 = torch.zeros(128 * 128, dtype=torch.float64, device=DEV)
+    u2 = torch.zeros(64 * 64, dtype=torch.float64, device=DEV)
+    res = solve_batch([clones[0], H2], [fs[0], _t(f2)], [gs[0], _t(g2)], [u1, u2], [1e-12, 1e-11])
+    assert torch.equal(u1, alone[0][0]) and torch.equal(u2, u2a)
+    # the clone outlives its source
+    H.close()
+    u3 = torch.zeros(128 * 128, dtype=torch.float64, device=DEV)
+    clones[1].solve(fs[1], gs[1], u3, 1e-12)
+    assert torch.equal(u3, alone[1][0])
+    with pytest.raises(CCError) as ei:
+        solve_batch([clones[0], clones[0]], fs[:2], gs[:2], us[:2], [1e-12] * 2)
+    assert ei.value.status == 1
