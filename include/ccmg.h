@@ -95,6 +95,13 @@ typedef struct {
                           the cycle converges like the W-cycle on the domains
                           tested while each coarse level is visited twice per
                           cycle instead of 2^l times */
+  int serve_slots;     /* cc_submit: requests of this handle in flight at once (4);
+                          the slots beyond the first are clones (cc_clone) made
+                          when needed, within the cc_serve_budget cap */
+  int cache;           /* 1: reuse the setup of an identical earlier cc_setup call
+                          of this process (same domain, coefficients, conditions,
+                          N, eps, omega, min_coarse_n): the handle is then a clone
+                          of that hierarchy and setup costs no host time (0) */
 } cc_options;
 
 /* Sizes of a hierarchy. */
@@ -237,17 +244,40 @@ cc_status cc_solve_host(cc_handle h, const double* h_f, const double* h_g, doubl
                         double tol, cc_stream stream, cc_result* out);
 
 /*
- * cc_submit / cc_poll: streamed requests.  cc_submit queues a solve of
- * (d_f, d_g) into d_u on the handle's own worker and returns at once with a
- * request id; the arrays must stay valid until cc_poll reports completion.
- * cc_poll returns CC_ERR_BUSY while the request is queued or running, else
- * the request's final status with its result in *out (timestamps are seconds
- * on a monotonic host clock).  A finished request is forgotten after the
- * first poll that reports it.
+ * cc_submit / cc_poll: streamed requests with continuous batching.
+ * cc_submit queues a solve of (d_f, d_g) into d_u on the handle and returns at
+ * once with a request id; the arrays must be ready (their producers finished)
+ * when cc_submit is called and must stay valid until cc_poll reports
+ * completion.  A scheduler thread of the handle admits queued requests in
+ * order whenever one of its serve_slots slots is free (the handle itself, or
+ * a clone made on demand within the cc_serve_budget cap) and advances every
+ * request in flight as soon as its previous step has completed on the GPU,
+ * so requests that arrive while others run overlap with them on the device.
+ * Each request does exactly the arithmetic of cc_solve.  Do not call cc_solve
+ * on a handle while it serves requests.  cc_poll returns CC_ERR_BUSY while
+ * the request is queued or running, else the request's final status with its
+ * result in *out (timestamps are seconds on a monotonic host clock: submit,
+ * admission to a slot, completion).  A finished request is forgotten after
+ * the first poll that reports it.
  */
 cc_status cc_submit(cc_handle h, const double* d_f, const double* d_g, double* d_u,
                     double tol, uint64_t* req_id);
 cc_status cc_poll(uint64_t req_id, cc_result* out);
+
+/*
+ * cc_cache_clear: destroy the hierarchies held by the setup cache
+ * (cc_options.cache).  Handles made from them stay valid: they keep the
+ * shared tables alive until they are destroyed.
+ */
+cc_status cc_cache_clear(void);
+
+/*
+ * cc_serve_budget: cap, in bytes, on the device memory that the serving
+ * clones of all handles of this process may hold together (0: no cap, the
+ * default).  A scheduler whose next clone would pass the cap keeps requests
+ * queued until one of its slots frees.  Errors: CC_ERR_ARG for bytes < 0.
+ */
+cc_status cc_serve_budget(int64_t bytes);
 
 /* ---- operator-level entry points (one step of the method each) ------------
  * All take FP64 device arrays of the named level's size N_l x N_l and run on

@@ -39,7 +39,8 @@ class cc_options(C.Structure):
     _fields_ = [("eps", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("cycle", C.c_int), ("min_coarse_n", C.c_int), ("precision", C.c_int),
                 ("max_cycles", C.c_int), ("use_graphs", C.c_int), ("host_only", C.c_int),
-                ("fmg_cycle", C.c_int), ("w_depth", C.c_int)]
+                ("fmg_cycle", C.c_int), ("w_depth", C.c_int), ("serve_slots", C.c_int),
+                ("cache", C.c_int)]
 
 
 class cc_info(C.Structure):
@@ -79,6 +80,8 @@ _SIGS = {
                                       C.POINTER(C.c_int64), _P, _P, _P, _P, _P, _P]),
     "cc_solve": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, C.POINTER(cc_result)]),
     "cc_clone": (C.c_int, [_P, _P, C.POINTER(_P)]),
+    "cc_serve_budget": (C.c_int, [C.c_int64]),
+    "cc_cache_clear": (C.c_int, []),
     "cc_solve_batch": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                  C.POINTER(_P), C.POINTER(C.c_double), C.POINTER(_P),
                                  C.POINTER(cc_result)]),
@@ -332,3 +335,13 @@ def solve_batch(hs, fs, gs, us, tols, streams=None):
     if st not in (CC_OK, CC_ERR_NOT_CONVERGED, CC_ERR_DIVERGED):
         _check(st, "cc_solve_batch")
     return [out[i] for i in range(n)]
+
+
+def serve_budget(nbytes: int):
+    """cc_serve_budget: cap on the device memory of all serving clones (0: none)."""
+    _check(lib().cc_serve_budget(int(nbytes)), "cc_serve_budget")
+
+
+def cache_clear():
+    """cc_cache_clear: drop the setup cache (handles made from it stay valid)."""
+    _check(lib().cc_cache_clear(), "cc_cache_clear")

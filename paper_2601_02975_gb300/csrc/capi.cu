@@ -14,6 +14,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -612,6 +613,8 @@ struct cc_hierarchy {
   std::deque<uint64_t> queue;
   std::thread worker;
   bool stop = false;
+  std::vector<cc_hierarchy*> slots;     // serving clones (slot 0 is the handle itself)
+  int64_t slot_bytes = 0;               // device memory of the clones, counted in g_serve_used
   cudaStream_t wstream = nullptr;
   // cuda graphs of one solve iteration
   cudaGraphExec_t gexec[6] = {};             // [timed kernel][mixed]
@@ -633,6 +636,49 @@ struct Request {
   cc_result res;
   bool done = false;
 };
+
+// the setup cache (cc_options.cache): key of the setup arguments -> a
+// hierarchy owned by the cache, which hands out clones of it
+std::mutex g_cache_mu;
+std::map<std::string, cc_hierarchy*> g_cache;
+
+std::string setup_key(const cc_domain* dom, double a, double b, double c, const cc_bc* bc,
+                      int n_bc, int n, const cc_options& o, int device) {
+  std::string k;
+  auto put = [&](const void* p, size_t len) { k.append(static_cast<const char*>(p), len); };
+  put(&device, sizeof(device));
+  put(&dom->x0, sizeof(double));
+  put(&dom->y0, sizeof(double));
+  put(&dom->x1, sizeof(double));
+  put(&dom->y1, sizeof(double));
+  for (int i = 0; i < dom->n_holes; ++i) {
+    const cc_hole& e = dom->holes[i];
+    put(&e.kind, sizeof(int));
+    put(&e.cx, sizeof(double));
+    put(&e.cy, sizeof(double));
+    put(&e.r1, sizeof(double));
+    put(&e.r2, sizeof(double));
+    put(&e.theta, sizeof(double));
+  }
+  put(&a, sizeof(a));
+  put(&b, sizeof(b));
+  put(&c, sizeof(c));
+  for (int i = 0; i < n_bc; ++i) {
+    put(&bc[i].type, sizeof(int));
+    put(&bc[i].alpha1, sizeof(double));
+    put(&bc[i].alpha2, sizeof(double));
+  }
+  put(&n, sizeof(n));
+  put(&o.eps, sizeof(o.eps));
+  put(&o.omega, sizeof(o.omega));
+  put(&o.min_coarse_n, sizeof(o.min_coarse_n));
+  return k;
+}
+
+// device memory held by the serving clones of all handles, and its cap
+// (cc_serve_budget; 0: no cap)
+std::atomic<int64_t> g_serve_used{0};
+std::atomic<int64_t> g_serve_budget{0};
 std::mutex g_reqmu;
 std::unordered_map<uint64_t, Request> g_req;
 std::atomic<uint64_t> g_next_id{1};
@@ -1279,40 +1325,123 @@ cc_status solve_impl(cc_hierarchy* H, const double* f, const double* g, double* 
   return T[0].res.status;
 }
 
+// The serving scheduler of a handle (continuous batching).  Requests wait in
+// the handle's queue; whenever a slot is free (the handle itself, or a clone
+// created on demand up to serve_slots and within the serving memory budget)
+// the oldest request is admitted and started, and every request in flight is
+// advanced as soon as its previous step has completed on the GPU, so
+// requests that arrive while others run overlap with them on the device.
 void worker_loop(cc_hierarchy* H) {
-  CK(cudaSetDevice(H->device));
-  for (;;) {
+  if (cudaSetDevice(H->device) != cudaSuccess) return;
+  struct Active {
     uint64_t id;
-    {
-      std::unique_lock<std::mutex> lk(H->qmu);
-      H->qcv.wait(lk, [&] { return H->stop || !H->queue.empty(); });
-      if (H->stop && H->queue.empty()) return;
-      id = H->queue.front();
-      H->queue.pop_front();
+    double t_start;
+    SolveTask task;
+  };
+  std::vector<int> busy;                       // per slot: index into act, or -1
+  std::vector<Active> act;
+  if (H->slots.empty()) H->slots.push_back(H);
+  busy.assign(H->slots.size(), -1);
+  for (;;) {
+    // admit
+    for (;;) {
+      int free_slot = -1;
+      for (size_t k = 0; k < busy.size(); ++k)
+        if (busy[k] < 0) { free_slot = (int)k; break; }
+      uint64_t id = 0;
+      {
+        std::unique_lock<std::mutex> lk(H->qmu);
+        if (act.empty())
+          H->qcv.wait(lk, [&] { return H->stop || !H->queue.empty(); });
+        if (H->queue.empty()) {
+          if (H->stop && act.empty()) return;
+          break;
+        }
+        if (free_slot < 0 && (int)H->slots.size() >= std::max(1, H->opt.serve_slots)) break;
+        if (free_slot < 0) {
+          // a new clone, if the serving budget allows it
+          cc_hierarchy* c = nullptr;
+          const int64_t est = H->slots.size() > 1 ? H->slot_bytes / (int64_t)(H->slots.size() - 1)
+                                                  : H->pool->bytes;
+          const int64_t cap = g_serve_budget.load();
+          if (cap > 0 && g_serve_used.load() + est > cap) break;
+          if (cc_clone(H, (cc_stream)H->wstream, &c) != CC_OK) break;
+          H->slots.push_back(c);
+          H->slot_bytes += c->pool->bytes;
+          g_serve_used += c->pool->bytes;
+          busy.push_back(-1);
+          free_slot = (int)busy.size() - 1;
+        }
+        id = H->queue.front();
+        H->queue.pop_front();
+      }
+      Request rq;
+      {
+        std::lock_guard<std::mutex> lk(g_reqmu);
+        rq = g_req[id];
+      }
+      Active a;
+      a.id = id;
+      a.t_start = now_s();
+      cc_hierarchy* S = H->slots[free_slot];
+      a.task.H = S;
+      a.task.f = rq.f;
+      a.task.g = rq.g;
+      a.task.u = rq.u;
+      a.task.tol = rq.tol;
+      a.task.s = S == H ? H->wstream : S->gstream;
+      busy[free_slot] = (int)act.size();
+      act.push_back(a);
+      try {
+        solve_step(act.back().task);
+      } catch (CudaError&) {
+        act.back().task.res.status = CC_ERR_CUDA;
+        act.back().task.phase = 5;
+      }
     }
-    Request rq;
-    {
-      std::lock_guard<std::mutex> lk(g_reqmu);
-      rq = g_req[id];
+    // advance
+    bool moved = false;
+    for (size_t k = 0; k < busy.size(); ++k) {
+      if (busy[k] < 0) continue;
+      Active& a = act[busy[k]];
+      cudaError_t q = cudaEventQuery(a.task.H->step_ev);
+      if (q == cudaErrorNotReady) continue;
+      bool done = true;
+      if (q == cudaSuccess) {
+        try {
+          done = solve_step(a.task);
+        } catch (CudaError&) {
+          a.task.res.status = CC_ERR_CUDA;
+        }
+      } else {
+        (void)cudaGetLastError();
+        a.task.res.status = CC_ERR_CUDA;
+      }
+      moved = true;
+      if (!done) continue;
+      cc_result res = a.task.res;
+      {
+        std::lock_guard<std::mutex> lk(g_reqmu);
+        auto it = g_req.find(a.id);
+        if (it != g_req.end()) {
+          res.t_submit = it->second.res.t_submit;
+          res.t_start = a.t_start;
+          res.t_done = now_s();
+          it->second.res = res;
+          it->second.done = true;
+        }
+      }
+      // release the slot; keep act compact
+      const int idx = busy[k];
+      busy[k] = -1;
+      if (idx != (int)act.size() - 1) {
+        act[idx] = act.back();
+        for (auto& b : busy)
+          if (b == (int)act.size() - 1) b = idx;
+      }
+      act.pop_back();
     }
-    cc_result res{};
-    const double t_start = now_s();
-    cc_status st;
-    try {
-      st = solve_impl(H, rq.f, rq.g, rq.u, rq.tol, H->wstream, &res);
-    } catch (CudaError&) {
-      st = CC_ERR_CUDA;
-    }
-    res.status = st;
-    res.t_submit = rq.res.t_submit;
-    res.t_start = t_start;
-    res.t_done = now_s();
-    std::lock_guard<std::mutex> lk(g_reqmu);
-    auto it = g_req.find(id);
-    if (it != g_req.end()) {
-      it->second.res = res;
-      it->second.done = true;
-    }
+    if (!moved) std::this_thread::yield();
   }
 }
 
@@ -1326,6 +1455,9 @@ void destroy_hierarchy(cc_hierarchy* H) {
     H->qcv.notify_all();
     H->worker.join();
   }
+  for (size_t k = 1; k < H->slots.size(); ++k) destroy_hierarchy(H->slots[k]);
+  g_serve_used -= H->slot_bytes;
+  H->slots.clear();
   if (!H->opt.host_only) cudaDeviceSynchronize();
   for (auto& g : H->gexec)
     if (g) cudaGraphExecDestroy(g);
@@ -1361,6 +1493,8 @@ void cc_default_options(cc_options* o) {
   o->host_only = 0;
   o->fmg_cycle = CC_CYCLE_V;
   o->w_depth = 0;
+  o->serve_slots = 4;
+  o->cache = 0;
 }
 
 const char* cc_last_error_string(void) { return t_last_error; }
@@ -1393,9 +1527,24 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   if (opt) o = *opt;
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 == 0 || o.min_coarse_n < 4 || o.max_cycles < 1 ||
       !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3) ||
-      (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W) || o.w_depth < 0)
+      (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W) || o.w_depth < 0 ||
+      o.serve_slots < 1)
     return CC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  // the setup cache: a clone of the hierarchy of an identical earlier call
+  std::string key;
+  if (o.cache && !o.host_only) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CC_ERR_CUDA;
+    key = setup_key(dom, a, b, c, bc, n_bc, n, o, dev);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      cc_status st = cc_clone(it->second, stream, out);
+      if (st == CC_OK) (*out)->opt = o;
+      return st;
+    }
+  }
   cc_hierarchy* H = new cc_hierarchy();
   H->opt = o;
   Problem& P = H->P;
@@ -1601,7 +1750,25 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     destroy_hierarchy(H);
     return CC_ERR_NO_MEMORY;
   }
+  if (!key.empty()) {
+    // the cache keeps a clone of its own, so destroying H leaves it valid
+    cc_hierarchy* T = nullptr;
+    if (cc_clone(H, stream, &T) == CC_OK) {
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      if (!g_cache.emplace(key, T).second) destroy_hierarchy(T);
+    }
+  }
   *out = H;
+  return CC_OK;
+}
+
+cc_status cc_cache_clear(void) {
+  std::map<std::string, cc_hierarchy*> old;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    old.swap(g_cache);
+  }
+  for (auto& kv : old) destroy_hierarchy(kv.second);
   return CC_OK;
 }
 
@@ -1845,6 +2012,12 @@ cc_status cc_submit(cc_handle H, const double* f, const double* g, double* u, do
   }
   H->qcv.notify_one();
   *req_id = id;
+  return CC_OK;
+}
+
+cc_status cc_serve_budget(int64_t bytes) {
+  if (bytes < 0) return CC_ERR_ARG;
+  g_serve_budget = bytes;
   return CC_OK;
 }
 

@@ -364,3 +364,72 @@ def test_clone_and_batch_match_single_solves():
     with pytest.raises(CCError) as ei:
         solve_batch([clones[0], clones[0]], fs[:2], gs[:2], us[:2], [1e-12] * 2)
     assert ei.value.status == 1
+
+
+def _serve(H, fs, gs, us, tol):
+    import time
+    torch.cuda.synchronize()
+    ids = [H.submit(f, g, u, tol) for f, g, u in zip(fs, gs, us)]
+    out = {}
+    t0 = time.time()
+    while len(out) < len(ids):
+        for i in ids:
+            if i in out:
+                continue
+            st, res = H.poll(i)
+            if st != 9:
+                out[i] = (st, res)
+        assert time.time() - t0 < 120
+        time.sleep(0.0005)
+    return [out[i] for i in ids]
+
+
+def test_serving_continuous_batching():
+    """cc_submit / cc_poll with three slots: nine requests with different
+    right-hand sides all finish with the bits of the same solve run alone,
+    several are in flight at once, and under a serving budget too small for
+    any clone every request still finishes (one at a time on the handle).  The
+    setup cache hands out a clone of an earlier identical setup that stays
+    valid after the cache is cleared."""
+    from paper_2601_02975_gb300 import cache_clear, serve_budget
+    P, H, _ = _pair("disk", 128, 16, cycle=2, precision=1, w_depth=2, serve_slots=3)
+    f, g, _, _ = _gpu_rhs(H, P)
+    fs = [_t(f + 50.0 * _fourier_f(128, 10 + k)) for k in range(9)]
+    gs = [_t(g)] * 9
+    Hs = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 128,
+                               default_options(min_coarse_n=16, cycle=2, precision=1, w_depth=2))
+    alone = []
+    for k in range(9):
+        u = torch.zeros(128 * 128, dtype=torch.float64, device=DEV)
+        Hs.solve(fs[k], gs[k], u, 1e-12)
+        alone.append(u)
+    us = [torch.zeros(128 * 128, dtype=torch.float64, device=DEV) for _ in range(9)]
+    res = _serve(H, fs, gs, us, 1e-12)
+    for k, (st, r) in enumerate(res):
+        assert st == 0 and r.t_done >= r.t_start >= r.t_submit
+        assert torch.equal(us[k], alone[k]), k
+    spans = sorted((r.t_start, r.t_done) for _, r in res)
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1)), "no overlap"
+    try:
+        serve_budget(1)
+        H2 = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 128,
+                                   default_options(min_coarse_n=16, cycle=2, precision=1,
+                                                   w_depth=2, serve_slots=3))
+        us2 = [torch.zeros(128 * 128, dtype=torch.float64, device=DEV) for _ in range(4)]
+        res2 = _serve(H2, fs[:4], gs[:4], us2, 1e-12)
+        assert all(st == 0 for st, _ in res2)
+        for k in range(4):
+            assert torch.equal(us2[k], alone[k])
+        spans = sorted((r.t_start, r.t_done) for _, r in res2)
+        assert all(spans[i + 1][0] >= spans[i][1] for i in range(len(spans) - 1))
+    finally:
+        serve_budget(0)
+    opt = default_options(min_coarse_n=16, cycle=2, precision=1, w_depth=2, cache=1)
+    Ha = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 128, opt)
+    Hb = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 128, opt)
+    assert Hb.info.device_bytes < Ha.info.device_bytes      # a clone: work arrays only
+    cache_clear()
+    Ha.close()
+    ub = torch.zeros(128 * 128, dtype=torch.float64, device=DEV)
+    Hb.solve(fs[0], gs[0], ub, 1e-12)
+    assert torch.equal(ub, alone[0])
