@@ -56,6 +56,10 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", type=int, default=120,
+                    help="requests in the serving measurement (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0,
+                    help="mean arrival rate of the serving measurement, requests per second")
     ap.add_argument("--batch", type=int, default=8,
                     help="independent solves in the concurrent-batch measurement (0: skip)")
     ap.add_argument("--min-coarse", type=int, default=MIN_COARSE,
@@ -350,6 +354,8 @@ def run_ours(a):
                  "cycles": [r.cycles for r in res], "timing": "host wall clock around the call "
                  "(the call returns when every result is in place)"}
 
+    serving = run_serving(a, dev) if a.serve > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -374,6 +380,7 @@ def run_ours(a):
         "clocks": clk.summary(),
         "max_error_vs_exact": err,
         "batch": batch,
+        "serving": serving,
         "fp64_solve": {"ms": fp64_ms, "dof_per_s": dof / (fp64_ms / 1e3), "cycles": r64.cycles,
                        "max_error_vs_exact": err64},
         "wall_s_timed": wall,
@@ -383,6 +390,87 @@ def run_ours(a):
 
 
 # ---------------------------------------------------------------------------
+SERVE_SIZES = (128, 256, 512, 1024)
+SERVE_WEIGHTS = (0.5 / 3, 0.5 / 3, 0.5 / 3, 0.3)   # the request mix without its 2048^2/4096^2 share
+
+
+def run_serving(a, dev):
+    """Poisson-arrival stream of disk-domain solves of mixed sizes through
+    cc_submit / cc_poll (continuous batching, 4 slots per size), in the mixed
+    and in the FP64 mode: p50 / p99 latency (submit to completion) and DOF/s."""
+    import numpy as np
+    import torch
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from paper_2601_02975_gb300 import inputs as I
+    P = _problem()
+    rng = np.random.default_rng(11)
+    w = np.array(SERVE_WEIGHTS) / sum(SERVE_WEIGHTS)
+    nreq = a.serve
+    sizes = rng.choice(len(SERVE_SIZES), size=nreq, p=w)
+    gaps = rng.exponential(1.0 / a.serve_rate, size=nreq)
+    out = {"requests": nreq, "rate_per_s": a.serve_rate,
+           "sizes": {str(n): int((sizes == i).sum()) for i, n in enumerate(SERVE_SIZES)},
+           "workload": "disk domain, Poisson arrivals, random-Fourier perturbation of f per "
+                       "request, tol 1e-13, 4 slots per size"}
+    for prec, name in ((1, "mixed"), (0, "fp64")):
+        hs, base = [], []
+        for n in SERVE_SIZES:
+            H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                      default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=prec,
+                                                      max_cycles=60, w_depth=W_DEPTH, serve_slots=4))
+            f, g, _ = I.problem_inputs(H, P)
+            hs.append(H)
+            base.append((f, torch.tensor(g, dtype=torch.float64, device=dev), int(H.info.n_dof)))
+        req = []
+        for k in range(nreq):
+            i = sizes[k]
+            n = SERVE_SIZES[i]
+            x = (np.arange(n) + 0.5) / n
+            pert = sum(rng.standard_normal() / (p * p + q * q) * np.outer(np.sin(q * np.pi * x),
+                                                                          np.sin(p * np.pi * x))
+                       for p in range(1, 9) for q in range(1, 9))
+            f = torch.tensor((base[i][0] + 20.0 * pert).ravel(), dtype=torch.float64, device=dev)
+            req.append((i, f, torch.zeros(n * n, dtype=torch.float64, device=dev)))
+        # warm-up: one request per size (graph capture, clones)
+        for i in range(len(SERVE_SIZES)):
+            u = torch.zeros(SERVE_SIZES[i] ** 2, dtype=torch.float64, device=dev)
+            fw = torch.tensor(base[i][0].ravel(), dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            rid = hs[i].submit(fw, base[i][1], u, TOL)
+            while hs[i].poll(rid)[0] == 9:
+                time.sleep(0.0005)
+        torch.cuda.synchronize()
+        pending, lat, dof_done, fails = {}, [], 0, 0
+        t0 = time.perf_counter()
+        t_next = t0
+        k = 0
+        while k < nreq or pending:
+            now = time.perf_counter()
+            while k < nreq and now >= t_next:
+                i, f, u = req[k]
+                pending[hs[i].submit(f, base[i][1], u, TOL)] = i
+                k += 1
+                if k < nreq:
+                    t_next += gaps[k]
+            for rid in list(pending):
+                st, r = Hierarchy.poll(rid)
+                if st == 9:
+                    continue
+                i = pending.pop(rid)
+                if st != 0:
+                    fails += 1
+                lat.append(r.t_done - r.t_submit)
+                dof_done += base[i][2]
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        lat = np.sort(np.array(lat)) * 1e3
+        out[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "dof_per_s": dof_done / wall, "wall_s": wall, "failed": fails}
+        for H in hs:
+            H.close()
+    return out
+
+
 def _oracle_sample(n: int):
     """Oracle solve of the same disk problem on an n x n grid (setup excluded)."""
     import numpy as np
