@@ -44,8 +44,9 @@ MIN_COARSE = 32
 W_DEPTH = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of each kernel, keyed like cc_kernel_timing's kernels; None
-# until captured for the kernels as they are now
-TRAFFIC = {1: None, 2: None}
+# until captured for the kernels as they are now (k_sweep_w: profiles/k_sweep_w_disk1024.md;
+# the timed dense block solves include gather + GEMV launches not captured yet)
+TRAFFIC = {1: 9.48e6, 2: None}
 
 
 def _args():
