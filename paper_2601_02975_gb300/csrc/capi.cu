@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -833,10 +834,35 @@ template <> const StencilP<float>& sparams<float>(Level& L) { return L.spf; }
 
 // Jacobi sweep on level L: 32 x 32 tiles (4 rows per thread) on large grids,
 // 32 x 8 tiles on small ones, where more CTAs matter more than fewer loads.
+// CTAs of the streamed sweep: one wave at its occupancy
+template <bool CROSS>
+int sweep_p_blocks() {
+  static const int blocks = [] {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_p<CROSS>, TX * TY, 0);
+    return std::max(1, sms) * std::max(1, occ);
+  }();
+  return blocks;
+}
+
 template <class T>
 void launch_sweep(Level& L, const T* in, T* out, const T* b, const T* ec, bool zero,
                   cudaStream_t s) {
   const auto& P = sparams<T>(L);
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.n >= 256 && L.n % 32 == 0) {
+      const int nt = (L.n / TX) * (L.n / WY);
+      if (L.sp.cross)
+        pdl_launch(k_sweep_p<true>, std::min(nt, sweep_p_blocks<true>()), TX * TY, 0, s, in, out, b, L.cls,
+                   ec, P, (int)zero);
+      else
+        pdl_launch(k_sweep_p<false>, std::min(nt, sweep_p_blocks<false>()), TX * TY, 0, s, in, out, b,
+                   L.cls, ec, P, (int)zero);
+      return;
+    }
+  }
   if (L.n >= 256) {
     dim3 g((L.n + TX - 1) / TX, (L.n + WY - 1) / WY);
     if (L.sp.cross) pdl_launch(k_sweep_w<T, true>, g, TX * TY, 0, s, in, out, b, L.cls, ec, P, zero);

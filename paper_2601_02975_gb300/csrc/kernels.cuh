@@ -286,6 +286,225 @@ k_sweep_w(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict
   pdl_exit();
 }
 
+// ---- a1 streamed: persistent, multi-buffered windowed sweep (FP32) -----------
+// The arithmetic of k_sweep_w on the same 32 x 32 tiles, but each CTA walks a
+// sequence of tiles and copies the next tile's u window, b, class bytes and
+// (on the fused post-sweep) coarse correction global -> shared with cp.async
+// while it computes the current one, so loads stay in flight for the whole
+// lifetime of the CTA.  Every copy is a 16-byte chunk that lies wholly inside
+// or wholly outside the grid (N a multiple of 16); outside chunks are
+// zero-filled and no byte is read for them.  Wall ghosts are formed in shared
+// memory from the loaded inward cells.
+constexpr int PW = 40;          // u window row: x0 - 4 .. x0 + 35 (16-byte aligned start)
+constexpr int CWC = 24;         // coarse row: x0/2 - 4 .. x0/2 + 19
+constexpr int CHC = 18;         // coarse rows: y0/2 - 1 .. y0/2 + 16
+
+struct __align__(16) SweepStage {
+  float u[WSH][PW];
+  float b[WY][TX];
+  uint8_t c[WY][TX];
+  float e[CHC][CWC];
+};
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Per-thread copy assignments of the streamed sweep, fixed for every tile:
+// thread t copies u-window chunks t and t + 256 (36 rows x 10 chunks), b chunk
+// t (32 x 8), class chunk t < 64 (32 x 2) and coarse chunk t < 108 (18 x 6).
+struct SweepLanes {
+  int ur0, uc0, ur1, uc1;     // u window: row, column of the chunk (ur1 < 0: none)
+  int br, bc, cr, cc, er, ec; // b, class, coarse (cr / er < 0: none)
+  __device__ __forceinline__ SweepLanes(int t) {
+    ur0 = t / (PW / 4); uc0 = 4 * (t % (PW / 4));
+    const int t1 = t + TX * TY;
+    ur1 = t1 < WSH * (PW / 4) ? t1 / (PW / 4) : -1;
+    uc1 = 4 * (t1 % (PW / 4));
+    br = t / (TX / 4); bc = 4 * (t % (TX / 4));
+    cr = t < WY * (TX / 16) ? t / (TX / 16) : -1;
+    cc = 16 * (t % (TX / 16));
+    er = t < CHC * (CWC / 4) ? t / (CWC / 4) : -1;
+    ec = 4 * (t % (CWC / 4));
+  }
+};
+
+__device__ __forceinline__ void sweep_issue(SweepStage& st, const SweepLanes& ln,
+                                            const float* __restrict__ u, const float* __restrict__ b,
+                                            const uint8_t* __restrict__ cls,
+                                            const float* __restrict__ ec, int n, int x0, int y0,
+                                            bool zero) {
+  {
+    const int gy = y0 - HALO + ln.ur0, gx = x0 - 4 + ln.uc0;
+    const bool ok = !zero && gy >= 0 && gy < n && gx >= 0 && gx < n;
+    cp_async16(&st.u[ln.ur0][ln.uc0], ok ? u + (size_t)gy * n + gx : u, ok);
+  }
+  if (ln.ur1 >= 0) {
+    const int gy = y0 - HALO + ln.ur1, gx = x0 - 4 + ln.uc1;
+    const bool ok = !zero && gy >= 0 && gy < n && gx >= 0 && gx < n;
+    cp_async16(&st.u[ln.ur1][ln.uc1], ok ? u + (size_t)gy * n + gx : u, ok);
+  }
+  {
+    const int gy = y0 + ln.br, gx = x0 + ln.bc;
+    const bool ok = gy < n && gx < n;
+    cp_async16(&st.b[ln.br][ln.bc], ok ? b + (size_t)gy * n + gx : b, ok);
+  }
+  if (ln.cr >= 0) {
+    const int gy = y0 + ln.cr, gx = x0 + ln.cc;
+    const bool ok = gy < n && gx < n;
+    cp_async16(&st.c[ln.cr][ln.cc], ok ? cls + (size_t)gy * n + gx : cls, ok);
+  }
+  if (ec && ln.er >= 0) {
+    const int nc = n >> 1;
+    const int cy = (y0 >> 1) - 1 + ln.er, cx = (x0 >> 1) - 4 + ln.ec;
+    const bool ok = cy >= 0 && cy < nc && cx >= 0 && cx < nc;
+    cp_async16(&st.e[ln.er][ln.ec], ok ? ec + (size_t)cy * nc + cx : ec, ok);
+  }
+}
+
+// u + I(ec) on the in-grid cells of the window (one 4-cell chunk per step:
+// the chunk's cells pair up on 2 coarse cells), then the wall ghosts (the
+// homogeneous part of each wall's formula, as halo_value)
+__device__ __forceinline__ void sweep_fixup(SweepStage& st, const SweepLanes& ln, const float* ec,
+                                            const StencilP<float>& P, int x0, int y0) {
+  const int n = P.n;
+  if (ec) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int r = k ? ln.ur1 : ln.ur0, c = k ? ln.uc1 : ln.uc0;
+      if (r < 0) continue;
+      const int gy = y0 - HALO + r, gx = x0 - 4 + c;
+      if (gy < 0 || gy >= n || gx < 0 || gx >= n) continue;
+      const float* e = &st.e[(gy >> 1) - ((y0 >> 1) - 1)][(gx >> 1) - ((x0 >> 1) - 4)];
+      float4 v = *reinterpret_cast<float4*>(&st.u[r][c]);
+      v.x += e[0];
+      v.y += e[0];
+      v.z += e[1];
+      v.w += e[1];
+      *reinterpret_cast<float4*>(&st.u[r][c]) = v;
+    }
+    __syncthreads();
+  }
+  const bool wl = x0 == 0, wr = x0 + TX >= n, wb = y0 == 0, wt = y0 + WY >= n;
+  if (!(wl || wr || wb || wt)) return;
+  // 2 ghost layers x WSH rows on the side walls, 2 x PW columns on the others
+  for (int i = threadIdx.x; i < 2 * WSH; i += blockDim.x) {
+    const int m = i / WSH, r = i % WSH;
+    const int gy = y0 - HALO + r;
+    if (gy < 0 || gy >= n) continue;
+    if (wl) {
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc += P.gh[3][m][q] * st.u[r][4 + q];
+      st.u[r][3 - m] = acc;
+    }
+    if (wr) {
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc += P.gh[1][m][q] * st.u[r][(n - 1 - q) - (x0 - 4)];
+      st.u[r][(n + m) - (x0 - 4)] = acc;
+    }
+  }
+  for (int i = threadIdx.x; i < 2 * PW; i += blockDim.x) {
+    const int m = i / PW, c = i % PW;
+    const int gx = x0 - 4 + c;
+    if (gx < 0 || gx >= n) continue;
+    if (wb) {
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc += P.gh[0][m][q] * st.u[HALO + q][c];
+      st.u[HALO - 1 - m][c] = acc;
+    }
+    if (wt) {
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc += P.gh[2][m][q] * st.u[(n - 1 - q) - (y0 - HALO)][c];
+      st.u[(n + m) - (y0 - HALO)][c] = acc;
+    }
+  }
+}
+
+// tile cursor: tile (bx, by) of a tpr-wide grid of tiles, advanced by the
+// grid size with an add and a carry (no division per tile)
+struct TileCursor {
+  int bx, by;
+  __device__ __forceinline__ void advance(int dx, int dy, int tpr) {
+    bx += dx;
+    by += dy;
+    if (bx >= tpr) {
+      bx -= tpr;
+      ++by;
+    }
+  }
+};
+
+template <bool CROSS>
+__global__ void __launch_bounds__(TX * TY)
+k_sweep_p(const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ b,
+          const uint8_t* __restrict__ cls, const float* __restrict__ ec, StencilP<float> P,
+          int zero) {
+  constexpr int NS = 2;            // stages: one tile in flight while one is computed
+  pdl_enter();
+  __shared__ SweepStage st[NS];
+  const int n = P.n;
+  const int tpr = (n + TX - 1) / TX, rows = (n + WY - 1) / WY;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const SweepLanes ln(threadIdx.x);
+  const int dx = (int)gridDim.x % tpr, dy = (int)gridDim.x / tpr;
+  TileCursor ct{(int)blockIdx.x % tpr, (int)blockIdx.x / tpr};   // tile being computed
+  TileCursor it = ct;                                              // next tile to copy
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) {
+    if (it.by < rows) sweep_issue(st[k], ln, u_in, b, cls, ec, n, it.bx * TX, it.by * WY, zero != 0);
+    cp_async_commit();
+    it.advance(dx, dy, tpr);
+  }
+  for (int i = 0; ct.by < rows; ++i) {
+    if (it.by < rows)
+      sweep_issue(st[(i + NS - 1) % NS], ln, u_in, b, cls, ec, n, it.bx * TX, it.by * WY, zero != 0);
+    cp_async_commit();
+    it.advance(dx, dy, tpr);
+    cp_async_wait<NS - 1>();      // the group of the tile being computed is complete
+    __syncthreads();
+    SweepStage& S = st[i % NS];
+    const int x0 = ct.bx * TX, y0 = ct.by * WY;
+    sweep_fixup(S, ln, ec, P, x0, y0);
+    __syncthreads();
+    // rows 4 ty - 2 .. 4 ty + 5 of the window (tile rows 4 ty .. 4 ty + 7),
+    // the arithmetic of k_sweep_w
+    float lx[8], gxr[8], cc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float* row = &S.u[4 * ty + k][tx + 2];
+      const float v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3], v4 = row[4];
+      lx[k] = 16.f * (v1 + v3) - 30.f * v2 - (v0 + v4);
+      gxr[k] = 8.f * (v3 - v1) + (v0 - v4);
+      cc[k] = v2;
+    }
+    float* out = u_out + (size_t)(y0 + 4 * ty) * n + x0 + tx;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (S.c[4 * ty + r][tx] != C_STENCIL) continue;
+      const int j = r + 2;
+      const float ly = 16.f * (cc[j - 1] + cc[j + 1]) - 30.f * cc[j] - (cc[j - 2] + cc[j + 2]);
+      float Au = P.sx * lx[j] + P.sy * ly;
+      if (CROSS) Au += P.sxy * (8.f * (gxr[j + 1] - gxr[j - 1]) + (gxr[j - 2] - gxr[j + 2]));
+      out[(size_t)r * n] = cc[j] + P.omega_over_diag * (S.b[4 * ty + r][tx] - Au);
+    }
+    __syncthreads();
+    ct.advance(dx, dy, tpr);
+  }
+  cp_async_wait<0>();
+  pdl_exit();
+}
+
 // ---- a4: residual and restriction (Eq. 5.10) ---------------------------------
 // r = b - A u on stencil cells, 0 on block and empty cells (the block residual
 // is zero after a block-smoother sweep); rc = average of the 4 children,

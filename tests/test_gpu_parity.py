@@ -433,3 +433,25 @@ def test_serving_continuous_batching():
     ub = torch.zeros(128 * 128, dtype=torch.float64, device=DEV)
     Hb.solve(fs[0], gs[0], ub, 1e-12)
     assert torch.equal(ub, alone[0])
+
+
+@pytest.mark.parametrize("name", ["disk", "ellipses0"])
+def test_streamed_sweep_in_mixed_solve(name):
+    """On grids of 256^2 and more the FP32 cycles sweep with the streamed
+    (cp.async double-buffered) kernel: the mixed solve at 256^2 takes the
+    FP64 solve's cycles to 1e-12 and lands within 1.1x of its error against
+    the exact cell averages."""
+    P = _problem(name)
+    res = {}
+    for prec in (0, 1):
+        H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 256,
+                                  default_options(min_coarse_n=32, cycle=2, w_depth=2, precision=prec))
+        f, g, ue, _ = _gpu_rhs(H, P)
+        u = torch.zeros(256 * 256, dtype=torch.float64, device=DEV)
+        r = H.solve(_t(f), _t(g), u, 1e-12)
+        present = H.cell_types()[0] != 0
+        res[prec] = (r, np.abs(_np(u, 256) - ue)[present].max())
+    (r64, e64), (rm, em) = res[0], res[1]
+    assert r64.status == 0 and rm.status == 0 and rm.rel_res < 1e-12
+    assert abs(rm.cycles - r64.cycles) <= 1
+    assert em <= 1.1 * e64 + 1e-14, (em, e64)
