@@ -431,6 +431,16 @@ __device__ __forceinline__ void sweep_fixup(SweepStage& st, const SweepLanes& ln
   }
 }
 
+// window columns 4 q4 .. 4 q4 + 11 of window row r (three 16-byte vectors):
+// the x-stencil of tile columns 4 q4 .. 4 q4 + 3 at w[2 + k .. 6 + k]
+__device__ __forceinline__ void load12(const SweepStage& S, int r, int q4, float* w) {
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    const float4 a = *reinterpret_cast<const float4*>(&S.u[r][4 * q4 + 4 * v]);
+    w[4 * v] = a.x; w[4 * v + 1] = a.y; w[4 * v + 2] = a.z; w[4 * v + 3] = a.w;
+  }
+}
+
 // tile cursor: tile (bx, by) of a tpr-wide grid of tiles, advanced by the
 // grid size with an add and a carry (no division per tile)
 struct TileCursor {
@@ -455,7 +465,7 @@ k_sweep_p(const float* __restrict__ u_in, float* __restrict__ u_out, const float
   __shared__ SweepStage st[NS];
   const int n = P.n;
   const int tpr = (n + TX - 1) / TX, rows = (n + WY - 1) / WY;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int q4 = threadIdx.x & 7, row = threadIdx.x >> 3;
   const SweepLanes ln(threadIdx.x);
   const int dx = (int)gridDim.x % tpr, dy = (int)gridDim.x / tpr;
   TileCursor ct{(int)blockIdx.x % tpr, (int)blockIdx.x / tpr};   // tile being computed
@@ -477,26 +487,55 @@ k_sweep_p(const float* __restrict__ u_in, float* __restrict__ u_out, const float
     const int x0 = ct.bx * TX, y0 = ct.by * WY;
     sweep_fixup(S, ln, ec, P, x0, y0);
     __syncthreads();
-    // rows 4 ty - 2 .. 4 ty + 5 of the window (tile rows 4 ty .. 4 ty + 7),
-    // the arithmetic of k_sweep_w
-    float lx[8], gxr[8], cc[8];
+    // thread (q4, row): tile row `row`, tile columns 4 q4 .. 4 q4 + 3 (window
+    // columns 4 q4 + 4 .. + 7), read as 16-byte vectors; per cell the
+    // arithmetic and its order are k_sweep_w's
+    const int rr = row + HALO;
+    float w[12];
+    load12(S, rr, q4, w);
+    float c[5][4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float* row = &S.u[4 * ty + k][tx + 2];
-      const float v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3], v4 = row[4];
-      lx[k] = 16.f * (v1 + v3) - 30.f * v2 - (v0 + v4);
-      gxr[k] = 8.f * (v3 - v1) + (v0 - v4);
-      cc[k] = v2;
+    for (int d = 0; d < 5; ++d) {
+      if (d == 2) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[2][k] = w[4 + k];
+      } else {
+        const float4 v = *reinterpret_cast<const float4*>(&S.u[rr - 2 + d][4 * q4 + 4]);
+        c[d][0] = v.x; c[d][1] = v.y; c[d][2] = v.z; c[d][3] = v.w;
+      }
     }
-    float* out = u_out + (size_t)(y0 + 4 * ty) * n + x0 + tx;
+    float g[5][4];
+    if (CROSS) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      if (S.c[4 * ty + r][tx] != C_STENCIL) continue;
-      const int j = r + 2;
-      const float ly = 16.f * (cc[j - 1] + cc[j + 1]) - 30.f * cc[j] - (cc[j - 2] + cc[j + 2]);
-      float Au = P.sx * lx[j] + P.sy * ly;
-      if (CROSS) Au += P.sxy * (8.f * (gxr[j + 1] - gxr[j - 1]) + (gxr[j - 2] - gxr[j + 2]));
-      out[(size_t)r * n] = cc[j] + P.omega_over_diag * (S.b[4 * ty + r][tx] - Au);
+      for (int d = 0; d < 5; ++d) {
+        if (d == 2) continue;
+        float wd[12];
+        load12(S, rr - 2 + d, q4, wd);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          g[d][k] = 8.f * (wd[5 + k] - wd[3 + k]) + (wd[2 + k] - wd[6 + k]);
+      }
+    }
+    const float4 bv = *reinterpret_cast<const float4*>(&S.b[row][4 * q4]);
+    const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+    const uint32_t cl = *reinterpret_cast<const uint32_t*>(&S.c[row][4 * q4]);
+    float o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float lx = 16.f * (w[3 + k] + w[5 + k]) - 30.f * w[4 + k] - (w[2 + k] + w[6 + k]);
+      const float ly = 16.f * (c[1][k] + c[3][k]) - 30.f * c[2][k] - (c[0][k] + c[4][k]);
+      float Au = P.sx * lx + P.sy * ly;
+      if (CROSS) Au += P.sxy * (8.f * (g[3][k] - g[1][k]) + (g[0][k] - g[4][k]));
+      o[k] = c[2][k] + P.omega_over_diag * (bb[k] - Au);
+    }
+    float* out = u_out + (size_t)(y0 + row) * n + x0 + 4 * q4;
+    const uint32_t all = C_STENCIL * 0x01010101u;
+    if (cl == all) {
+      *reinterpret_cast<float4*>(out) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (((cl >> (8 * k)) & 0xffu) == C_STENCIL) out[k] = o[k];
     }
     __syncthreads();
     ct.advance(dx, dy, tpr);
