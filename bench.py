@@ -61,6 +61,8 @@ def _args():
                     help="requests in the serving measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0,
                     help="mean arrival rate of the serving measurement, requests per second")
+    ap.add_argument("--hbm-n", type=int, default=4096,
+                    help="grid of the HBM-bound sweep measurement (0: skip)")
     ap.add_argument("--batch", type=int, default=8,
                     help="independent solves in the concurrent-batch measurement (0: skip)")
     ap.add_argument("--min-coarse", type=int, default=MIN_COARSE,
@@ -356,6 +358,7 @@ def run_ours(a):
                  "(the call returns when every result is in place)"}
 
     serving = run_serving(a, dev) if a.serve > 0 else None
+    roof_hbm = hbm_sweep(a, dev, peak, src) if a.hbm_n > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -377,6 +380,7 @@ def run_ours(a):
         "gpu_launches": kernels,
         "roofline": roof,
         "roofline_other": roof_other,
+        "roofline_hbm": roof_hbm,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "max_error_vs_exact": err,
@@ -391,6 +395,39 @@ def run_ours(a):
 
 
 # ---------------------------------------------------------------------------
+def hbm_sweep(a, dev, peak, src):
+    """The finest-level FP32 sweep where it streams from HBM: two cycles of a
+    Poisson solve on the unit square at hbm_n^2 (levels too large for L2),
+    timed with CUDA events around each launch inside the solve graph."""
+    import torch
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from paper_2601_02975_gb300 import inputs as I
+    from paper_2601_02975_gb300 import workloads as W
+    P = W.problem_poisson_square()
+    n = a.hbm_n
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                              default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1,
+                                              max_cycles=2, w_depth=W_DEPTH))
+    f, g, _ = I.problem_inputs(H, P)
+    ft = torch.tensor(f.ravel(), dtype=torch.float64, device=dev)
+    gt = torch.tensor(g, dtype=torch.float64, device=dev)
+    u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    H.solve(ft, gt, u, 1e-300)
+    H.kernel_timing(1)
+    u.zero_()
+    H.solve(ft, gt, u, 1e-300)
+    launches, tot_ms, bytes_per = H.kernel_timing_read()
+    H.kernel_timing(0)
+    H.close()
+    achieved = bytes_per / (tot_ms / launches) / 1e6
+    return {"kernel": f"k_sweep_p<float> (finest level, Poisson unit square {n}x{n})", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": src, "launches": launches,
+            "us_per_launch": 1e3 * tot_ms / launches, "bytes_per_launch": bytes_per,
+            "note": "algorithmic bytes 3 x 4 x N^2 (u, b read; u written); each interval includes "
+                    "the launch latency"}
+
+
 SERVE_SIZES = (128, 256, 512, 1024)
 SERVE_WEIGHTS = (0.5 / 3, 0.5 / 3, 0.5 / 3, 0.3)   # the request mix without its 2048^2/4096^2 share
 
