@@ -289,7 +289,7 @@ def run_ours(a):
     peak = float(peaks["hbm_gbs"])
     roofs = {}
     for which, name in ((2, "k_block_dense<float> (coarse levels, blocks <= 1024 cells)"),
-                        (1, "k_sweep_w<float> (finest level)")):
+                        (1, "k_sweep_p<float> (finest level)")):
         H.kernel_timing(which)
         for _ in range(2):
             flush.fill_(3.0)

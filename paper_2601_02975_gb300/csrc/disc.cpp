@@ -37,6 +37,8 @@
 #include <functional>
 #include <map>
 #include <numeric>
+#include <string>
+#include <thread>
 
 #include "setup.h"
 
@@ -276,7 +278,19 @@ LevelDisc discretize(const Problem& P, int n) {
   for (int k = 0; k < n * n; ++k)
     if (D.kind[k] == K_PLG) D.plg.push_back(k);
   const auto& B = basis();
-  for (int k : D.plg) {
+  // the fits are independent: computed on all host cores into per-cell slots,
+  // then appended in PLG order (the result does not depend on the threads)
+  struct PlgOut {
+    std::array<int, 15> lat{};
+    std::array<double, 16> bt{};
+    bool withb = false;
+    int err = 0;
+    const char* msg = "";
+  };
+  std::vector<PlgOut> outs(D.plg.size());
+  auto fit_one = [&](size_t pr) {
+    const int k = D.plg[pr];
+    PlgOut& O = outs[pr];
     const int i0 = k % n, j0 = k / n;
     // lattice: dynamic programme over lines
     struct Cand { int cost; int orient; std::vector<int> key; std::vector<int> cells; bool ok = false; };
@@ -359,12 +373,15 @@ LevelDisc discretize(const Problem& P, int n) {
         }
       }
     }
-    if (!best.ok || best.cells.size() != 15)
-      throw SetupError(3, "no poised lattice for a PLG cell");
+    if (!best.ok || best.cells.size() != 15) {
+      O.err = 3;
+      O.msg = "no poised lattice for a PLG cell";
+      return;
+    }
     std::sort(best.cells.begin(), best.cells.end());
     std::array<int, 15> lat;
     std::copy(best.cells.begin(), best.cells.end(), lat.begin());
-    D.lattice.push_back(lat);
+    O.lat = lat;
     // --- fit: rows basis functions, columns lattice cells (+ boundary) -------
     bool withb = false;
     std::vector<BNode> bn;
@@ -425,18 +442,47 @@ LevelDisc discretize(const Problem& P, int n) {
       for (int r = 0; r < 15; ++r)
         for (int c = 0; c < 16; ++c) Ms[(size_t)r * 16 + c] *= sw[c];
       std::vector<double> g;
-      if (!min_norm(Ms, rhs, 15, 16, g)) throw SetupError(3, "singular PLG fit");
+      if (!min_norm(Ms, rhs, 15, 16, g)) {
+        O.err = 3;
+        O.msg = "singular PLG fit";
+        return;
+      }
       for (int c = 0; c < 16; ++c) bt[c] = sw[c] * g[c];
-      D.bd_of_plg.push_back((int)D.bd_cells.size());
-      D.bd_cells.push_back(k);
+      O.withb = true;
     } else {
       std::vector<double> x(rhs);
-      if (!lu_solve(M, x, 15)) throw SetupError(3, "singular PLG fit");
+      if (!lu_solve(M, x, 15)) {
+        O.err = 3;
+        O.msg = "singular PLG fit";
+        return;
+      }
       for (int c = 0; c < 15; ++c) bt[c] = x[c];
       bt[15] = 0.0;
-      D.bd_of_plg.push_back(-1);
     }
-    D.beta.push_back(bt);
+    O.bt = bt;
+  };
+  {
+    const size_t np = D.plg.size();
+    unsigned T = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+    if (np < 256) T = 1;
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < T; ++t)
+      pool.emplace_back([&, t] {
+        for (size_t r = t; r < np; r += T) fit_one(r);
+      });
+    for (size_t r = 0; r < np; r += T) fit_one(r);
+    for (auto& th : pool) th.join();
+    for (size_t r = 0; r < np; ++r) {
+      if (outs[r].err) throw SetupError(outs[r].err, outs[r].msg);
+      D.lattice.push_back(outs[r].lat);
+      if (outs[r].withb) {
+        D.bd_of_plg.push_back((int)D.bd_cells.size());
+        D.bd_cells.push_back(D.plg[r]);
+      } else {
+        D.bd_of_plg.push_back(-1);
+      }
+      D.beta.push_back(outs[r].bt);
+    }
   }
   // --- block of the smoother: PLG cells + corner blocks when b != 0 --------
   std::vector<int> blk(D.plg);
@@ -507,6 +553,10 @@ LevelDisc discretize(const Problem& P, int n) {
   }
   for (int k = 0; k < n * n; ++k) {
     if (D.kind[k] == K_EMPTY) continue;
+    // only PLG rows (boundary datum) and the rows of cells within two cells
+    // of a box wall (ghost data) have terms in N
+    const int i = k % n, j = k / n;
+    if (D.kind[k] != K_PLG && i >= 2 && j >= 2 && i < n - 2 && j < n - 2) continue;
     D.row(k, ar, &nr);
     if (!nr.empty()) {
       D.nrows.push(nr);

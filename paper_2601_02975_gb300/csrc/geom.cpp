@@ -232,15 +232,18 @@ void count_loops(const Problem& P, const std::vector<Piece>& pcs, double px, dou
 }  // namespace
 
 void shift_moments(const double in[kMoments], double dx, double dy, double out[kMoments]) {
-  static double C[7][7];
-  static bool init = false;
-  if (!init) {
-    for (int n = 0; n < 7; ++n) {
-      C[n][0] = C[n][n] = 1;
-      for (int k = 1; k < n; ++k) C[n][k] = C[n - 1][k - 1] + C[n - 1][k];
+  // binomial coefficients, built once (thread-safe static initialisation)
+  struct Binom {
+    double c[7][7] = {};
+    Binom() {
+      for (int n = 0; n < 7; ++n) {
+        c[n][0] = c[n][n] = 1;
+        for (int k = 1; k < n; ++k) c[n][k] = c[n - 1][k - 1] + c[n - 1][k];
+      }
     }
-    init = true;
-  }
+  };
+  static const Binom binom;
+  const auto& C = binom.c;
   double px[7], py[7];
   px[0] = py[0] = 1;
   for (int k = 1; k < 7; ++k) { px[k] = px[k - 1] * dx; py[k] = py[k - 1] * dy; }
