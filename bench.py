@@ -61,6 +61,8 @@ def _args():
                     help="requests in the serving measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0,
                     help="mean arrival rate of the serving measurement, requests per second")
+    ap.add_argument("--config3", type=int, nargs="*", default=[2048, 4096],
+                    help="grids of the ellipse-union measurement (none: skip)")
     ap.add_argument("--hbm-n", type=int, default=4096,
                     help="grid of the HBM-bound sweep measurement (0: skip)")
     ap.add_argument("--batch", type=int, default=8,
@@ -359,6 +361,7 @@ def run_ours(a):
 
     serving = run_serving(a, dev) if a.serve > 0 else None
     roof_hbm = hbm_sweep(a, dev, peak, src) if a.hbm_n > 0 else None
+    config3 = run_config3(a, dev) if a.config3 else None
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -386,6 +389,7 @@ def run_ours(a):
         "max_error_vs_exact": err,
         "batch": batch,
         "serving": serving,
+        "config3": config3,
         "fp64_solve": {"ms": fp64_ms, "dof_per_s": dof / (fp64_ms / 1e3), "cycles": r64.cycles,
                        "max_error_vs_exact": err64},
         "wall_s_timed": wall,
@@ -426,6 +430,55 @@ def hbm_sweep(a, dev, peak, src):
             "us_per_launch": 1e3 * tot_ms / launches, "bytes_per_launch": bytes_per,
             "note": "algorithmic bytes 3 x 4 x N^2 (u, b read; u written); each interval includes "
                     "the launch latency"}
+
+
+def run_config3(a, dev):
+    """The ellipse-union workload at 2048^2 and 4096^2: FP32 cycles in FP64
+    refinement against the plain FP64 solve, both to 1e-10 relative residual
+    (the accuracy floor at these sizes: the max-norm error against the exact
+    cell averages no longer falls for tighter tolerances).  The FP64
+    hierarchy is a clone from the setup cache, so host setup runs once."""
+    import numpy as np
+    import torch
+    from paper_2601_02975_gb300 import Hierarchy, cache_clear, default_options
+    from paper_2601_02975_gb300 import inputs as I
+    from paper_2601_02975_gb300 import workloads as W
+    P = W.problem_ellipses(0)
+    out = {"workload": "unit square minus ellipse union seed 0, Robin (1, 0.5), (a,b,c)=(1.5,-0.8,1), "
+                       "u = sin(3x) exp(y), tol 1e-10"}
+    for n in a.config3:
+        row = {}
+        for prec, name in ((1, "mixed"), (0, "fp64")):
+            t = time.perf_counter()
+            H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                      default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=prec,
+                                                      max_cycles=80, w_depth=W_DEPTH, cache=1))
+            setup = time.perf_counter() - t
+            f, g, ue = I.problem_inputs(H, P)
+            present = H.cell_types()[0] != 0
+            ft = torch.tensor(f.ravel(), dtype=torch.float64, device=dev)
+            gt = torch.tensor(g, dtype=torch.float64, device=dev)
+            u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+            H.solve(ft, gt, u, 1e-10)
+            ms = []
+            for _ in range(2):
+                u.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                r = H.solve(ft, gt, u, 1e-10)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            err = float(np.abs(u.cpu().numpy().reshape(n, n) - ue)[present].max())
+            row[name] = {"ms": min(ms), "dof_per_s": H.info.n_dof / (min(ms) / 1e3), "cycles": r.cycles,
+                         "status": r.status, "rel_res": r.rel_res, "max_error_vs_exact": err,
+                         "setup_s": setup}
+            row["dof"] = int(H.info.n_dof)
+            H.close()
+        out[str(n)] = row
+    cache_clear()
+    return out
 
 
 SERVE_SIZES = (128, 256, 512, 1024)
