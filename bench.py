@@ -44,9 +44,9 @@ MIN_COARSE = 32
 W_DEPTH = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of each kernel, keyed like cc_kernel_timing's kernels; None
-# until captured for the kernels as they are now (k_sweep_w: profiles/k_sweep_w_disk1024.md;
+# until captured for the kernels as they are now (k_sweep_p: profiles/k_sweep_p_poisson4096_disk1024.md;
 # the timed dense block solves include gather + GEMV launches not captured yet)
-TRAFFIC = {1: 9.48e6, 2: None}
+TRAFFIC = {1: 9.46e6, 2: None}
 
 
 def _args():
@@ -426,7 +426,7 @@ def hbm_sweep(a, dev, peak, src):
     achieved = bytes_per / (tot_ms / launches) / 1e6
     return {"kernel": f"k_sweep_p<float> (finest level, Poisson unit square {n}x{n})", "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": src, "launches": launches,
+            "traffic": 190.9e6 if n == 4096 else None, "peak_source": src, "launches": launches,
             "us_per_launch": 1e3 * tot_ms / launches, "bytes_per_launch": bytes_per,
             "note": "algorithmic bytes 3 x 4 x N^2 (u, b read; u written); each interval includes "
                     "the launch latency"}
