@@ -69,6 +69,9 @@ def _args():
                     help="independent solves in the concurrent-batch measurement (0: skip)")
     ap.add_argument("--min-coarse", type=int, default=MIN_COARSE,
                     help="cells a side of the coarsest level")
+    ap.add_argument("--profile-sweep", type=int, default=0, metavar="N",
+                    help="set up the Poisson unit-square hierarchy at N^2 and run one mixed cycle "
+                         "without graphs, then exit (for ncu -k regex:k_sweep_p)")
     ap.add_argument("--profile", action="store_true",
                     help="warm up, then run one solve inside the NVTX range 'solve' and exit "
                          "(for ncu --nvtx --nvtx-include solve/)")
@@ -619,9 +622,33 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+def run_profile_sweep(a):
+    import torch
+
+    import __graft_entry__
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from paper_2601_02975_gb300 import inputs as I
+    from paper_2601_02975_gb300 import workloads as W
+    __graft_entry__.build()
+    P = W.problem_poisson_square()
+    n = a.profile_sweep
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                              default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1, max_cycles=1,
+                                              w_depth=W_DEPTH, use_graphs=0))
+    f, g, _ = I.problem_inputs(H, P)
+    ft = torch.tensor(f.ravel(), dtype=torch.float64, device="cuda")
+    gt = torch.tensor(g, dtype=torch.float64, device="cuda")
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    r = H.solve(ft, gt, u, 1e-300)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "one cycle", "n": n, "cycles": r.cycles, "kernels": r.kernels}))
+
+
 def main():
     a = _args()
-    if a.profile:
+    if a.profile_sweep:
+        run_profile_sweep(a)
+    elif a.profile:
         run_profile(a)
     elif a.impl == "reference":
         run_reference(a)
