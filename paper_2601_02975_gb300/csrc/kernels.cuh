@@ -719,6 +719,27 @@ __device__ __forceinline__ void block_write(const BlockDev& B, T* u, int p, T v)
   for (int q = B.alias_ptr[p]; q < B.alias_ptr[p + 1]; ++q) u[B.alias_cell[q]] = v;
 }
 
+// The destinations of block row p (its cell and up to two merged-away
+// cells), loaded ahead of the product so the final writes wait on nothing.
+struct BlockDst {
+  int cell = -1, a0 = 0, a1 = 0, al[2] = {-1, -1};
+  __device__ __forceinline__ void load(const BlockDev& B, int p) {
+    if (p >= B.m) return;
+    cell = B.cell[p];
+    a0 = B.alias_ptr[p];
+    a1 = B.alias_ptr[p + 1];
+    if (a1 > a0) al[0] = B.alias_cell[a0];
+    if (a1 > a0 + 1) al[1] = B.alias_cell[a0 + 1];
+  }
+  template <class T>
+  __device__ __forceinline__ void write(const BlockDev& B, T* u, T v) const {
+    u[cell] = v;
+    if (a1 > a0) u[al[0]] = v;
+    if (a1 > a0 + 1) u[al[1]] = v;
+    for (int q = a0 + 2; q < a1; ++q) u[B.alias_cell[q]] = v;
+  }
+};
+
 // t = b - A(block, rest) u for block row p: the padded terms are laid out
 // term-major, so the loads of consecutive rows are coalesced and the loads of
 // one row are independent of one another.
@@ -872,10 +893,12 @@ __global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
   extern __shared__ float4 smem_f4[];
   T* t = reinterpret_cast<T*>(smem_f4);
   const T* tg = static_cast<const T*>(B.tblk);
-  for (int c = threadIdx.x; c < B.ld; c += blockDim.x) t[c] = c < B.m ? tg[c] : T(0);
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  BlockDst dst;
+  if (lane == 0) dst.load(B, r);
+  for (int c = threadIdx.x; c < B.ld; c += blockDim.x) t[c] = c < B.m ? tg[c] : T(0);
+  __syncthreads();
   if (r >= B.m) { pdl_exit(); return; }
   const V* A = reinterpret_cast<const V*>(static_cast<const T*>(B.ainv) + (size_t)r * B.ld);
   const int nv = B.ld / W;
@@ -883,7 +906,7 @@ __global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
 #pragma unroll 8
   for (int c = lane; c < nv; c += 32) acc += dot16(A[c], t + c * W);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) block_write(B, u, r, acc);
+  if (lane == 0) dst.write(B, u, acc);
   pdl_exit();
 }
 
@@ -966,11 +989,11 @@ k_smooth(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict_
 // loads the first PFV 16-byte vectors per lane of its row of the inverse into
 // registers before the gather, so those loads overlap it.
 template <class T>
-__global__ void __launch_bounds__(1024) k_block_dense(BlockDev B, const T* __restrict__ b,
+__global__ void __launch_bounds__(1024, 1) k_block_dense(BlockDev B, const T* __restrict__ b,
                                                       T* __restrict__ u) {
   using V = vec16_t<T>;
   constexpr int W = 16 / sizeof(T);
-  constexpr int PFV = 6;
+  constexpr int PFV = sizeof(T) == 4 ? 4 : 3;
   pdl_enter();
   extern __shared__ float4 smem_f4[];
   T* t = reinterpret_cast<T*>(smem_f4);
@@ -986,6 +1009,8 @@ __global__ void __launch_bounds__(1024) k_block_dense(BlockDev B, const T* __res
     if (c < nv) a[j] = A0[c];
     else a[j] = V{};
   }
+  BlockDst dst;
+  if (lane == 0) dst.load(B, r0);
   for (int p = threadIdx.x; p < B.ld; p += blockDim.x) t[p] = p < B.m ? block_rhs(B, b, u, p) : T(0);
   __syncthreads();
   for (int r = r0; r < B.m; r += gridDim.x * wpb) {
@@ -1003,7 +1028,10 @@ __global__ void __launch_bounds__(1024) k_block_dense(BlockDev B, const T* __res
 #pragma unroll 4
     for (int c = c0; c < nv; c += 32) acc += dot16(A[c], t + c * W);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) block_write(B, u, r, acc);
+    if (lane == 0) {
+      if (r == r0) dst.write(B, u, acc);
+      else block_write(B, u, r, acc);
+    }
   }
   pdl_exit();
 }
