@@ -358,3 +358,42 @@ def problem_ellipses(seed: int = 0) -> Problem:
     u = u_sinexp()
     return Problem(f"ellipses{seed}", dom, 1.5, -0.8, 1.0, u,
                    apply_L(u, 1.5, -0.8, 1.0))
+
+
+def problem_batch(seed: int) -> Tuple[Problem, int]:
+    """Problem `seed` of the many-problem batch and its grid size N.
+
+    N = 2^round(U[6, 10]) (log-uniform 64..1024); 1-8 holes, each a circle or
+    an ellipse with semi-axes U[0.03, 0.15] and rotation U[0, pi), whose
+    bounding circles keep 0.02 from the box and from one another; a, c ~
+    U[0.5, 2], b ~ U(-sqrt(3ac), sqrt(3ac)); Dirichlet on the box and a
+    condition drawn from {Dirichlet, Neumann, Robin(1, 0.5)} on each hole;
+    f a 16 x 16-mode random Fourier series and g = 0 (u = 0 on the data; no
+    exact solution)."""
+    rng = np.random.default_rng(5000 + seed)
+    n = 2 ** int(round(rng.uniform(6.0, 10.0)))
+    nh = int(rng.integers(1, 9))
+    holes: List[Ellipse] = []
+    for _ in range(4000):
+        if len(holes) == nh:
+            break
+        circle = rng.random() < 0.5
+        r1 = float(rng.uniform(0.03, 0.15))
+        r2 = r1 if circle else float(rng.uniform(0.03, 0.15))
+        th = 0.0 if circle else float(rng.uniform(0.0, math.pi))
+        cx, cy = (float(v) for v in rng.uniform(0.0, 1.0, 2))
+        R = max(r1, r2)
+        if min(cx, cy, 1.0 - cx, 1.0 - cy) - R < 0.02:
+            continue
+        if any(math.hypot(cx - o.cx, cy - o.cy) - R - max(o.r1, o.r2) < 0.02 for o in holes):
+            continue
+        holes.append(Ellipse(cx, cy, r1, r2, th))
+    a = float(rng.uniform(0.5, 2.0))
+    c = float(rng.uniform(0.5, 2.0))
+    bmax = math.sqrt(3.0 * a * c)
+    b = float(rng.uniform(-bmax, bmax))
+    kinds = [BC(), BC(NEUMANN, 0.0, 1.0), BC(ROBIN, 1.0, 0.5)]
+    hole_bc = [kinds[int(rng.integers(0, 3))] for _ in holes]
+    dom = Domain(holes=holes, box_bc=(BC(), BC(), BC(), BC()), hole_bc=hole_bc)
+    f = random_fourier(7000 + seed, 16)
+    return Problem(f"batch{seed}", dom, a, b, c, Separable([]), f, exact=False), n

@@ -455,3 +455,24 @@ def test_streamed_sweep_in_mixed_solve(name):
     assert r64.status == 0 and rm.status == 0 and rm.rel_res < 1e-12
     assert abs(rm.cycles - r64.cycles) <= 1
     assert em <= 1.1 * e64 + 1e-14, (em, e64)
+
+
+def test_batch_workload_problem_matches_oracle():
+    """A problem of the batch workload (random holes, operator and conditions,
+    random-Fourier right-hand side, g = 0, no exact solution): the mixed GPU
+    solve and the FP64 oracle solve of the same problem, both to 1e-12
+    relative residual, agree to 1e-8 relative max-norm."""
+    P, n = W.problem_batch(0)
+    assert n == 64
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                              default_options(min_coarse_n=16, cycle=2, precision=1, w_depth=2))
+    O = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=16)
+    assert H.info.n_levels == O.nl
+    f, g, _, _ = _gpu_rhs(H, P)
+    u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    r = H.solve(_t(f), _t(g), u, 1e-12)
+    assert r.status == 0
+    ro = M.solve(O, _oracle_rhs(O, P), tol=1e-12, gamma=2, w_depth=2)
+    d = O.levels[0]
+    diff = np.abs(_np(u, n) - ro.u)[d.lev.present].max() / np.abs(ro.u).max()
+    assert diff < 1e-8, diff
