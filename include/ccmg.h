@@ -100,8 +100,15 @@ typedef struct {
                           when needed, within the cc_serve_budget cap */
   int cache;           /* 1: reuse the setup of an identical earlier cc_setup call
                           of this process (same domain, coefficients, conditions,
-                          N, eps, omega, min_coarse_n): the handle is then a clone
-                          of that hierarchy and setup costs no host time (0) */
+                          N, eps, omega, min_coarse_n, hole_cells): the handle is
+                          then a clone of that hierarchy and setup costs no host
+                          time (0) */
+  double hole_cells;   /* a coarse level must resolve every hole by this many cells
+                          across its smaller semi-axis (2.0).  Domains with holes
+                          of 2-3.5 coarse cells can make the coarse-grid
+                          correction diverge; 3.5 avoids it, at the price of a
+                          finer coarsest level (setup rejects one above 4096
+                          unknowns with CC_ERR_ARG) */
 } cc_options;
 
 /* Sizes of a hierarchy. */

@@ -164,17 +164,18 @@ class Hierarchy:
 
 def build_hierarchy(dom: Domain, n: int, a: float, b: float, c: float,
                     eps: float = 0.1, min_coarse: int = 4,
-                    max_levels: int = 32, omega: float = 0.5) -> Hierarchy:
+                    max_levels: int = 32, omega: float = 0.5,
+                    hole_cells: float = 2.0) -> Hierarchy:
     """Eq. 5.9: rediscretise every level h_f 2^l; the coarsest level is the
     smallest N >= min_coarse reached by halving while every level resolves
     the domain: single-component cut cells (Alg. 1 precondition), every hole
-    at least two cells across its smaller semi-axis, and every PLG fit
-    possible."""
+    at least hole_cells cells across its smaller semi-axis on the coarse
+    levels, and every PLG fit possible."""
     levels = []
     nl = n
     while len(levels) < max_levels:
         h = (dom.x1 - dom.x0) / nl
-        if levels and any(min(e.r1, e.r2) < 2.0 * h for e in dom.holes):
+        if levels and any(min(e.r1, e.r2) < hole_cells * h for e in dom.holes):
             break
         lev = G.build_level(dom, nl, eps)
         if not lev.resolved:

@@ -673,6 +673,7 @@ std::string setup_key(const cc_domain* dom, double a, double b, double c, const 
   put(&o.eps, sizeof(o.eps));
   put(&o.omega, sizeof(o.omega));
   put(&o.min_coarse_n, sizeof(o.min_coarse_n));
+  put(&o.hole_cells, sizeof(o.hole_cells));
   return k;
 }
 
@@ -1521,6 +1522,7 @@ void cc_default_options(cc_options* o) {
   o->w_depth = 0;
   o->serve_slots = 4;
   o->cache = 0;
+  o->hole_cells = 2.0;
 }
 
 const char* cc_last_error_string(void) { return t_last_error; }
@@ -1554,7 +1556,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 == 0 || o.min_coarse_n < 4 || o.max_cycles < 1 ||
       !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3) ||
       (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W) || o.w_depth < 0 ||
-      o.serve_slots < 1)
+      o.serve_slots < 1 || !(o.hole_cells > 0))
     return CC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // the setup cache: a clone of the hierarchy of an identical earlier call
@@ -1595,12 +1597,12 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     // levels: halve while the level is resolved and discretisable (Eq. 5.9)
     int nl = n;
     while (true) {
-      // a coarse level must resolve every hole: two cells across its smaller
-      // semi-axis (the precondition of Alg. 1, made concrete)
+      // a coarse level must resolve every hole: hole_cells cells across its
+      // smaller semi-axis (the precondition of Alg. 1, made concrete)
       if (!H->lv.empty()) {
         double hl = (P.x1 - P.x0) / nl;
         bool fine_enough = true;
-        for (const Hole& e : P.holes) fine_enough = fine_enough && std::min(e.r1, e.r2) >= 2.0 * hl;
+        for (const Hole& e : P.holes) fine_enough = fine_enough && std::min(e.r1, e.r2) >= o.hole_cells * hl;
         if (!fine_enough) break;
       }
       LevelDisc D;
