@@ -492,7 +492,8 @@ def run_config4(a, dev):
     """Independent problems of the batch workload (random domains, operators,
     conditions and right-hand sides, N log-uniform in 64..1024), FP32 cycles
     in FP64 refinement to 1e-10: solved one at a time, then all at once with
-    one cc_solve_batch call (the DOF/s count every problem, converged or not).
+    one cc_solve_batch call (the DOF/s count the converged problems' DOF over
+    the time of all).
     Problems the setup rejects (a finest-grid cut cell of two components, or
     a coarsest level too large for the dense bottom solve) are listed as
     skipped; holes of 2-3.5 coarse cells can make a solve diverge, which is
@@ -542,7 +543,8 @@ def run_config4(a, dev):
     ok = [r.status == 0 for r in res]
     return {"problems": len(hs), "skipped_at_setup": skipped, "sizes": sizes, "dof": sum(dofs),
             "setup_s": setup, "one_at_a_time_ms": seq * 1e3, "batch_ms": bat * 1e3,
-            "dof_per_s_one_at_a_time": sum(dofs) / seq, "dof_per_s_batch": sum(dofs) / bat,
+            "dof_per_s_one_at_a_time": sum(d for d, o in zip(dofs, ok) if o) / seq,
+            "dof_per_s_batch": sum(d for d, o in zip(dofs, ok) if o) / bat,
             "converged": sum(ok), "diverged": [sizes[i] for i, r in enumerate(res) if r.status == 6],
             "statuses": [r.status for r in res], "cycles": [r.cycles for r in res],
             "single_statuses_match": [r.status for r in single] == [r.status for r in res],
