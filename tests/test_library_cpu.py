@@ -109,3 +109,66 @@ def test_setup_rejects_bad_arguments(lib, case):
     with pytest.raises(CCError) as ei:
         Hierarchy(dom, a, b, c, bcs, n, default_options(host_only=1))
     assert ei.value.status in (1, 2)
+
+
+def test_new_options_are_checked(lib):
+    """hole_cells and serve_slots are validated by cc_setup; cc_serve_budget
+    rejects a negative cap."""
+    from paper_2601_02975_gb300 import CCError, Hierarchy, default_options, serve_budget
+    P = W.problem_disk()
+    for kw in ({"hole_cells": 0.0}, {"hole_cells": -1.0}, {"serve_slots": 0}, {"w_depth": -1},
+               {"fmg_cycle": 3}):
+        with pytest.raises(CCError) as ei:
+            Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 32, default_options(host_only=1, **kw))
+        assert ei.value.status == 1, kw
+    with pytest.raises(CCError):
+        serve_budget(-1)
+    serve_budget(0)
+
+
+def test_hole_cells_sets_the_depth(lib):
+    """The coarse-level hole resolution decides where coarsening stops, the
+    same way in the library and in the oracle: the disk (r = 0.2) keeps 16^2
+    with 2 cells (0.2 >= 2/16) and stops at 32^2 with 3.5 cells."""
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from oracle import multigrid as M
+    P = W.problem_disk()
+    for hc, want in ((2.0, [64, 32, 16]), (3.5, [64, 32])):
+        H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 64,
+                                  default_options(host_only=1, min_coarse_n=8, hole_cells=hc))
+        assert list(H.info.level_n[:H.info.n_levels]) == want
+        levels = [64]
+        n = 64
+        while n // 2 >= 8 and 0.2 >= hc / (n // 2):
+            n //= 2
+            levels.append(n)
+        assert levels == want
+    O = M.build_hierarchy(P.dom, 32, P.a, P.b, P.c, min_coarse=8, hole_cells=3.5)
+    assert [d.n for d in O.levels] == [32]
+
+
+def test_batch_generator_properties():
+    """The batch workload generator keeps its stated ranges: N a power of two
+    in 64..1024, 1-8 holes with semi-axes in [0.03, 0.15] whose bounding
+    circles keep 0.02 from the box and from one another, a, c in [0.5, 2],
+    b^2 < 3ac, Dirichlet box, g = 0; and it is seeded."""
+    import math
+    seen = set()
+    for k in range(40):
+        P, n = W.problem_batch(k)
+        assert n in (64, 128, 256, 512, 1024)
+        seen.add(n)
+        hs = P.dom.holes
+        assert 1 <= len(hs) <= 8
+        for i, e in enumerate(hs):
+            R = max(e.r1, e.r2)
+            assert 0.03 <= min(e.r1, e.r2) and R <= 0.15
+            assert min(e.cx, e.cy, 1 - e.cx, 1 - e.cy) - R >= 0.02
+            for o in hs[:i]:
+                assert math.hypot(e.cx - o.cx, e.cy - o.cy) - R - max(o.r1, o.r2) >= 0.02
+        assert 0.5 <= P.a <= 2 and 0.5 <= P.c <= 2 and P.b * P.b < 3 * P.a * P.c
+        assert all(bc.kind == W.DIRICHLET for bc in P.dom.box_bc)
+        assert not P.exact and len(P.u.terms) == 0
+        P2, n2 = W.problem_batch(k)
+        assert n2 == n and P2.dom.holes == hs and P2.a == P.a
+    assert len(seen) >= 4
