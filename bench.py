@@ -123,7 +123,10 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples go to $BENCH_CLOCKS_DIR (default _bench_out/); the JSON
+        # line carries their summary
+        out = os.environ.get("BENCH_CLOCKS_DIR", os.path.join(ROOT, "_bench_out"))
+        self.path = os.path.join(out, f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
