@@ -15,12 +15,12 @@ of the control volume.  Straight pieces are integrated exactly by 6-point
 Gauss-Legendre; arcs by composite 8-point Gauss-Legendre in the angle, with
 sub-arcs no longer than 0.2 rad.
 
-Alg. 1, lines 8-11 (merging cells of volume fraction below epsilon) is
+The merging step of Alg. 1 (cells of volume fraction below epsilon) is
 applied with the reading listed in the design notes: cells are visited once
 in row-major order (y index outer), the volume is the current one, a merge
 target is a present cell reachable through a shared face piece of positive
 length, the argmin ties go to the first neighbour in the order -x, +x, -y,
-+y.  Alg. 1 lines 2-7 (cells with several connected components) are not
++y.  The step of Alg. 1 for cells with several connected components is not
 exercised: a level where some cut cell has more than one component violates
 the algorithm's precondition ("h is sufficiently small to resolve the
 topology") and is reported as unresolved.
@@ -481,7 +481,7 @@ def _wall_nodes(lev: Level, i: int, j: int) -> list:
 
 
 def _merge_small(lev: Level) -> None:
-    """Alg. 1, lines 8-11: merge every cell of volume < eps h^2 into the face
+    """Alg. 1, merging step: merge every cell of volume < eps h^2 into the face
     neighbour that brings the merged volume closest to h^2."""
     n, h = lev.n, lev.h
     h2 = h * h

@@ -1,5 +1,5 @@
 // Cut cells of a box minus a union of ellipses (Sec. 3.1) and the merging of
-// small cells (Alg. 1, lines 8-11), in FP64 on the host.
+// small cells (the merging step of Alg. 1), in FP64 on the host.
 //
 // A cut cell is described by its oriented boundary pieces: the parts of its
 // four faces that lie in the domain (counter-clockwise) and the arcs of hole
@@ -11,7 +11,7 @@
 // integrated by 5-point Gauss-Legendre (exact for these polynomials), arcs by
 // 10-point Gauss-Legendre on sub-arcs of at most 0.25 rad.
 //
-// Alg. 1 lines 8-11 are applied once in row-major order (y index outer) with
+// The merging step of Alg. 1 is applied once in row-major order (y index outer) with
 // the current volumes; the merge target is a present neighbour reached
 // through a shared face piece of positive length (following the chain of
 // earlier merges), minimising |vol + vol' - h^2|, ties to the first of the
@@ -424,7 +424,7 @@ LevelGeom build_geometry(const Problem& P, int n) {
     G.cut[k] = C;
   }
 
-  // ---- Alg. 1, lines 8-11 ------------------------------------------------
+  // ---- Alg. 1, merging of small cells -----------------------------------------
   G.owner.assign((size_t)n * n, -1);
   for (int k = 0; k < n * n; ++k)
     if (G.type[k] != CT_EMPTY) G.owner[k] = k;
