@@ -307,6 +307,20 @@ def problem_disk() -> Problem:
     return Problem("disk", dom, 1.0, 0.5, 2.0, u, apply_L(u, 1.0, 0.5, 2.0))
 
 
+def problem_four_disks(kind: int = DIRICHLET) -> Problem:
+    """Sec. 6, a square minus four disks: Poisson's equation on the unit
+    square minus the union of four overlapping disks (six kinks on the
+    union's boundary), u = sin(pi x) sin(pi y), Dirichlet on the square and
+    `kind` (Dirichlet or Neumann) on the disks; the paper uses eps = 0.08."""
+    u = u_sinpi()
+    disks = [Ellipse(0.5, 0.5, 0.2, 0.2), Ellipse(0.5, 0.735, 0.1, 0.1),
+             Ellipse(0.2965, 0.3825, 0.1, 0.1), Ellipse(0.7035, 0.3825, 0.1, 0.1)]
+    bc = BC(DIRICHLET, 1.0, 0.0) if kind == DIRICHLET else BC(NEUMANN, 0.0, 1.0)
+    dom = Domain(holes=disks, hole_bc=[bc] * 4)
+    return Problem("four_disks_" + ("D" if kind == DIRICHLET else "N"), dom, 1.0, 0.0, 1.0, u,
+                   apply_L(u, 1.0, 0.0, 1.0))
+
+
 def _boundary_points(e: Ellipse, m: int = 720):
     t = np.linspace(0, 2 * math.pi, m, endpoint=False)
     c, s = math.cos(e.theta), math.sin(e.theta)
