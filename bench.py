@@ -4,8 +4,8 @@ Workload: the unit square minus the disk of radius 0.2 at (0.5, 0.5),
 a u_xx + b u_xy + c u_yy = f with (a, b, c) = (1, 0.5, 2), Dirichlet data on
 the box and Neumann data on the circle, manufactured u = exp(x) cos(2y), on
 1024 x 1024 cells (the finest grid of the disk refinement sweep).  A step is
-one whole solve through the C ABI: assembly of b = f - N g, then FP32 W(3,3)
-cycles (gamma = 2 on the two finest levels only) inside FP64 iterative
+one whole solve through the C ABI: assembly of b = f - N g, then FP32 W(4,4)
+cycles (gamma = 2 on the finest level only) inside FP64 iterative
 refinement until ||b - A u||_inf / ||b||_inf < 1e-13, from u = 0.  That tolerance is what discretisation-error accuracy takes
 on this workload: ||b||_inf grows like h^-2 (boundary data enters b through
 the ghost formulas), and at 1e-10 the algebraic error (4e-9 max-norm) is far
@@ -39,9 +39,12 @@ sys.path.insert(0, ROOT)
 N_GRID = 1024
 TOL = 1e-13
 MIN_COARSE = 32
-# the W-cycle's repeated coarse-grid correction on the 2 finest levels only:
-# the cycle count of the full W-cycle (26 at 1024^2) with half its launches
-W_DEPTH = 2
+# W(4,4) with the W-cycle's repeated coarse-grid correction on the finest
+# level only (gamma = 2 there, V below): at 1024^2 it needs 22 cycles and
+# 4361 launches per solve, against 26 cycles and 6193 launches for W(3,3)
+# repeated on the 2 finest levels and 11,975 for the full W(3,3)
+NU = 4
+W_DEPTH = 1
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of each kernel, keyed like cc_kernel_timing's kernels; None
 # until captured for the kernels as they are now (k_sweep_p: profiles/k_sweep_p_poisson4096_disk1024.md;
@@ -91,7 +94,7 @@ def run_profile(a):
     n = a.n
     H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                               default_options(min_coarse_n=a.min_coarse, cycle=2, precision=1,
-                                              max_cycles=60, w_depth=W_DEPTH))
+                                              max_cycles=60, w_depth=W_DEPTH, nu1=NU, nu2=NU))
     f, g, _ = I.problem_inputs(H, P)
     ft = torch.tensor(f.ravel(), dtype=torch.float64, device="cuda")
     gt = torch.tensor(g, dtype=torch.float64, device="cuda")
@@ -228,7 +231,7 @@ def run_ours(a):
     P = _problem()
     n = a.n
     opts = default_options(min_coarse_n=a.min_coarse, cycle=2, precision=1, max_cycles=60,
-                           w_depth=W_DEPTH)
+                           w_depth=W_DEPTH, nu1=NU, nu2=NU)
     H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n, opts)
     f, g, ue = I.problem_inputs(H, P)
     present = H.cell_types()[0] != 0
@@ -321,7 +324,7 @@ def run_ours(a):
     # plain FP64 solve of the same problem, for comparison
     H64 = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                                 default_options(min_coarse_n=a.min_coarse, cycle=2, precision=0,
-                                                max_cycles=60, w_depth=W_DEPTH))
+                                                max_cycles=60, w_depth=W_DEPTH, nu1=NU, nu2=NU))
     u64 = torch.zeros(n * n, dtype=torch.float64, device=dev)
     H64.solve(ft, gt, u64, TOL, stream)
     torch.cuda.synchronize()
@@ -383,7 +386,7 @@ def run_ours(a):
         "data": "synthetic (manufactured solution exp(x)cos(2y), seeded geometry)",
         "config": {"workload": f"disk domain, (a,b,c)=(1,0.5,2), Dirichlet box + Neumann circle, "
                                f"{n}x{n} cells", "n": n, "dof_per_gpu": dof,
-                   "cycle": f"W(3,3), gamma = 2 on the {W_DEPTH} finest levels",
+                   "cycle": f"W({NU},{NU}), gamma = 2 on the {W_DEPTH} finest level(s)",
                    "levels": [H.info.level_n[l] for l in range(H.info.n_levels)],
                    "precision": "mixed", "tol": TOL, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}", "cycles_per_solve": cycles[-1]},
@@ -421,7 +424,7 @@ def hbm_sweep(a, dev, peak, src):
     n = a.hbm_n
     H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                               default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1,
-                                              max_cycles=2, w_depth=W_DEPTH))
+                                              max_cycles=2, w_depth=W_DEPTH, nu1=NU, nu2=NU))
     f, g, _ = I.problem_inputs(H, P)
     ft = torch.tensor(f.ravel(), dtype=torch.float64, device=dev)
     gt = torch.tensor(g, dtype=torch.float64, device=dev)
@@ -462,7 +465,7 @@ def run_config3(a, dev):
             t = time.perf_counter()
             H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                                       default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=prec,
-                                                      max_cycles=80, w_depth=W_DEPTH, cache=1))
+                                                      max_cycles=80, w_depth=W_DEPTH, nu1=NU, nu2=NU, cache=1))
             setup = time.perf_counter() - t
             f, g, ue = I.problem_inputs(H, P)
             present = H.cell_types()[0] != 0
@@ -512,7 +515,7 @@ def run_config4(a, dev):
         try:
             H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                                       default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1,
-                                                      max_cycles=80, w_depth=W_DEPTH))
+                                                      max_cycles=80, w_depth=W_DEPTH, nu1=NU, nu2=NU))
         except CCError as e:
             skipped.append({"problem": k, "n": n, "status": e.status})
             continue
@@ -583,7 +586,7 @@ def run_serving(a, dev):
         for n in SERVE_SIZES:
             H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                                       default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=prec,
-                                                      max_cycles=60, w_depth=W_DEPTH, serve_slots=4))
+                                                      max_cycles=60, w_depth=W_DEPTH, nu1=NU, nu2=NU, serve_slots=4))
             f, g, _ = I.problem_inputs(H, P)
             hs.append(H)
             base.append((f, torch.tensor(g, dtype=torch.float64, device=dev), int(H.info.n_dof)))
@@ -649,7 +652,7 @@ def _oracle_sample(n: int):
     dof = int(d.lev.present.sum())
 
     def solve():
-        return M.solve(H, b, tol=TOL, gamma=2, w_depth=W_DEPTH)
+        return M.solve(H, b, tol=TOL, gamma=2, w_depth=W_DEPTH, nu1=NU, nu2=NU)
     return solve, dof
 
 
@@ -660,7 +663,7 @@ def cpu_baseline():
     r = solve()
     dt = time.perf_counter() - t
     return {"value": dof / dt, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"one FP64 oracle W(3,3) solve (gamma = 2 on the {W_DEPTH} finest levels) of the same disk problem at {n}x{n} "
+            "sample": f"one FP64 oracle W({NU},{NU}) solve (gamma = 2 on the {W_DEPTH} finest level(s)) of the same disk problem at {n}x{n} "
                       f"({len(r.history)} cycles, {dt:.1f} s; setup excluded); "
                       f"BLAS threads pinned to 1"}
 
@@ -688,7 +691,7 @@ def run_reference(a):
            "config": {"workload": f"disk domain, (a,b,c)=(1,0.5,2), sample at {n}x{n} cells "
                                   f"of the {N_GRID}x{N_GRID} workload", "n": n},
            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                            "sample": f"FP64 oracle W(3,3) solves (gamma = 2 on the {W_DEPTH} finest levels) at {n}x{n}, setup excluded"},
+                            "sample": f"FP64 oracle W({NU},{NU}) solves (gamma = 2 on the {W_DEPTH} finest level(s)) at {n}x{n}, setup excluded"},
            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -706,7 +709,7 @@ def run_profile_sweep(a):
     n = a.profile_sweep
     H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                               default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1, max_cycles=1,
-                                              w_depth=W_DEPTH, use_graphs=0))
+                                              w_depth=W_DEPTH, nu1=NU, nu2=NU, use_graphs=0))
     f, g, _ = I.problem_inputs(H, P)
     ft = torch.tensor(f.ravel(), dtype=torch.float64, device="cuda")
     gt = torch.tensor(g, dtype=torch.float64, device="cuda")

@@ -101,20 +101,20 @@ def test_rhs_parity(name, n, mc):
 
 
 @pytest.mark.parametrize("name,n,mc", CASES)
-@pytest.mark.parametrize("gamma,w_depth", [(1, 0), (2, 0), (2, 1)])
-def test_cycle_parity_fp64(name, n, mc, gamma, w_depth):
+@pytest.mark.parametrize("gamma,w_depth,nu", [(1, 0, 3), (2, 0, 3), (2, 1, 3), (2, 1, 4)])
+def test_cycle_parity_fp64(name, n, mc, gamma, w_depth, nu):
     """FP64 iterates of Alg. 2 (V), its W form and the W form truncated to
-    the finest level (w_depth = 1) match the oracle to 1e-11 relative
-    max-norm after every cycle."""
+    the finest level (w_depth = 1), with nu1 = nu2 = 3 or 4, match the
+    oracle to 1e-11 relative max-norm after every cycle."""
     cyc = 1 if gamma == 1 else 2
-    P, H, O = _pair(name, n, mc, cycle=cyc, w_depth=w_depth)
+    P, H, O = _pair(name, n, mc, cycle=cyc, w_depth=w_depth, nu1=nu, nu2=nu)
     _, _, _, b = _gpu_rhs(H, P)
     bo = _oracle_rhs(O, P)
     u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
     uo = np.zeros((n, n))
     for k in range(5):
         H.cycle(u, b)
-        uo = M.cycle(O, 0, uo, bo, 3, 3, gamma, w_depth)
+        uo = M.cycle(O, 0, uo, bo, nu, nu, gamma, w_depth)
         err = np.abs(_np(u, n) - uo).max() / np.abs(uo).max()
         assert err < 1e-11, (k, err)
 
@@ -171,17 +171,18 @@ def test_block_residual_zero_after_sweep():
     assert np.abs(rn[blk]).max() < 1e-11 * np.abs(rn).max()
 
 
-@pytest.mark.parametrize("name,n,mc,cyc,w_depth", [("poisson", 64, 4, 1, 0), ("disk", 64, 16, 2, 0),
-                                                   ("ellipses0", 128, 16, 2, 0),
-                                                   ("ellipses0", 128, 16, 2, 1)])
-def test_solve_fp64_and_mixed(name, n, mc, cyc, w_depth):
+@pytest.mark.parametrize("name,n,mc,cyc,w_depth,nu", [("poisson", 64, 4, 1, 0, 3), ("disk", 64, 16, 2, 0, 3),
+                                                      ("ellipses0", 128, 16, 2, 0, 3),
+                                                      ("ellipses0", 128, 16, 2, 1, 3),
+                                                      ("disk", 128, 16, 2, 1, 4)])
+def test_solve_fp64_and_mixed(name, n, mc, cyc, w_depth, nu):
     """cc_solve in FP64 and in the mixed mode (FP32 cycles in FP64
     refinement) reach 1e-10 relative residual; the mixed solution's error
     against the exact cell averages is within 1.1x of the oracle's."""
-    P, H, O = _pair(name, n, mc, cycle=cyc, w_depth=w_depth)
+    P, H, O = _pair(name, n, mc, cycle=cyc, w_depth=w_depth, nu1=nu, nu2=nu)
     f, g, ue, b = _gpu_rhs(H, P)
     bo = _oracle_rhs(O, P)
-    ro = M.solve(O, bo, tol=1e-10, gamma=cyc, w_depth=w_depth)
+    ro = M.solve(O, bo, tol=1e-10, nu1=nu, nu2=nu, gamma=cyc, w_depth=w_depth)
     d = O.levels[0]
     err_o = np.abs(ro.u - D.cell_averages(d.lev, P.u))[d.lev.present].max()
     u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
@@ -193,7 +194,7 @@ def test_solve_fp64_and_mixed(name, n, mc, cyc, w_depth):
     assert err64 <= 1.1 * err_o + 1e-14
     Hm = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                                default_options(min_coarse_n=mc, cycle=cyc, precision=1,
-                                               w_depth=w_depth))
+                                               w_depth=w_depth, nu1=nu, nu2=nu))
     um = torch.zeros(n * n, dtype=torch.float64, device=DEV)
     rm = Hm.solve(_t(f), _t(g), um, 1e-10)
     assert rm.status == 0 and rm.rel_res < 1e-10
