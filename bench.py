@@ -301,7 +301,8 @@ def run_ours(a):
     peaks, src = _peaks()
     peak = float(peaks["hbm_gbs"])
     roofs = {}
-    for which, name in ((2, "k_block_dense<float> (coarse levels, blocks <= 1024 cells)"),
+    for which, name in ((2, "exact block solve: k_block_dense<float> (blocks <= 1024 cells), "
+                         "k_block_gather + k_block_gemv (1025-2560 cells); levels 512..64"),
                         (1, "k_sweep_p<float> (finest level)")):
         H.kernel_timing(which)
         for _ in range(2):
