@@ -46,10 +46,12 @@ MIN_COARSE = 32
 NU = 4
 W_DEPTH = 1
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of each kernel, keyed like cc_kernel_timing's kernels; None
-# until captured for the kernels as they are now (k_sweep_p: profiles/k_sweep_p_poisson4096_disk1024.md;
-# the timed dense block solves include gather + GEMV launches not captured yet)
-TRAFFIC = {1: 9.46e6, 2: None}
+# one ncu capture of each kernel, keyed like cc_kernel_timing's kernels:
+# k_sweep_p per 1024^2 launch (profiles/k_sweep_p_poisson4096_disk1024.md);
+# the exact block solve per solve (one k_block_dense, or one gather + GEMV
+# pair) with the caches as a solve leaves them
+# (profiles/block_solves_disk1024_warm_dram.md)
+TRAFFIC = {1: 9.46e6, 2: 1.50e5}
 
 
 def _args():
