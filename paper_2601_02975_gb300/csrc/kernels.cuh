@@ -782,14 +782,16 @@ __device__ void cta_matvec_cm(const T* __restrict__ M, int rows, int ld, int col
 
 // K_a: gather t = b - A(block, rest) u for the chunk, z = inv(A_cc) t_I;
 // interface rows' t go to tblk.  With no interfaces z is the solution.
+// The chunk's extents are setup data and are read before the wait on the
+// previous kernel.
 template <class T>
 __global__ void k_block_chunk(BlockDev B, const T* __restrict__ b, T* __restrict__ u) {
-  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* tI = reinterpret_cast<T*>(smem_raw);
   const int c = blockIdx.x;
   const int p0 = B.cstart[c], p1 = B.cstart[c + 1];
   const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
+  pdl_enter();
   T* partial = tI + ((ni + 31) & ~31);
   T* zI = partial + blockDim.x;
   T* tblk = static_cast<T*>(B.tblk);
@@ -805,6 +807,7 @@ __global__ void k_block_chunk(BlockDev B, const T* __restrict__ b, T* __restrict
     zblk[p] = zI[q];
     if (B.ns == 0) block_write(B, u, p, zI[q]);
   }
+  pdl_exit();
 }
 
 // K_b: x_S = inv(S) (t_S - A_S,I z) for 32 interface rows per CTA.
@@ -837,18 +840,20 @@ __global__ void k_block_schur(BlockDev B, T* __restrict__ u) {
     xs[r0 + q] = y[q];
     block_write(B, u, B.spos[r0 + q], y[q]);
   }
+  pdl_exit();
 }
 
 // K_c: x_I = z - W_c x_S for the chunk's interior unknowns.
+// The chunk's extents are setup data and are read before the wait.
 template <class T>
 __global__ void k_block_back(BlockDev B, T* __restrict__ u) {
-  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* xl = reinterpret_cast<T*>(smem_raw);
   const int c = blockIdx.x;
   const int w0 = B.wptr[c], nw_ = B.wptr[c + 1] - w0;
-  T* partial = xl + ((nw_ + 31) & ~31);
   const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
+  pdl_enter();
+  T* partial = xl + ((nw_ + 31) & ~31);
   T* y = partial + blockDim.x;
   const T* xs = static_cast<const T*>(B.xs);
   for (int q = threadIdx.x; q < nw_; q += blockDim.x) xl[q] = xs[B.widx[w0 + q]];
@@ -860,16 +865,41 @@ __global__ void k_block_back(BlockDev B, T* __restrict__ u) {
     int p = B.ipos[i0 + q];
     block_write(B, u, p, zblk[p] - y[q]);
   }
+  pdl_exit();
 }
 
 // Dense blocks (a few thousand unknowns at most) are solved with the dense
 // inverse: one kernel gathers t = b - A(block, rest) u for every block row,
 // the next applies inv(A) row-major, one warp per row.
+// The row's cell, columns and coefficients are setup data, so they are
+// fetched before waiting on the previous kernel; only b and u are read after.
+constexpr int kGatherMax = 16;   // the ELL width of BlockDev (gk) never exceeds it
 template <class T>
 __global__ void k_block_gather(BlockDev B, const T* __restrict__ b, const T* __restrict__ u) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = p < B.m;
+  const T* gval = static_cast<const T*>(B.gval);
+  int col[kGatherMax];
+  T val[kGatherMax];
+  int cell = 0;
+  if (on) cell = B.cell[p];
+#pragma unroll
+  for (int q = 0; q < kGatherMax; ++q) {
+    const bool use = on && q < B.gk;
+    const size_t e = (size_t)q * B.m + p;
+    col[q] = use ? B.gcol[e] : 0;
+    val[q] = use ? gval[e] : T(0);
+  }
   pdl_enter();
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < B.m) static_cast<T*>(B.tblk)[p] = block_rhs(B, b, u, p);
+  if (on) {
+    T acc = b[cell];
+#pragma unroll
+    for (int q = 0; q < kGatherMax; ++q)
+      if (q < B.gk) acc -= val[q] * u[col[q]];
+    const T* tval = static_cast<const T*>(B.tval);
+    for (int q = B.tptr[p]; q < B.tptr[p + 1]; ++q) acc -= tval[q] * u[B.tcol[q]];
+    static_cast<T*>(B.tblk)[p] = acc;
+  }
   pdl_exit();
 }
 
@@ -885,26 +915,44 @@ __device__ __forceinline__ double dot16(const double2& a, const double* t) {
   return a.x * b.x + a.y * b.y;
 }
 
+// The row of the inverse and the row's destinations are setup data: each
+// warp loads the first PFV 16-byte vectors per lane of its row (1536 columns
+// in FP32, 512 in FP64) into registers before waiting on the gather, so
+// after the wait only t and the rest of longer rows are read.  PFV keeps the
+// kernel at two 256-thread CTAs per SM, one wave for the largest blocks.
 template <class T>
-__global__ void k_block_gemv(BlockDev B, T* __restrict__ u) {
-  pdl_enter();
+__global__ void __launch_bounds__(256, 2) k_block_gemv(BlockDev B, T* __restrict__ u) {
   using V = vec16_t<T>;
   constexpr int W = 16 / sizeof(T);
+  constexpr int PFV = sizeof(T) == 4 ? 12 : 8;
   extern __shared__ float4 smem_f4[];
   T* t = reinterpret_cast<T*>(smem_f4);
   const T* tg = static_cast<const T*>(B.tblk);
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nv = B.ld / W;
+  const V* A = reinterpret_cast<const V*>(static_cast<const T*>(B.ainv) +
+                                          (size_t)min(r, B.m - 1) * B.ld);
+  V a[PFV];
+#pragma unroll
+  for (int j = 0; j < PFV; ++j) {
+    const int c = lane + 32 * j;
+    a[j] = c < nv ? A[c] : V{};
+  }
   BlockDst dst;
   if (lane == 0) dst.load(B, r);
+  pdl_enter();
   for (int c = threadIdx.x; c < B.ld; c += blockDim.x) t[c] = c < B.m ? tg[c] : T(0);
   __syncthreads();
   if (r >= B.m) { pdl_exit(); return; }
-  const V* A = reinterpret_cast<const V*>(static_cast<const T*>(B.ainv) + (size_t)r * B.ld);
-  const int nv = B.ld / W;
   T acc = T(0);
-#pragma unroll 8
-  for (int c = lane; c < nv; c += 32) acc += dot16(A[c], t + c * W);
+#pragma unroll
+  for (int j = 0; j < PFV; ++j) {
+    const int c = lane + 32 * j;
+    if (c < nv) acc += dot16(a[j], t + c * W);
+  }
+#pragma unroll 4
+  for (int c = lane + 32 * PFV; c < nv; c += 32) acc += dot16(A[c], t + c * W);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) dst.write(B, u, acc);
   pdl_exit();
@@ -987,14 +1035,14 @@ k_smooth(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict_
 // block cell, so rows written meanwhile by other CTAs do not disturb it), then
 // applies its share of the rows of inv(A_block), one warp per row.  Each warp
 // loads the first PFV 16-byte vectors per lane of its row of the inverse into
-// registers before the gather, so those loads overlap it.
+// registers before waiting on the previous kernel (the inverse is setup data),
+// so those loads overlap the wait and the gather.
 template <class T>
 __global__ void __launch_bounds__(1024, 1) k_block_dense(BlockDev B, const T* __restrict__ b,
                                                       T* __restrict__ u) {
   using V = vec16_t<T>;
   constexpr int W = 16 / sizeof(T);
   constexpr int PFV = sizeof(T) == 4 ? 4 : 3;
-  pdl_enter();
   extern __shared__ float4 smem_f4[];
   T* t = reinterpret_cast<T*>(smem_f4);
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -1011,6 +1059,8 @@ __global__ void __launch_bounds__(1024, 1) k_block_dense(BlockDev B, const T* __
   }
   BlockDst dst;
   if (lane == 0) dst.load(B, r0);
+  // everything above reads setup data only; b and u come from earlier kernels
+  pdl_enter();
   for (int p = threadIdx.x; p < B.ld; p += blockDim.x) t[p] = p < B.m ? block_rhs(B, b, u, p) : T(0);
   __syncthreads();
   for (int r = r0; r < B.m; r += gridDim.x * wpb) {
