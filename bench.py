@@ -51,7 +51,7 @@ W_DEPTH = 1
 # the exact block solve per solve (one k_block_dense, or one gather + GEMV
 # pair) with the caches as a solve leaves them
 # (profiles/block_solves_disk1024_warm_dram.md)
-TRAFFIC = {1: 9.46e6, 2: 1.50e5}
+TRAFFIC = {1: 9.46e6, 2: 1.24e5}
 
 
 def _args():
