@@ -230,8 +230,9 @@ double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, doub
 void make_ell(BlockPlan& B) {
   const int m = B.m;
   // width: the longest PLG row (at most 15 terms) rounded up; the few
-  // longer rows (box-corner rows with ghost expansions) spill into a tail
-  const int kMaxWidth = 16;
+  // longer rows (box-corner rows with ghost expansions) spill into a tail.
+  // k_block_gather holds a row's terms in registers, kGatherMax of them.
+  const int kMaxWidth = kGatherMax;
   B.gk = 0;
   for (int p = 0; p < m; ++p) B.gk = std::max<int>(B.gk, (int)(B.gptr[p + 1] - B.gptr[p]));
   B.gk = std::min(B.gk, kMaxWidth);
