@@ -919,7 +919,8 @@ __device__ __forceinline__ double dot16(const double2& a, const double* t) {
 // warp loads the first PFV 16-byte vectors per lane of its row (1536 columns
 // in FP32, 512 in FP64) into registers before waiting on the gather, so
 // after the wait only t and the rest of longer rows are read.  PFV keeps the
-// kernel at two 256-thread CTAs per SM, one wave for the largest blocks.
+// kernel at two 256-thread CTAs per SM: one wave for blocks of up to 2432
+// cells (304 CTAs of 8 rows on 152 SMs).
 template <class T>
 __global__ void __launch_bounds__(256, 2) k_block_gemv(BlockDev B, T* __restrict__ u) {
   using V = vec16_t<T>;

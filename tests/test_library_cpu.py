@@ -39,10 +39,12 @@ def _host(P, n, **kw):
 
 
 @pytest.mark.parametrize("name,n", [("disk", 32), ("disk", 64), ("ellipses0", 64),
-                                    ("ellipses3", 96), ("box_cross", 24)])
+                                    ("ellipses3", 96), ("box_cross", 24), ("four_disks_N", 64)])
 def test_setup_tables_match_oracle(lib, name, n):
     if name == "disk":
         P = W.problem_disk()
+    elif name == "four_disks_N":
+        P = W.problem_four_disks(W.NEUMANN)
     elif name.startswith("ellipses"):
         P = W.problem_ellipses(int(name[-1]))
     else:
