@@ -45,6 +45,10 @@ MIN_COARSE = 32
 # repeated on the 2 finest levels and 11,975 for the full W(3,3)
 NU = 4
 W_DEPTH = 1
+# the random-domain batch is also solved with the Krylov outer iteration
+# (cc_options.krylov): FGMRES(20) preconditioned by the same cycle
+KRYLOV = 20
+KRYLOV_MAX_CYCLES = 400
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of each kernel, keyed like cc_kernel_timing's kernels:
 # k_sweep_p per 1024^2 launch (profiles/k_sweep_p_poisson4096_disk1024.md);
@@ -505,24 +509,28 @@ def run_config4(a, dev):
     the time of all).
     Problems the setup rejects (a finest-grid cut cell of two components, or
     a coarsest level too large for the dense bottom solve) are listed as
-    skipped; holes of 2-3.5 coarse cells can make a solve diverge, which is
-    reported, not hidden."""
+    skipped; holes of 2-5 coarse cells can give coarsest-level cut-cell rows
+    of the wrong sign and make the cycle diverge, which is reported, not
+    hidden.  The same problems are then solved once more, as one batch, with
+    the Krylov outer iteration (`krylov`)."""
     import torch
-    from paper_2601_02975_gb300 import CCError, Hierarchy, default_options, solve_batch
+    from paper_2601_02975_gb300 import CCError, Hierarchy, cache_clear, default_options, solve_batch
     from paper_2601_02975_gb300 import inputs as I
     from paper_2601_02975_gb300 import workloads as W
-    hs, fs, gs, dofs, sizes, skipped = [], [], [], [], [], []
+    hs, fs, gs, dofs, sizes, skipped, probs = [], [], [], [], [], [], []
     t = time.perf_counter()
     for k in range(a.config4):
         P, n = W.problem_batch(k)
         try:
             H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                                       default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1,
-                                                      max_cycles=80, w_depth=W_DEPTH, nu1=NU, nu2=NU))
+                                                      max_cycles=80, w_depth=W_DEPTH, nu1=NU, nu2=NU,
+                                                      cache=1))
         except CCError as e:
             skipped.append({"problem": k, "n": n, "status": e.status})
             continue
         f, g, _ = I.problem_inputs(H, P)
+        probs.append((P, n))
         hs.append(H)
         fs.append(torch.tensor(f.ravel(), dtype=torch.float64, device=dev))
         gs.append(torch.tensor(g, dtype=torch.float64, device=dev))
@@ -550,6 +558,28 @@ def run_config4(a, dev):
     for H in hs:
         H.close()
     ok = [r.status == 0 for r in res]
+    # the same problems through the Krylov outer iteration (FGMRES preconditioned
+    # by the same cycle): clones of the cached hierarchies, no second host setup
+    hk = [Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1,
+                                                max_cycles=KRYLOV_MAX_CYCLES, w_depth=W_DEPTH, nu1=NU,
+                                                nu2=NU, cache=1, krylov=KRYLOV))
+          for P, n in probs]
+    uk = [torch.zeros(n * n, dtype=torch.float64, device=dev) for n in sizes]
+    solve_batch(hk, fs, gs, uk, tol)                     # warm-up (graph capture)
+    for u_ in uk:
+        u_.zero_()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    rk = solve_batch(hk, fs, gs, uk, tol)
+    bk = time.perf_counter() - t
+    for H in hk:
+        H.close()
+    cache_clear()
+    okk = [r.status == 0 for r in rk]
+    krylov = {"restart": KRYLOV, "converged": sum(okk), "statuses": [r.status for r in rk],
+              "cycles": [r.cycles for r in rk], "rel_res": [r.rel_res for r in rk], "batch_ms": bk * 1e3,
+              "dof_per_s_batch": sum(d for d, o in zip(dofs, okk) if o) / bk}
     return {"problems": len(hs), "skipped_at_setup": skipped, "sizes": sizes, "dof": sum(dofs),
             "setup_s": setup, "one_at_a_time_ms": seq * 1e3, "batch_ms": bat * 1e3,
             "dof_per_s_one_at_a_time": sum(d for d, o in zip(dofs, ok) if o) / seq,
@@ -557,7 +587,7 @@ def run_config4(a, dev):
             "converged": sum(ok), "diverged": [sizes[i] for i, r in enumerate(res) if r.status == 6],
             "statuses": [r.status for r in res], "cycles": [r.cycles for r in res],
             "single_statuses_match": [r.status for r in single] == [r.status for r in res],
-            "batch_equals_one_at_a_time": same,
+            "batch_equals_one_at_a_time": same, "krylov": krylov,
             "workload": "problems 0.. of the batch generator (1-8 holes, random a,b,c, D/N/R holes, "
                         "random-Fourier f, g = 0), tol 1e-10, host wall clock"}
 

@@ -104,11 +104,20 @@ typedef struct {
                           then a clone of that hierarchy and setup costs no host
                           time (0) */
   double hole_cells;   /* a coarse level must resolve every hole by this many cells
-                          across its smaller semi-axis (2.0).  Domains with holes
-                          of 2-3.5 coarse cells can make the coarse-grid
-                          correction diverge; 3.5 avoids it, at the price of a
-                          finer coarsest level (setup rejects one above 4096
-                          unknowns with CC_ERR_ARG) */
+                          across its smaller semi-axis (2.0).  With holes of 2-5
+                          coarse cells some cut-cell rows of the coarsest level can
+                          get a diagonal of the wrong sign, and the cycle alone then
+                          diverges (see krylov).  A larger value makes the coarsest
+                          level finer (setup rejects one above 4096 unknowns with
+                          CC_ERR_ARG) */
+  int krylov;          /* 0 (default): the solve iterates the cycle (Alg. 2, inside
+                          FP64 refinement in the mixed mode).  k in 1..32: restarted
+                          flexible GMRES(k) in FP64 on A u = b instead, each step
+                          preconditioned by one FP32 cycle from zero, so solves
+                          converge where the cycle alone diverges.  Not part of the
+                          paper's method.  Needs CC_PREC_MIXED and cycle V or W;
+                          cc_result.cycles then counts preconditioner cycles.  The
+                          handle holds 2k + 2 extra FP64 vectors of the finest grid */
 } cc_options;
 
 /* Sizes of a hierarchy. */

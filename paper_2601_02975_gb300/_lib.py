@@ -40,7 +40,7 @@ class cc_options(C.Structure):
                 ("cycle", C.c_int), ("min_coarse_n", C.c_int), ("precision", C.c_int),
                 ("max_cycles", C.c_int), ("use_graphs", C.c_int), ("host_only", C.c_int),
                 ("fmg_cycle", C.c_int), ("w_depth", C.c_int), ("serve_slots", C.c_int),
-                ("cache", C.c_int), ("hole_cells", C.c_double)]
+                ("cache", C.c_int), ("hole_cells", C.c_double), ("krylov", C.c_int)]
 
 
 class cc_info(C.Structure):

@@ -623,6 +623,22 @@ struct cc_hierarchy {
   int64_t gexec_launches[6] = {};            // kernels in one replay of each graph
   size_t gexec_events[6] = {};               // timing event pairs in each graph
   cudaStream_t gstream = nullptr;
+  // Krylov outer iteration (cc_options.krylov = k): basis V [(k + 1) nn],
+  // preconditioned vectors Z [k nn], a zero right-hand side, multi-dot
+  // partials and results, the least-squares coefficients, and their pinned
+  // host copies; the preconditioner cycle's graph and the buffer it ends in
+  int kr_k = 0;
+  double* kr_v = nullptr;
+  double* kr_z = nullptr;
+  double* kr_zero = nullptr;
+  double* kr_part = nullptr;
+  double* kr_dot = nullptr;
+  double* kr_y = nullptr;
+  double* kr_dot_host = nullptr;
+  double* kr_y_host = nullptr;
+  cudaGraphExec_t kr_graph = nullptr;
+  int64_t kr_graph_launches = 0;
+  int kr_cur = 0;
 };
 
 namespace {
@@ -1170,6 +1186,81 @@ void iteration(cc_hierarchy* H, bool mixed, cudaStream_t s) {
   }
 }
 
+// ---- Krylov outer iteration (cc_options.krylov) -------------------------------
+// Restarted flexible GMRES (right preconditioning) on A u = b in FP64; the
+// preconditioner is one FP32 cycle from zero on the vector as right-hand
+// side.  The Arnoldi vectors are orthogonalised by classical Gram-Schmidt run
+// twice; the small least-squares problem is solved on the host with Givens
+// rotations.  Not part of the paper's solver: an option for domains where the
+// cycle alone diverges.
+
+// buffers of the handle's Krylov iteration (restart length opt.krylov)
+void ensure_krylov(cc_hierarchy* H, cudaStream_t s) {
+  const int k = H->opt.krylov;
+  if (k <= H->kr_k || H->opt.host_only) return;
+  const int64_t nn = H->lv[0]->nn;
+  H->kr_v = H->pool->alloc<double>((size_t)(k + 1) * nn);
+  H->kr_z = H->pool->alloc<double>((size_t)k * nn);
+  H->kr_zero = H->pool->alloc<double>(nn);
+  CK(cudaMemsetAsync(H->kr_zero, 0, nn * sizeof(double), s));
+  H->kr_part = H->pool->alloc<double>((size_t)KR_BLOCKS * KR_MAXV);
+  H->kr_dot = H->pool->alloc<double>(KR_MAXV);
+  H->kr_y = H->pool->alloc<double>(KR_MAXV);
+  if (H->kr_dot_host) cudaFreeHost(H->kr_dot_host);
+  if (H->kr_y_host) cudaFreeHost(H->kr_y_host);
+  H->kr_dot_host = nullptr;
+  H->kr_y_host = nullptr;
+  CK(cudaMallocHost(&H->kr_dot_host, KR_MAXV * sizeof(double)));
+  CK(cudaMallocHost(&H->kr_y_host, KR_MAXV * sizeof(double)));
+  H->kr_k = k;
+}
+
+double* kr_vec(cc_hierarchy* H, int i) { return H->kr_v + (size_t)i * H->lv[0]->nn; }
+double* kr_zvec(cc_hierarchy* H, int i) { return H->kr_z + (size_t)i * H->lv[0]->nn; }
+
+// out[0..nx) = <w, V_i> (and out[nx] = <w, w> when self) into kr_dot, then
+// its pinned host copy; the caller records the step event after it
+void kr_dots(cc_hierarchy* H, int nx, const double* w, int self, cudaStream_t s) {
+  const int64_t nn = H->lv[0]->nn;
+  const int nv = nx + self;
+  pdl_launch(k_mdot, KR_BLOCKS, 256, 0, s, (const double*)H->kr_v, nx, w, self, nn, H->kr_part);
+  pdl_launch(k_mdot_sum, nv, 32, 0, s, (const double*)H->kr_part, nv, KR_BLOCKS, H->kr_dot);
+  CK(cudaMemcpyAsync(H->kr_dot_host, H->kr_dot, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
+// the FP32 cycle of the preconditioner, on b32 from zero; leaves e in
+// u32[kr_cur]
+void kr_cycle(cc_hierarchy* H, cudaStream_t s) {
+  std::vector<int> cur(H->lv.size(), 0);
+  cycle_level<float>(H, 0, cur, true, s, false);
+  H->kr_cur = cur[0];
+}
+
+// z = M^-1 v: v narrowed to the FP32 right-hand side, one cycle, e widened
+void kr_precond(cc_hierarchy* H, const double* v, double* z, cudaStream_t s) {
+  Level& L = *H->lv[0];
+  pdl_launch(k_convert<double, float>, nblk(L.nn), 256, 0, s, v, L.b32, L.nn);
+  if (H->opt.use_graphs) {
+    if (!H->kr_graph) {
+      cudaGraph_t gr;
+      int64_t before = t_launches;
+      CK(cudaStreamBeginCapture(H->gstream, cudaStreamCaptureModeThreadLocal));
+      kr_cycle(H, H->gstream);
+      CK(cudaStreamEndCapture(H->gstream, &gr));
+      CK(cudaGraphInstantiate(&H->kr_graph, gr, 0));
+      CK(cudaGraphDestroy(gr));
+      H->kr_graph_launches = t_launches - before;
+      t_launches = before;
+    }
+    CK(cudaGraphLaunch(H->kr_graph, s));
+    t_launches += H->kr_graph_launches;
+  } else {
+    kr_cycle(H, s);
+  }
+  pdl_launch(k_widen_masked, nblk(L.nn), 256, 0, s, (const float*)L.u32[H->kr_cur], (const uint8_t*)L.cls,
+             z, L.nn);
+}
+
 // One solve as a sequence of steps that never wait on the GPU: every step
 // enqueues its work and the copy of one norm to pinned memory, then records
 // the handle's step event; the next step runs once that event has completed.
@@ -1187,6 +1278,11 @@ struct SolveTask {
   int it = 0;
   int64_t launches = 0;
   cc_result res{};
+  // Krylov state: column j of the Hessenberg matrix being built, the
+  // restart's initial residual norm, the rotated least-squares system
+  int kj = 0;
+  double kbeta = 0;
+  std::vector<double> kH, kcs, ksn, kg, kh1;
 };
 
 void enqueue_norm(cc_hierarchy* H, cudaStream_t s) {
@@ -1250,6 +1346,52 @@ void finish_task(SolveTask& T) {
   T.phase = 4;
 }
 
+// Krylov: start a restart; the residual is in V_0, its squared 2-norm goes
+// to the host
+void kr_restart(SolveTask& T) {
+  kr_dots(T.H, 0, kr_vec(T.H, 0), 1, T.s);
+  CK(cudaEventRecord(T.H->step_ev, T.s));
+  T.phase = 10;
+}
+
+// Krylov: first half of Arnoldi step j: Z_j = M^-1 V_j, V_{j+1} = -A Z_j (the
+// FP64 residual of Z_j against a zero right-hand side), and the projections
+// of V_{j+1} on V_0..V_j to the host
+void kr_arnoldi(SolveTask& T) {
+  cc_hierarchy* H = T.H;
+  const int j = T.kj;
+  kr_precond(H, kr_vec(H, j), kr_zvec(H, j), T.s);
+  residual64<double>(H, kr_zvec(H, j), H->kr_zero, kr_vec(H, j + 1), T.s);
+  kr_dots(H, j + 1, kr_vec(H, j + 1), 0, T.s);
+  CK(cudaEventRecord(H->step_ev, T.s));
+  T.phase = 11;
+}
+
+// Krylov: end of a restart after m Arnoldi steps.  The Hessenberg matrix is
+// that of the operator -A M^-1, so with y solving the rotated triangular
+// system the update is u -= Z y; then the true FP64 residual goes to V_0 and
+// its max-norm to the host.
+void kr_end_restart(SolveTask& T, int m) {
+  cc_hierarchy* H = T.H;
+  Level& L = *H->lv[0];
+  const int k = H->opt.krylov;
+  std::vector<double> y(m, 0.0);
+  for (int i = m - 1; i >= 0; --i) {
+    double v = T.kg[i];
+    for (int q = i + 1; q < m; ++q) v -= T.kH[(size_t)q * (k + 1) + i] * y[q];
+    const double d = T.kH[(size_t)i * (k + 1) + i];
+    y[i] = d != 0.0 ? v / d : 0.0;
+  }
+  for (int i = 0; i < m; ++i) H->kr_y_host[i] = y[i];
+  CK(cudaMemcpyAsync(H->kr_y, H->kr_y_host, m * sizeof(double), cudaMemcpyHostToDevice, T.s));
+  pdl_launch(k_maxpy, KR_BLOCKS, 256, 0, T.s, (const double*)H->kr_z, m, (const double*)H->kr_y, L.u64[0],
+             1.0, L.nn);
+  CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), T.s));
+  residual64<double>(H, L.u64[0], L.b64, kr_vec(H, 0), T.s);
+  enqueue_norm(H, T.s);
+  T.phase = 13;
+}
+
 // Advance T by one step (its previous step has completed on the GPU); true
 // once the solve is done and its result copied out.
 bool solve_step(SolveTask& T) {
@@ -1262,6 +1404,7 @@ bool solve_step(SolveTask& T) {
     case 0:
       H->cur64 = 0;
       T.res.status = CC_ERR_NOT_CONVERGED;
+      if (H->opt.krylov) ensure_krylov(H, s);
       assemble_rhs(H, T.f, T.g, L.b64, s);
       CK(cudaMemcpyAsync(L.u64[0], T.u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
       CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
@@ -1275,7 +1418,8 @@ bool solve_step(SolveTask& T) {
       T.bn = host_norm(H);
       if (T.bn == 0.0) T.bn = 1.0;
       CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
-      if (mixed) residual64<float>(H, L.u64[0], L.b64, L.b32, s, mixed_e0(H), L.spf.omega_over_diag);
+      if (H->opt.krylov) residual64<double>(H, L.u64[0], L.b64, kr_vec(H, 0), s);
+      else if (mixed) residual64<float>(H, L.u64[0], L.b64, L.b32, s, mixed_e0(H), L.spf.omega_over_diag);
       else residual64<double>(H, L.u64[0], L.b64, H->r64, s);
       enqueue_norm(H, s);
       T.phase = 2;
@@ -1287,6 +1431,8 @@ bool solve_step(SolveTask& T) {
         finish_task(T);
       } else if (H->opt.max_cycles <= 0) {
         finish_task(T);
+      } else if (H->opt.krylov) {
+        kr_restart(T);
       } else {
         launch_iteration(H, mixed, s);
         T.phase = 3;
@@ -1306,6 +1452,93 @@ bool solve_step(SolveTask& T) {
         finish_task(T);
       } else {
         launch_iteration(H, mixed, s);
+      }
+      break;
+    case 10: {   // Krylov: squared 2-norm of the restart's residual
+      const int k = H->opt.krylov;
+      T.kbeta = std::sqrt(std::max(H->kr_dot_host[0], 0.0));
+      if (!std::isfinite(T.kbeta)) {
+        T.res.status = CC_ERR_DIVERGED;
+        finish_task(T);
+        break;
+      }
+      if (T.kbeta == 0.0) {
+        T.res.status = CC_OK;
+        finish_task(T);
+        break;
+      }
+      T.kH.assign((size_t)k * (k + 1), 0.0);   // column j at j (k + 1)
+      T.kcs.assign(k, 0.0);
+      T.ksn.assign(k, 0.0);
+      T.kg.assign(k + 1, 0.0);
+      T.kg[0] = T.kbeta;
+      pdl_launch(k_maxpy, KR_BLOCKS, 256, 0, s, (const double*)nullptr, 0, (const double*)nullptr,
+                 kr_vec(H, 0), 1.0 / T.kbeta, L.nn);
+      T.kj = 0;
+      kr_arnoldi(T);
+      break;
+    }
+    case 11: {   // Krylov: first projections of V_{j+1}; subtract them, project again
+      const int j = T.kj;
+      T.kh1.assign(H->kr_dot_host, H->kr_dot_host + j + 1);
+      pdl_launch(k_maxpy, KR_BLOCKS, 256, 0, s, (const double*)H->kr_v, j + 1, (const double*)H->kr_dot,
+                 kr_vec(H, j + 1), 1.0, L.nn);
+      kr_dots(H, j + 1, kr_vec(H, j + 1), 1, s);
+      CK(cudaEventRecord(H->step_ev, s));
+      T.phase = 12;
+      break;
+    }
+    case 12: {   // Krylov: second projections and |w|^2 give column j of the Hessenberg matrix
+      const int k = H->opt.krylov, j = T.kj;
+      double* col = &T.kH[(size_t)j * (k + 1)];
+      double h2n = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        const double h2 = H->kr_dot_host[i];
+        col[i] = T.kh1[i] + h2;
+        h2n += h2 * h2;
+      }
+      const double hn = std::sqrt(std::max(H->kr_dot_host[j + 1] - h2n, 0.0));
+      col[j + 1] = hn;
+      pdl_launch(k_maxpy, KR_BLOCKS, 256, 0, s, (const double*)H->kr_v, j + 1, (const double*)H->kr_dot,
+                 kr_vec(H, j + 1), hn > 0.0 ? 1.0 / hn : 1.0, L.nn);
+      for (int i = 0; i < j; ++i) {
+        const double t = T.kcs[i] * col[i] + T.ksn[i] * col[i + 1];
+        col[i + 1] = -T.ksn[i] * col[i] + T.kcs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double d = std::hypot(col[j], col[j + 1]);
+      T.kcs[j] = d > 0.0 ? col[j] / d : 1.0;
+      T.ksn[j] = d > 0.0 ? col[j + 1] / d : 0.0;
+      col[j] = d;
+      col[j + 1] = 0.0;
+      T.kg[j + 1] = -T.ksn[j] * T.kg[j];
+      T.kg[j] = T.kcs[j] * T.kg[j];
+      ++T.it;
+      const double est = std::fabs(T.kg[j + 1]);
+      const int m = j + 1;
+      if (!std::isfinite(est) || !std::isfinite(d)) {
+        T.res.status = CC_ERR_DIVERGED;
+        finish_task(T);
+      } else if (est < T.tol * T.bn || m == k || hn == 0.0 || T.it >= H->opt.max_cycles) {
+        kr_end_restart(T, m);
+      } else {
+        T.kj = m;
+        kr_arnoldi(T);
+      }
+      break;
+    }
+    case 13:   // Krylov: max-norm of the true residual after a restart
+      T.rel = host_norm(H) / T.bn;
+      if (T.rel < T.tol) {
+        T.res.status = CC_OK;
+        finish_task(T);
+      } else if (!std::isfinite(T.rel) || (T.first > 0 && T.rel > 1e3 * T.first)) {
+        T.res.status = CC_ERR_DIVERGED;
+        finish_task(T);
+      } else if (T.it >= H->opt.max_cycles) {
+        finish_task(T);
+      } else {
+        kr_restart(T);
       }
       break;
     case 4:
@@ -1489,6 +1722,9 @@ void destroy_hierarchy(cc_hierarchy* H) {
   if (!H->opt.host_only) cudaDeviceSynchronize();
   for (auto& g : H->gexec)
     if (g) cudaGraphExecDestroy(g);
+  if (H->kr_graph) cudaGraphExecDestroy(H->kr_graph);
+  if (H->kr_dot_host) cudaFreeHost(H->kr_dot_host);
+  if (H->kr_y_host) cudaFreeHost(H->kr_y_host);
   for (auto& e : H->ev) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -1524,6 +1760,7 @@ void cc_default_options(cc_options* o) {
   o->serve_slots = 4;
   o->cache = 0;
   o->hole_cells = 2.0;
+  o->krylov = 0;
 }
 
 const char* cc_last_error_string(void) { return t_last_error; }
@@ -1557,7 +1794,8 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 == 0 || o.min_coarse_n < 4 || o.max_cycles < 1 ||
       !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3) ||
       (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W) || o.w_depth < 0 ||
-      o.serve_slots < 1 || !(o.hole_cells > 0))
+      o.serve_slots < 1 || !(o.hole_cells > 0) || o.krylov < 0 || o.krylov > KR_MAXV - 1 ||
+      (o.krylov && (o.precision != CC_PREC_MIXED || o.cycle == CC_CYCLE_FMG)))
     return CC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // the setup cache: a clone of the hierarchy of an identical earlier call
@@ -1570,7 +1808,17 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
       cc_status st = cc_clone(it->second, stream, out);
-      if (st == CC_OK) (*out)->opt = o;
+      if (st == CC_OK) {
+        (*out)->opt = o;
+        try {
+          ensure_krylov(*out, s);
+          CK(cudaStreamSynchronize(s));
+        } catch (CudaError& e) {
+          destroy_hierarchy(*out);
+          *out = nullptr;
+          return e.e == cudaErrorMemoryAllocation ? CC_ERR_NO_MEMORY : CC_ERR_CUDA;
+        }
+      }
       return st;
     }
   }
@@ -1764,6 +2012,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       H->d_norm = H->pool->alloc<unsigned long long>(2);
       CK(cudaMallocHost(&H->h_norm, 2 * sizeof(unsigned long long)));
       CK(cudaEventCreateWithFlags(&H->step_ev, cudaEventDisableTiming));
+      ensure_krylov(H, s);
     }
     CK(cudaStreamCreateWithFlags(&H->gstream, cudaStreamNonBlocking));
     CK(cudaStreamSynchronize(s));
@@ -1934,6 +2183,7 @@ cc_status cc_clone(cc_handle S, cc_stream stream, cc_handle* out) {
     H->d_norm = H->pool->alloc<unsigned long long>(2);
     CK(cudaMallocHost(&H->h_norm, 2 * sizeof(unsigned long long)));
     CK(cudaEventCreateWithFlags(&H->step_ev, cudaEventDisableTiming));
+    ensure_krylov(H, s);
     CK(cudaStreamCreateWithFlags(&H->gstream, cudaStreamNonBlocking));
     CK(cudaStreamSynchronize(s));
   } catch (CudaError& e) {

@@ -1160,6 +1160,89 @@ __global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, int64_t nn
   if (k < nn) y[k] = (B)x[k];
 }
 
+// ---- Krylov outer iteration (cc_options.krylov): FGMRES building blocks ------
+// Not part of the paper's solver, which iterates the cycle alone: a restarted
+// flexible GMRES in FP64 whose preconditioner is one FP32 cycle.  Every sum
+// below runs in a fixed order, so a solve gives the same bits every time.
+constexpr int KR_MAXV = 33;     // vectors of one multi-dot: restart length <= 32, plus one
+constexpr int KR_BLOCKS = 152;  // CTAs of a multi-dot (one wave: one per SM at 156 registers)
+
+// part[blk * nv + i] = this CTA's share of sum_k w[k] x_i[k] for i < nx, with
+// x_i = x + i nn; when self, part[blk * nv + nx] is its share of sum_k w[k]^2
+// (nv = nx + self).
+__global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ x, int nx,
+                                              const double* __restrict__ w, int self, int64_t nn,
+                                              double* __restrict__ part) {
+  pdl_enter();
+  __shared__ double red[8][KR_MAXV + 1];
+  double acc[KR_MAXV];
+#pragma unroll
+  for (int i = 0; i < KR_MAXV; ++i) acc[i] = 0.0;
+  double ws = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nn;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double wk = w[k];
+#pragma unroll
+    for (int i = 0; i < KR_MAXV; ++i)
+      if (i < nx) acc[i] += wk * x[(size_t)i * nn + k];
+    ws += wk * wk;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < KR_MAXV; ++i) {
+    if (i >= nx) break;
+    double v = acc[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+  if (lane == 0) red[warp][KR_MAXV] = ws;
+  __syncthreads();
+  const int nv = nx + self;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const int src = i < nx ? i : KR_MAXV;
+    double v = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][src];
+    part[(size_t)blockIdx.x * nv + i] = v;
+  }
+  pdl_exit();
+}
+
+// out[i] = sum over the nb CTAs of part[b * nv + i]; one warp per vector
+__global__ void k_mdot_sum(const double* __restrict__ part, int nv, int nb, double* __restrict__ out) {
+  pdl_enter();
+  const int i = blockIdx.x, lane = threadIdx.x;
+  double v = 0.0;
+  for (int b = lane; b < nb; b += 32) v += part[(size_t)b * nv + i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) out[i] = v;
+  pdl_exit();
+}
+
+// y = (y - sum_{i < nx} c[i] x_i) * scale, x_i = x + i nn (c in device memory)
+__global__ void k_maxpy(const double* __restrict__ x, int nx, const double* __restrict__ c,
+                        double* __restrict__ y, double scale, int64_t nn) {
+  pdl_enter();
+  __shared__ double cs[KR_MAXV];
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) cs[i] = c[i];
+  __syncthreads();
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nn;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double v = y[k];
+    for (int i = 0; i < nx; ++i) v -= cs[i] * x[(size_t)i * nn + k];
+    y[k] = v * scale;
+  }
+  pdl_exit();
+}
+
+// z = e on present control volumes, 0 on empty ones (FP32 -> FP64)
+__global__ void k_widen_masked(const float* __restrict__ e, const uint8_t* __restrict__ cls,
+                               double* __restrict__ z, int64_t nn) {
+  pdl_enter();
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nn) z[k] = cls[k] == C_EMPTY ? 0.0 : (double)e[k];
+}
+
 __global__ void k_absmax(const double* __restrict__ x, int64_t nn, unsigned long long* out) {
   pdl_enter();
   double av = 0.0;

@@ -562,3 +562,59 @@ def test_full_size_bench_configuration():
     assert abs(res[0][0] - res[1][0]) <= 1, res
     assert res[1][1] <= 1.1 * res[0][1], res
     assert max(res[0][1], res[1][1]) < 2e-11, res
+
+
+@pytest.mark.slow
+def test_krylov_solves_where_the_cycle_diverges():
+    """Problem 8 of the batch workload (256^2, three small holes): coarsest-level
+    cut-cell rows of the wrong sign make the mixed W(4,4) iteration diverge.
+    With cc_options.krylov = 20 (FGMRES in FP64, one FP32 cycle per step as
+    preconditioner) the same hierarchy reaches 1e-10, and the solution equals
+    the oracle's direct solve of the same system."""
+    P, n = W.problem_batch(8)
+    assert n == 256
+    opts = dict(min_coarse_n=32, cycle=2, precision=1, w_depth=1, nu1=4, nu2=4)
+    f, g = None, None
+    for kr, mc in ((0, 40), (20, 200)):
+        H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                  default_options(max_cycles=mc, krylov=kr, **opts))
+        if f is None:
+            f, g, _ = I.problem_inputs(H, P)
+        u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+        r = H.solve(_t(f), _t(g), u, 1e-10)
+        if kr == 0:
+            assert r.status == 6, (r.status, r.rel_res)          # CC_ERR_DIVERGED
+        else:
+            assert r.status == 0 and r.rel_res < 1e-10, (r.status, r.cycles, r.rel_res)
+            ug = _np(u, n)
+        H.close()
+    O = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=32)
+    d = O.levels[0]
+    ud = spl.spsolve(d.A.tocsc(), _oracle_rhs(O, P).ravel()).reshape(n, n)
+    present = d.lev.present
+    assert np.abs(ug - ud)[present].max() <= 1e-7 * np.abs(ud).max()
+
+
+def test_krylov_solve_on_the_disk_is_deterministic():
+    """On the disk domain the Krylov solve reaches 1e-10 with an error against
+    the exact cell averages within 1.1x of the oracle's cycle solve; a clone
+    solving the same problem in the same cc_solve_batch call gives the same
+    bits (the reductions run in a fixed order)."""
+    from paper_2601_02975_gb300 import solve_batch
+    n, mc = 64, 16
+    P, H, O = _pair("disk", n, mc, cycle=2, precision=1, krylov=10)
+    f, g, ue, _ = _gpu_rhs(H, P)
+    ro = M.solve(O, _oracle_rhs(O, P), tol=1e-10, gamma=2)
+    d = O.levels[0]
+    err_o = np.abs(ro.u - D.cell_averages(d.lev, P.u))[d.lev.present].max()
+    u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    r = H.solve(_t(f), _t(g), u, 1e-10)
+    assert r.status == 0 and r.rel_res < 1e-10, (r.status, r.rel_res)
+    assert r.cycles <= len(ro.history) + 2, (r.cycles, len(ro.history))
+    err = np.abs(_np(u, n) - ue)[d.lev.present].max()
+    assert err <= 1.1 * err_o + 1e-14, (err, err_o)
+    C = H.clone()
+    us = [torch.zeros(n * n, dtype=torch.float64, device=DEV) for _ in range(2)]
+    res = solve_batch([H, C], [_t(f)] * 2, [_t(g)] * 2, us, [1e-10] * 2)
+    assert all(x.status == 0 for x in res)
+    assert torch.equal(us[0], u) and torch.equal(us[1], u)
