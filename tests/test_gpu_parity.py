@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 import __graft_entry__  # noqa: E402
 from oracle import discretize as D  # noqa: E402
 from oracle import multigrid as M  # noqa: E402
-from paper_2601_02975_gb300 import Hierarchy, default_options  # noqa: E402
+from paper_2601_02975_gb300 import CCError, Hierarchy, default_options  # noqa: E402
 from paper_2601_02975_gb300 import inputs as I  # noqa: E402
 from paper_2601_02975_gb300 import workloads as W  # noqa: E402
 
@@ -581,10 +581,12 @@ def test_krylov_solves_where_the_cycle_diverges():
         if f is None:
             f, g, _ = I.problem_inputs(H, P)
         u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
-        r = H.solve(_t(f), _t(g), u, 1e-10)
         if kr == 0:
-            assert r.status == 6, (r.status, r.rel_res)          # CC_ERR_DIVERGED
+            with pytest.raises(CCError) as ei:
+                H.solve(_t(f), _t(g), u, 1e-10)
+            assert ei.value.status == 6                           # CC_ERR_DIVERGED
         else:
+            r = H.solve(_t(f), _t(g), u, 1e-10)
             assert r.status == 0 and r.rel_res < 1e-10, (r.status, r.cycles, r.rel_res)
             ug = _np(u, n)
         H.close()
