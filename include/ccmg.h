@@ -113,11 +113,14 @@ typedef struct {
   int krylov;          /* 0 (default): the solve iterates the cycle (Alg. 2, inside
                           FP64 refinement in the mixed mode).  k in 1..32: restarted
                           flexible GMRES(k) in FP64 on A u = b instead, each step
-                          preconditioned by one FP32 cycle from zero, so solves
-                          converge where the cycle alone diverges.  Not part of the
-                          paper's method.  Needs CC_PREC_MIXED and cycle V or W;
-                          cc_result.cycles then counts preconditioner cycles.  The
-                          handle holds 2k + 2 extra FP64 vectors of the finest grid */
+                          preconditioned by one cycle from zero in the handle's
+                          precision, so solves can converge where the cycle alone
+                          diverges.  Not part of the paper's method.  Cycle V or W
+                          only; cc_result.cycles then counts preconditioner cycles.
+                          Where the cycle amplifies some error modes by ~1e6 an FP32
+                          cycle keeps too few digits of the rest: use CC_PREC_FP64
+                          there.  The handle holds 2k + 4 extra FP64 vectors of the
+                          finest grid */
 } cc_options;
 
 /* Sizes of a hierarchy. */

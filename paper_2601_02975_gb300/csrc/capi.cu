@@ -628,6 +628,8 @@ struct cc_hierarchy {
   // partials and results, the least-squares coefficients, and their pinned
   // host copies; the preconditioner cycle's graph and the buffer it ends in
   int kr_k = 0;
+  double* kr_u = nullptr;   // the solution and right-hand side of a Krylov solve (the
+  double* kr_b = nullptr;   // level-0 u and b buffers are the preconditioner's scratch)
   double* kr_v = nullptr;
   double* kr_z = nullptr;
   double* kr_zero = nullptr;
@@ -1199,6 +1201,10 @@ void ensure_krylov(cc_hierarchy* H, cudaStream_t s) {
   const int k = H->opt.krylov;
   if (k <= H->kr_k || H->opt.host_only) return;
   const int64_t nn = H->lv[0]->nn;
+  if (!H->kr_u) {
+    H->kr_u = H->pool->alloc<double>(nn);
+    H->kr_b = H->pool->alloc<double>(nn);
+  }
   H->kr_v = H->pool->alloc<double>((size_t)(k + 1) * nn);
   H->kr_z = H->pool->alloc<double>((size_t)k * nn);
   H->kr_zero = H->pool->alloc<double>(nn);
@@ -1228,18 +1234,22 @@ void kr_dots(cc_hierarchy* H, int nx, const double* w, int self, cudaStream_t s)
   CK(cudaMemcpyAsync(H->kr_dot_host, H->kr_dot, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
-// the FP32 cycle of the preconditioner, on b32 from zero; leaves e in
-// u32[kr_cur]
+// the preconditioner's cycle from zero, in the handle's precision, on the
+// level-0 right-hand side buffer (b32 or b64); leaves e in u32 / u64[kr_cur]
 void kr_cycle(cc_hierarchy* H, cudaStream_t s) {
   std::vector<int> cur(H->lv.size(), 0);
-  cycle_level<float>(H, 0, cur, true, s, false);
+  if (H->opt.precision == CC_PREC_MIXED) cycle_level<float>(H, 0, cur, true, s, false);
+  else cycle_level<double>(H, 0, cur, true, s, false);
   H->kr_cur = cur[0];
 }
 
-// z = M^-1 v: v narrowed to the FP32 right-hand side, one cycle, e widened
+// z = M^-1 v: v into the cycle's right-hand side (narrowed to FP32 in the
+// mixed mode), one cycle, e widened and zeroed on empty control volumes
 void kr_precond(cc_hierarchy* H, const double* v, double* z, cudaStream_t s) {
   Level& L = *H->lv[0];
-  pdl_launch(k_convert<double, float>, nblk(L.nn), 256, 0, s, v, L.b32, L.nn);
+  const bool mixed = H->opt.precision == CC_PREC_MIXED;
+  if (mixed) pdl_launch(k_convert<double, float>, nblk(L.nn), 256, 0, s, v, L.b32, L.nn);
+  else CK(cudaMemcpyAsync(L.b64, v, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (H->opt.use_graphs) {
     if (!H->kr_graph) {
       cudaGraph_t gr;
@@ -1257,8 +1267,12 @@ void kr_precond(cc_hierarchy* H, const double* v, double* z, cudaStream_t s) {
   } else {
     kr_cycle(H, s);
   }
-  pdl_launch(k_widen_masked, nblk(L.nn), 256, 0, s, (const float*)L.u32[H->kr_cur], (const uint8_t*)L.cls,
-             z, L.nn);
+  if (mixed)
+    pdl_launch(k_widen_masked<float>, nblk(L.nn), 256, 0, s, (const float*)L.u32[H->kr_cur],
+               (const uint8_t*)L.cls, z, L.nn);
+  else
+    pdl_launch(k_widen_masked<double>, nblk(L.nn), 256, 0, s, (const double*)L.u64[H->kr_cur],
+               (const uint8_t*)L.cls, z, L.nn);
 }
 
 // One solve as a sequence of steps that never wait on the GPU: every step
@@ -1341,7 +1355,8 @@ void collect_timing(cc_hierarchy* H, bool mixed) {
 
 void finish_task(SolveTask& T) {
   Level& L = *T.H->lv[0];
-  CK(cudaMemcpyAsync(T.u, L.u64[T.H->cur64], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, T.s));
+  const double* sol = T.H->opt.krylov ? T.H->kr_u : L.u64[T.H->cur64];
+  CK(cudaMemcpyAsync(T.u, sol, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, T.s));
   CK(cudaEventRecord(T.H->step_ev, T.s));
   T.phase = 4;
 }
@@ -1384,10 +1399,10 @@ void kr_end_restart(SolveTask& T, int m) {
   }
   for (int i = 0; i < m; ++i) H->kr_y_host[i] = y[i];
   CK(cudaMemcpyAsync(H->kr_y, H->kr_y_host, m * sizeof(double), cudaMemcpyHostToDevice, T.s));
-  pdl_launch(k_maxpy, KR_BLOCKS, 256, 0, T.s, (const double*)H->kr_z, m, (const double*)H->kr_y, L.u64[0],
+  pdl_launch(k_maxpy, KR_BLOCKS, 256, 0, T.s, (const double*)H->kr_z, m, (const double*)H->kr_y, H->kr_u,
              1.0, L.nn);
   CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), T.s));
-  residual64<double>(H, L.u64[0], L.b64, kr_vec(H, 0), T.s);
+  residual64<double>(H, H->kr_u, H->kr_b, kr_vec(H, 0), T.s);
   enqueue_norm(H, T.s);
   T.phase = 13;
 }
@@ -1405,10 +1420,14 @@ bool solve_step(SolveTask& T) {
       H->cur64 = 0;
       T.res.status = CC_ERR_NOT_CONVERGED;
       if (H->opt.krylov) ensure_krylov(H, s);
-      assemble_rhs(H, T.f, T.g, L.b64, s);
-      CK(cudaMemcpyAsync(L.u64[0], T.u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
-      pdl_launch(k_absmax, 152 * 4, 256, 0, s, L.b64, L.nn, H->d_norm);
+      {
+        double* b0 = H->opt.krylov ? H->kr_b : L.b64;
+        double* u0 = H->opt.krylov ? H->kr_u : L.u64[0];
+        assemble_rhs(H, T.f, T.g, b0, s);
+        CK(cudaMemcpyAsync(u0, T.u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
+        pdl_launch(k_absmax, 152 * 4, 256, 0, s, (const double*)b0, L.nn, H->d_norm);
+      }
       enqueue_norm(H, s);
       T.phase = 1;
       break;
@@ -1418,7 +1437,7 @@ bool solve_step(SolveTask& T) {
       T.bn = host_norm(H);
       if (T.bn == 0.0) T.bn = 1.0;
       CK(cudaMemsetAsync(H->d_norm, 0, sizeof(unsigned long long), s));
-      if (H->opt.krylov) residual64<double>(H, L.u64[0], L.b64, kr_vec(H, 0), s);
+      if (H->opt.krylov) residual64<double>(H, H->kr_u, H->kr_b, kr_vec(H, 0), s);
       else if (mixed) residual64<float>(H, L.u64[0], L.b64, L.b32, s, mixed_e0(H), L.spf.omega_over_diag);
       else residual64<double>(H, L.u64[0], L.b64, H->r64, s);
       enqueue_norm(H, s);
@@ -1795,7 +1814,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3) ||
       (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W) || o.w_depth < 0 ||
       o.serve_slots < 1 || !(o.hole_cells > 0) || o.krylov < 0 || o.krylov > KR_MAXV - 1 ||
-      (o.krylov && (o.precision != CC_PREC_MIXED || o.cycle == CC_CYCLE_FMG)))
+      (o.krylov && o.cycle == CC_CYCLE_FMG))
     return CC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // the setup cache: a clone of the hierarchy of an identical earlier call

@@ -1235,8 +1235,9 @@ __global__ void k_maxpy(const double* __restrict__ x, int nx, const double* __re
   pdl_exit();
 }
 
-// z = e on present control volumes, 0 on empty ones (FP32 -> FP64)
-__global__ void k_widen_masked(const float* __restrict__ e, const uint8_t* __restrict__ cls,
+// z = e on present control volumes, 0 on empty ones (to FP64)
+template <class T>
+__global__ void k_widen_masked(const T* __restrict__ e, const uint8_t* __restrict__ cls,
                                double* __restrict__ z, int64_t nn) {
   pdl_enter();
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

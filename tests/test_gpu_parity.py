@@ -568,16 +568,16 @@ def test_full_size_bench_configuration():
 def test_krylov_solves_where_the_cycle_diverges():
     """Problem 8 of the batch workload (256^2, three small holes): coarsest-level
     cut-cell rows of the wrong sign make the mixed W(4,4) iteration diverge.
-    With cc_options.krylov = 20 (FGMRES in FP64, one FP32 cycle per step as
-    preconditioner) the same hierarchy reaches 1e-10, and the solution equals
-    the oracle's direct solve of the same system."""
+    With cc_options.krylov = 20 and FP64 cycles (FGMRES in FP64, one FP64
+    cycle per step as preconditioner) the same hierarchy reaches 1e-10, and
+    the solution equals the oracle's direct solve of the same system."""
     P, n = W.problem_batch(8)
     assert n == 256
-    opts = dict(min_coarse_n=32, cycle=2, precision=1, w_depth=1, nu1=4, nu2=4)
+    opts = dict(min_coarse_n=32, cycle=2, w_depth=1, nu1=4, nu2=4)
     f, g = None, None
-    for kr, mc in ((0, 40), (20, 200)):
+    for kr, mc, prec in ((0, 40, 1), (20, 200, 0)):
         H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
-                                  default_options(max_cycles=mc, krylov=kr, **opts))
+                                  default_options(max_cycles=mc, krylov=kr, precision=prec, **opts))
         if f is None:
             f, g, _ = I.problem_inputs(H, P)
         u = torch.zeros(n * n, dtype=torch.float64, device=DEV)

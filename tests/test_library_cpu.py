@@ -115,22 +115,23 @@ def test_setup_rejects_bad_arguments(lib, case):
 
 def test_new_options_are_checked(lib):
     """hole_cells, serve_slots, w_depth, fmg_cycle and krylov are validated
-    by cc_setup (krylov: 0..32, the mixed precision and a V or W cycle only);
-    cc_serve_budget rejects a negative cap."""
+    by cc_setup (krylov: 0..32, with a V or W cycle); cc_serve_budget rejects
+    a negative cap."""
     from paper_2601_02975_gb300 import CCError, Hierarchy, default_options, serve_budget
     P = W.problem_disk()
     for kw in ({"hole_cells": 0.0}, {"hole_cells": -1.0}, {"serve_slots": 0}, {"w_depth": -1},
                {"fmg_cycle": 3}, {"krylov": -1}, {"krylov": 33, "precision": 1},
-               {"krylov": 8, "precision": 0}, {"krylov": 8, "precision": 1, "cycle": 3}):
+               {"krylov": 8, "precision": 1, "cycle": 3}):
         with pytest.raises(CCError) as ei:
             Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 32, default_options(host_only=1, **kw))
         assert ei.value.status == 1, kw
     with pytest.raises(CCError):
         serve_budget(-1)
     serve_budget(0)
-    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 32,
-                              default_options(host_only=1, krylov=32, precision=1, cycle=2))
-    H.close()
+    for prec in (0, 1):
+        H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 32,
+                                  default_options(host_only=1, krylov=32, precision=prec, cycle=2))
+        H.close()
 
 
 def test_hole_cells_sets_the_depth(lib):
