@@ -476,6 +476,51 @@ def test_four_disks_error_magnitudes(kind):
         assert math.log2(got[64][q] / got[128][q]) > 3.7, (kind, got)
 
 
+@pytest.mark.parametrize("name", ["disk", "ellipses0", "four_disks"])
+def test_irregular_cells_are_plg_and_covered_by_coarse_plg(name):
+    """Sec. 5.3: every irregular (cut) cell is a PLG cell, and every fine PLG
+    cell is covered by a coarse PLG cell.  A fine cell whose coarse parent
+    control volume was merged away (Alg. 1) is covered by the coarse cut cell
+    that absorbed it."""
+    P = {"disk": W.problem_disk, "ellipses0": lambda: W.problem_ellipses(0),
+         "four_disks": lambda: W.problem_four_disks(W.DIRICHLET)}[name]()
+    H = M.build_hierarchy(P.dom, 64, P.a, P.b, P.c, min_coarse=16)
+    assert H.nl >= 2
+    for l, d in enumerate(H.levels):
+        cut = (d.lev.ctype != G.REGULAR) & d.lev.present
+        assert np.all(d.kind[cut] == D.PLG), (name, l)
+        if l + 1 == H.nl:
+            continue
+        c = H.levels[l + 1]
+        js, is_ = np.nonzero(d.kind == D.PLG)
+        for j, i in zip(js, is_):
+            pj, pi = j // 2, i // 2
+            k = pj * c.n + pi if c.lev.present[pj, pi] else int(c.lev.owner[pj, pi])
+            assert k >= 0 and c.kind.ravel()[k] == D.PLG, (name, l, i, j)
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_block_bandwidth_near_one_curve(n):
+    """Lemma 5.2: with the PLG cells of one smooth Jordan curve ordered as in
+    Def. 5.1, A22 is a band of width at most 17 plus two corner blocks (the
+    curve closes on itself), i.e. its cyclic bandwidth is at most 17.  The
+    disk with b = 0 has no other block cells."""
+    P = W.problem_disk()
+    lev = G.build_level(P.dom, n, 0.1)
+    d = D.discretize(lev, 1.0, 0.0, 2.0)
+    order = d.plg_order
+    m = len(order)
+    pos = {k: i for i, k in enumerate(order)}
+    A = d.A.tocsr()
+    cbw = 0
+    for k in order:
+        for kk in A.indices[A.indptr[k]:A.indptr[k + 1]]:
+            if kk in pos:
+                dd = abs(pos[kk] - pos[k])
+                cbw = max(cbw, min(dd, m - dd))
+    assert 0 < cbw <= 17, cbw
+
+
 @pytest.mark.parametrize("name,n,mc", [("box", 16, 4), ("disk", 32, 16)])
 @pytest.mark.parametrize("gamma", [1, 2])
 def test_cycles_converge_to_direct_solve(name, n, mc, gamma):
