@@ -88,14 +88,37 @@ void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
 
 // ---------------------------------------------------------------------------
 // dense helpers (host, FP64)
-// in-place inverse by Gauss-Jordan with partial pivoting; false if singular
+// A reusable barrier for the threads of one host computation.
+struct HostBarrier {
+  std::mutex m;
+  std::condition_variable cv;
+  unsigned n, count = 0;
+  uint64_t gen = 0;
+  explicit HostBarrier(unsigned n_) : n(n_) {}
+  void wait() {
+    std::unique_lock<std::mutex> lk(m);
+    const uint64_t g = gen;
+    if (++count == n) {
+      count = 0;
+      ++gen;
+      cv.notify_all();
+    } else {
+      cv.wait(lk, [&] { return gen != g; });
+    }
+  }
+};
+
+// in-place inverse by Gauss-Jordan with partial pivoting; false if singular.
+// From n = 512 on, the row eliminations of each pivot step are split over
+// host threads; every element sees the same operations in the same order as
+// with one thread, so the result does not depend on the thread count.
 bool invert(std::vector<double>& A, int n) {
-  std::vector<int> piv(n);
   std::vector<double> I((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
   double amax = 0;
   for (double v : A) amax = std::max(amax, std::fabs(v));
-  for (int c = 0; c < n; ++c) {
+  // pivot search, row swap and scaling of pivot row c; false if singular
+  auto pivot = [&](int c) {
     int p = c;
     for (int r = c + 1; r < n; ++r)
       if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)p * n + c])) p = r;
@@ -111,15 +134,49 @@ bool invert(std::vector<double>& A, int n) {
       A[(size_t)c * n + k] *= d;
       I[(size_t)c * n + k] *= d;
     }
-    for (int r = 0; r < n; ++r) {
+    return true;
+  };
+  // elimination of column c from rows [r0, r1) other than c
+  auto eliminate = [&](int c, int r0, int r1) {
+    const double* ac = &A[(size_t)c * n];
+    const double* ic = &I[(size_t)c * n];
+    for (int r = r0; r < r1; ++r) {
       if (r == c) continue;
-      double l = A[(size_t)r * n + c];
+      double* ar = &A[(size_t)r * n];
+      double* ir = &I[(size_t)r * n];
+      const double l = ar[c];
       if (l == 0.0) continue;
       for (int k = 0; k < n; ++k) {
-        A[(size_t)r * n + k] -= l * A[(size_t)c * n + k];
-        I[(size_t)r * n + k] -= l * I[(size_t)c * n + k];
+        ar[k] -= l * ac[k];
+        ir[k] -= l * ic[k];
       }
     }
+  };
+  unsigned T = 1;
+  if (n >= 512) T = std::max(1u, std::min({std::thread::hardware_concurrency(), 16u, (unsigned)(n / 128)}));
+  if (T == 1) {
+    for (int c = 0; c < n; ++c) {
+      if (!pivot(c)) return false;
+      eliminate(c, 0, n);
+    }
+  } else {
+    HostBarrier bar(T);
+    bool singular = false;
+    auto work = [&](unsigned t) {
+      const int r0 = (int)((int64_t)n * t / T), r1 = (int)((int64_t)n * (t + 1) / T);
+      for (int c = 0; c < n; ++c) {
+        if (t == 0) singular = !pivot(c);
+        bar.wait();                      // pivot row ready (or the matrix is singular)
+        if (singular) return;
+        eliminate(c, r0, r1);
+        bar.wait();                      // column c eliminated everywhere
+      }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < T; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+    if (singular) return false;
   }
   A.swap(I);
   return true;
