@@ -71,9 +71,9 @@ def _args():
                     help="requests in the serving measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0,
                     help="mean arrival rate of the serving measurement, requests per second")
-    ap.add_argument("--config4", type=int, default=16,
+    ap.add_argument("--random-domains", type=int, default=16,
                     help="problems of the batch-workload measurement (0: skip)")
-    ap.add_argument("--config3", type=int, nargs="*", default=[2048, 4096],
+    ap.add_argument("--ellipse-union", type=int, nargs="*", default=[2048, 4096],
                     help="grids of the ellipse-union measurement (none: skip)")
     ap.add_argument("--hbm-n", type=int, default=4096,
                     help="grid of the HBM-bound sweep measurement (0: skip)")
@@ -380,8 +380,8 @@ def run_ours(a):
 
     serving = run_serving(a, dev) if a.serve > 0 else None
     roof_hbm = hbm_sweep(a, dev, peak, src) if a.hbm_n > 0 else None
-    config3 = run_config3(a, dev) if a.config3 else None
-    config4 = run_config4(a, dev) if a.config4 > 0 else None
+    ellipse = run_ellipse_union(a, dev) if a.ellipse_union else None
+    random_domains = run_random_domains(a, dev) if a.random_domains > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -409,8 +409,8 @@ def run_ours(a):
         "max_error_vs_exact": err,
         "batch": batch,
         "serving": serving,
-        "config3": config3,
-        "config4": config4,
+        "ellipse_union": ellipse,
+        "random_domains": random_domains,
         "fp64_solve": {"ms": fp64_ms, "dof_per_s": dof / (fp64_ms / 1e3), "cycles": r64.cycles,
                        "max_error_vs_exact": err64},
         "wall_s_timed": wall,
@@ -453,7 +453,7 @@ def hbm_sweep(a, dev, peak, src):
                     "the launch latency"}
 
 
-def run_config3(a, dev):
+def run_ellipse_union(a, dev):
     """The ellipse-union workload at 2048^2 and 4096^2: FP32 cycles in FP64
     refinement against the plain FP64 solve, both to 1e-10 relative residual
     (the accuracy floor at these sizes: the max-norm error against the exact
@@ -467,7 +467,7 @@ def run_config3(a, dev):
     P = W.problem_ellipses(0)
     out = {"workload": "unit square minus ellipse union seed 0, Robin (1, 0.5), (a,b,c)=(1.5,-0.8,1), "
                        "u = sin(3x) exp(y), tol 1e-10"}
-    for n in a.config3:
+    for n in a.ellipse_union:
         row = {}
         for prec, name in ((1, "mixed"), (0, "fp64")):
             t = time.perf_counter()
@@ -502,7 +502,7 @@ def run_config3(a, dev):
     return out
 
 
-def run_config4(a, dev):
+def run_random_domains(a, dev):
     """Independent problems of the batch workload (random domains, operators,
     conditions and right-hand sides, N log-uniform in 64..1024), FP32 cycles
     in FP64 refinement to 1e-10: solved one at a time, then all at once with
@@ -520,7 +520,7 @@ def run_config4(a, dev):
     from paper_2601_02975_gb300 import workloads as W
     hs, fs, gs, dofs, sizes, skipped, probs = [], [], [], [], [], [], []
     t = time.perf_counter()
-    for k in range(a.config4):
+    for k in range(a.random_domains):
         P, n = W.problem_batch(k)
         try:
             H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
