@@ -191,3 +191,18 @@ def test_large_block_inverse_is_exact(lib):
     assert H.info.n_block > 2000
     assert H.info.block_error < 1e-14, H.info.block_error
     H.close()
+
+
+def test_default_options_match_the_header(lib):
+    """cc_default_options fills the defaults that include/ccmg.h documents, read
+    back through the binding's copy of the struct (a layout mismatch between
+    the two would show as wrong values here)."""
+    from paper_2601_02975_gb300 import default_options
+    o = default_options()
+    want = {"eps": 0.1, "nu1": 3, "nu2": 3, "omega": 0.5, "cycle": 1, "min_coarse_n": 4,
+            "precision": 0, "max_cycles": 100, "use_graphs": 1, "host_only": 0, "fmg_cycle": 1,
+            "w_depth": 0, "serve_slots": 4, "cache": 0, "hole_cells": 2.0, "krylov": 0}
+    got = {k: getattr(o, k) for k in want}
+    assert got == want, got
+    o = default_options(krylov=7, hole_cells=3.5)
+    assert (o.krylov, o.hole_cells, o.cache) == (7, 3.5, 0)
