@@ -324,7 +324,10 @@ def run_ours(a):
                         "launches_per_solve": launches / 2, "ms_per_solve": tot_ms / 2,
                         "bytes_per_launch": bytes_per,
                         "note": "working set L2-resident within a solve (a level of 1024^2 "
-                                "in FP32 is 12 MB)"}
+                                "in FP32 is 12 MB); ms_per_solve sums event intervals of a "
+                                "solve with timing events in its graph, which serialise the "
+                                "launches, so each interval holds the kernel's launch latency "
+                                "and the sum exceeds the kernel's share of an untimed solve"}
     dom = max(roofs, key=lambda w: roofs[w]["ms_per_solve"])
     roof = roofs[dom]
     roof_other = roofs[3 - dom]
