@@ -39,7 +39,8 @@ def _host(P, n, **kw):
 
 
 @pytest.mark.parametrize("name,n", [("disk", 32), ("disk", 64), ("ellipses0", 64),
-                                    ("ellipses3", 96), ("box_cross", 24), ("four_disks_N", 64)])
+                                    ("ellipses3", 96), ("box_cross", 24), ("four_disks_N", 64),
+                                    ("ellipses0", 256)])
 def test_setup_tables_match_oracle(lib, name, n):
     if name == "disk":
         P = W.problem_disk()
