@@ -207,3 +207,26 @@ def test_default_options_match_the_header(lib):
     assert got == want, got
     o = default_options(krylov=7, hole_cells=3.5)
     assert (o.krylov, o.hole_cells, o.cache) == (7, 3.5, 0)
+
+
+@pytest.mark.parametrize("name,n,mc", [("disk", 128, 16), ("four_disks_D", 128, 16)])
+def test_coarse_level_tables_match_oracle(lib, name, n, mc):
+    """Every level of the hierarchy (Eq. 5.9: each coarse level discretised
+    on its own grid) has the same cell kinds, lattices and PLG coefficients
+    in the library and in the oracle, and both stop coarsening at the same
+    level."""
+    from oracle import multigrid as M
+    P = W.problem_disk() if name == "disk" else W.problem_four_disks(W.DIRICHLET)
+    H = _host(P, n, min_coarse_n=mc)
+    O = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=mc)
+    assert H.info.n_levels == O.nl
+    for l, d in enumerate(O.levels):
+        kind, lat, beta = H.level_tables(l)
+        np.testing.assert_array_equal(kind, d.kind)
+        plg = sorted(d.lattices)
+        assert len(plg) == len(lat), l
+        for r, k in enumerate(plg):
+            np.testing.assert_array_equal(lat[r], d.lattices[k])
+            want = np.array(list(d.betas[k]))
+            assert np.abs(beta[r, :15] - want).max() < 1e-11 * np.abs(want).max(), (l, k)
+    H.close()
