@@ -209,14 +209,22 @@ def test_default_options_match_the_header(lib):
     assert (o.krylov, o.hole_cells, o.cache) == (7, 3.5, 0)
 
 
-@pytest.mark.parametrize("name,n,mc", [("disk", 128, 16), ("four_disks_D", 128, 16)])
+@pytest.mark.parametrize("name,n,mc", [("disk", 128, 16), ("four_disks_D", 128, 16),
+                                       ("batch8", 256, 32)])
 def test_coarse_level_tables_match_oracle(lib, name, n, mc):
     """Every level of the hierarchy (Eq. 5.9: each coarse level discretised
     on its own grid) has the same cell kinds, lattices and PLG coefficients
     in the library and in the oracle, and both stop coarsening at the same
-    level."""
+    level.  Problem 8 of the batch workload is the one whose coarsest level
+    has PLG rows with a positive diagonal: both sides build the same rows."""
     from oracle import multigrid as M
-    P = W.problem_disk() if name == "disk" else W.problem_four_disks(W.DIRICHLET)
+    if name == "disk":
+        P = W.problem_disk()
+    elif name == "four_disks_D":
+        P = W.problem_four_disks(W.DIRICHLET)
+    else:
+        P, n2 = W.problem_batch(8)
+        assert n2 == n
     H = _host(P, n, min_coarse_n=mc)
     O = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=mc)
     assert H.info.n_levels == O.nl
