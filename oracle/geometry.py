@@ -482,7 +482,8 @@ def _wall_nodes(lev: Level, i: int, j: int) -> list:
 
 def _merge_small(lev: Level) -> None:
     """Alg. 1, merging step: merge every cell of volume < eps h^2 into the face
-    neighbour that brings the merged volume closest to h^2."""
+    neighbour that brings the merged volume closest to h^2 (near-ties to the
+    first neighbour in the order -x, +x, -y, +y)."""
     n, h = lev.n, lev.h
     h2 = h * h
 
@@ -508,7 +509,13 @@ def _merge_small(lev: Level) -> None:
                 nbrs.append(t)
         if not nbrs:
             raise GeometryError(f"small cell ({i},{j}) has no neighbour to merge into")
-        best = min(nbrs, key=lambda t: abs(lev.vol.flat[t] + lev.vol[j, i] - h2))
+        # the neighbour that brings the merged volume closest to h^2; scores
+        # within 1e-9 h^2 of the smallest are ties (they differ by rounding
+        # only, e.g. the mirror cells on a diagonal of a disk) and go to the
+        # first neighbour in the order -x, +x, -y, +y
+        score = [abs(lev.vol.flat[t] + lev.vol[j, i] - h2) for t in nbrs]
+        smin = min(score)
+        best = next(t for t, sc in zip(nbrs, score) if sc <= smin + 1e-9 * h2)
         bj, bi = divmod(best, n)
         # merge: volumes, moments about the target's centre, boundary pieces
         mk = lev.moments(k)

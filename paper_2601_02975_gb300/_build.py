@@ -52,11 +52,14 @@ def build(verbose: bool = False, force: bool = False) -> str:
     for name in ("geom.cpp", "disc.cpp"):
         obj = os.path.join(BUILD, name + ".o")
         objs.append(obj)
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-Wno-unused-variable",
-                     "-c", os.path.join(CSRC, name), "-o", obj] + inc)
+        # no contraction of a * b + c into one rounding: the host setup then
+        # gives the same bits on x86-64 and on aarch64 (where gcc fuses by default)
+        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall",
+                     "-Wno-unused-variable", "-c", os.path.join(CSRC, name), "-o", obj] + inc)
     obj = os.path.join(BUILD, "capi.cu.o")
     objs.append(obj)
     jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
+                 "-Xcompiler", "-ffp-contract=off",
                  "-Xptxas", "-v" if verbose else "-O3",
                  "-c", os.path.join(CSRC, "capi.cu"), "-o", obj] + inc)
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:

@@ -14,8 +14,9 @@
 // The merging step of Alg. 1 is applied once in row-major order (y index outer) with
 // the current volumes; the merge target is a present neighbour reached
 // through a shared face piece of positive length (following the chain of
-// earlier merges), minimising |vol + vol' - h^2|, ties to the first of the
-// neighbours in the order -x, +x, -y, +y.  A level whose cut cells have more
+// earlier merges), minimising |vol + vol' - h^2|, ties (scores within
+// 1e-9 h^2 of the smallest) to the first of the neighbours in the order
+// -x, +x, -y, +y.  A level whose cut cells have more
 // than one connected component violates the precondition of Alg. 1 and is
 // marked unresolved.
 #include <algorithm>
@@ -449,12 +450,18 @@ LevelGeom build_geometry(const Problem& P, int n) {
       if (t != k && std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
     }
     if (cand.empty()) throw SetupError(2, "a small cut cell has no neighbour to merge into");
-    int best = cand[0];
-    double bv = std::fabs(G.vol[best] + G.vol[k] - h2);
-    for (size_t q = 1; q < cand.size(); ++q) {
-      double v = std::fabs(G.vol[cand[q]] + G.vol[k] - h2);
-      if (v < bv) { bv = v; best = cand[q]; }
+    // scores within 1e-9 h^2 of the smallest are ties (they differ by
+    // rounding only, e.g. the mirror cells on a diagonal of a disk): the
+    // first such neighbour wins, so the choice does not depend on rounding
+    std::vector<double> score(cand.size());
+    double smin = 0;
+    for (size_t q = 0; q < cand.size(); ++q) {
+      score[q] = std::fabs(G.vol[cand[q]] + G.vol[k] - h2);
+      smin = q == 0 ? score[q] : std::min(smin, score[q]);
     }
+    int best = cand[0];
+    for (size_t q = 0; q < cand.size(); ++q)
+      if (score[q] <= smin + 1e-9 * h2) { best = cand[q]; break; }
     int bi = best % n, bj = best / n;
     double mk[kMoments], mt[kMoments], sh[kMoments];
     G.moments(k, mk);
