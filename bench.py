@@ -315,7 +315,7 @@ def run_ours(a):
         for _ in range(2):
             flush.fill_(3.0)
             step()
-        launches, tot_ms, bytes_per = H.kernel_timing_read()
+        launches, tot_ms, bytes_per, moved_per = H.kernel_timing_read()
         H.kernel_timing(0)
         achieved = bytes_per / (tot_ms / launches) / 1e6 if launches else None   # GB/s
         roofs[which] = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
@@ -444,7 +444,7 @@ def hbm_sweep(a, dev, peak, src):
     H.kernel_timing(1)
     u.zero_()
     H.solve(ft, gt, u, 1e-300)
-    launches, tot_ms, bytes_per = H.kernel_timing_read()
+    launches, tot_ms, bytes_per, moved_per = H.kernel_timing_read()
     H.kernel_timing(0)
     H.close()
     achieved = bytes_per / (tot_ms / launches) / 1e6

@@ -137,6 +137,10 @@ typedef struct {
   double block_error;  /* largest normwise backward error of the exact block solves, measured
                           at setup on a fixed vector: |A x - t|_inf / (|A|_inf |x|_inf) */
   double bottom_error; /* the same for the coarsest-level solve */
+  int block_m[32];     /* cells of each level's exactly solved block (Eq. 5.8) */
+  int block_chunks[32];/* how that block is solved: 0 with its dense inverse in one launch
+                          (up to 1024 cells), else the number of chunks of the two-launch
+                          chunked form (one CTA per chunk) */
 } cc_info;
 
 /* Outcome of a solve. */
@@ -318,8 +322,10 @@ cc_status cc_restrict_residual(cc_handle h, int level, const double* d_u, const 
 /* u += interpolation (Eq. 5.11) of e_c from level l+1 to level l. */
 cc_status cc_prolong_add(cc_handle h, int level, const double* d_ec, double* d_u,
                          cc_stream stream);
-/* One cycle of Alg. 2 (or its W form, as set up) on the finest level in FP64,
- * u in place. */
+/* One cycle of Alg. 2 (or its W form, as set up) on the finest level, u in
+ * place, in the handle's cycle precision: FP64, or with CC_PREC_MIXED the
+ * FP32 cycle of the mixed mode (u and b rounded to FP32 on entry, the
+ * result widened to FP64; empty cells come back as the cycle left them). */
 cc_status cc_cycle(cc_handle h, double* d_u, const double* d_b, cc_stream stream);
 
 /*
@@ -331,9 +337,10 @@ cc_status cc_cycle(cc_handle h, double* d_u, const double* d_b, cc_stream stream
  * owned by another allocator.  The paper has no counterpart: this only
  * changes where the sweep keeps its temporaries.
  *
- * The call allocates nothing and writes none of the handle's level buffers.
- * The Jacobi output and the exact block solve's temporaries (gathered
- * right-hand sides, chunk and interface solutions) live in one file-scope
+ * The call allocates nothing and writes none of the handle's buffers.
+ * The Jacobi output and the chunked block solve's temporaries (the
+ * interface right-hand sides, the chunk interior solutions and the chunks'
+ * contributions to the interface right-hand sides) live in one file-scope
  * device array of CC_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB) in the
  * library.  Every GPU that loads the library's device code holds that array
  * until the process exits.  The first call on a device looks up the
@@ -351,9 +358,12 @@ cc_status cc_cycle(cc_handle h, double* d_u, const double* d_b, cc_stream stream
  *   d_b     N_l^2 FP64 right-hand side
  * Errors: CC_ERR_ARG for a bad argument, a device other than the handle's,
  * or a level that needs more than CC_NOALLOC_SCRATCH_DOUBLES doubles
- * (N_l^2 plus twice the block size plus the interface count;
- * cc_last_error_string() gives the numbers).  CC_ERR_CUDA if the
- * address lookup or a launch fails.
+ * (N_l^2, plus for a chunked block its size, its interface count and its
+ * contribution count; cc_last_error_string() gives the numbers).
+ * CC_ERR_CUDA if the address lookup or a launch fails.  The call cannot
+ * report a bounded wait that expires inside its kernels (a shared-memory
+ * copy that never completes, which the library does not expect): such a
+ * kernel gives up after about 0.1 s and leaves its rows of d_u unwritten.
  */
 #define CC_NOALLOC_SCRATCH_DOUBLES (1 << 20)
 cc_status cc_smooth_noalloc(cc_handle h, int level, double* d_u, const double* d_b,
@@ -372,24 +382,33 @@ cc_status cc_level_tables(cc_handle h, int level, uint8_t* h_kind, int* h_lattic
                           double* h_beta, int* n_plg);
 
 /* Kernels that cc_kernel_timing can time. */
-enum { CC_TIME_OFF = 0, CC_TIME_FINE_SWEEP = 1, CC_TIME_BLOCK_DENSE = 2 };
+enum { CC_TIME_OFF = 0, CC_TIME_FINE_SWEEP = 1, CC_TIME_BLOCK = 2 };
 
 /*
  * cc_kernel_timing: with which = CC_TIME_FINE_SWEEP the library records CUDA
  * events around every launch of the finest-level Jacobi sweep kernel (Eq.
- * 5.7); with CC_TIME_BLOCK_DENSE around every one-launch dense block solve
- * (Eq. 5.8, any level); CC_TIME_OFF stops.  The
- * events are recorded on the solve's stream, inside its CUDA graph, so host
- * launch gaps are not measured, but each interval includes the launch latency
- * of the kernel it brackets.  cc_kernel_timing_read returns the launch count,
- * the total milliseconds and the average algorithmic bytes of one launch
- * (sweep: reads of u and b plus the write of u; block solve: the inverse, the
- * gather terms, b and the writes; at the cycle's precision).  Enabling resets
- * the counters.  Errors: CC_ERR_ARG for an unknown kernel.
+ * 5.7); with CC_TIME_BLOCK around every exact block solve (Eq. 5.8, any
+ * level: its one launch, or its two chunked launches together);
+ * CC_TIME_OFF stops.  The events are recorded on the solve's stream, inside
+ * its CUDA graph, so host launch gaps are not measured, but each interval
+ * includes the launch latency of the kernels it brackets.
+ * cc_kernel_timing_read returns the number of timed intervals, their total
+ * milliseconds and, per interval, the average algorithmic bytes and the
+ * average bytes the library's kernels actually move (either pointer may be
+ * NULL), at the cycle's precision w:
+ *   sweep        algorithmic = moved = 3 w per cell (u and b read, u written);
+ *   block solve  algorithmic: the method's own price of the solve, the gather
+ *                terms (column, coefficient, gathered value), b and the cell
+ *                of every row, banded LU factors of 2 bw + 1 values per row
+ *                (Def. 5.3, bw the block's bandwidth in curve order) and the
+ *                writes; moved: the same gather and writes plus the dense
+ *                inverse, or every chunk's two stages and the interface
+ *                vectors.
+ * Enabling resets the counters.  Errors: CC_ERR_ARG for an unknown kernel.
  */
 cc_status cc_kernel_timing(cc_handle h, int which);
 cc_status cc_kernel_timing_read(cc_handle h, int64_t* launches, double* total_ms,
-                                double* bytes_per_launch);
+                                double* bytes_per_launch, double* moved_bytes_per_launch);
 
 #ifdef __cplusplus
 }

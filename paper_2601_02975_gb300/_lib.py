@@ -47,7 +47,8 @@ class cc_info(C.Structure):
     _fields_ = [("n", C.c_int), ("n_levels", C.c_int), ("n_dof", C.c_int64), ("n_bd", C.c_int),
                 ("n_g", C.c_int), ("n_plg", C.c_int), ("n_block", C.c_int),
                 ("device_bytes", C.c_int64), ("level_n", C.c_int * 32),
-                ("block_error", C.c_double), ("bottom_error", C.c_double)]
+                ("block_error", C.c_double), ("bottom_error", C.c_double),
+                ("block_m", C.c_int * 32), ("block_chunks", C.c_int * 32)]
 
 
 class cc_result(C.Structure):
@@ -98,7 +99,7 @@ _SIGS = {
     "cc_level_tables": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(C.c_int)]),
     "cc_kernel_timing": (C.c_int, [_P, C.c_int]),
     "cc_kernel_timing_read": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_double),
-                                        C.POINTER(C.c_double)]),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 
@@ -313,10 +314,12 @@ class Hierarchy:
         _check(lib().cc_kernel_timing(self.h, int(which)), "cc_kernel_timing")
 
     def kernel_timing_read(self):
-        n, ms, by = C.c_int64(), C.c_double(), C.c_double()
-        _check(lib().cc_kernel_timing_read(self.h, C.byref(n), C.byref(ms), C.byref(by)),
-               "cc_kernel_timing_read")
-        return n.value, ms.value, by.value
+        """(timed intervals, total ms, algorithmic bytes per interval, bytes the
+        kernels move per interval)"""
+        n, ms, by, mv = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+        _check(lib().cc_kernel_timing_read(self.h, C.byref(n), C.byref(ms), C.byref(by),
+                                           C.byref(mv)), "cc_kernel_timing_read")
+        return n.value, ms.value, by.value, mv.value
 
 
 def solve_batch(hs, fs, gs, us, tols, streams=None):

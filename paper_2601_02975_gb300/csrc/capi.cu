@@ -193,7 +193,7 @@ std::vector<double> to_cm(const std::vector<double>& A, int rows, int cols) {
 // ---------------------------------------------------------------------------
 // exact block solve plan (host)
 struct BlockPlan {
-  int m = 0, nch = 0, ns = 0;
+  int m = 0;
   std::vector<int> cell;
   std::vector<int64_t> gptr{0};
   std::vector<int> gcol;
@@ -203,75 +203,82 @@ struct BlockPlan {
   std::vector<double> ell_val;
   std::vector<int> tail_ptr{0}, tail_col;   // terms beyond the width
   std::vector<double> tail_val;
-  int sk = 0;                          // ELL width of A_S,I
-  std::vector<int> asi_ell_col;        // [sk * ns]
-  std::vector<double> asi_ell_val;
-  std::vector<int> cstart, iptr{0}, ipos;
-  std::vector<int64_t> aoff;
-  std::vector<double> ainv;
-  std::vector<int> spos;
-  std::vector<int64_t> asi_ptr{0};
-  std::vector<int> asi_col;
-  std::vector<double> asi_val;
-  std::vector<double> sinv;
-  std::vector<int> wptr{0}, widx;
-  std::vector<int64_t> woff;
-  std::vector<double> wmat;
-  size_t smem_chunk = 0, smem_back = 0;
-  double error = 0;   // backward error of the scheme on a fixed vector (FP64, host)
-  bool dense = false; // one chunk holding the whole block (its inverse in ainv)
   std::vector<int> alias_ptr{0}, alias_cell;
+  double error = 0;    // backward error of the solve on a fixed vector (FP64, host)
+  int band = 0;        // bandwidth of the block in curve order (couplings <= 64 apart)
+  // dense form (m <= kDenseMax): the inverse, row-major
+  bool dense = false;
+  std::vector<double> ainv;
+  // chunked form
+  int nch = 0, ns = 0, s = 0, nslots = 0;
+  std::vector<ChunkDev> ch;
+  std::vector<int> slot, sidx, ipos, vslot, wrow, orow, opos, qptr, spos;
+  std::vector<double> blob;
+  ChunkSmem sm{};      // shared-memory layout at w = 1 element (st1, st2 filled per precision)
+  int b1max = 0, b2max = 0;
 };
 
-const int kDenseDirect = 1024;  // blocks up to this size: dense inverse by Gauss-Jordan
-const int kBlockOneLaunch = 1024;  // dense blocks up to this size: gather and solve in one launch
-const int kDenseMax = 2560;     // up to this size: dense inverse from the chunked plan
+const int kDenseMax = 1024;     // blocks up to this size: dense inverse, one launch
+// dynamic shared memory of one CTA that the chunked launches may use (the
+// opt-in limit is 227 KiB per CTA, static shared memory included)
+const int kSmemBudget = 226 * 1024;
 
-// Apply the chunked scheme to t in FP64 exactly as the device does.
-void apply_plan(const BlockPlan& B, const std::vector<double>& t, std::vector<double>& x) {
+// The chunked solve applied to t in FP64, as the device does it.
+void apply_chunked(const BlockPlan& B, const std::vector<double>& t, std::vector<double>& x) {
   const int m = B.m;
-  std::vector<double> z(m, 0.0), xs(B.ns, 0.0);
+  std::vector<double> z(m, 0.0), q(std::max(1, B.nslots), 0.0), ys(B.ns, 0.0);
   x.assign(m, 0.0);
-  for (int c = 0; c < B.nch; ++c) {
-    const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
-    const double* A = &B.ainv[B.aoff[c]];
-    for (int r = 0; r < ni; ++r) {
+  for (const ChunkDev& C : B.ch) {
+    std::vector<double> tl(C.p1 - C.p0);
+    for (int p = C.p0; p < C.p1; ++p) tl[B.slot[p]] = t[p];
+    const double* M = &B.blob[C.b1];
+    const int ld = C.ni + C.nv;
+    for (int r = 0; r < ld; ++r) {
       double acc = 0;
-      for (int k = 0; k < ni; ++k) acc += A[(size_t)k * ni + r] * t[B.ipos[i0 + k]];
-      z[B.ipos[i0 + r]] = acc;
+      for (int k = 0; k < C.ni; ++k) acc += M[(size_t)k * ld + r] * tl[k];
+      if (r < C.ni) z[B.ipos[C.ipos_off + r]] = acc;
+      else q[B.vslot[C.v_off + r - C.ni]] = acc;
     }
   }
-  std::vector<double> ts(B.ns);
-  for (int q = 0; q < B.ns; ++q) {
-    double acc = t[B.spos[q]];
-    for (int64_t e = B.asi_ptr[q]; e < B.asi_ptr[q + 1]; ++e) acc -= B.asi_val[e] * z[B.asi_col[e]];
-    ts[q] = acc;
+  for (int k = 0; k < B.ns; ++k) {
+    double acc = t[B.spos[k]];
+    for (int j = B.qptr[k]; j < B.qptr[k + 1]; ++j) acc -= q[j];
+    ys[k] = acc;
   }
-  for (int r = 0; r < B.ns; ++r) {
-    double acc = 0;
-    for (int k = 0; k < B.ns; ++k) acc += B.sinv[(size_t)k * B.ns + r] * ts[k];
-    xs[r] = acc;
-    x[B.spos[r]] = acc;
-  }
-  for (int c = 0; c < B.nch; ++c) {
-    const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
-    const int w0 = B.wptr[c], nw = B.wptr[c + 1] - w0;
-    const double* W = &B.wmat[B.woff[c]];
-    for (int r = 0; r < ni; ++r) {
+  for (const ChunkDev& C : B.ch) {
+    const double* S = &B.blob[C.b2];
+    const double* W = S + (size_t)C.nr * B.ns;
+    std::vector<double> xr(C.nr, 0.0), xw(C.nw);
+    for (int r = 0; r < C.nr; ++r)
+      for (int k = 0; k < B.ns; ++k) xr[r] += S[(size_t)r * B.ns + k] * ys[k];
+    for (int k = 0; k < C.nw; ++k) xw[k] = xr[B.wrow[C.w_off + k]];
+    for (int r = 0; r < C.ni; ++r) {
       double acc = 0;
-      for (int k = 0; k < nw; ++k) acc += W[(size_t)k * ni + r] * xs[B.widx[w0 + k]];
-      x[B.ipos[i0 + r]] = z[B.ipos[i0 + r]] - acc;
+      for (int k = 0; k < C.nw; ++k) acc += W[(size_t)k * C.ni + r] * xw[k];
+      const int pos = B.ipos[C.ipos_off + r];
+      x[pos] = z[pos] - acc;
     }
+    for (int k = 0; k < C.nown; ++k) x[B.opos[C.o_off + k]] = xr[B.orow[C.o_off + k]];
   }
 }
 
-// Apply the scheme to a fixed vector and return the normwise backward error
+void apply_dense(const BlockPlan& B, const std::vector<double>& t, std::vector<double>& x) {
+  x.assign(B.m, 0.0);
+  for (int r = 0; r < B.m; ++r) {
+    double acc = 0;
+    for (int k = 0; k < B.m; ++k) acc += B.ainv[(size_t)r * B.m + k] * t[k];
+    x[r] = acc;
+  }
+}
+
+// Apply the solve to a fixed vector and return the normwise backward error
 // |A x - t|_inf / (|A|_inf |x|_inf).
 double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, double>>& Abb) {
   const int m = B.m;
   std::vector<double> t(m), x;
   for (int p = 0; p < m; ++p) t[p] = std::sin(1.0 + 0.7 * p) + 0.25 * std::cos(3.1 * p);
-  apply_plan(B, t, x);
+  if (B.dense) apply_dense(B, t, x);
+  else apply_chunked(B, t, x);
   double rmax = 0, amax = 0, xmax = 0;
   for (int p = 0; p < m; ++p) {
     double acc = -t[p], arow = 0;
@@ -283,16 +290,15 @@ double block_plan_error(const BlockPlan& B, const std::vector<std::map<int, doub
   return rmax / (amax * xmax);
 }
 
-// padded term-major (ELL) copies of the gather rows and of A_S,I
+// padded term-major (ELL) copy of the gather rows
 void make_ell(BlockPlan& B) {
   const int m = B.m;
-  // width: the longest PLG row (at most 15 terms) rounded up; the few
-  // longer rows (box-corner rows with ghost expansions) spill into a tail.
-  // k_block_gather holds a row's terms in registers, kGatherMax of them.
-  const int kMaxWidth = kGatherMax;
+  // width: the longest PLG row (at most 15 terms); the few longer rows
+  // (box-corner rows with ghost expansions) spill into a tail.  The chunked
+  // launch holds a row's terms in registers, kGatherMax of them.
   B.gk = 0;
   for (int p = 0; p < m; ++p) B.gk = std::max<int>(B.gk, (int)(B.gptr[p + 1] - B.gptr[p]));
-  B.gk = std::min(B.gk, kMaxWidth);
+  B.gk = std::min(B.gk, kGatherMax);
   B.ell_col.assign((size_t)B.gk * m, 0);
   B.ell_val.assign((size_t)B.gk * m, 0.0);
   B.tail_ptr.assign(1, 0);
@@ -312,32 +318,252 @@ void make_ell(BlockPlan& B) {
     for (; q < B.gk; ++q) B.ell_col[(size_t)q * m + p] = B.cell[p];   // value 0
     B.tail_ptr.push_back((int)B.tail_col.size());
   }
-  const int ns = B.ns;
-  B.sk = 0;
-  for (int i = 0; i < ns; ++i) B.sk = std::max<int>(B.sk, (int)(B.asi_ptr[i + 1] - B.asi_ptr[i]));
-  B.asi_ell_col.assign((size_t)B.sk * ns, 0);
-  B.asi_ell_val.assign((size_t)B.sk * ns, 0.0);
-  for (int i = 0; i < ns; ++i) {
-    int q = 0;
-    for (int64_t e = B.asi_ptr[i]; e < B.asi_ptr[i + 1]; ++e, ++q) {
-      B.asi_ell_col[(size_t)q * ns + i] = B.asi_col[e];
-      B.asi_ell_val[(size_t)q * ns + i] = B.asi_val[e];
+}
+
+inline int round4(int v) { return (v + 3) & ~3; }
+
+// Structure of the chunked solve for chunks of s rows (no numbers): interface
+// rows, interior lists, the interface rows each chunk reads and is read by.
+struct ChunkShape {
+  int s = 0, nch = 0, ns = 0;
+  std::vector<int> sidx, spos;
+  std::vector<std::vector<int>> I, own, sout, sin, held;   // per chunk
+  double cost = 0;   // largest per-CTA stage bytes (FP32), doubled beyond one wave
+  bool ok = true;
+};
+
+ChunkShape chunk_shape(const std::vector<std::map<int, double>>& Abb, int s) {
+  ChunkShape S;
+  const int m = (int)Abb.size();
+  S.s = s;
+  S.nch = (m + s - 1) / s;
+  std::vector<char> iface(m, 0);
+  for (int r = 0; r < m; ++r)
+    for (auto& kv : Abb[r]) {
+      const int c = kv.first, cr = r / s, cc = c / s;
+      if (cr != cc) iface[cr < cc ? r : c] = 1;
+    }
+  S.sidx.assign(m, -1);
+  for (int p = 0; p < m; ++p)
+    if (iface[p]) { S.sidx[p] = (int)S.spos.size(); S.spos.push_back(p); }
+  S.ns = (int)S.spos.size();
+  S.I.resize(S.nch);
+  S.own.resize(S.nch);
+  S.sout.resize(S.nch);
+  S.sin.resize(S.nch);
+  S.held.resize(S.nch);
+  std::vector<std::vector<int>> readers(S.ns);   // interior chunks an interface row reads
+  for (int p = 0; p < m; ++p) {
+    if (iface[p]) {
+      S.own[p / s].push_back(S.sidx[p]);
+      for (auto& kv : Abb[p])
+        if (!iface[kv.first]) readers[S.sidx[p]].push_back(kv.first / s);
+    } else {
+      S.I[p / s].push_back(p);
     }
   }
+  for (int i = 0; i < S.ns; ++i) {
+    auto& v = readers[i];
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    for (int c : v) S.sin[c].push_back(i);
+  }
+  double worst = 0;
+  for (int c = 0; c < S.nch; ++c) {
+    std::vector<int> so;
+    for (int p : S.I[c])
+      for (auto& kv : Abb[p])
+        if (iface[kv.first]) so.push_back(S.sidx[kv.first]);
+    std::sort(so.begin(), so.end());
+    so.erase(std::unique(so.begin(), so.end()), so.end());
+    S.sout[c] = so;
+    std::vector<int> hd = so;
+    hd.insert(hd.end(), S.own[c].begin(), S.own[c].end());
+    std::sort(hd.begin(), hd.end());
+    hd.erase(std::unique(hd.begin(), hd.end()), hd.end());
+    S.held[c] = hd;
+    const double ni = (double)S.I[c].size(), nv = (double)S.sin[c].size();
+    // launch 1 forms up to 2 product rows per thread, launch 2 takes one
+    // interior row, one own interface row and one W_c column per thread
+    if (ni + nv > 32 * kRB || so.size() > (size_t)kChunkThreads) S.ok = false;
+    const double b1 = (ni + nv) * ni, b2 = (double)hd.size() * S.ns + ni * (double)so.size();
+    worst = std::max(worst, 4.0 * (b1 + b2));
+  }
+  S.cost = worst * (S.nch > 148 ? 2.0 : 1.0);
+  return S;
 }
 
-BlockPlan plan_block_impl(const LevelDisc& D);
+// Numbers of the chunked solve for shape S (FP64): chunk inverses, V_c, W_c,
+// the interface Schur complement and its inverse, laid out per chunk.
+void build_chunked(BlockPlan& B, const std::vector<std::map<int, double>>& Abb, const ChunkShape& S) {
+  const int m = B.m, ns = S.ns, nch = S.nch;
+  B.s = S.s;
+  B.nch = nch;
+  B.ns = ns;
+  B.spos = S.spos;
+  B.sidx = S.sidx;
+  B.slot.assign(m, 0);
+  B.ch.assign(nch, ChunkDev{});
+  B.ipos.clear();
+  B.vslot.clear();
+  B.wrow.clear();
+  B.orow.clear();
+  B.opos.clear();
+  B.blob.clear();
+  // q slots: the contributions to interface i, in chunk order
+  B.qptr.assign(ns + 1, 0);
+  for (int c = 0; c < nch; ++c)
+    for (int i : S.sin[c]) ++B.qptr[i + 1];
+  for (int i = 0; i < ns; ++i) B.qptr[i + 1] += B.qptr[i];
+  B.nslots = B.qptr[ns];
+  std::vector<int> qnext(B.qptr.begin(), B.qptr.end() - 1);
+  std::vector<double> Sm((size_t)ns * ns, 0.0);
+  for (int i = 0; i < ns; ++i)
+    for (auto& kv : Abb[S.spos[i]])
+      if (S.sidx[kv.first] >= 0) Sm[(size_t)i * ns + S.sidx[kv.first]] += kv.second;
+  // per chunk: inverse of the interior block, V_c and W_c (parallel over chunks)
+  std::vector<std::vector<double>> Ainv(nch), V(nch), W(nch);
+  std::atomic<int> next{0};
+  std::atomic<bool> singular{false};
+  auto work = [&]() {
+    for (int c = next++; c < nch; c = next++) {
+      const auto& Ic = S.I[c];
+      const int ni = (int)Ic.size(), nv = (int)S.sin[c].size(), nw = (int)S.sout[c].size();
+      std::unordered_map<int, int> lp;
+      for (int k = 0; k < ni; ++k) lp[Ic[k]] = k;
+      std::vector<double> A((size_t)ni * ni, 0.0);
+      for (int k = 0; k < ni; ++k)
+        for (auto& kv : Abb[Ic[k]]) {
+          auto it = lp.find(kv.first);
+          if (it != lp.end()) A[(size_t)k * ni + it->second] += kv.second;
+        }
+      if (ni && !invert(A, ni)) { singular = true; continue; }
+      // W_c = inv(A_cc) A_{c,S} on the columns sout[c]
+      std::unordered_map<int, int> wc;
+      for (int k = 0; k < nw; ++k) wc[S.sout[c][k]] = k;
+      std::vector<double> AcS((size_t)ni * nw, 0.0);
+      for (int k = 0; k < ni; ++k)
+        for (auto& kv : Abb[Ic[k]])
+          if (S.sidx[kv.first] >= 0) AcS[(size_t)k * nw + wc[S.sidx[kv.first]]] += kv.second;
+      std::vector<double> Wc((size_t)ni * nw, 0.0);
+      for (int r = 0; r < ni; ++r)
+        for (int k = 0; k < ni; ++k) {
+          const double a = A[(size_t)r * ni + k];
+          if (a == 0.0) continue;
+          for (int j = 0; j < nw; ++j) Wc[(size_t)r * nw + j] += a * AcS[(size_t)k * nw + j];
+        }
+      // V_c = A_{S,c} inv(A_cc) on the rows sin[c]
+      std::vector<double> Vc((size_t)nv * ni, 0.0);
+      for (int a = 0; a < nv; ++a)
+        for (auto& kv : Abb[S.spos[S.sin[c][a]]]) {
+          auto it = lp.find(kv.first);
+          if (it == lp.end()) continue;
+          const double v = kv.second;
+          const double* ar = &A[(size_t)it->second * ni];
+          for (int k = 0; k < ni; ++k) Vc[(size_t)a * ni + k] += v * ar[k];
+        }
+      Ainv[c].swap(A);
+      W[c].swap(Wc);
+      V[c].swap(Vc);
+    }
+  };
+  {
+    const unsigned T = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < T && (int)t < nch; ++t) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+  }
+  if (singular) throw SetupError(3, "singular interior block of the smoother");
+  // Schur complement: S -= A_{S,c} W_c, in chunk order
+  for (int c = 0; c < nch; ++c) {
+    const int ni = (int)S.I[c].size(), nw = (int)S.sout[c].size();
+    std::unordered_map<int, int> lp;
+    for (int k = 0; k < ni; ++k) lp[S.I[c][k]] = k;
+    for (int i : S.sin[c])
+      for (auto& kv : Abb[S.spos[i]]) {
+        auto it = lp.find(kv.first);
+        if (it == lp.end()) continue;
+        const double a = kv.second;
+        const double* wr = &W[c][(size_t)it->second * nw];
+        for (int j = 0; j < nw; ++j) Sm[(size_t)i * ns + S.sout[c][j]] -= a * wr[j];
+      }
+  }
+  if (ns && !invert(Sm, ns)) throw SetupError(3, "singular interface Schur complement");
+  // per-chunk tables and the two stages
+  for (int c = 0; c < nch; ++c) {
+    ChunkDev& C = B.ch[c];
+    const auto& Ic = S.I[c];
+    const int ni = (int)Ic.size(), nv = (int)S.sin[c].size(), nw = (int)S.sout[c].size();
+    const int nr = (int)S.held[c].size(), nown = (int)S.own[c].size();
+    C.p0 = c * S.s;
+    C.p1 = std::min(m, (c + 1) * S.s);
+    C.ni = ni; C.nv = nv; C.nr = nr; C.nw = nw; C.nown = nown;
+    C.ipos_off = (int)B.ipos.size();
+    C.v_off = (int)B.vslot.size();
+    C.w_off = (int)B.wrow.size();
+    C.o_off = (int)B.orow.size();
+    for (int k = 0; k < ni; ++k) { B.slot[Ic[k]] = k; B.ipos.push_back(Ic[k]); }
+    for (int k = 0; k < nown; ++k) B.slot[S.spos[S.own[c][k]]] = ni + k;
+    for (int i : S.sin[c]) B.vslot.push_back(qnext[i]++);
+    std::unordered_map<int, int> hidx;
+    for (int k = 0; k < nr; ++k) hidx[S.held[c][k]] = k;
+    for (int j : S.sout[c]) B.wrow.push_back(hidx[j]);
+    for (int i : S.own[c]) { B.orow.push_back(hidx[i]); B.opos.push_back(S.spos[i]); }
+    // stage 1: [inv(A_cc); V_c], column-major, ld = ni + nv
+    const int ld = ni + nv;
+    C.b1 = (long long)B.blob.size();
+    C.b1n = round4(ld * ni);
+    B.blob.resize(B.blob.size() + C.b1n, 0.0);
+    double* s1 = &B.blob[C.b1];
+    for (int k = 0; k < ni; ++k) {
+      for (int r = 0; r < ni; ++r) s1[(size_t)k * ld + r] = Ainv[c][(size_t)r * ni + k];
+      for (int a = 0; a < nv; ++a) s1[(size_t)k * ld + ni + a] = V[c][(size_t)a * ni + k];
+    }
+    // stage 2: the held rows of inv(S) (row-major, ld = ns), then W_c (column-major, ld = ni)
+    C.b2 = (long long)B.blob.size();
+    C.b2n = round4(nr * ns + ni * nw);
+    B.blob.resize(B.blob.size() + C.b2n, 0.0);
+    double* s2 = &B.blob[C.b2];
+    for (int r = 0; r < nr; ++r)
+      for (int k = 0; k < ns; ++k) s2[(size_t)r * ns + k] = Sm[(size_t)S.held[c][r] * ns + k];
+    double* w2 = s2 + (size_t)nr * ns;
+    for (int j = 0; j < nw; ++j)
+      for (int r = 0; r < ni; ++r) w2[(size_t)j * ni + r] = W[c][(size_t)r * nw + j];
+  }
+  ChunkSmem L{};
+  L.ns4 = round4(ns);
+  L.sl4 = round4(B.nslots);
+  B.b1max = B.b2max = 0;
+  for (const ChunkDev& C : B.ch) {
+    L.rows1 = std::max(L.rows1, C.ni + C.nv);
+    L.rows2 = std::max(L.rows2, C.nr);
+    L.nwmax = std::max(L.nwmax, C.nw);
+    L.nimax = std::max(L.nimax, C.ni);
+    B.b1max = std::max(B.b1max, C.b1n);
+    B.b2max = std::max(B.b2max, C.b2n);
+  }
+  L.rows1 = round4(L.rows1);
+  L.rows2 = round4(L.rows2);
+  L.nwmax = round4(L.nwmax);
+  L.nimax = round4(L.nimax);
+  B.sm = L;
+}
+
+// Shared-memory layout of the chunked launches at element size w: the
+// stages are staged when the launch's whole layout fits the budget.
+ChunkSmem chunk_smem(const BlockPlan& B, int w, int& stage1, int& stage2) {
+  ChunkSmem L = B.sm;
+  L.st1 = B.b1max;
+  stage1 = (size_t)L.p1_total() * w <= (size_t)kSmemBudget;
+  if (!stage1) L.st1 = 0;
+  L.st2 = B.b2max;
+  stage2 = L.p2_bytes(w) <= (size_t)kSmemBudget;
+  if (!stage2) L.st2 = 0;
+  return L;
+}
 
 BlockPlan plan_block(const LevelDisc& D) {
-  BlockPlan B = plan_block_impl(D);
-  if (B.m) {
-    if (B.dense) B.ainv = to_cm(B.ainv, B.m, B.m);   // column-major -> row-major (square)
-    make_ell(B);
-  }
-  return B;
-}
-
-BlockPlan plan_block_impl(const LevelDisc& D) {
   BlockPlan B;
   const int m = (int)D.block.size();
   B.m = m;
@@ -356,201 +582,46 @@ BlockPlan plan_block_impl(const LevelDisc& D) {
     }
     B.gptr.push_back((int64_t)B.gcol.size());
   }
-  // choose the chunk size with the least dense storage
-  auto build = [&](int s, bool commit, double& storage) {
-    int nch = (m + s - 1) / s;
-    std::vector<char> iface(m, 0);
-    if (nch > 1)
-      for (int r = 0; r < m; ++r)
-        for (auto& kv : Abb[r]) {
-          int c = kv.first;
-          int cr = r / s, cc = c / s;
-          if (cr == cc) continue;
-          iface[cr < cc ? r : c] = 1;
-        }
-    std::vector<int> S;
-    std::vector<int> sidx(m, -1);
+  for (int p = 0; p < m; ++p)
+    for (auto& kv : Abb[p])
+      if (std::abs(kv.first - p) <= 64) B.band = std::max(B.band, std::abs(kv.first - p));
+  make_ell(B);
+  if (m <= kDenseMax) {
+    // small blocks: the dense inverse of the whole block (Gauss-Jordan)
+    std::vector<double> A((size_t)m * m, 0.0);
     for (int p = 0; p < m; ++p)
-      if (iface[p]) { sidx[p] = (int)S.size(); S.push_back(p); }
-    const int ns = (int)S.size();
-    storage = (double)ns * ns;
-    std::vector<std::vector<int>> I(nch);
-    for (int p = 0; p < m; ++p)
-      if (!iface[p]) I[p / s].push_back(p);
-    std::vector<std::vector<int>> Sc(nch);
-    for (int c = 0; c < nch; ++c) {
-      std::vector<char> used(ns, 0);
-      for (int p : I[c])
-        for (auto& kv : Abb[p])
-          if (sidx[kv.first] >= 0) used[sidx[kv.first]] = 1;
-      for (int q = 0; q < ns; ++q)
-        if (used[q]) Sc[c].push_back(q);
-      storage += (double)I[c].size() * I[c].size() + (double)I[c].size() * Sc[c].size();
-    }
-    if (!commit) return true;
-    B.iptr.assign(1, 0);
-    B.ipos.clear();
-    B.aoff.clear();
-    B.ainv.clear();
-    B.asi_ptr.assign(1, 0);
-    B.asi_col.clear();
-    B.asi_val.clear();
-    B.wptr.assign(1, 0);
-    B.widx.clear();
-    B.woff.clear();
-    B.wmat.clear();
-    B.nch = nch;
-    B.ns = ns;
-    B.spos = S;
-    B.cstart.clear();
-    for (int c = 0; c <= nch; ++c) B.cstart.push_back(std::min(m, c * s));
-    std::vector<double> Sm((size_t)ns * ns, 0.0);
-    for (int q = 0; q < ns; ++q)
-      for (auto& kv : Abb[S[q]])
-        if (sidx[kv.first] >= 0) Sm[(size_t)q * ns + sidx[kv.first]] += kv.second;
-    for (int c = 0; c < nch; ++c) {
-      const auto& Ic = I[c];
-      const int ni = (int)Ic.size();
-      std::unordered_map<int, int> lpos;
-      for (int q = 0; q < ni; ++q) lpos[Ic[q]] = q;
-      std::vector<double> A((size_t)ni * ni, 0.0);
-      for (int q = 0; q < ni; ++q)
-        for (auto& kv : Abb[Ic[q]]) {
-          auto it = lpos.find(kv.first);
-          if (it != lpos.end()) A[(size_t)q * ni + it->second] += kv.second;
-        }
-      if (ni && !invert(A, ni)) throw SetupError(3, "singular interior block of the smoother");
-      for (int q = 0; q < ni; ++q) B.ipos.push_back(Ic[q]);
-      B.iptr.push_back((int)B.ipos.size());
-      B.aoff.push_back((int64_t)B.ainv.size());
-      auto Acm = to_cm(A, ni, ni);
-      B.ainv.insert(B.ainv.end(), Acm.begin(), Acm.end());
-      // W_c = inv(A_cc) A_c,S restricted to the interface columns Sc
-      const auto& sc = Sc[c];
-      const int nw = (int)sc.size();
-      std::unordered_map<int, int> wcol;
-      for (int q = 0; q < nw; ++q) wcol[sc[q]] = q;
-      std::vector<double> AcS((size_t)ni * nw, 0.0);
-      for (int q = 0; q < ni; ++q)
-        for (auto& kv : Abb[Ic[q]])
-          if (sidx[kv.first] >= 0) AcS[(size_t)q * nw + wcol[sidx[kv.first]]] += kv.second;
-      std::vector<double> Wc((size_t)ni * nw, 0.0);
-      for (int r = 0; r < ni; ++r)
-        for (int k = 0; k < ni; ++k) {
-          double a = A[(size_t)r * ni + k];
-          if (a == 0.0) continue;
-          for (int q = 0; q < nw; ++q) Wc[(size_t)r * nw + q] += a * AcS[(size_t)k * nw + q];
-        }
-      for (int q = 0; q < nw; ++q) B.widx.push_back(sc[q]);
-      B.wptr.push_back((int)B.widx.size());
-      B.woff.push_back((int64_t)B.wmat.size());
-      auto Wcm = to_cm(Wc, ni, nw);
-      B.wmat.insert(B.wmat.end(), Wcm.begin(), Wcm.end());
-      // Schur: S -= A_S,c W_c
-      for (int q = 0; q < ns; ++q)
-        for (auto& kv : Abb[S[q]]) {
-          auto it = lpos.find(kv.first);
-          if (it == lpos.end()) continue;
-          double a = kv.second;
-          int r = it->second;
-          for (int w = 0; w < nw; ++w) Sm[(size_t)q * ns + sc[w]] -= a * Wc[(size_t)r * nw + w];
-        }
-    }
-    // A_S,I rows for the runtime
-    for (int q = 0; q < ns; ++q) {
-      for (auto& kv : Abb[S[q]])
-        if (sidx[kv.first] < 0) { B.asi_col.push_back(kv.first); B.asi_val.push_back(kv.second); }
-      B.asi_ptr.push_back((int64_t)B.asi_col.size());
-    }
-    if (ns && !invert(Sm, ns)) throw SetupError(3, "singular interface Schur complement");
-    B.sinv = to_cm(Sm, ns, ns);
-    return true;
-  };
-  // small blocks: one chunk, dense inverse of the whole block
-  if (m <= kDenseDirect) {
-    double st;
-    build(m, true, st);
-    B.error = block_plan_error(B, Abb);
+      for (auto& kv : Abb[p]) A[(size_t)p * m + kv.first] += kv.second;
+    if (!invert(A, m)) throw SetupError(3, "singular block of the smoother");
+    B.ainv.swap(A);
     B.dense = true;
-    B.smem_chunk = (size_t)((m + 31) & ~31);
+    B.error = block_plan_error(B, Abb);
     return B;
   }
-  // candidate chunk sizes by dense storage; keep the cheapest whose
+  // chunk sizes by the largest per-CTA stage; keep the cheapest whose
   // backward error on a fixed vector is at the level of rounding
-  std::vector<std::pair<double, int>> cands;
-  {
-    double st;
-    build(m, false, st);
-    cands.push_back({st, m});
-    for (int s : {64, 96, 128, 192, 256, 384, 512}) {
-      if (s >= m) break;
-      build(s, false, st);
-      cands.push_back({st, s});
-    }
+  std::vector<ChunkShape> shapes;
+  for (int s : {48, 64, 80, 96, 112, 128, 160, 192, 224, 256}) {
+    if (s >= m) break;
+    ChunkShape S = chunk_shape(Abb, s);
+    if (S.ok) shapes.push_back(std::move(S));
   }
-  std::sort(cands.begin(), cands.end());
-  BlockPlan best_plan;
+  std::sort(shapes.begin(), shapes.end(), [](const ChunkShape& a, const ChunkShape& b) { return a.cost < b.cost; });
+  BlockPlan best;
   bool have = false;
-  for (auto& cs : cands) {
-    BlockPlan keep = B;
-    double st;
+  for (const ChunkShape& S : shapes) {
+    BlockPlan P = B;
     try {
-      build(cs.second, true, st);
+      build_chunked(P, Abb, S);
     } catch (SetupError&) {
-      B = keep;
       continue;
     }
-    B.error = block_plan_error(B, Abb);
-    if (!have || B.error < best_plan.error) { best_plan = B; have = true; }
-    if (B.error < 1e-13) break;
-    B = keep;
+    P.error = block_plan_error(P, Abb);
+    if (!have || P.error < best.error) { best = std::move(P); have = true; }
+    if (best.error < 1e-13) break;
   }
   if (!have) throw SetupError(3, "singular block of the smoother");
-  B = best_plan;
-  if (m <= kDenseMax) {
-    // mid-sized blocks: the dense inverse, column by column from the plan
-    std::vector<double> inv((size_t)m * m), e(m, 0.0), x;
-    for (int c = 0; c < m; ++c) {
-      e[c] = 1.0;
-      apply_plan(B, e, x);
-      e[c] = 0.0;
-      for (int r = 0; r < m; ++r) inv[(size_t)c * m + r] = x[r];   // column-major
-    }
-    BlockPlan D = B;
-    D.nch = 1;
-    D.ns = 0;
-    D.cstart = {0, m};
-    D.iptr = {0, m};
-    D.ipos.resize(m);
-    for (int p = 0; p < m; ++p) D.ipos[p] = p;
-    D.aoff = {0};
-    D.ainv.swap(inv);
-    D.spos.clear();
-    D.asi_ptr = {0};
-    D.asi_col.clear();
-    D.asi_val.clear();
-    D.sinv.clear();
-    D.wptr = {0, 0};
-    D.widx.clear();
-    D.woff = {0};
-    D.wmat.clear();
-    D.error = block_plan_error(D, Abb);
-    if (D.error < 1e-13) {
-      D.dense = true;
-      D.smem_chunk = (size_t)((m + 31) & ~31);
-      return D;
-    }
-  }
-  int maxni = 0, maxnw = 0;
-  for (int c = 0; c < B.nch; ++c) {
-    maxni = std::max(maxni, B.iptr[c + 1] - B.iptr[c]);
-    maxnw = std::max(maxnw, B.wptr[c + 1] - B.wptr[c]);
-  }
-  B.smem_chunk = (size_t)(((maxni + 31) & ~31) + 256 + maxni);
-  B.smem_back = (size_t)(((maxnw + 31) & ~31) + 256 + maxni);
-  return B;
+  return best;
 }
-
 // ---------------------------------------------------------------------------
 // device memory
 struct DevBuf {
@@ -591,6 +662,7 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
 
 struct BlockDevSet {
   BlockDev d64, d32;
+  ChunkSmem sm64{}, sm32{};   // shared-memory layouts of the chunked launches
 };
 
 struct Level {
@@ -613,11 +685,6 @@ struct Level {
   int64_t* brow_ptr = nullptr;
   int* brow_col = nullptr;
   double* brow_val = nullptr;
-  // one-launch block-smoother sweeps (k_smooth), for dense blocks
-  bool fused = false;
-  int fuse_nb = 0;                     // block-solving CTAs
-  size_t fuse_smem[2] = {0, 0};        // their shared memory, [FP64, FP32]
-  FrontierDev fr64{}, fr32{};
   // owner fix-up list: merged-away control volumes of this level
   int nfix = 0;
   int* fix_dst = nullptr;
@@ -659,11 +726,11 @@ struct cc_hierarchy {
   // algorithmic bytes of the launch each pair brackets
   int timing = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-  std::vector<double> ev_bytes;
+  std::vector<double> ev_bytes, ev_rbytes;   // algorithmic and actually moved bytes
   size_t ev_used = 0;
   int64_t timed_launches = 0;
   double timed_ms = 0;
-  double timed_bytes = 0;
+  double timed_bytes = 0, timed_rbytes = 0;
   // level-0 FP64 buffer that holds u during a cycle
   int cur64 = 0;
   // submit/poll worker
@@ -799,13 +866,13 @@ StencilParams make_stencil(const LevelDisc& D, double omega) {
   return P;
 }
 
+// The block's read-only tables at precision T (shared by clones); the work
+// vectors are the handle's own (alloc_block_work).
 template <class T>
 BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
   BlockDev d;
   std::memset(&d, 0, sizeof(d));
   d.m = B.m;
-  d.nch = B.nch;
-  d.ns = B.ns;
   if (B.m == 0) return d;
   d.cell = pool.upload(B.cell, s);
   d.gk = B.gk;
@@ -814,10 +881,9 @@ BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
   d.tptr = pool.upload(B.tail_ptr, s);
   d.tcol = pool.upload(B.tail_col, s);
   d.tval = pool.upload(cast_vec<T>(B.tail_val), s);
-  d.cstart = pool.upload(B.cstart, s);
-  d.iptr = pool.upload(B.iptr, s);
-  d.ipos = pool.upload(B.ipos, s);
-  d.aoff = pool.upload(B.aoff, s);
+  d.alias_ptr = pool.upload(B.alias_ptr, s);
+  d.alias_cell = pool.upload(B.alias_cell, s);
+  d.dense = B.dense ? 1 : 0;
   if (B.dense) {
     // row-major with 16-byte rows, zero padded, for vector loads
     const int w = 16 / (int)sizeof(T);
@@ -826,64 +892,35 @@ BlockDev upload_block(Pool& pool, const BlockPlan& B, cudaStream_t s) {
     for (int r = 0; r < B.m; ++r)
       for (int c = 0; c < B.m; ++c) a[(size_t)r * d.ld + c] = (T)B.ainv[(size_t)r * B.m + c];
     d.ainv = pool.upload(a, s);
-  } else {
-    d.ainv = pool.upload(cast_vec<T>(B.ainv), s);
+    return d;
   }
-  d.spos = pool.upload(B.spos, s);
-  d.sk = B.sk;
-  d.asi_col = pool.upload(B.asi_ell_col, s);
-  d.asi_val = pool.upload(cast_vec<T>(B.asi_ell_val), s);
-  d.sinv = pool.upload(cast_vec<T>(B.sinv), s);
-  d.wptr = pool.upload(B.wptr, s);
-  d.widx = pool.upload(B.widx, s);
-  d.woff = pool.upload(B.woff, s);
-  d.wmat = pool.upload(cast_vec<T>(B.wmat), s);
-  d.tblk = pool.alloc<T>(B.m);
-  d.zblk = pool.alloc<T>(B.m);
-  d.xs = pool.alloc<T>(std::max(1, B.ns));
-  d.dense = B.dense ? 1 : 0;
-  d.alias_ptr = pool.upload(B.alias_ptr, s);
-  d.alias_cell = pool.upload(B.alias_cell, s);
+  d.nch = B.nch;
+  d.ns = B.ns;
+  d.nslots = B.nslots;
+  d.ch = pool.upload(B.ch, s);
+  d.slot = pool.upload(B.slot, s);
+  d.sidx = pool.upload(B.sidx, s);
+  d.ipos = pool.upload(B.ipos, s);
+  d.vslot = pool.upload(B.vslot, s);
+  d.wrow = pool.upload(B.wrow, s);
+  d.orow = pool.upload(B.orow, s);
+  d.opos = pool.upload(B.opos, s);
+  d.qptr = pool.upload(B.qptr, s);
+  d.blob = pool.upload(cast_vec<T>(B.blob), s);
+  chunk_smem(B, (int)sizeof(T), d.stage1, d.stage2);
+  d.rows1 = B.sm.rows1;
+  d.rows2 = B.sm.rows2;
   return d;
 }
 
-// The stencil cells that the block rows couple to (the frontier) and the
-// gather rows over them, in the term order of the gather; false if a coupled
-// cell is not a stencil cell (its new value would then not be the sweep's).
-bool build_frontier(const BlockPlan& B, const std::vector<uint8_t>& cls, std::vector<int>& qcell,
-                    std::vector<int>& fptr, std::vector<int>& fidx, std::vector<double>& fval) {
-  std::map<int, int> pos;
-  for (int64_t e = 0; e < B.gptr[B.m]; ++e) pos[B.gcol[e]] = 0;
-  qcell.clear();
-  for (auto& kv : pos) {
-    if (cls[kv.first] != C_STENCIL) return false;
-    kv.second = (int)qcell.size();
-    qcell.push_back(kv.first);
-  }
-  fptr.assign(1, 0);
-  fidx.clear();
-  fval.clear();
-  for (int p = 0; p < B.m; ++p) {
-    for (int64_t e = B.gptr[p]; e < B.gptr[p + 1]; ++e) {
-      fidx.push_back(pos[B.gcol[e]]);
-      fval.push_back(B.gval[e]);
-    }
-    fptr.push_back((int)fidx.size());
-  }
-  return true;
-}
-
+// the handle's work vectors of a chunked block solve, and its fault word
 template <class T>
-FrontierDev upload_frontier(Pool& pool, const std::vector<int>& qcell, const std::vector<int>& fptr,
-                            const std::vector<int>& fidx, const std::vector<double>& fval,
-                            cudaStream_t s) {
-  FrontierDev f{};
-  f.nq = (int)qcell.size();
-  f.qcell = pool.upload(qcell, s);
-  f.fptr = pool.upload(fptr, s);
-  f.fidx = pool.upload(fidx, s);
-  f.fval = pool.upload(cast_vec<T>(fval), s);
-  return f;
+void alloc_block_work(Pool& pool, const BlockPlan& B, BlockDev& d, unsigned int* fault) {
+  d.fault = fault;
+  if (B.m == 0 || B.dense) return;
+  d.tS = pool.alloc<T>(std::max(1, B.ns));
+  d.z = pool.alloc<T>(B.m);
+  d.q = pool.alloc<T>(std::max(1, B.nslots));
 }
 
 inline dim3 tiles(int n) { return dim3((n + TX - 1) / TX, (n + TY - 1) / TY); }
@@ -900,10 +937,6 @@ template <> float* bbuf<float>(Level& L) { return L.b32; }
 template <class T> const BlockDev& bdev(Level& L);
 template <> const BlockDev& bdev<double>(Level& L) { return L.blk.d64; }
 template <> const BlockDev& bdev<float>(Level& L) { return L.blk.d32; }
-
-template <class T> const FrontierDev& fdev(Level& L);
-template <> const FrontierDev& fdev<double>(Level& L) { return L.fr64; }
-template <> const FrontierDev& fdev<float>(Level& L) { return L.fr32; }
 
 template <class T> const StencilP<T>& sparams(Level& L);
 template <> const StencilP<double>& sparams<double>(Level& L) { return L.sp; }
@@ -950,32 +983,6 @@ void launch_sweep(Level& L, const T* in, T* out, const T* b, const T* ec, bool z
   }
 }
 
-// Largest dense block whose sweeps run as one k_smooth launch; CCMG_FUSE in
-// the environment sets it (0, the default, keeps sweep and block solve as
-// separate launches: the redundant frontier work of k_smooth costs more than
-// the launch it saves on the grids measured so far).
-int fuse_max_m() {
-  static const int v = [] {
-    const char* e = getenv("CCMG_FUSE");
-    return e ? atoi(e) : 0;
-  }();
-  return v;
-}
-
-// Raise the dynamic shared memory limit of k_smooth to at least `bytes` (the
-// limit is per function and process-wide, so it only grows).
-void smooth_smem_limit(int bytes) {
-  static std::mutex mu;
-  static int limit = 48 * 1024;
-  std::lock_guard<std::mutex> lock(mu);
-  if (bytes <= limit) return;
-  CK(cudaFuncSetAttribute(k_smooth<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(cudaFuncSetAttribute(k_smooth<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(cudaFuncSetAttribute(k_smooth<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CK(cudaFuncSetAttribute(k_smooth<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  limit = bytes;
-}
-
 // event pair around one timed launch (the pairs are created up front by
 // cc_kernel_timing, so none is created while a graph is being captured)
 bool time_begin(cc_hierarchy* H, cudaStream_t s) {
@@ -983,63 +990,70 @@ bool time_begin(cc_hierarchy* H, cudaStream_t s) {
   CK(cudaEventRecordWithFlags(H->ev[H->ev_used].first, s, cudaEventRecordExternal));
   return true;
 }
-void time_end(cc_hierarchy* H, cudaStream_t s, double bytes) {
+void time_end(cc_hierarchy* H, cudaStream_t s, double bytes, double rbytes) {
   CK(cudaEventRecordWithFlags(H->ev[H->ev_used].second, s, cudaEventRecordExternal));
   H->ev_bytes[H->ev_used] = bytes;
+  H->ev_rbytes[H->ev_used] = rbytes;
   ++H->ev_used;
 }
 
-// algorithmic bytes of one one-launch dense block solve: the inverse, the
-// gather terms (column, coefficient, gathered value), b and the cell index of
-// every row, the writes of the block and alias cells
-double dense_block_bytes(const BlockPlan& P, int w) {
-  const double m = P.m, nnz = (double)P.gptr[P.m], na = (double)P.alias_cell.size();
-  return m * m * w + nnz * (4 + 2 * w) + m * (4 + w) + m * w + (m + 1) * 4 + na * (4 + w);
+// Algorithmic bytes of one exact block solve as the method prices it
+// (Eq. 5.8 with the factors of Def. 5.3): the gather terms (column,
+// coefficient, gathered value), b and the cell of every row, the banded LU
+// factors (2 band + 1 per row) and the write of every row.
+double block_method_bytes(const BlockPlan& P, int w) {
+  const double m = P.m, nnz = (double)P.gptr[P.m];
+  return nnz * (4 + 2 * w) + m * (4 + w) + m * (2.0 * P.band + 1) * w + m * w;
 }
 
-// one block-smoother sweep of a level with a dense block: one launch
+// Bytes the library's form of the solve reads and writes: the gather as
+// above, the dense inverse or the two stages of every chunk, the interface
+// vectors (written once, read by every chunk) and the writes.
+double block_read_bytes(const BlockPlan& P, int w) {
+  const double m = P.m, nnz = (double)P.gptr[P.m], na = (double)P.alias_cell.size();
+  double b = nnz * (4 + 2 * w) + m * (4 + w) + (m + na) * w;
+  if (P.dense) return b + m * m * w;
+  b += (double)P.blob.size() * w;
+  b += (double)P.nch * (P.ns + P.nslots) * w + 2.0 * (P.ns + m + P.nslots) * w;
+  return b;
+}
+
+// The chunked launches may use up to kSmemBudget bytes of dynamic shared
+// memory (the attribute is per function; set once per device)
+void chunk_smem_attributes() {
+  CK(cudaFuncSetAttribute(k_block_p1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+  CK(cudaFuncSetAttribute(k_block_p2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+  CK(cudaFuncSetAttribute(k_block_p1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+  CK(cudaFuncSetAttribute(k_block_p2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+}
+
+template <class T> const ChunkSmem& csmem(Level& L);
+template <> const ChunkSmem& csmem<double>(Level& L) { return L.blk.sm64; }
+template <> const ChunkSmem& csmem<float>(Level& L) { return L.blk.sm32; }
+
+// one exact block solve (Eq. 5.8) of level L on the stencil-swept u, with the
+// block's tables B (the handle's, or the same with other work vectors)
 template <class T>
-void launch_smooth(Level& L, const T* in, T* out, const T* b, const T* ec, bool zero,
-                   cudaStream_t s) {
-  const int pi = sizeof(T) == sizeof(float) ? 1 : 0;
-  const int ntiles = (int)(((L.n + TX - 1) / TX) * ((L.n + TY - 1) / TY));
-  const dim3 grid(ntiles + L.fuse_nb);
-  if (L.sp.cross)
-    pdl_launch(k_smooth<T, true>, grid, TX * TY, L.fuse_smem[pi], s, in, out, b, L.cls, ec,
-               sparams<T>(L), (int)zero, bdev<T>(L), fdev<T>(L), ntiles);
-  else
-    pdl_launch(k_smooth<T, false>, grid, TX * TY, L.fuse_smem[pi], s, in, out, b, L.cls, ec,
-               sparams<T>(L), (int)zero, bdev<T>(L), fdev<T>(L), ntiles);
+void launch_block(const BlockPlan& P, const BlockDev& B, const ChunkSmem& sm, T* u, const T* b,
+                  cudaStream_t s) {
+  if (P.dense) {
+    // 1024-thread CTAs: every thread gathers at most one row, every warp
+    // applies one row of the inverse
+    pdl_launch(k_block_dense<T>, (unsigned)((P.m + 31) / 32), 1024, (size_t)B.ld * sizeof(T), s, B, b, u);
+    return;
+  }
+  pdl_launch(k_block_p1<T>, P.nch, kChunkThreads, (size_t)sm.p1_total() * sizeof(T), s, B, sm, b,
+             (const T*)u);
+  pdl_launch(k_block_p2<T>, P.nch, kChunkThreads, sm.p2_bytes((int)sizeof(T)), s, B, sm, u);
 }
 
 template <class T>
 void block_solve(cc_hierarchy* H, Level& L, T* u, const T* b, cudaStream_t s) {
-  const BlockDev& B = bdev<T>(L);
-  if (B.m == 0) return;
   const BlockPlan& P = L.plan();
-  if (P.dense && P.m <= kBlockOneLaunch) {
-    // 1024-thread CTAs: every thread gathers at most one row, every warp
-    // applies one row of the inverse
-    const bool timed = H->timing == CC_TIME_BLOCK_DENSE && time_begin(H, s);
-    pdl_launch(k_block_dense<T>, (unsigned)((P.m + 31) / 32), 1024, (size_t)B.ld * sizeof(T), s, B, b, u);
-    if (timed) time_end(H, s, dense_block_bytes(P, (int)sizeof(T)));
-    return;
-  }
-  if (P.dense) {
-    // the gathered right-hand side goes through global memory: written once,
-    // read once per CTA of the product
-    const bool timed = H->timing == CC_TIME_BLOCK_DENSE && time_begin(H, s);
-    pdl_launch(k_block_gather<T>, nblk(P.m), 256, 0, s, B, b, u);
-    pdl_launch(k_block_gemv<T>, (P.m + 7) / 8, 256, (size_t)B.ld * sizeof(T), s, B, u);
-    if (timed) time_end(H, s, dense_block_bytes(P, (int)sizeof(T)) + 2.0 * P.m * sizeof(T));
-    return;
-  }
-  pdl_launch(k_block_chunk<T>, P.nch, 256, P.smem_chunk * sizeof(T), s, B, b, u);
-  if (P.ns > 0) {
-    size_t sm = (size_t)(((P.ns + 31) & ~31) + 256 + 32) * sizeof(T);
-    pdl_launch(k_block_schur<T>, (P.ns + 31) / 32, 256, sm, s, B, u);
-    pdl_launch(k_block_back<T>, P.nch, 256, P.smem_back * sizeof(T), s, B, u);
-  }
+  if (P.m == 0) return;
+  const bool timed = H->timing == CC_TIME_BLOCK && time_begin(H, s);
+  launch_block<T>(P, bdev<T>(L), csmem<T>(L), u, b, s);
+  if (timed) time_end(H, s, block_method_bytes(P, (int)sizeof(T)), block_read_bytes(P, (int)sizeof(T)));
 }
 
 template <class T>
@@ -1047,15 +1061,9 @@ void sweep(cc_hierarchy* H, int l, int& cur, bool zero, const T* ec, cudaStream_
   Level& L = *H->lv[l];
   T* in = ubuf<T>(L, cur);
   T* out = ubuf<T>(L, 1 - cur);
-  bool timed = H->timing == CC_TIME_FINE_SWEEP && l == 0;
-  if (L.fused && !timed) {
-    launch_smooth<T>(L, in, out, bbuf<T>(L), ec, zero, s);
-    cur = 1 - cur;
-    return;
-  }
-  timed = timed && time_begin(H, s);
+  const bool timed = H->timing == CC_TIME_FINE_SWEEP && l == 0 && time_begin(H, s);
   launch_sweep<T>(L, in, out, bbuf<T>(L), ec, zero, s);
-  if (timed) time_end(H, s, 3.0 * sizeof(T) * (double)L.nn);
+  if (timed) time_end(H, s, 3.0 * sizeof(T) * (double)L.nn, 3.0 * sizeof(T) * (double)L.nn);
   block_solve<T>(H, L, out, bbuf<T>(L), s);
   cur = 1 - cur;
 }
@@ -1357,7 +1365,7 @@ struct SolveTask {
 };
 
 void enqueue_norm(cc_hierarchy* H, cudaStream_t s) {
-  CK(cudaMemcpyAsync(H->h_norm, H->d_norm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(H->h_norm, H->d_norm, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(H->step_ev, s));
 }
 
@@ -1405,6 +1413,7 @@ void collect_timing(cc_hierarchy* H, bool mixed) {
     CK(cudaEventElapsedTime(&ms, H->ev[i].first, H->ev[i].second));
     H->timed_ms += ms;
     H->timed_bytes += H->ev_bytes[i];
+    H->timed_rbytes += H->ev_rbytes[i];
     ++H->timed_launches;
   }
   if (!H->opt.use_graphs) H->ev_used = 0;
@@ -1472,10 +1481,20 @@ bool solve_step(SolveTask& T) {
   const bool mixed = H->opt.precision == CC_PREC_MIXED;
   const cudaStream_t s = T.s;
   const int64_t l0 = t_launches;
+  // a bounded wait that expired in a kernel ends the solve
+  if ((T.phase == 1 || T.phase == 2 || T.phase == 3 || T.phase == 13) && H->h_norm[1] != 0) {
+    T.res.status = CC_ERR_TIMEOUT;
+    finish_task(T);
+    T.launches += t_launches - l0;
+    T.res.kernels = T.launches;
+    return false;
+  }
   switch (T.phase) {
     case 0:
       H->cur64 = 0;
       T.res.status = CC_ERR_NOT_CONVERGED;
+      H->h_norm[1] = 0;
+      CK(cudaMemsetAsync(H->d_norm + 1, 0, sizeof(unsigned long long), s));
       if (H->opt.krylov) ensure_krylov(H, s);
       {
         double* b0 = H->opt.krylov ? H->kr_b : L.b64;
@@ -1918,6 +1937,11 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     if (dev) {
       CK(cudaGetDevice(&H->device));
       pdl_setup_device();
+      chunk_smem_attributes();
+      // norm words: [0] the max-norm of a residual, [1] the fault word of
+      // bounded waits in the kernels
+      H->d_norm = H->pool->alloc<unsigned long long>(2);
+      CK(cudaMemsetAsync(H->d_norm, 0, 2 * sizeof(unsigned long long), s));
     }
     // levels: halve while the level is resolved and discretisable (Eq. 5.9)
     int nl = n;
@@ -1990,24 +2014,15 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       CK(cudaMemsetAsync(L.b64, 0, L.nn * sizeof(double), s));
       CK(cudaMemsetAsync(L.b32, 0, L.nn * sizeof(float), s));
       if (l + 1 < H->lv.size()) {
+        unsigned int* fault = reinterpret_cast<unsigned int*>(H->d_norm + 1);
         L.blk.d64 = upload_block<double>(*H->pool, L.plan(), s);
         L.blk.d32 = upload_block<float>(*H->pool, L.plan(), s);
-        // sweep and dense block solve in one launch (k_smooth) on the grids
-        // that the 32 x 8 tile sweep serves
-        std::vector<int> qcell, fptr, fidx;
-        std::vector<double> fval;
-        if (fuse_max_m() > 0 && L.plan().m > 0 && L.plan().m <= fuse_max_m() && L.plan().dense &&
-            L.n < 512 && build_frontier(L.plan(), cls, qcell, fptr, fidx, fval)) {
-          const size_t words = qcell.size() + (size_t)L.plan().m;
-          if (words * sizeof(double) <= 96 * 1024) {
-            L.fr64 = upload_frontier<double>(*H->pool, qcell, fptr, fidx, fval, s);
-            L.fr32 = upload_frontier<float>(*H->pool, qcell, fptr, fidx, fval, s);
-            L.fuse_smem[0] = words * sizeof(double);
-            L.fuse_smem[1] = words * sizeof(float);
-            L.fuse_nb = std::min(128, std::max(1, (L.plan().m + 15) / 16));
-            smooth_smem_limit((int)L.fuse_smem[0]);
-            L.fused = true;
-          }
+        alloc_block_work<double>(*H->pool, L.plan(), L.blk.d64, fault);
+        alloc_block_work<float>(*H->pool, L.plan(), L.blk.d32, fault);
+        if (!L.plan().dense && L.plan().m) {
+          int s1, s2;
+          L.blk.sm64 = chunk_smem(L.plan(), 8, s1, s2);
+          L.blk.sm32 = chunk_smem(L.plan(), 4, s1, s2);
         }
       }
       if (!D.block.empty()) {
@@ -2085,8 +2100,8 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       }
       H->r64 = H->pool->alloc<double>(L.nn);
       CK(cudaMemsetAsync(H->r64, 0, L.nn * sizeof(double), s));
-      H->d_norm = H->pool->alloc<unsigned long long>(2);
       CK(cudaMallocHost(&H->h_norm, 2 * sizeof(unsigned long long)));
+      H->h_norm[0] = H->h_norm[1] = 0;
       CK(cudaEventCreateWithFlags(&H->step_ev, cudaEventDisableTiming));
       ensure_krylov(H, s);
     }
@@ -2140,6 +2155,8 @@ cc_status cc_query(cc_handle H, cc_info* out) {
   for (size_t l = 0; l < H->lv.size() && l < 32; ++l) {
     out->level_n[l] = H->lv[l]->n;
     out->block_error = std::max(out->block_error, H->lv[l]->plan().error);
+    out->block_m[l] = H->lv[l]->plan().m;
+    out->block_chunks[l] = H->lv[l]->plan().dense ? 0 : H->lv[l]->plan().nch;
   }
   out->bottom_error = H->bottom_error;
   return CC_OK;
@@ -2227,6 +2244,9 @@ cc_status cc_clone(cc_handle S, cc_stream stream, cc_handle* out) {
     H->n_g = S->n_g;
     H->n_bd = S->n_bd;
     H->n_dof = S->n_dof;
+    H->d_norm = H->pool->alloc<unsigned long long>(2);
+    CK(cudaMemsetAsync(H->d_norm, 0, 2 * sizeof(unsigned long long), s));
+    unsigned int* fault = reinterpret_cast<unsigned int*>(H->d_norm + 1);
     const size_t nl = S->lv.size();
     for (size_t l = 0; l < nl; ++l) {
       // shares the plan, the discretisation and every device table ...
@@ -2244,20 +2264,16 @@ cc_status cc_clone(cc_handle S, cc_stream stream, cc_handle* out) {
       CK(cudaMemsetAsync(L->b32, 0, L->nn * sizeof(float), s));
       const BlockPlan& B = L->plan();
       if (l + 1 < nl && B.m > 0) {
-        L->blk.d64.tblk = H->pool->alloc<double>(B.m);
-        L->blk.d64.zblk = H->pool->alloc<double>(B.m);
-        L->blk.d64.xs = H->pool->alloc<double>(std::max(1, B.ns));
-        L->blk.d32.tblk = H->pool->alloc<float>(B.m);
-        L->blk.d32.zblk = H->pool->alloc<float>(B.m);
-        L->blk.d32.xs = H->pool->alloc<float>(std::max(1, B.ns));
+        alloc_block_work<double>(*H->pool, B, L->blk.d64, fault);
+        alloc_block_work<float>(*H->pool, B, L->blk.d32, fault);
       }
       H->lv.push_back(std::move(L));
     }
     Level& L0 = *H->lv[0];
     H->r64 = H->pool->alloc<double>(L0.nn);
     CK(cudaMemsetAsync(H->r64, 0, L0.nn * sizeof(double), s));
-    H->d_norm = H->pool->alloc<unsigned long long>(2);
     CK(cudaMallocHost(&H->h_norm, 2 * sizeof(unsigned long long)));
+    H->h_norm[0] = H->h_norm[1] = 0;
     CK(cudaEventCreateWithFlags(&H->step_ev, cudaEventDisableTiming));
     ensure_krylov(H, s);
     CK(cudaStreamCreateWithFlags(&H->gstream, cudaStreamNonBlocking));
@@ -2476,11 +2492,19 @@ cc_status cc_cycle(cc_handle H, double* u, const double* b, cc_stream st) {
   cudaStream_t s = (cudaStream_t)st;
   try {
     Level& L = *H->lv[0];
-    CK(cudaMemcpyAsync(L.u64[0], u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(L.b64, b, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
     std::vector<int> cur(H->lv.size(), 0);
-    cycle_level<double>(H, 0, cur, false, s);
-    CK(cudaMemcpyAsync(u, L.u64[cur[0]], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (H->opt.precision == CC_PREC_MIXED) {
+      // the cycle of the mixed mode: FP32 on u and b rounded to FP32
+      pdl_launch(k_convert<double, float>, nblk(L.nn), 256, 0, s, (const double*)u, L.u32[0], L.nn);
+      pdl_launch(k_convert<double, float>, nblk(L.nn), 256, 0, s, b, L.b32, L.nn);
+      cycle_level<float>(H, 0, cur, false, s);
+      pdl_launch(k_convert<float, double>, nblk(L.nn), 256, 0, s, (const float*)L.u32[cur[0]], u, L.nn);
+    } else {
+      CK(cudaMemcpyAsync(L.u64[0], u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(L.b64, b, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      cycle_level<double>(H, 0, cur, false, s);
+      CK(cudaMemcpyAsync(u, L.u64[cur[0]], L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     CK(cudaGetLastError());
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
@@ -2525,7 +2549,8 @@ cc_status cc_smooth_noalloc(cc_handle H, int l, double* u, const double* b, cc_s
     }
     Level& L = *H->lv[l];
     const BlockPlan& P = L.plan();
-    const int64_t need = L.nn + 2 * (int64_t)P.m + P.ns;
+    const bool chunked = P.m > 0 && !P.dense;
+    const int64_t need = L.nn + (chunked ? (int64_t)P.ns + P.m + P.nslots : 0);
     if (need > CC_NOALLOC_SCRATCH_DOUBLES) {
       snprintf(t_last_error, sizeof(t_last_error),
                "cc_smooth_noalloc: level %d needs %lld doubles of scratch, more than the %d "
@@ -2535,23 +2560,14 @@ cc_status cc_smooth_noalloc(cc_handle H, int l, double* u, const double* b, cc_s
     double* scr = noalloc_scratch(dev);
     double* out = scr;                      // [0, nn): Jacobi output
     BlockDev B = L.blk.d64;                 // the handle's tables, temporaries in scratch
-    B.tblk = scr + L.nn;                    // [nn, nn + m)
-    B.zblk = scr + L.nn + P.m;              // [nn + m, nn + 2m)
-    B.xs = scr + L.nn + 2 * P.m;            // [nn + 2m, nn + 2m + ns)
-    launch_sweep<double>(L, u, out, b, (const double*)nullptr, false, s);
-    if (P.m) {
-      if (P.dense) {
-        pdl_launch(k_block_gather<double>, nblk(P.m), 256, 0, s, B, b, out);
-        pdl_launch(k_block_gemv<double>, (P.m + 7) / 8, 256, P.smem_chunk * sizeof(double), s, B, out);
-      } else {
-        pdl_launch(k_block_chunk<double>, P.nch, 256, P.smem_chunk * sizeof(double), s, B, b, out);
-        if (P.ns > 0) {
-          size_t sm = (size_t)(((P.ns + 31) & ~31) + 256 + 32) * sizeof(double);
-          pdl_launch(k_block_schur<double>, (P.ns + 31) / 32, 256, sm, s, B, out);
-          pdl_launch(k_block_back<double>, P.nch, 256, P.smem_back * sizeof(double), s, B, out);
-        }
-      }
+    B.fault = nullptr;                      // nothing of the handle is written
+    if (chunked) {
+      B.tS = scr + L.nn;                    // [nn, nn + ns): interface right-hand sides
+      B.z = scr + L.nn + P.ns;              // [.., + m): chunk interior solutions
+      B.q = scr + L.nn + P.ns + P.m;        // [.., + slots): interface contributions
     }
+    launch_sweep<double>(L, u, out, b, (const double*)nullptr, false, s);
+    if (P.m) launch_block<double>(P, B, L.blk.sm64, out, b, s);
     // every non-empty cell of `out` was written above; empty cells go out as 0
     pdl_launch(k_rhs_copy, nblk(L.nn), 256, 0, s, out, L.cls, u, L.nn);
     CK(cudaGetLastError());
@@ -2574,12 +2590,13 @@ cc_status cc_level_tables(cc_handle H, int l, uint8_t* h_kind, int* h_lattice, d
 
 cc_status cc_kernel_timing(cc_handle H, int which) {
   if (H && H->opt.host_only) return CC_ERR_ARG;
-  if (!H || which < CC_TIME_OFF || which > CC_TIME_BLOCK_DENSE) return CC_ERR_ARG;
+  if (!H || which < CC_TIME_OFF || which > CC_TIME_BLOCK) return CC_ERR_ARG;
   H->timing = which;
   H->ev_used = 0;
   H->timed_launches = 0;
   H->timed_ms = 0;
   H->timed_bytes = 0;
+  H->timed_rbytes = 0;
   try {
     // event pairs for every timed launch of one solve iteration, created up
     // front so that none is created during graph capture: a cycle visits
@@ -2595,12 +2612,13 @@ cc_status cc_kernel_timing(cc_handle H, int which) {
       H->ev.push_back({a, b});
     }
     H->ev_bytes.assign(H->ev.size(), 0.0);
+    H->ev_rbytes.assign(H->ev.size(), 0.0);
   } catch (CudaError&) { return CC_ERR_CUDA; }
   return CC_OK;
 }
 
 cc_status cc_kernel_timing_read(cc_handle H, int64_t* launches, double* total_ms,
-                                double* bytes_per_launch) {
+                                double* bytes_per_launch, double* moved_bytes_per_launch) {
   if (H && H->opt.host_only) return CC_ERR_ARG;
   if (!H) return CC_ERR_ARG;
   try {
@@ -2610,6 +2628,8 @@ cc_status cc_kernel_timing_read(cc_handle H, int64_t* launches, double* total_ms
   if (total_ms) *total_ms = H->timed_ms;
   if (bytes_per_launch)
     *bytes_per_launch = H->timed_launches ? H->timed_bytes / (double)H->timed_launches : 0.0;
+  if (moved_bytes_per_launch)
+    *moved_bytes_per_launch = H->timed_launches ? H->timed_rbytes / (double)H->timed_launches : 0.0;
   return CC_OK;
 }
 

@@ -674,15 +674,39 @@ __global__ void k_block_resid(int m, const int* __restrict__ cell, const int64_t
   }
 }
 
-// ---- a3: exact solve on the block (Eq. 5.8), two-level Schur scheme ---------
-// The block unknowns (in curve order) are split into chunks; interface
-// unknowns couple chunks, interior unknowns only their own chunk and the
-// interfaces.  Precomputed in FP64 on the host: the inverse of each chunk's
-// interior block (column-major), the inverse of the interface Schur
-// complement (column-major), W_c = inv(A_cc) A_c,S on each chunk's interface
-// columns, and A_S,I.
+// ---- a2 + a3: exact solve on the block (Eq. 5.8) ------------------------------
+// The block rows are ordered along the boundary curves (Def. 5.1), where the
+// block matrix is banded up to its periodic corner (Lemma 5.2, Def. 5.3).
+// Small blocks are solved with their dense inverse in one launch.  Larger
+// ones are cut into chunks of consecutive rows; a row of a chunk that couples
+// to a later chunk (or, across the periodic corner, to the last one) is an
+// interface row, all other rows are interior rows.  Interior rows couple only
+// to their own chunk and to interface rows, so with t the gathered right-hand
+// side the exact solution is
+//   x_I(c) = inv(A_cc) t_I(c) - W_c x_S,       W_c = inv(A_cc) A_{c,S},
+//   S x_S = t_S - sum_c V_c t_I(c),            V_c = A_{S,c} inv(A_cc),
+// S = A_SS - sum_c A_{S,c} inv(A_cc) A_{c,S} the interface Schur complement.
+// Setup (FP64, host) stores per chunk the stacked [inv(A_cc); V_c] (launch 1)
+// and the rows of inv(S) that the chunk needs with W_c (launch 2), each
+// contiguous, so one bulk (TMA) copy stages them in shared memory before the
+// kernel waits on its predecessor.  Launch 1 gathers t, forms z = inv(A_cc)
+// t_I and the chunk's contributions V_c t_I to the interface right-hand
+// side; launch 2 sums those contributions in a fixed order, applies its rows
+// of inv(S) and finishes x_I = z - W_c x_S.  Both launch one CTA per chunk.
+struct ChunkDev {
+  int p0, p1;        // block positions [p0, p1) of the chunk's rows
+  int ni, nv;        // interior rows; interface rows that read the interior (V_c rows)
+  int nr, nw, nown;  // rows of inv(S) held; W_c columns; interface rows of the chunk
+  int ipos_off;      // interior block positions: ipos[ipos_off .. + ni)
+  int v_off;         // q slot of each V_c row: vslot[v_off .. + nv)
+  int w_off;         // row of inv(S) (index into the held rows) of each W_c column
+  int o_off;         // own interface rows: orow[o_off ..] (held-row index), opos (position)
+  int b1n, b2n;      // elements of the two stages (multiples of 4)
+  long long b1, b2;  // element offsets of the two stages in the blob
+};
+
 struct BlockDev {
-  int m, nch, ns;
+  int m;
   const int* cell;          // [m] grid cell of block position
   int gk;                   // gather width: terms per row (padded)
   const int* gcol;          // [gk * m] term-major: entry q of row p at q * m + p
@@ -690,27 +714,30 @@ struct BlockDev {
   const int* tptr;          // [m+1] terms beyond gk (rows longer than the width)
   const int* tcol;
   const void* tval;         // T
-  const int* cstart;        // [nch+1] block positions of each chunk
-  const int* iptr;          // [nch+1] interior list ptr
-  const int* ipos;          // interior block positions
-  const int64_t* aoff;      // [nch] offset of chunk inverse
-  const void* ainv;         // T, column-major per chunk
-  const int* spos;          // [ns] block positions of interfaces
-  int sk;                   // A_S,I width (padded)
-  const int* asi_col;       // [sk * ns] term-major, interior block positions
-  const void* asi_val;      // T, padded terms have value 0
-  const void* sinv;         // T, ns x ns column-major
-  const int* wptr;          // [nch+1] interface columns of W_c
-  const int* widx;          // interface indices (into 0..ns-1)
-  const int64_t* woff;      // [nch] offset of W_c (column-major, rows = interior)
-  const void* wmat;         // T
-  void* tblk;               // T scratch [m]: gathered right-hand side
-  void* zblk;               // T scratch [m]: interior solutions
-  void* xs;                 // T scratch [ns]
-  int dense;                // 1: one chunk, inverse of the whole block in ainv,
-  int ld;                   //    row-major with row stride ld (16-byte rows, zero padded)
   const int* alias_ptr;     // [m+1] merged-away control volumes owned by each block cell
   const int* alias_cell;    //       (they carry the owner's value for Eq. 5.11)
+  // dense form: the inverse of the whole block, row-major, row stride ld
+  int dense, ld;
+  const void* ainv;         // T
+  // chunked form
+  int nch, ns, nslots;
+  const ChunkDev* ch;       // [nch]
+  const int* slot;          // [m] row of a position within its chunk: interior rows first
+  const int* sidx;          // [m] interface index of a position, -1 for interior rows
+  const int* ipos;          // interior positions of every chunk
+  const int* vslot;         // q slot of every V_c row
+  const int* wrow;          // held-row index of every W_c column
+  const int* orow;          // held-row index of every own interface row
+  const int* opos;          //   and its block position
+  const int* qptr;          // [ns+1] slots of each interface's contributions (chunk order)
+  const void* blob;         // T, the per-chunk stages
+  int stage1, stage2;       // 1: the stage is copied to shared memory (it fits)
+  int rows1, rows2;         // largest ni + nv; largest nr (partial-sum buffer sizes)
+  // work vectors (per handle)
+  void* tS;                 // T [ns]    gathered t of the interface rows
+  void* z;                  // T [m]     inv(A_cc) t_I at interior positions
+  void* q;                  // T [slots] contributions V_c t_I
+  unsigned int* fault;      // set when a bounded wait expires
 };
 
 template <class T>
@@ -758,148 +785,284 @@ __device__ __forceinline__ T block_rhs(const BlockDev& B, const T* __restrict__ 
   return acc;
 }
 
-// y[0..rows) = M x, M column-major (rows x cols), x in shared memory; the CTA
-// cooperates: lanes run over rows, warps split the columns.
+// ---- bulk (TMA) copies global -> shared, completed on an mbarrier ---------------
+// A device-wide flag that kernels set when a bounded wait expires; the solve
+// loop reads it with every norm and reports CC_ERR_TIMEOUT.
+constexpr unsigned kWaitLimit = 1u << 20;     // polls of a bounded wait (about 0.1 s)
+constexpr unsigned kBulkPiece = 32768;        // bytes per bulk copy instruction
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// One thread: initialise the barrier for one arrival, announce `bytes`, and
+// copy them (16-byte aligned on both sides, a multiple of 16) into shared memory.
+__device__ __forceinline__ void bulk_stage(void* sdst, const void* gsrc, unsigned bytes,
+                                           uint64_t* bar) {
+  const unsigned b = smem_u32(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  const unsigned d = smem_u32(sdst);
+  for (unsigned off = 0; off < bytes; off += kBulkPiece) {
+    const unsigned n = bytes - off < kBulkPiece ? bytes - off : kBulkPiece;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d + off),
+        "l"(static_cast<const char*>(gsrc) + off), "r"(n), "r"(b)
+        : "memory");
+  }
+}
+
+// Wait for phase 0 of the barrier, at most kWaitLimit polls; false if it expired.
+__device__ __forceinline__ bool bulk_wait(uint64_t* bar) {
+  const unsigned b = smem_u32(bar);
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(b)
+        : "memory");
+    if (done) return true;
+    if (it > 32) __nanosleep(64);
+  }
+  return false;
+}
+
+// All threads wait for the staged copy (after a CTA barrier, so that the
+// barrier's initialisation by thread 0 is visible); if the wait expired
+// anywhere the CTA flags the fault, waits once more (bounded) for its copy in
+// flight, and the caller returns without using the data.  Ends with a CTA
+// barrier.
+__device__ __forceinline__ bool stage_ready(bool staged, uint64_t* bar, unsigned int* fault) {
+  __syncthreads();
+  const int bad = staged && !bulk_wait(bar);
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0 && fault) atomicOr(fault, 1u);
+    if (staged) bulk_wait(bar);
+    return false;
+  }
+  return true;
+}
+
+// ---- chunked exact block solve (the two launches) -------------------------------
+constexpr int kChunkThreads = 256;   // threads of both launches; a chunk has at most this many rows
+constexpr int kRB = 9;               // rows per lane of cta_gemv_cm: products of up to 288 rows
+constexpr int kGatherMax = 16;       // the ELL width of the gather (gk) never exceeds it
+
+// y[0..rows) = M x, M column-major (rows x cols, column stride ld), x in
+// shared memory: lane l of warp w accumulates rows l, l + 32, ... over the
+// columns w, w + nwarps, ...; the partial sums of the warps go through part
+// (nwarps x rows) and are added in warp order.  Ends with a CTA barrier.
 template <class T>
-__device__ void cta_matvec_cm(const T* __restrict__ M, int rows, int ld, int cols,
-                              const T* __restrict__ x, T* __restrict__ partial, T* __restrict__ y) {
+__device__ void cta_gemv_cm(const T* M, int rows, int ld, int cols, const T* x, T* part, T* y) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r0 = 0; r0 < rows; r0 += 32) {
-    int r = r0 + lane;
-    T acc = T(0);
-    if (r < rows)
-      for (int c = warp; c < cols; c += nw) acc += M[(size_t)c * ld + r] * x[c];
-    partial[warp * 32 + lane] = acc;
-    __syncthreads();
-    if (warp == 0 && r < rows) {
-      T s = T(0);
-      for (int q = 0; q < nw; ++q) s += partial[q * 32 + lane];
-      y[r] = s;
+  T acc[kRB];
+#pragma unroll
+  for (int i = 0; i < kRB; ++i) acc[i] = T(0);
+  for (int c = warp; c < cols; c += nw) {
+    const T xc = x[c];
+    const T* col = M + (size_t)c * ld;
+#pragma unroll
+    for (int i = 0; i < kRB; ++i) {
+      const int r = lane + 32 * i;
+      if (r < rows) acc[i] += col[r] * xc;
     }
-    __syncthreads();
   }
+#pragma unroll
+  for (int i = 0; i < kRB; ++i) {
+    const int r = lane + 32 * i;
+    if (r < rows) part[warp * rows + r] = acc[i];
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    T s = T(0);
+    for (int w = 0; w < nw; ++w) s += part[w * rows + r];
+    y[r] = s;
+  }
+  __syncthreads();
 }
 
-// K_a: gather t = b - A(block, rest) u for the chunk, z = inv(A_cc) t_I;
-// interface rows' t go to tblk.  With no interfaces z is the solution.
-// The chunk's extents are setup data and are read before the wait on the
-// previous kernel.
+// y[0..rows) = M x, M row-major (rows x cols, row stride ld), x in shared
+// memory: warp w takes rows w, w + nwarps, ... (four at a time), its lanes
+// split the columns and each row's sum is reduced across the warp in a fixed
+// order.  Ends with a CTA barrier.
 template <class T>
-__global__ void k_block_chunk(BlockDev B, const T* __restrict__ b, T* __restrict__ u) {
-  extern __shared__ unsigned char smem_raw[];
-  T* tI = reinterpret_cast<T*>(smem_raw);
-  const int c = blockIdx.x;
-  const int p0 = B.cstart[c], p1 = B.cstart[c + 1];
-  const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
-  pdl_enter();
-  T* partial = tI + ((ni + 31) & ~31);
-  T* zI = partial + blockDim.x;
-  T* tblk = static_cast<T*>(B.tblk);
-  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) tblk[p] = block_rhs(B, b, u, p);
-  __syncthreads();
-  for (int q = threadIdx.x; q < ni; q += blockDim.x) tI[q] = tblk[B.ipos[i0 + q]];
-  __syncthreads();
-  const T* A = static_cast<const T*>(B.ainv) + B.aoff[c];
-  cta_matvec_cm<T>(A, ni, ni, ni, tI, partial, zI);
-  T* zblk = static_cast<T*>(B.zblk);
-  for (int q = threadIdx.x; q < ni; q += blockDim.x) {
-    int p = B.ipos[i0 + q];
-    zblk[p] = zI[q];
-    if (B.ns == 0) block_write(B, u, p, zI[q]);
-  }
-  pdl_exit();
-}
-
-// K_b: x_S = inv(S) (t_S - A_S,I z) for 32 interface rows per CTA.
-template <class T>
-__global__ void k_block_schur(BlockDev B, T* __restrict__ u) {
-  pdl_enter();
-  extern __shared__ unsigned char smem_raw[];
-  T* tS = reinterpret_cast<T*>(smem_raw);
-  T* partial = tS + ((B.ns + 31) & ~31);
-  T* y = partial + blockDim.x;
-  const T* tblk = static_cast<const T*>(B.tblk);
-  const T* zblk = static_cast<const T*>(B.zblk);
-  const T* av = static_cast<const T*>(B.asi_val);
-  for (int i = threadIdx.x; i < B.ns; i += blockDim.x) {
-    T acc = tblk[B.spos[i]];
-#pragma unroll 8
-    for (int q = 0; q < B.sk; ++q) {
-      size_t e = (size_t)q * B.ns + i;
-      acc -= av[e] * zblk[B.asi_col[e]];
+__device__ void cta_gemv_rm(const T* M, int rows, int ld, int cols, const T* x, T* y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r0 = warp; r0 < rows; r0 += 4 * nw) {
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int c = lane; c < cols; c += 32) {
+      const T xc = x[c];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = r0 + i * nw;
+        if (r < rows) acc[i] += M[(size_t)r * ld + c] * xc;
+      }
     }
-    tS[i] = acc;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T v = acc[i];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const int r = r0 + i * nw;
+      if (lane == 0 && r < rows) y[r] = v;
+    }
   }
   __syncthreads();
-  const int r0 = blockIdx.x * 32;
-  const int rows = min(32, B.ns - r0);
-  const T* S = static_cast<const T*>(B.sinv) + r0;
-  cta_matvec_cm<T>(S, rows, B.ns, B.ns, tS, partial, y);
-  T* xs = static_cast<T*>(B.xs);
-  for (int q = threadIdx.x; q < rows; q += blockDim.x) {
-    xs[r0 + q] = y[q];
-    block_write(B, u, B.spos[r0 + q], y[q]);
-  }
-  pdl_exit();
 }
 
-// K_c: x_I = z - W_c x_S for the chunk's interior unknowns.
-// The chunk's extents are setup data and are read before the wait.
-template <class T>
-__global__ void k_block_back(BlockDev B, T* __restrict__ u) {
-  extern __shared__ unsigned char smem_raw[];
-  T* xl = reinterpret_cast<T*>(smem_raw);
-  const int c = blockIdx.x;
-  const int w0 = B.wptr[c], nw_ = B.wptr[c + 1] - w0;
-  const int i0 = B.iptr[c], ni = B.iptr[c + 1] - i0;
-  pdl_enter();
-  T* partial = xl + ((nw_ + 31) & ~31);
-  T* y = partial + blockDim.x;
-  const T* xs = static_cast<const T*>(B.xs);
-  for (int q = threadIdx.x; q < nw_; q += blockDim.x) xl[q] = xs[B.widx[w0 + q]];
-  __syncthreads();
-  const T* W = static_cast<const T*>(B.wmat) + B.woff[c];
-  cta_matvec_cm<T>(W, ni, ni, nw_, xl, partial, y);
-  const T* zblk = static_cast<const T*>(B.zblk);
-  for (int q = threadIdx.x; q < ni; q += blockDim.x) {
-    int p = B.ipos[i0 + q];
-    block_write(B, u, p, zblk[p] - y[q]);
+// Shared-memory layout of the two launches (elements of T); st1 / st2 are
+// the staged regions (0 when the stage is read from global memory).  Launch
+// 2 ends with the interface pointers qptr as ints.
+struct ChunkSmem {
+  int st1, st2;       // staged regions
+  int ns4, sl4;       // interface count and contribution-slot count, rounded up to 4
+  int rows1, rows2;   // largest ni + nv; largest nr
+  int nwmax, nimax;   // largest nw; largest ni
+  __host__ __device__ int p1_tl() const { return st1; }
+  __host__ __device__ int p1_part() const { return st1 + kChunkThreads; }
+  __host__ __device__ int p1_y() const { return p1_part() + (kChunkThreads / 32) * rows1; }
+  __host__ __device__ int p1_total() const { return p1_y() + rows1; }
+  __host__ __device__ int p2_ys() const { return st2; }
+  __host__ __device__ int p2_q() const { return st2 + ns4; }
+  __host__ __device__ int p2_xr() const { return p2_q() + sl4; }
+  __host__ __device__ int p2_xw() const { return p2_xr() + rows2; }
+  __host__ __device__ int p2_part() const { return p2_xw() + nwmax; }
+  __host__ __device__ int p2_y() const {
+    return p2_part() + (kChunkThreads / 32) * (rows2 > nimax ? rows2 : nimax);
   }
-  pdl_exit();
-}
+  __host__ __device__ int p2_total() const { return p2_y() + nimax; }
+  // bytes of launch 2 at element size w: the elements, then ns4 + 4 ints
+  __host__ __device__ size_t p2_bytes(int w) const { return (size_t)p2_total() * w + (size_t)(ns4 + 4) * 4; }
+};
 
-// Dense blocks (a few thousand unknowns at most) are solved with the dense
-// inverse: one kernel gathers t = b - A(block, rest) u for every block row,
-// the next applies inv(A) row-major, one warp per row.
-// The row's cell, columns and coefficients are setup data, so they are
-// fetched before waiting on the previous kernel; only b and u are read after.
-constexpr int kGatherMax = 16;   // the ELL width of BlockDev (gk) never exceeds it
+// Launch 1, one CTA per chunk: stage [inv(A_cc); V_c], gather t of the
+// chunk's rows, then z = inv(A_cc) t_I and the contributions q = V_c t_I.
+// Everything that comes from setup (the staged stage, the row's gather
+// terms, its slot, the output index of each product row) is read before
+// the wait on the previous kernel; after it, one batch of independent loads
+// of b and u.
 template <class T>
-__global__ void k_block_gather(BlockDev B, const T* __restrict__ b, const T* __restrict__ u) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool on = p < B.m;
-  const T* gval = static_cast<const T*>(B.gval);
+__global__ void __launch_bounds__(kChunkThreads) k_block_p1(BlockDev B, ChunkSmem L,
+                                                          const T* __restrict__ b,
+                                                          const T* __restrict__ u) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ __align__(8) uint64_t bar;
+  T* sm = reinterpret_cast<T*>(smem_f4);
+  const ChunkDev C = B.ch[blockIdx.x];
+  const int tid = threadIdx.x;
+  if (B.stage1 && tid == 0)
+    bulk_stage(sm, static_cast<const T*>(B.blob) + C.b1, (unsigned)(C.b1n * sizeof(T)), &bar);
+  const bool on = tid < C.p1 - C.p0;
+  const int p = C.p0 + tid;
+  int cell = 0, sl = 0, si = -1, t0 = 0, t1 = 0;
   int col[kGatherMax];
   T val[kGatherMax];
-  int cell = 0;
-  if (on) cell = B.cell[p];
+  const T* gval = static_cast<const T*>(B.gval);
+  if (on) {
+    cell = B.cell[p];
+    sl = B.slot[p];
+    si = B.sidx[p];
+    t0 = B.tptr[p];
+    t1 = B.tptr[p + 1];
+  }
 #pragma unroll
-  for (int q = 0; q < kGatherMax; ++q) {
-    const bool use = on && q < B.gk;
-    const size_t e = (size_t)q * B.m + p;
-    col[q] = use ? B.gcol[e] : 0;
-    val[q] = use ? gval[e] : T(0);
+  for (int k = 0; k < kGatherMax; ++k) {
+    const bool use = on && k < B.gk;
+    const size_t e = (size_t)k * B.m + p;
+    col[k] = use ? B.gcol[e] : 0;
+    val[k] = use ? gval[e] : T(0);
+  }
+  // output index of product rows tid and tid + kChunkThreads: interior rows
+  // go to z at their block position, V_c rows to their contribution slot
+  int oi[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int r = tid + k * kChunkThreads;
+    oi[k] = r < C.ni ? B.ipos[C.ipos_off + r] : r < C.ni + C.nv ? B.vslot[C.v_off + r - C.ni] : -1;
   }
   pdl_enter();
+  T* tl = sm + L.p1_tl();
   if (on) {
     T acc = b[cell];
 #pragma unroll
-    for (int q = 0; q < kGatherMax; ++q)
-      if (q < B.gk) acc -= val[q] * u[col[q]];
+    for (int k = 0; k < kGatherMax; ++k)
+      if (k < B.gk) acc -= val[k] * u[col[k]];
     const T* tval = static_cast<const T*>(B.tval);
-    for (int q = B.tptr[p]; q < B.tptr[p + 1]; ++q) acc -= tval[q] * u[B.tcol[q]];
-    static_cast<T*>(B.tblk)[p] = acc;
+    for (int k = t0; k < t1; ++k) acc -= tval[k] * u[B.tcol[k]];
+    tl[sl] = acc;
+    if (si >= 0) static_cast<T*>(B.tS)[si] = acc;
   }
+  if (!stage_ready(B.stage1 != 0, &bar, B.fault)) { pdl_exit(); return; }
+  const T* M = B.stage1 ? sm : static_cast<const T*>(B.blob) + C.b1;
+  T* y = sm + L.p1_y();
+  cta_gemv_cm<T>(M, C.ni + C.nv, C.ni + C.nv, C.ni, tl, sm + L.p1_part(), y);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int r = tid + k * kChunkThreads;
+    if (oi[k] < 0) continue;
+    if (r < C.ni) static_cast<T*>(B.z)[oi[k]] = y[r];
+    else static_cast<T*>(B.q)[oi[k]] = y[r];
+  }
+  pdl_exit();
+}
+
+// Launch 2, one CTA per chunk: stage the held rows of inv(S) (row-major) and
+// W_c (column-major), form the
+// interface right-hand side t_S - sum of contributions (each interface's in
+// chunk order), x = inv(S) rows times it, then x_I = z - W_c x_S, and write
+// the interior and own interface rows (with their merged-away cells).  The
+// interface pointers, this thread's rows and their destinations are setup
+// data, read before the wait; after it, t_S, the contributions and z come
+// in one batch of independent loads.
+template <class T>
+__global__ void __launch_bounds__(kChunkThreads) k_block_p2(BlockDev B, ChunkSmem L,
+                                                          T* __restrict__ u) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ __align__(8) uint64_t bar;
+  T* sm = reinterpret_cast<T*>(smem_f4);
+  int* qp = reinterpret_cast<int*>(sm + L.p2_total());
+  const ChunkDev C = B.ch[blockIdx.x];
+  const int tid = threadIdx.x;
+  if (B.stage2 && tid == 0)
+    bulk_stage(sm, static_cast<const T*>(B.blob) + C.b2, (unsigned)(C.b2n * sizeof(T)), &bar);
+  for (int k = tid; k <= B.ns; k += blockDim.x) qp[k] = B.qptr[k];
+  // this thread's interior row (tid < ni) and own interface row (tid < nown)
+  const bool hi = tid < C.ni, ho = tid < C.nown;
+  const int pi = hi ? B.ipos[C.ipos_off + tid] : 0;
+  const int ro = ho ? B.orow[C.o_off + tid] : 0;
+  const int wr = tid < C.nw ? B.wrow[C.w_off + tid] : 0;
+  BlockDst di, dob;
+  if (hi) di.load(B, pi);
+  if (ho) dob.load(B, B.opos[C.o_off + tid]);
+  pdl_enter();
+  T* ys = sm + L.p2_ys();
+  T* qs = sm + L.p2_q();
+  const T* tS = static_cast<const T*>(B.tS);
+  const T* q = static_cast<const T*>(B.q);
+  for (int k = tid; k < B.ns; k += blockDim.x) ys[k] = tS[k];
+  for (int j = tid; j < B.nslots; j += blockDim.x) qs[j] = q[j];
+  const T zi = hi ? static_cast<const T*>(B.z)[pi] : T(0);
+  __syncthreads();
+  for (int k = tid; k < B.ns; k += blockDim.x) {
+    T acc = ys[k];
+    for (int j = qp[k]; j < qp[k + 1]; ++j) acc -= qs[j];
+    ys[k] = acc;
+  }
+  if (!stage_ready(B.stage2 != 0, &bar, B.fault)) { pdl_exit(); return; }
+  const T* S = B.stage2 ? sm : static_cast<const T*>(B.blob) + C.b2;
+  const T* W = S + (size_t)C.nr * B.ns;
+  T* xr = sm + L.p2_xr();
+  T* xw = sm + L.p2_xw();
+  T* part = sm + L.p2_part();
+  T* y = sm + L.p2_y();
+  cta_gemv_rm<T>(S, C.nr, B.ns, B.ns, ys, xr);
+  if (tid < C.nw) xw[tid] = xr[wr];
+  __syncthreads();
+  cta_gemv_cm<T>(W, C.ni, C.ni, C.nw, xw, part, y);
+  if (hi) di.write(B, u, zi - y[tid]);
+  if (ho) dob.write(B, u, xr[ro]);
   pdl_exit();
 }
 
@@ -913,122 +1076,6 @@ __device__ __forceinline__ float dot16(const float4& a, const float* t) {
 __device__ __forceinline__ double dot16(const double2& a, const double* t) {
   const double2 b = *reinterpret_cast<const double2*>(t);
   return a.x * b.x + a.y * b.y;
-}
-
-// The row of the inverse and the row's destinations are setup data: each
-// warp loads the first PFV 16-byte vectors per lane of its row (1536 columns
-// in FP32, 512 in FP64) into registers before waiting on the gather, so
-// after the wait only t and the rest of longer rows are read.  PFV keeps the
-// kernel at two 256-thread CTAs per SM: one wave for blocks of up to 2432
-// cells (304 CTAs of 8 rows on 152 SMs).
-template <class T>
-__global__ void __launch_bounds__(256, 2) k_block_gemv(BlockDev B, T* __restrict__ u) {
-  using V = vec16_t<T>;
-  constexpr int W = 16 / sizeof(T);
-  constexpr int PFV = sizeof(T) == 4 ? 12 : 8;
-  extern __shared__ float4 smem_f4[];
-  T* t = reinterpret_cast<T*>(smem_f4);
-  const T* tg = static_cast<const T*>(B.tblk);
-  const int lane = threadIdx.x & 31;
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int nv = B.ld / W;
-  const V* A = reinterpret_cast<const V*>(static_cast<const T*>(B.ainv) +
-                                          (size_t)min(r, B.m - 1) * B.ld);
-  V a[PFV];
-#pragma unroll
-  for (int j = 0; j < PFV; ++j) {
-    const int c = lane + 32 * j;
-    a[j] = c < nv ? A[c] : V{};
-  }
-  BlockDst dst;
-  if (lane == 0) dst.load(B, r);
-  pdl_enter();
-  for (int c = threadIdx.x; c < B.ld; c += blockDim.x) t[c] = c < B.m ? tg[c] : T(0);
-  __syncthreads();
-  if (r >= B.m) { pdl_exit(); return; }
-  T acc = T(0);
-#pragma unroll
-  for (int j = 0; j < PFV; ++j) {
-    const int c = lane + 32 * j;
-    if (c < nv) acc += dot16(a[j], t + c * W);
-  }
-#pragma unroll 4
-  for (int c = lane + 32 * PFV; c < nv; c += 32) acc += dot16(A[c], t + c * W);
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) dst.write(B, u, acc);
-  pdl_exit();
-}
-
-// ---- a1 + a3 fused: one block-smoother sweep (Def. 5.6) in one launch -------
-// For a block small enough to hold its dense inverse.  The first ntiles CTAs
-// run the Jacobi sweep on 32 x 8 tiles (as k_sweep).  The remaining CTAs solve
-// the block exactly: the block rows couple to a few stencil cells (the
-// frontier) whose new values the sweep is writing at the same time, so each
-// of these CTAs evaluates the Jacobi update of every frontier cell from u_in
-// itself (sweep_point, the same arithmetic), gathers t = b - A(block, rest)
-// u_new in shared memory and applies its share of the rows of inv(A_block).
-// No CTA reads what another writes, so the sweep and the block solve need no
-// grid-wide ordering between them.
-struct FrontierDev {
-  int nq;
-  const int* qcell;        // [nq] grid cell of each frontier cell
-  const int* fptr;         // [m+1] gather rows over frontier indices (CSR, the
-  const int* fidx;         //       term order of block_rhs)
-  const void* fval;        // T
-};
-
-template <class T, bool CROSS>
-__global__ void __launch_bounds__(TX * TY)
-k_smooth(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ b,
-         const uint8_t* __restrict__ cls, const T* __restrict__ ec, StencilP<T> P, int zero,
-         BlockDev B, FrontierDev F, int ntiles) {
-  pdl_enter();
-  const int n = P.n;
-  if ((int)blockIdx.x < ntiles) {
-    __shared__ T s[SY][SX];
-    const int tpr = (n + TX - 1) / TX;
-    const int x0 = (blockIdx.x % tpr) * TX, y0 = (blockIdx.x / tpr) * TY;
-    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-    const int gx = x0 + lx, gy = y0 + ly;
-    const bool in = gx < n && gy < n;
-    const size_t k = (size_t)gy * n + gx;
-    const uint8_t c = in ? cls[k] : (uint8_t)C_EMPTY;
-    const T bv = in ? b[k] : T(0);
-    load_tile<T>(s, u_in, ec, P, x0, y0, zero != 0);
-    __syncthreads();
-    if (c == C_STENCIL) {
-      T Au = apply_A<T, CROSS>(s, P.w, lx, ly);
-      u_out[k] = s[ly + HALO][lx + HALO] + P.omega_over_diag * (bv - Au);
-    }
-    pdl_exit();
-    return;
-  }
-  extern __shared__ unsigned char smem_raw[];
-  T* ut = reinterpret_cast<T*>(smem_raw);   // [nq] new frontier values
-  T* t = ut + F.nq;                         // [m]  gathered right-hand side
-  for (int q = threadIdx.x; q < F.nq; q += blockDim.x) {
-    const int kq = F.qcell[q];
-    ut[q] = sweep_point<T, CROSS>(u_in, ec, b, P, kq % n, kq / n, zero != 0);
-  }
-  __syncthreads();
-  const T* fval = static_cast<const T*>(F.fval);
-  for (int p = threadIdx.x; p < B.m; p += blockDim.x) {
-    T acc = b[B.cell[p]];
-    for (int e = F.fptr[p]; e < F.fptr[p + 1]; ++e) acc -= fval[e] * ut[F.fidx[e]];
-    t[p] = acc;
-  }
-  __syncthreads();
-  const int j = blockIdx.x - ntiles, nb = gridDim.x - ntiles;
-  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int r = j * wpb + (threadIdx.x >> 5); r < B.m; r += nb * wpb) {
-    const T* A = static_cast<const T*>(B.ainv) + (size_t)r * B.ld;
-    T acc = T(0);
-#pragma unroll 4
-    for (int c = lane; c < B.m; c += 32) acc += A[c] * t[c];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) block_write(B, u_out, r, acc);
-  }
-  pdl_exit();
 }
 
 // Dense block solve in one launch: every CTA gathers the whole right-hand

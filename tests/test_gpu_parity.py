@@ -312,7 +312,7 @@ def test_kernel_timing_leaves_the_solve_unchanged():
         H.kernel_timing(which)
         u = torch.zeros_like(u0)
         r = H.solve(ft, gt, u, 1e-12)
-        launches, ms, bytes_per = H.kernel_timing_read()
+        launches, ms, bytes_per, moved = H.kernel_timing_read()
         H.kernel_timing(0)
         assert r.cycles == r0.cycles
         assert torch.equal(u, u0)

@@ -26,8 +26,9 @@ def hier():
         pytest.skip("no CUDA device")
     __graft_entry__.build()
     P = W.problem_disk()
-    # 256^2: the finest level's exact block (about 1200 cells) uses the
-    # chunked solve with scratch vectors, the 128^2 level the dense one
+    # 256^2: the finest level's exact block (1256 cells) takes the chunked
+    # solve, whose temporaries live in the scratch array; the 128^2 level's
+    # block (668 cells) the one-launch dense solve
     return Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 256, default_options(min_coarse_n=16))
 
 
@@ -35,6 +36,8 @@ def hier():
 def test_noalloc_sweep_matches_cc_smooth(hier, level):
     H = hier
     n = H.info.level_n[level]
+    # level 0 takes the chunked branch, level 1 the dense one
+    assert (H.info.block_chunks[level] > 0) == (level == 0), list(H.info.block_chunks[:2])
     typ = None
     if level == 0:
         typ = H.cell_types()[0].ravel() != 0
