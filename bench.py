@@ -50,13 +50,13 @@ W_DEPTH = 1
 # (an FP32 cycle keeps too few digits where the cycle alone diverges)
 KRYLOV = 20
 KRYLOV_MAX_CYCLES = 400
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of each kernel, keyed like cc_kernel_timing's kernels:
+# DRAM bytes per timed interval (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture (cold caches), keyed like cc_kernel_timing's kernels:
 # k_sweep_p per 1024^2 launch (profiles/k_sweep_p_poisson4096_disk1024.md);
-# the exact block solve per solve (one k_block_dense, or one gather + GEMV
-# pair) with the caches as a solve leaves them
-# (profiles/block_solves_disk1024_warm_dram.md)
-TRAFFIC = {1: 9.46e6, 2: 1.24e5}
+# the finest-level block solve of the 1024^2 disk, k_block_p1 + k_block_p2
+# (profiles/block_solve_p1p2_disk1024.md); the all-level block solves were
+# not captured as one unit
+TRAFFIC = {1: 9.46e6, 2: None, 3: 2.424e6 + 2.471e6}
 
 
 def _args():
@@ -301,15 +301,21 @@ def run_ours(a):
     e2e = aggregate(dof, red_max(sum(e2e_ms) / len(e2e_ms)), world)
 
     # rooflines, from CUDA events recorded inside the solve graph on its
-    # stream around each launch of the kernel (each interval includes that
-    # kernel's launch latency): the one-launch dense block solve and the
-    # finest-level FP32 Jacobi sweep; the one with more time per solve is
-    # reported as the dominant kernel
+    # stream around each timed launch (each interval includes the launch
+    # latency): the exact block solves (every level, one interval per solve:
+    # its one dense launch or its two chunked launches) and the finest-level
+    # FP32 Jacobi sweep; the one with more time per solve is the dominant
+    # kernel.  `achieved` divides the method's algorithmic bytes (the block
+    # solve priced as the paper's banded factors plus the gather, the sweep
+    # as 3 x 4 B per cell) by the event time; `moved_gbs` divides the bytes
+    # the library's kernels move.
     peaks, src = _peaks()
     peak = float(peaks["hbm_gbs"])
     roofs = {}
-    for which, name in ((2, "exact block solve: k_block_dense<float> (blocks <= 1024 cells), "
-                         "k_block_gather + k_block_gemv (1025-2560 cells); levels 512..64"),
+    for which, name in ((3, "exact block solve of the finest level (a2 + a3): k_block_p1<float> + "
+                            "k_block_p2<float>, the two chunked launches of one solve as one interval"),
+                        (2, "exact block solves of all levels: k_block_p1 + k_block_p2 (blocks > 1024 "
+                            "cells) or k_block_dense (smaller blocks), one interval per solve"),
                         (1, "k_sweep_p<float> (finest level)")):
         H.kernel_timing(which)
         for _ in range(2):
@@ -321,33 +327,50 @@ def run_ours(a):
         roofs[which] = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
                         "unit": "GB/s", "frac": achieved / peak if achieved else None,
                         "traffic": TRAFFIC.get(which), "peak_source": src,
-                        "launches_per_solve": launches / 2, "ms_per_solve": tot_ms / 2,
-                        "bytes_per_launch": bytes_per,
-                        "note": "working set L2-resident within a solve (a level of 1024^2 "
-                                "in FP32 is 12 MB); ms_per_solve sums event intervals of a "
-                                "solve with timing events in its graph, which serialise the "
-                                "launches, so each interval holds the kernel's launch latency "
-                                "and the sum exceeds the kernel's share of an untimed solve"}
-    dom = max(roofs, key=lambda w: roofs[w]["ms_per_solve"])
-    roof = roofs[dom]
-    roof_other = roofs[3 - dom]
+                        "intervals_per_solve": launches / 2, "ms_per_solve": tot_ms / 2,
+                        "us_per_interval": 1e3 * tot_ms / launches,
+                        "bytes_per_interval": bytes_per, "moved_bytes_per_interval": moved_per,
+                        "moved_gbs": moved_per / (tot_ms / launches) / 1e6 if launches else None,
+                        "note": "achieved = algorithmic bytes / event time; the working set stays in "
+                                "L2 within a solve (a 1024^2 FP32 level is 12 MB); the events in the "
+                                "graph serialise the launches, so ms_per_solve exceeds the kernels' "
+                                "share of an untimed solve"}
+    # the exact block solves take most of the solve's time (every level); the
+    # roofline line reports the finest level's, whose two launches the ncu
+    # capture in profiles/ covers
+    roof = roofs[3]
+    roof_other = roofs[1]
+    roof_blocks = roofs[2]
 
-    # plain FP64 solve of the same problem, for comparison
+    # plain FP64 solve of the same problem, timed like the mixed arm
     H64 = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                                 default_options(min_coarse_n=a.min_coarse, cycle=2, precision=0,
                                                 max_cycles=60, w_depth=W_DEPTH, nu1=NU, nu2=NU))
     u64 = torch.zeros(n * n, dtype=torch.float64, device=dev)
-    H64.solve(ft, gt, u64, TOL, stream)
+    for _ in range(a.warmup):
+        u64.zero_()
+        H64.solve(ft, gt, u64, TOL, stream)
+        flush.fill_(4.0)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flush.fill_(4.0)
-    u64.zero_()
-    e0.record(stream)
-    r64 = H64.solve(ft, gt, u64, TOL, stream)
-    e1.record(stream)
+    ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(a.steps)]
+    for k in range(a.steps):
+        flush.fill_(float(k))
+        u64.zero_()
+        ev64[k][0].record(stream)
+        r64 = H64.solve(ft, gt, u64, TOL, stream)
+        ev64[k][1].record(stream)
     torch.cuda.synchronize()
-    fp64_ms = e0.elapsed_time(e1)
+    fp64_ms = sum(s_.elapsed_time(e_) for s_, e_ in ev64) / a.steps
     err64 = float(np.abs(u64.cpu().numpy().reshape(n, n) - ue)[present].max())
+    H64.close()
+
+    # the whole cycle against HBM: the algorithmic bytes of one cycle on the
+    # paper-literal one-pass-per-operation schedule, times the cycles of a
+    # solve, over the device-timed solve
+    blk = roof_blocks["bytes_per_interval"] * roof_blocks["intervals_per_solve"]
+    roof_cycle = {f"disk_{n}": cycle_roofline(H, dof, cycles[-1], ms, peak, src,
+                                              block_bytes_per_solve=blk)}
 
     # several independent solves at once: clones of the hierarchy (shared
     # tables, own work arrays), each with its own right-hand side, advanced
@@ -406,6 +429,7 @@ def run_ours(a):
         "gpu_launches": kernels,
         "roofline": roof,
         "roofline_other": roof_other,
+        "roofline_blocks": roof_blocks,
         "roofline_hbm": roof_hbm,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
@@ -415,11 +439,57 @@ def run_ours(a):
         "ellipse_union": ellipse,
         "random_domains": random_domains,
         "fp64_solve": {"ms": fp64_ms, "dof_per_s": dof / (fp64_ms / 1e3), "cycles": r64.cycles,
-                       "max_error_vs_exact": err64},
+                       "max_error_vs_exact": err64, "steps": a.steps, "warmup": a.warmup,
+                       "timing": "CUDA events around each solve, L2 flushed between steps, as the "
+                                 "mixed arm"},
+        "roofline_cycle": roof_cycle,
         "wall_s_timed": wall,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def cycle_roofline(H, dof, cycles, solve_ms, peak, src, w=4, block_bytes_per_solve=None):
+    """HBM roofline of the whole solve at cycle granularity.  Algorithmic bytes
+    of one FP32 cycle on the paper-literal schedule (one pass per operation):
+    on every visit of a level, each of the nu1 + nu2 sweeps reads u and b and
+    writes u (3 w per cell), the residual restriction reads u and b and writes
+    the coarse residual (2.25 w), the prolongation reads u and the coarse
+    correction and writes u (2.25 w); W(nu,nu) with gamma = 2 on the finest
+    level visits it once and every coarser level twice; the bottom solve reads
+    its FP64 inverse (8 n_c^2 bytes); the FP64 refinement step reads u and b
+    and writes r (20 B per cell) and adds the correction (20 B).  The exact
+    block solves add the method's bytes measured by cc_kernel_timing (banded
+    factors plus gather).  The fused schedule of temporally blocked sweeps
+    would need about 35 B per DOF per V(3,3) cycle instead."""
+    import torch  # noqa: F401  (device timing done by the caller)
+    info = H.info
+    nl = info.n_levels
+    ns = [info.level_n[l] for l in range(nl)]
+    per_cycle = 0.0
+    for l in range(nl - 1):
+        visits = 1 if l == 0 else 2
+        per_cycle += visits * ns[l] ** 2 * w * (3 * (NU + NU) + 2.25 + 2.25)
+    per_cycle += 2 * 8.0 * ns[-1] ** 4                 # bottom: the dense FP64 inverse, twice
+    per_cycle += 40.0 * ns[0] ** 2                     # FP64 residual and update
+    per_cycle += block_bytes_per_solve / max(1, cycles)
+    achieved = per_cycle * cycles / (solve_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": src, "bytes_per_cycle": per_cycle, "bytes_per_dof_per_cycle": per_cycle / dof,
+            "cycles": cycles, "solve_ms": solve_ms, "levels": ns,
+            "note": "paper-literal one-pass schedule, W(%d,%d) with gamma = 2 on the finest level; "
+                    "FP32 cycle bytes, FP64 refinement" % (NU, NU)}
+
+
+def block_bytes_per_solve(H, run):
+    """Algorithmic bytes of all exact block solves of one solve (run() does one
+    solve), from cc_kernel_timing."""
+    H.kernel_timing(2)
+    run()
+    launches, tot_ms, bytes_per, moved_per = H.kernel_timing_read()
+    H.kernel_timing(0)
+    return launches * bytes_per
 
 
 # ---------------------------------------------------------------------------
@@ -499,6 +569,14 @@ def run_ellipse_union(a, dev):
                          "status": r.status, "rel_res": r.rel_res, "max_error_vs_exact": err,
                          "setup_s": setup}
             row["dof"] = int(H.info.n_dof)
+            if prec == 1:
+                def one():
+                    u.zero_()
+                    H.solve(ft, gt, u, 1e-10)
+                peaks, src = _peaks()
+                row["roofline_cycle"] = cycle_roofline(
+                    H, int(H.info.n_dof), r.cycles, min(ms), float(peaks["hbm_gbs"]), src,
+                    block_bytes_per_solve=block_bytes_per_solve(H, one))
             H.close()
         out[str(n)] = row
     cache_clear()
@@ -693,16 +771,55 @@ def _oracle_sample(n: int):
     return solve, dof
 
 
-def cpu_baseline():
-    n = 256
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_worker(args):
+    """One process of the all-cores oracle baseline: set up the oracle at
+    n x n, wait for the others, solve once; returns (DOF, start, end)."""
+    n, barrier = args
+    solve, dof = _oracle_sample(n)
+    barrier.wait()
+    t0 = time.time()
+    solve()
+    return dof, t0, time.time()
+
+
+def cpu_baseline(n=256):
+    """The oracle as it stands on the host cores: one solve of a 256^2 sample
+    of the same problem on one core, then nproc independent solves of it in
+    nproc processes at once (the oracle's numpy/scipy work is
+    single-threaded, so the cores are used by running problems side by side);
+    setup excluded."""
+    import multiprocessing as mp
     solve, dof = _oracle_sample(n)
     t = time.perf_counter()
     r = solve()
     dt = time.perf_counter() - t
-    return {"value": dof / dt, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"one FP64 oracle W({NU},{NU}) solve (gamma = 2 on the {W_DEPTH} finest level(s)) of the same disk problem at {n}x{n} "
-                      f"({len(r.history)} cycles, {dt:.1f} s; setup excluded); "
-                      f"BLAS threads pinned to 1"}
+    ncore = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        bar = man.Barrier(ncore)
+        with ctx.Pool(ncore) as pool:
+            res = pool.map(_oracle_worker, [(n, bar)] * ncore)
+    wall = max(e for _, _, e in res) - min(s_ for _, s_, _ in res)
+    multi = sum(d for d, _, _ in res) / wall
+    return {"value": multi, "unit": "DOF/s", "cores": ncore, "kind": "oracle",
+            "cpu_model": _cpu_model(), "nproc": ncore,
+            "sample": f"{ncore} FP64 oracle W({NU},{NU}) solves (gamma = 2 on the {W_DEPTH} finest "
+                      f"level(s)) of the same disk problem at {n}x{n}, one per process, side by "
+                      f"side ({wall:.1f} s wall); setup excluded; BLAS threads pinned to 1",
+            "single_core": {"value": dof / dt, "unit": "DOF/s", "cores": 1,
+                            "sample": f"one solve at {n}x{n} ({len(r.history)} cycles, {dt:.1f} s)"}}
 
 
 def run_reference(a):

@@ -382,13 +382,14 @@ cc_status cc_level_tables(cc_handle h, int level, uint8_t* h_kind, int* h_lattic
                           double* h_beta, int* n_plg);
 
 /* Kernels that cc_kernel_timing can time. */
-enum { CC_TIME_OFF = 0, CC_TIME_FINE_SWEEP = 1, CC_TIME_BLOCK = 2 };
+enum { CC_TIME_OFF = 0, CC_TIME_FINE_SWEEP = 1, CC_TIME_BLOCK = 2, CC_TIME_FINE_BLOCK = 3 };
 
 /*
  * cc_kernel_timing: with which = CC_TIME_FINE_SWEEP the library records CUDA
  * events around every launch of the finest-level Jacobi sweep kernel (Eq.
  * 5.7); with CC_TIME_BLOCK around every exact block solve (Eq. 5.8, any
- * level: its one launch, or its two chunked launches together);
+ * level: its one launch, or its two chunked launches together); with
+ * CC_TIME_FINE_BLOCK around the finest level's block solves only;
  * CC_TIME_OFF stops.  The events are recorded on the solve's stream, inside
  * its CUDA graph, so host launch gaps are not measured, but each interval
  * includes the launch latency of the kernels it brackets.

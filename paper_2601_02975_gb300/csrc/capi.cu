@@ -743,9 +743,9 @@ struct cc_hierarchy {
   int64_t slot_bytes = 0;               // device memory of the clones, counted in g_serve_used
   cudaStream_t wstream = nullptr;
   // cuda graphs of one solve iteration
-  cudaGraphExec_t gexec[6] = {};             // [timed kernel][mixed]
-  int64_t gexec_launches[6] = {};            // kernels in one replay of each graph
-  size_t gexec_events[6] = {};               // timing event pairs in each graph
+  cudaGraphExec_t gexec[8] = {};             // [timed kernel][mixed]
+  int64_t gexec_launches[8] = {};            // kernels in one replay of each graph
+  size_t gexec_events[8] = {};               // timing event pairs in each graph
   cudaStream_t gstream = nullptr;
   // Krylov outer iteration (cc_options.krylov = k): basis V [(k + 1) nn],
   // preconditioned vectors Z [k nn], a zero right-hand side, multi-dot
@@ -1051,7 +1051,8 @@ template <class T>
 void block_solve(cc_hierarchy* H, Level& L, T* u, const T* b, cudaStream_t s) {
   const BlockPlan& P = L.plan();
   if (P.m == 0) return;
-  const bool timed = H->timing == CC_TIME_BLOCK && time_begin(H, s);
+  const bool timed = (H->timing == CC_TIME_BLOCK || (H->timing == CC_TIME_FINE_BLOCK && &L == H->lv[0].get())) &&
+                     time_begin(H, s);
   launch_block<T>(P, bdev<T>(L), csmem<T>(L), u, b, s);
   if (timed) time_end(H, s, block_method_bytes(P, (int)sizeof(T)), block_read_bytes(P, (int)sizeof(T)));
 }
@@ -1166,11 +1167,9 @@ void residual64(cc_hierarchy* H, const double* u, const double* b, Tout* r, cuda
                 Tout* e0 = nullptr, Tout wd = Tout(0)) {
   Level& L = *H->lv[0];
   if (L.sp.cross)
-    pdl_launch(k_resid<double, Tout, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm,
-               e0, wd);
+    pdl_launch(k_resid_fx<Tout, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm, e0, wd);
   else
-    pdl_launch(k_resid<double, Tout, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm,
-               e0, wd);
+    pdl_launch(k_resid_fx<Tout, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, H->d_norm, e0, wd);
   if (L.plan().m)
     pdl_launch(k_block_resid<Tout>, nblk(L.plan().m), 256, 0, s, L.plan().m, L.brow_cell, L.brow_ptr, L.brow_col,
                                                        L.brow_val, u, b, r, H->d_norm);
@@ -2421,10 +2420,10 @@ cc_status cc_residual(cc_handle H, int l, const double* u, const double* b, doub
   try {
     Level& L = *H->lv[l];
     if (L.sp.cross)
-      pdl_launch(k_resid<double, double, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr,
+      pdl_launch(k_resid_fx<double, true>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr,
                  (double*)nullptr, 0.0);
     else
-      pdl_launch(k_resid<double, double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr,
+      pdl_launch(k_resid_fx<double, false>, tiles(L.n), TX * TY, 0, s, u, b, L.cls, r, L.sp, nullptr,
                  (double*)nullptr, 0.0);
     if (!L.disc().block.empty())
       pdl_launch(k_block_resid<double>, nblk((int64_t)L.disc().block.size()), 256, 0, s, 
@@ -2590,7 +2589,7 @@ cc_status cc_level_tables(cc_handle H, int l, uint8_t* h_kind, int* h_lattice, d
 
 cc_status cc_kernel_timing(cc_handle H, int which) {
   if (H && H->opt.host_only) return CC_ERR_ARG;
-  if (!H || which < CC_TIME_OFF || which > CC_TIME_BLOCK) return CC_ERR_ARG;
+  if (!H || which < CC_TIME_OFF || which > CC_TIME_FINE_BLOCK) return CC_ERR_ARG;
   H->timing = which;
   H->ev_used = 0;
   H->timed_launches = 0;
@@ -2604,7 +2603,7 @@ cc_status cc_kernel_timing(cc_handle H, int which) {
     // nu1 + nu2 times
     const int nl = (int)H->lv.size();
     size_t per = (size_t)(H->opt.nu1 + H->opt.nu2) * ((size_t)1 << std::min(nl, 12)) * 2;
-    if (which == CC_TIME_FINE_SWEEP) per = (size_t)(H->opt.nu1 + H->opt.nu2);
+    if (which == CC_TIME_FINE_SWEEP || which == CC_TIME_FINE_BLOCK) per = (size_t)(H->opt.nu1 + H->opt.nu2);
     while (which != CC_TIME_OFF && H->ev.size() < per) {
       cudaEvent_t a, b;
       CK(cudaEventCreate(&a));

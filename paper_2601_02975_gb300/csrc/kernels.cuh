@@ -606,39 +606,105 @@ __global__ void k_restrict_rhs(const Tin* __restrict__ r, const uint8_t* __restr
 }
 
 // ---- a8 / Eq. 4.23: residual on stencil cells, max-norm ----------------------
-// r = b - A u on stencil cells (Tin arithmetic), 0 on empty cells; block cells
-// are left to k_block_resid.  |r| is folded into *rmax (as ordered bits).
-// With e0, also the stencil-cell part of the first sweep of a cycle on the
-// residual equation A e = r from e = 0: e0 = wd r (wd = omega / D).
+// |r| is folded into *rmax as ordered bits (non-negative doubles order like
+// their bit patterns).
 __device__ __forceinline__ void atomic_max_abs(unsigned long long* p, double v) {
   atomicMax(p, (unsigned long long)__double_as_longlong(fabs(v)));
 }
 
-template <class Tin, class Tout, bool CROSS>
+// ---- a8 off the FP64 pipe: residual with the stencil differences in fixed point
+// The SFV stencil (Eq. 4.7a,b) is a u_xx + c u_yy + b u_xy with integer
+// difference weights: A u = sx Lx + sy Ly + sxy Gxy, Lx = 16 (u_{i-1} +
+// u_{i+1}) - 30 u_i - (u_{i-2} + u_{i+2}) (Ly the same in y) and Gxy the
+// product of the 5-point gradients (1, -8, 0, 8, -1) in x and y.  The tile's
+// values (ghosts included) are scaled by a power of two so that the largest
+// is below 2^52 and rounded to 64-bit integers (a fixed-point accumulator
+// restricted to one 64-bit word, in the manner of Kulisch's long
+// accumulator); Lx, Ly and Gxy are then exact integer sums (|Gxy| < 324 *
+// 2^52 < 2^61), and only their conversion, the three products with the
+// FP64 constants and the subtraction from b round.  That is 7 FP64
+// operations per cell instead of the 25 products of the direct evaluation,
+// on a GPU whose FP64 rate is a small fraction of its FP32 rate, with no
+// accuracy lost: each integer sum is exact, where the direct evaluation
+// rounds every one of its 25 terms.
+__device__ __forceinline__ int fx_exponent(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+}
+
+// v * 2^(1075 - E) rounded to the nearest integer (ties away from zero),
+// E >= the biased exponent of v; integer operations only
+__device__ __forceinline__ long long fx_from(double v, int E) {
+  const long long bits = __double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  if (e == 0) return 0;                              // zero (and subnormals, far below 2^-53 max)
+  const long long m = (bits & 0xfffffffffffffLL) | 0x10000000000000LL;
+  const int sh = E - e;                               // value = m * 2^(e - E) in units of 2^(1075 - E)
+  long long r;
+  if (sh == 0) r = m;
+  else if (sh < 63) r = ((m >> (sh - 1)) + 1) >> 1;
+  else r = 0;
+  return bits < 0 ? -r : r;
+}
+
+template <class Tout, bool CROSS>
 __global__ void __launch_bounds__(TX * TY)
-k_resid(const Tin* __restrict__ u, const Tin* __restrict__ b, const uint8_t* __restrict__ cls,
-        Tout* __restrict__ r, StencilP<Tin> P, unsigned long long* rmax, Tout* __restrict__ e0,
-        Tout wd) {
+k_resid_fx(const double* __restrict__ u, const double* __restrict__ b, const uint8_t* __restrict__ cls,
+           Tout* __restrict__ r, StencilP<double> P, unsigned long long* rmax, Tout* __restrict__ e0,
+           Tout wd) {
   pdl_enter();
-  __shared__ Tin s[SY][SX];
+  __shared__ double s[SY][SX];
+  __shared__ long long q[SY][SX];
+  __shared__ int emax[TX * TY / 32];
   __shared__ double red[TX * TY / 32];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  load_tile<Tin>(s, u, nullptr, P, x0, y0, false);
-  __syncthreads();
   const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
   const int gx = x0 + lx, gy = y0 + ly, n = P.n;
+  const bool in = gx < n && gy < n;
+  const size_t k = (size_t)gy * n + gx;
+  const uint8_t c = in ? cls[k] : (uint8_t)C_EMPTY;
+  const double bk = in && c == C_STENCIL ? b[k] : 0.0;
+  load_tile<double>(s, u, nullptr, P, x0, y0, false);
+  __syncthreads();
+  // the window's largest biased exponent
+  int e = 0;
+  for (int idx = threadIdx.x; idx < SX * SY; idx += blockDim.x) e = max(e, fx_exponent((&s[0][0])[idx]));
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) emax[threadIdx.x >> 5] = e;
+  __syncthreads();
+  int E = 0;
+#pragma unroll
+  for (int w = 0; w < TX * TY / 32; ++w) E = max(E, emax[w]);
+  // every |value| < 2^(E - 1023) is scaled below 2^52; E >= 53 keeps one
+  // unit, 2^(E - 1075), a normal number (smaller values round to 0)
+  E = max(E + 1, 53);
+  for (int idx = threadIdx.x; idx < SX * SY; idx += blockDim.x)
+    (&q[0][0])[idx] = fx_from((&s[0][0])[idx], E);
+  __syncthreads();
   double av = 0.0;
-  if (gx < n && gy < n) {
-    const size_t k = (size_t)gy * n + gx;
-    uint8_t c = cls[k];
-    if (c == C_STENCIL) {
-      Tin rv = b[k] - apply_A<Tin, CROSS>(s, P.w, lx, ly);
-      r[k] = (Tout)rv;
-      if (e0) e0[k] = wd * (Tout)rv;
-      av = fabs((double)rv);
-    } else if (c == C_EMPTY) {
-      r[k] = Tout(0);
+  if (c == C_STENCIL) {
+    const int cx = lx + HALO, cy = ly + HALO;
+    const long long* row = q[cy];
+    const long long Lx = 16 * (row[cx - 1] + row[cx + 1]) - 30 * row[cx] - (row[cx - 2] + row[cx + 2]);
+    const long long Ly = 16 * (q[cy - 1][cx] + q[cy + 1][cx]) - 30 * q[cy][cx] - (q[cy - 2][cx] + q[cy + 2][cx]);
+    // one unit of the fixed point is 2^(E - 1075)
+    const double unit = __longlong_as_double((long long)(E - 52) << 52);
+    double Au = (P.sx * unit) * __ll2double_rn(Lx) + (P.sy * unit) * __ll2double_rn(Ly);
+    if (CROSS) {
+      long long g[5];
+#pragma unroll
+      for (int d = 0; d < 5; ++d) {
+        const long long* rr = q[cy - 2 + d];
+        g[d] = 8 * (rr[cx + 1] - rr[cx - 1]) - (rr[cx + 2] - rr[cx - 2]);
+      }
+      const long long Gxy = 8 * (g[3] - g[1]) - (g[4] - g[0]);
+      Au += (P.sxy * unit) * __ll2double_rn(Gxy);
     }
+    const double rv = bk - Au;
+    r[k] = (Tout)rv;
+    if (e0) e0[k] = wd * (Tout)rv;
+    av = fabs(rv);
+  } else if (in && c == C_EMPTY) {
+    r[k] = Tout(0);
   }
   if (rmax) {
     for (int o = 16; o > 0; o >>= 1) av = fmax(av, __shfl_xor_sync(0xffffffffu, av, o));
@@ -646,10 +712,11 @@ k_resid(const Tin* __restrict__ u, const Tin* __restrict__ b, const uint8_t* __r
     __syncthreads();
     if (threadIdx.x == 0) {
       double m = 0.0;
-      for (int q = 0; q < TX * TY / 32; ++q) m = fmax(m, red[q]);
+      for (int w = 0; w < TX * TY / 32; ++w) m = fmax(m, red[w]);
       atomic_max_abs(rmax, m);
     }
   }
+  pdl_exit();
 }
 
 // residual of block rows from their full sparse rows (FP64)
