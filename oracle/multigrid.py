@@ -9,7 +9,8 @@
                SFV unknowns with the old PLG values (Eq. 5.7), then the exact
                solve L22 U22 u2 = b2 - A21 u1 (Eq. 5.8).  D11 is the constant
                centre weight of the SFV stencil (the reading that reproduces
-               Table 2).
+               Table 2).  A variant outside the paper replaces the Jacobi step
+               by multicolour Gauss-Seidel (colours, smoother = "mcgs").
   restrict     Eq. 5.10: the average of the 4 children; the residual of the
                exactly solved cells is 0 after a sweep (Sec. 5.3) and is
                taken as exactly 0.
@@ -156,6 +157,7 @@ class Hierarchy:
     lus: List[A22LU]
     bottom: np.ndarray               # dense inverse-free: LU factors via numpy solve
     omega: float = 0.5
+    smoother: str = "jacobi"         # "jacobi" (Def. 5.6) or "mcgs" (the multicolour variant)
 
     @property
     def nl(self):
@@ -165,7 +167,7 @@ class Hierarchy:
 def build_hierarchy(dom: Domain, n: int, a: float, b: float, c: float,
                     eps: float = 0.1, min_coarse: int = 4,
                     max_levels: int = 32, omega: float = 0.5,
-                    hole_cells: float = 2.0) -> Hierarchy:
+                    hole_cells: float = 2.0, smoother: str = "jacobi") -> Hierarchy:
     """Eq. 5.9: rediscretise every level h_f 2^l; the coarsest level is the
     smallest N >= min_coarse reached by halving while every level resolves
     the domain: single-component cut cells (Alg. 1 precondition), every hole
@@ -194,7 +196,7 @@ def build_hierarchy(dom: Domain, n: int, a: float, b: float, c: float,
         nl //= 2
     lus = [A22LU(d) for d in levels]
     bottom = levels[-1].A.toarray()
-    return Hierarchy(levels, lus, bottom, omega)
+    return Hierarchy(levels, lus, bottom, omega, smoother)
 
 
 def residual(d: D.Disc, u: np.ndarray, b: np.ndarray) -> np.ndarray:
@@ -202,16 +204,44 @@ def residual(d: D.Disc, u: np.ndarray, b: np.ndarray) -> np.ndarray:
     return (b.ravel() - d.A @ u.ravel()).reshape(u.shape)
 
 
+def colours(d: D.Disc) -> np.ndarray:
+    """Colour classes of the cells for the multicolour Gauss-Seidel variant, so
+    that no two SFV cells of one class are coupled.  A row couples to the
+    cells its stencil (Eq. 4.7a,b) reaches and, next to a box wall, to the
+    four inward cells each ghost value is formed from (Sec. 4.1), up to 3
+    cells from the row's own along the wall normal.  With b = 0 the couplings
+    are along the axes, up to 3 cells, and the 4 classes (i + j) mod 4
+    separate them; with b != 0 they are the 5 x 5 box plus offsets (3, t) and
+    (t, 3), |t| <= 2, and the 15 classes (i + 4 j) mod 15 do (the smallest
+    such colouring of the form (i + k j) mod m)."""
+    n = d.n
+    j, i = np.mgrid[0:n, 0:n]
+    if d.b == 0.0:
+        return (i + j) % 4
+    return (i + 4 * j) % 15
+
+
 def smooth(H: Hierarchy, l: int, u: np.ndarray, b: np.ndarray) -> np.ndarray:
-    """One sweep of the block smoother T_omega (Def. 5.6, Eq. 5.7-5.8)."""
+    """One sweep of the block smoother T_omega (Def. 5.6, Eq. 5.7-5.8), or of
+    its multicolour variant: the SFV unknowns relaxed colour by colour, each
+    class with the latest values of the others (u_i += omega r_i / D), then
+    the same exact block solve."""
     d, lu = H.levels[l], H.lus[l]
     blk = np.zeros(d.n * d.n, dtype=bool)
     blk[lu.order] = True
     jac = (d.kind.ravel() == D.SFV) & ~blk
     uf = u.ravel()
-    r = b.ravel() - d.A @ uf
-    un = uf.copy()
-    un[jac] = uf[jac] + H.omega * r[jac] / d.diag
+    if H.smoother == "mcgs":
+        col = colours(d).ravel()
+        un = uf.copy()
+        for c in range(int(col.max()) + 1):
+            m = jac & (col == c)
+            r = b.ravel() - d.A @ un
+            un[m] = un[m] + H.omega * r[m] / d.diag
+    else:
+        r = b.ravel() - d.A @ uf
+        un = uf.copy()
+        un[jac] = uf[jac] + H.omega * r[jac] / d.diag
     if lu.m:
         u1 = un.copy()
         u1[blk] = 0.0
