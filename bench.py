@@ -77,6 +77,8 @@ def _args():
                     help="grids of the ellipse-union measurement (none: skip)")
     ap.add_argument("--hbm-n", type=int, default=4096,
                     help="grid of the HBM-bound sweep measurement (0: skip)")
+    ap.add_argument("--mcgs", type=int, default=1,
+                    help="also time the headline problem with the multicolour smoother (0: skip)")
     ap.add_argument("--batch", type=int, default=8,
                     help="independent solves in the concurrent-batch measurement (0: skip)")
     ap.add_argument("--min-coarse", type=int, default=MIN_COARSE,
@@ -408,6 +410,7 @@ def run_ours(a):
     roof_hbm = hbm_sweep(a, dev, peak, src) if a.hbm_n > 0 else None
     ellipse = run_ellipse_union(a, dev) if a.ellipse_union else None
     random_domains = run_random_domains(a, dev) if a.random_domains > 0 else None
+    mcgs = run_mcgs(a, dev) if a.mcgs else None
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -438,6 +441,7 @@ def run_ours(a):
         "serving": serving,
         "ellipse_union": ellipse,
         "random_domains": random_domains,
+        "multicolour_smoother": mcgs,
         "fp64_solve": {"ms": fp64_ms, "dof_per_s": dof / (fp64_ms / 1e3), "cycles": r64.cycles,
                        "max_error_vs_exact": err64, "steps": a.steps, "warmup": a.warmup,
                        "timing": "CUDA events around each solve, L2 flushed between steps, as the "
@@ -581,6 +585,48 @@ def run_ellipse_union(a, dev):
         out[str(n)] = row
     cache_clear()
     return out
+
+
+def run_mcgs(a, dev, nu=2):
+    """The headline problem (1024^2 disk, mixed precision, W cycles with gamma
+    = 2 on the finest level, tol 1e-13) with the multicolour Gauss-Seidel
+    variant of the smoother (outside the paper; omega 0.6, nu1 = nu2 = 2,
+    15 colour classes since b != 0), timed like the main arm."""
+    import numpy as np
+    import torch
+    from paper_2601_02975_gb300 import SMOOTHER_MCGS, Hierarchy, default_options
+    from paper_2601_02975_gb300 import inputs as I
+    P = _problem()
+    n = a.n
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                              default_options(min_coarse_n=a.min_coarse, cycle=2, precision=1, max_cycles=80,
+                                              w_depth=W_DEPTH, nu1=nu, nu2=nu, smoother=SMOOTHER_MCGS,
+                                              omega=0.6))
+    f, g, ue = I.problem_inputs(H, P)
+    present = H.cell_types()[0] != 0
+    ft = torch.tensor(f.ravel(), dtype=torch.float64, device=dev)
+    gt = torch.tensor(g, dtype=torch.float64, device=dev)
+    u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        u.zero_()
+        r = H.solve(ft, gt, u, TOL)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(3):
+        u.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = H.solve(ft, gt, u, TOL)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    err = float(np.abs(u.cpu().numpy().reshape(n, n) - ue)[present].max())
+    dof = int(H.info.n_dof)
+    H.close()
+    return {"workload": f"the headline disk problem at {n}x{n}, mixed, W({nu},{nu}) with gamma = 2 on the "
+                        "finest level, multicolour smoother (15 classes, omega 0.6), tol 1e-13",
+            "ms": min(ms), "dof_per_s": dof / (min(ms) / 1e3), "cycles": r.cycles, "status": r.status,
+            "rel_res": r.rel_res, "kernels": r.kernels, "max_error_vs_exact": err}
 
 
 def run_random_domains(a, dev):

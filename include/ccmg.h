@@ -61,6 +61,7 @@ enum { CC_HOLE_ELLIPSE = 0 };
 enum { CC_BC_DIRICHLET = 0, CC_BC_NEUMANN = 1, CC_BC_ROBIN = 2 };
 enum { CC_CYCLE_V = 1, CC_CYCLE_W = 2, CC_CYCLE_FMG = 3 };
 enum { CC_PREC_FP64 = 0, CC_PREC_MIXED = 1 };
+enum { CC_SMOOTHER_JACOBI = 0, CC_SMOOTHER_MCGS = 1 };
 
 /* An elliptic hole: centre (cx, cy), semi-axes r1, r2, rotation theta (rad). */
 typedef struct { int kind; double cx, cy, r1, r2, theta; } cc_hole;
@@ -121,6 +122,16 @@ typedef struct {
                           cycle keeps too few digits of the rest: use CC_PREC_FP64
                           there.  The handle holds 2k + 4 extra FP64 vectors of the
                           finest grid */
+  int smoother;        /* CC_SMOOTHER_JACOBI (default): the block smoother of Def. 5.6,
+                          weighted Jacobi on the SFV cells, then the exact block solve.
+                          CC_SMOOTHER_MCGS: a variant outside the paper, the SFV cells
+                          relaxed colour class by colour class with the latest values
+                          of the others (4 classes (i + j) mod 4 for b = 0, 15 classes
+                          (i + 4 j) mod 15 otherwise, one in-place launch each), then
+                          the same exact block solve; omega 0.6 suits it (the
+                          two-grid rate of 2 + 2 sweeps is then about that of the
+                          Jacobi smoother's 3 + 3), and omega 1 diverges on this
+                          fourth-order stencil */
 } cc_options;
 
 /* Sizes of a hierarchy. */

@@ -19,6 +19,7 @@ CC_OK, CC_ERR_ARG, CC_ERR_GEOMETRY, CC_ERR_SINGULAR, CC_ERR_NO_MEMORY = 0, 1, 2,
 CC_ERR_NOT_CONVERGED, CC_ERR_DIVERGED, CC_ERR_TIMEOUT, CC_ERR_CUDA, CC_ERR_BUSY = 5, 6, 7, 8, 9
 CYCLE_V, CYCLE_W, CYCLE_FMG = 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
+SMOOTHER_JACOBI, SMOOTHER_MCGS = 0, 1
 
 
 class cc_hole(C.Structure):
@@ -40,7 +41,8 @@ class cc_options(C.Structure):
                 ("cycle", C.c_int), ("min_coarse_n", C.c_int), ("precision", C.c_int),
                 ("max_cycles", C.c_int), ("use_graphs", C.c_int), ("host_only", C.c_int),
                 ("fmg_cycle", C.c_int), ("w_depth", C.c_int), ("serve_slots", C.c_int),
-                ("cache", C.c_int), ("hole_cells", C.c_double), ("krylov", C.c_int)]
+                ("cache", C.c_int), ("hole_cells", C.c_double), ("krylov", C.c_int),
+                ("smoother", C.c_int)]
 
 
 class cc_info(C.Structure):

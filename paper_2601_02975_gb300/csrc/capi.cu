@@ -1057,9 +1057,33 @@ void block_solve(cc_hierarchy* H, Level& L, T* u, const T* b, cudaStream_t s) {
   if (timed) time_end(H, s, block_method_bytes(P, (int)sizeof(T)), block_read_bytes(P, (int)sizeof(T)));
 }
 
+// the multicolour variant's sweep, in place on u: the initial guess (0, or u
+// plus the interpolated coarse correction), the colour classes in order, then
+// the exact block solve
+template <class T>
+void color_passes(Level& L, T* u, const T* b, cudaStream_t s) {
+  const bool cross = L.sp.cross != 0;
+  for (int c = 0; c < mc_colors(cross); ++c) {
+    if (cross) pdl_launch(k_sweep_color<T, true>, tiles(L.n), TX * TY, 0, s, u, b, (const uint8_t*)L.cls, sparams<T>(L), c);
+    else pdl_launch(k_sweep_color<T, false>, tiles(L.n), TX * TY, 0, s, u, b, (const uint8_t*)L.cls, sparams<T>(L), c);
+  }
+}
+
+template <class T>
+void sweep_mc(cc_hierarchy* H, Level& L, T* u, bool zero, const T* ec, cudaStream_t s) {
+  if (zero) CK(cudaMemsetAsync(u, 0, L.nn * sizeof(T), s));
+  if (ec) pdl_launch(k_prolong_add<T>, nblk(L.nn), 256, 0, s, u, ec, L.cls, L.n);
+  color_passes<T>(L, u, (const T*)bbuf<T>(L), s);
+  block_solve<T>(H, L, u, bbuf<T>(L), s);
+}
+
 template <class T>
 void sweep(cc_hierarchy* H, int l, int& cur, bool zero, const T* ec, cudaStream_t s) {
   Level& L = *H->lv[l];
+  if (H->opt.smoother == CC_SMOOTHER_MCGS) {
+    sweep_mc<T>(H, L, ubuf<T>(L, cur), zero, ec, s);
+    return;
+  }
   T* in = ubuf<T>(L, cur);
   T* out = ubuf<T>(L, 1 - cur);
   const bool timed = H->timing == CC_TIME_FINE_SWEEP && l == 0 && time_begin(H, s);
@@ -1127,7 +1151,7 @@ void cycle_level(cc_hierarchy* H, int l, std::vector<int>& cur, bool zero, cudaS
   Level& C = *H->lv[l + 1];
   // the coarse level's first visit starts from zero: its first sweep is
   // written by the restriction kernel (not on the bottom level, which has none)
-  const bool fuse_c = l + 1 < nl - 1 && nu1 > 0;
+  const bool fuse_c = l + 1 < nl - 1 && nu1 > 0 && H->opt.smoother == CC_SMOOTHER_JACOBI;
   T* uc = fuse_c ? ubuf<T>(C, 1 - cur[l + 1]) : nullptr;
   const T wd_c = sparams<T>(C).omega_over_diag;
   if (L.sp.cross)
@@ -1210,7 +1234,8 @@ void fmg_below(cc_hierarchy* H, int l0, std::vector<int>& cur, cudaStream_t s) {
 // starts in buffer 0) when that cycle has a pre-sweep on the finest level
 // from a zero initial guess (not in Alg. 3, which starts it from I(e)).
 bool mixed_pre(cc_hierarchy* H) {
-  return H->opt.nu1 > 0 && H->lv.size() > 1 && H->opt.cycle != CC_CYCLE_FMG;
+  return H->opt.nu1 > 0 && H->lv.size() > 1 && H->opt.cycle != CC_CYCLE_FMG &&
+         H->opt.smoother == CC_SMOOTHER_JACOBI;
 }
 float* mixed_e0(cc_hierarchy* H) { return mixed_pre(H) ? H->lv[0]->u32[1] : nullptr; }
 
@@ -1855,6 +1880,7 @@ void cc_default_options(cc_options* o) {
   o->cache = 0;
   o->hole_cells = 2.0;
   o->krylov = 0;
+  o->smoother = CC_SMOOTHER_JACOBI;
 }
 
 const char* cc_last_error_string(void) { return t_last_error; }
@@ -1889,7 +1915,8 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       !(o.eps > 0 && o.eps < 1) || (o.cycle < 1 || o.cycle > 3) ||
       (o.fmg_cycle != CC_CYCLE_V && o.fmg_cycle != CC_CYCLE_W) || o.w_depth < 0 ||
       o.serve_slots < 1 || !(o.hole_cells > 0) || o.krylov < 0 || o.krylov > KR_MAXV - 1 ||
-      (o.krylov && o.cycle == CC_CYCLE_FMG))
+      (o.krylov && o.cycle == CC_CYCLE_FMG) ||
+      (o.smoother != CC_SMOOTHER_JACOBI && o.smoother != CC_SMOOTHER_MCGS))
     return CC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // the setup cache: a clone of the hierarchy of an identical earlier call
@@ -2565,7 +2592,13 @@ cc_status cc_smooth_noalloc(cc_handle H, int l, double* u, const double* b, cc_s
       B.z = scr + L.nn + P.ns;              // [.., + m): chunk interior solutions
       B.q = scr + L.nn + P.ns + P.m;        // [.., + slots): interface contributions
     }
-    launch_sweep<double>(L, u, out, b, (const double*)nullptr, false, s);
+    if (H->opt.smoother == CC_SMOOTHER_MCGS) {
+      // the multicolour variant works in place, on a copy of u
+      CK(cudaMemcpyAsync(out, u, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      color_passes<double>(L, out, b, s);
+    } else {
+      launch_sweep<double>(L, u, out, b, (const double*)nullptr, false, s);
+    }
     if (P.m) launch_block<double>(P, B, L.blk.sm64, out, b, s);
     // every non-empty cell of `out` was written above; empty cells go out as 0
     pdl_launch(k_rhs_copy, nblk(L.nn), 256, 0, s, out, L.cls, u, L.nn);

@@ -209,6 +209,41 @@ k_sweep(const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__
   pdl_exit();
 }
 
+// ---- a1, multicolour variant (outside the paper): one colour class in place ---
+// The SFV cells are relaxed class by class, each class with the latest values
+// of the others: u_i += omega / D (b - A u)_i for the cells of class `color`.
+// The classes, (i + j) mod 4 for b = 0 and (i + 4 j) mod 15 for b != 0, hold no
+// two cells that one row couples (wall ghosts included), so a class is
+// updated in place: no cell of the class reads another.
+__device__ __forceinline__ int mc_color(int gx, int gy, bool cross) {
+  return cross ? (gx + 4 * gy) % 15 : (gx + gy) % 4;
+}
+__host__ __device__ inline int mc_colors(bool cross) { return cross ? 15 : 4; }
+
+template <class T, bool CROSS>
+__global__ void __launch_bounds__(TX * TY)
+k_sweep_color(T* __restrict__ u, const T* __restrict__ b, const uint8_t* __restrict__ cls,
+              StencilP<T> P, int color) {
+  pdl_enter();
+  __shared__ T s[SY][SX];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int n = P.n;
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const int gx = x0 + lx, gy = y0 + ly;
+  const bool in = gx < n && gy < n;
+  const size_t k = (size_t)gy * n + gx;
+  const bool mine = in && mc_color(gx, gy, CROSS) == color && cls[k] == C_STENCIL;
+  const T bv = mine ? b[k] : T(0);
+  // the window holds cells of other classes only where this class reads
+  load_tile<T>(s, u, nullptr, P, x0, y0, false);
+  __syncthreads();
+  if (mine) {
+    const T Au = apply_A<T, CROSS>(s, P.w, lx, ly);
+    u[k] = s[ly + HALO][lx + HALO] + P.omega_over_diag * (bv - Au);
+  }
+  pdl_exit();
+}
+
 // ---- a1 on large grids: 32 x 32 tiles, 4 consecutive rows per thread ---------
 // The stencil is a dxx + c dyy + b dx(dy) with the one-dimensional formulas of
 // Eq. 4.7a,b.  Each thread reads the 5 values of each row of its 8-row window

@@ -73,3 +73,34 @@ def test_noalloc_rejects_levels_beyond_the_scratch():
     assert ei.value.status == 1 and "scratch" in str(ei.value)
     H.smooth_noalloc(1, u[: 512 * 512], b[: 512 * 512])     # 512^2 fits
     torch.cuda.synchronize()
+
+
+def test_noalloc_multicolour_sweep_matches_cc_smooth():
+    """The same on a handle with the multicolour smoother (its classes relaxed
+    in place on a copy of u in the scratch array), levels 0 and 1 (the
+    chunked and the dense block), two calls in a row each."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    from paper_2601_02975_gb300 import SMOOTHER_MCGS
+    P = W.problem_disk()
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, 256,
+                              default_options(min_coarse_n=16, smoother=SMOOTHER_MCGS, omega=0.6))
+    for level in (0, 1):
+        n = H.info.level_n[level]
+        rng = np.random.default_rng(200 + level)
+        for call in range(2):
+            u0 = rng.standard_normal(n * n)
+            b0 = rng.standard_normal(n * n)
+            ref = torch.tensor(u0, dtype=torch.float64, device=DEV)
+            got = ref.clone()
+            bt = torch.tensor(b0, dtype=torch.float64, device=DEV)
+            H.smooth(level, ref, bt)
+            H.smooth_noalloc(level, got, bt)
+            torch.cuda.synchronize()
+            typ = H.cell_types()[0].ravel() != 0 if level == 0 else None
+            r = ref.cpu().numpy()
+            g = got.cpu().numpy()
+            if typ is not None:
+                r, g = r[typ], g[typ]
+            assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max(), (level, call)
