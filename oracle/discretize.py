@@ -333,7 +333,7 @@ def _curve_order(lev: G.Level, plg: List[int]) -> List[int]:
     point, the cells near one curve consecutively.  Curves are the box and
     each group of mutually overlapping holes."""
     dom, n, h = lev.dom, lev.n, lev.h
-    curves = [G.Curve(e) for e in dom.holes]
+    curves = [G.make_curve(e) for e in dom.holes]
     # groups of overlapping ellipses
     grp = list(range(len(curves)))
 
@@ -519,7 +519,7 @@ def cell_averages(lev: G.Level, fun) -> np.ndarray:
         out = np.einsum('jiab,a,b->ji', vals, 0.5 * w, 0.5 * w)
     out = np.array(out, dtype=np.float64)
     out[~lev.present] = 0.0
-    curves = [G.Curve(e) for e in lev.dom.holes]
+    curves = [G.make_curve(e) for e in lev.dom.holes]
     gi, wi = _GL_INNER
     for k, cc in lev.cut.items():
         j, i = divmod(k, n)

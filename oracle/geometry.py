@@ -33,7 +33,7 @@ from typing import Dict, List, Tuple
 
 import numpy as np
 
-from paper_2601_02975_gb300.workloads import Domain, Ellipse
+from paper_2601_02975_gb300.workloads import Domain, Ellipse, Flower
 
 EMPTY, REGULAR, IRREGULAR = 0, 1, 2
 
@@ -107,6 +107,106 @@ class Curve:
         hx = math.hypot(e.r1 * self.co, e.r2 * self.si)
         hy = math.hypot(e.r1 * self.si, e.r2 * self.co)
         return e.cx - hx, e.cx + hx, e.cy - hy, e.cy + hy
+
+
+class FlowerCurve:
+    """Polar curve P(t) = c + r(t) (cos t, sin t), r(t) = r0 + amp cos(k t)
+    (Sec. 6.2); t increases CCW.  Its crossings with a grid line are found on
+    the arcs between consecutive extrema of the curve's coordinate (taken
+    cyclically), where the coordinate is monotone: one crossing at most per
+    arc, refined by bisection.  A line that meets the curve only at an
+    extremum of the coordinate touches it without crossing, and gives no
+    crossing (the flower's tips and valleys lie on grid lines of the paper's
+    grids)."""
+
+    NS = 4096          # samples of t for the extrema of each coordinate
+    TOL = 1e-13        # a coordinate this close to a line at an extremum touches it
+
+    def __init__(self, e: Flower):
+        self.e = e
+        self._ext = {0: self._extrema(0), 1: self._extrema(1)}
+
+    def r(self, t):
+        return self.e.r0 + self.e.amp * np.cos(self.e.k * t)
+
+    def point(self, t):
+        rr = self.r(t)
+        return self.e.cx + rr * np.cos(t), self.e.cy + rr * np.sin(t)
+
+    def deriv(self, t):
+        rr = self.r(t)
+        dr = -self.e.amp * self.e.k * np.sin(self.e.k * t)
+        return dr * np.cos(t) - rr * np.sin(t), dr * np.sin(t) + rr * np.cos(t)
+
+    def level(self, x, y):
+        dx = np.asarray(x) - self.e.cx
+        dy = np.asarray(y) - self.e.cy
+        return np.hypot(dx, dy) - self.r(np.arctan2(dy, dx))
+
+    @staticmethod
+    def _bisect(fn, a, b):
+        fa = fn(a)
+        for _ in range(200):
+            m = 0.5 * (a + b)
+            fm = fn(m)
+            if fm == 0.0 or b - a < 1e-15:
+                return m
+            if (fm < 0) == (fa < 0):
+                a, fa = m, fm
+            else:
+                b = m
+        return 0.5 * (a + b)
+
+    def _extrema(self, axis):
+        """Parameters in [0, 2 pi) where the coordinate `axis` is extremal (the
+        sign changes of its derivative on NS samples, refined by bisection)."""
+        dco = lambda s: float(self.deriv(s)[axis])
+        t = [2 * math.pi * k / self.NS for k in range(self.NS + 1)]
+        d = [dco(s) for s in t]
+        out = []
+        for k in range(self.NS):
+            if d[k] == 0.0:
+                out.append(t[k])
+            elif d[k] * d[k + 1] < 0.0:
+                out.append(self._bisect(dco, t[k], t[k + 1]))
+        return out
+
+    def _cross(self, axis, X):
+        ext = self._ext[axis]
+        f = lambda s: float(self.point(s)[axis]) - X
+        out = []
+        m = len(ext)
+        for q in range(m):
+            a = ext[q]
+            b = ext[q + 1] if q + 1 < m else ext[0] + 2 * math.pi
+            fa, fb = f(a), f(b)
+            if abs(fa) <= self.TOL or abs(fb) <= self.TOL or fa * fb > 0.0:
+                continue
+            t = math.fmod(self._bisect(f, a, b), 2 * math.pi)
+            out.append(0.0 if t < 0.0 or t >= 2 * math.pi else t)
+        return sorted(set(out))
+
+    def cross_x(self, X):
+        return self._cross(0, X)
+
+    def cross_y(self, Y):
+        return self._cross(1, Y)
+
+    def bbox(self):
+        e = self.e
+        R = e.r0 + e.amp
+        return e.cx - R, e.cx + R, e.cy - R, e.cy + R
+
+
+def make_curve(e):
+    """The oracle's curve for a hole of the workload."""
+    return FlowerCurve(e) if isinstance(e, Flower) else Curve(e)
+
+
+def hole_halfwidth(e) -> float:
+    """Half the smallest width of a hole: the smaller semi-axis of an ellipse,
+    the smallest radius r0 - amp of a flower."""
+    return e.r0 - e.amp if isinstance(e, Flower) else min(e.r1, e.r2)
 
 
 def _curve_crossings(ci: Curve, cj: Curve) -> List[float]:
@@ -265,7 +365,7 @@ def build_level(dom: Domain, n: int, eps: float) -> Level:
     h = (dom.x1 - dom.x0) / n
     if abs((dom.y1 - dom.y0) - h * n) > 1e-12 * max(1.0, dom.y1 - dom.y0):
         raise GeometryError("the box must be square with square cells")
-    curves = [Curve(e) for e in dom.holes]
+    curves = [make_curve(e) for e in dom.holes]
     x0, y0 = dom.x0, dom.y0
 
     def outside_all(x, y, skip=-1):

@@ -177,7 +177,7 @@ def build_hierarchy(dom: Domain, n: int, a: float, b: float, c: float,
     nl = n
     while len(levels) < max_levels:
         h = (dom.x1 - dom.x0) / nl
-        if levels and any(min(e.r1, e.r2) < hole_cells * h for e in dom.holes):
+        if levels and any(G.hole_halfwidth(e) < hole_cells * h for e in dom.holes):
             break
         lev = G.build_level(dom, nl, eps)
         if not lev.resolved:
@@ -346,10 +346,11 @@ def two_grid_operator(H: Hierarchy, nu1: int, nu2: int):
     """TG of Eq. 5.12 on level 0 with an exact solve on level 1, as a
     scipy LinearOperator on the vector of all control volumes."""
     from scipy.sparse.linalg import LinearOperator
+    import scipy.sparse.linalg as spl
     d0, d1 = H.levels[0], H.levels[1]
     n = d0.n
     zero = np.zeros((n, n))
-    A1 = d1.A.toarray()
+    A1 = spl.splu(d1.A.tocsc())       # the exact coarse solve of Eq. 5.12, factored once
 
     def mv(v):
         e = np.asarray(v, dtype=np.float64).reshape(n, n).copy()
@@ -357,7 +358,7 @@ def two_grid_operator(H: Hierarchy, nu1: int, nu2: int):
         for _ in range(nu1):
             e = smooth(H, 0, e, zero)
         rc = restrict(H, 0, -residual(d0, e, zero))        # R A e
-        ec = np.linalg.solve(A1, rc.ravel()).reshape(rc.shape)
+        ec = A1.solve(rc.ravel()).reshape(rc.shape)
         e = e - interpolate(H, 0, ec)
         for _ in range(nu2):
             e = smooth(H, 0, e, zero)

@@ -1950,8 +1950,17 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   P.a = a; P.b = b; P.c = c; P.eps = o.eps;
   for (int k = 0; k < dom->n_holes; ++k) {
     const cc_hole& hh = dom->holes[k];
-    if (!(hh.r1 > 0 && hh.r2 > 0)) { delete H; return CC_ERR_ARG; }
+    if (!(hh.r1 > 0 && hh.r2 > 0) || (hh.kind != CC_HOLE_ELLIPSE && hh.kind != CC_HOLE_FLOWER)) {
+      delete H;
+      return CC_ERR_ARG;
+    }
+    if (hh.kind == CC_HOLE_FLOWER && !(hh.r2 < hh.r1 && hh.theta >= 1 && hh.theta == std::floor(hh.theta))) {
+      delete H;
+      return CC_ERR_ARG;
+    }
     Hole e{hh.cx, hh.cy, hh.r1, hh.r2, hh.theta, std::cos(hh.theta), std::sin(hh.theta)};
+    e.kind = hh.kind;
+    e.petals = hh.kind == CC_HOLE_FLOWER ? (int)hh.theta : 0;
     P.holes.push_back(e);
   }
   for (int k = 0; k < n_bc; ++k) {
@@ -1977,7 +1986,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       if (!H->lv.empty()) {
         double hl = (P.x1 - P.x0) / nl;
         bool fine_enough = true;
-        for (const Hole& e : P.holes) fine_enough = fine_enough && std::min(e.r1, e.r2) >= o.hole_cells * hl;
+        for (const Hole& e : P.holes) fine_enough = fine_enough && e.halfwidth() >= o.hole_cells * hl;
         if (!fine_enough) break;
       }
       LevelDisc D;

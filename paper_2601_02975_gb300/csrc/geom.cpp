@@ -31,16 +31,29 @@ namespace ccmg {
 
 void Hole::at(double t, double& x, double& y) const {
   double ct = std::cos(t), st = std::sin(t);
+  if (kind == 1) {
+    const double r = r1 + r2 * std::cos(petals * t);
+    x = cx + r * ct;
+    y = cy + r * st;
+    return;
+  }
   x = cx + co * r1 * ct - si * r2 * st;
   y = cy + si * r1 * ct + co * r2 * st;
 }
 void Hole::dat(double t, double& dx, double& dy) const {
   double ct = std::cos(t), st = std::sin(t);
+  if (kind == 1) {
+    const double r = r1 + r2 * std::cos(petals * t), dr = -r2 * petals * std::sin(petals * t);
+    dx = dr * ct - r * st;
+    dy = dr * st + r * ct;
+    return;
+  }
   dx = -co * r1 * st - si * r2 * ct;
   dy = -si * r1 * st + co * r2 * ct;
 }
 double Hole::level(double x, double y) const {
   double dx = x - cx, dy = y - cy;
+  if (kind == 1) return std::hypot(dx, dy) - (r1 + r2 * std::cos(petals * std::atan2(dy, dx)));
   double u = co * dx + si * dy, v = -si * dx + co * dy;
   return (u / r1) * (u / r1) + (v / r2) * (v / r2) - 1.0;
 }
@@ -150,6 +163,63 @@ void trig_roots(double A, double B, double C, std::vector<double>& out) {
     if (t < 0) t += kTwoPi;
     out.push_back(t);
   }
+}
+
+// Crossings of a flower with the grid line x = c (axis 0) or y = c (axis 1).
+// Between consecutive extrema of the coordinate (cyclically) the coordinate
+// is monotone, so each such arc crosses the line at most once; the crossing
+// is refined by bisection.  A line met only at an extremum is touched, not
+// crossed (tips and valleys of the flower lie on grid lines), and gives none.
+double bisect_root(const std::function<double(double)>& f, double a, double b) {
+  double fa = f(a);
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (a + b), fm = f(m);
+    if (fm == 0.0 || b - a < 1e-15) return m;
+    if ((fm < 0) == (fa < 0)) { a = m; fa = fm; } else { b = m; }
+  }
+  return 0.5 * (a + b);
+}
+
+// parameters in [0, 2pi) where coordinate `axis` of the flower is extremal
+std::vector<double> flower_extrema(const Hole& H, int axis) {
+  const int ns = 4096;
+  std::function<double(double)> d = [&](double t) {
+    double dx, dy;
+    H.dat(t, dx, dy);
+    return axis == 0 ? dx : dy;
+  };
+  std::vector<double> out;
+  double d0 = d(0.0);
+  for (int k = 0; k < ns; ++k) {
+    const double ta = kTwoPi * k / ns, tb = kTwoPi * (k + 1) / ns, d1 = d(tb);
+    if (d0 == 0.0) out.push_back(ta);
+    else if (d0 * d1 < 0.0) out.push_back(bisect_root(d, ta, tb));
+    d0 = d1;
+  }
+  return out;
+}
+
+void flower_line_roots(const Hole& H, int axis, double c, std::vector<double>& out) {
+  const double tol = 1e-13;
+  const std::vector<double> ext = flower_extrema(H, axis);
+  std::function<double(double)> f = [&](double t) {
+    double x, y;
+    H.at(t, x, y);
+    return (axis == 0 ? x : y) - c;
+  };
+  std::vector<double> r;
+  const size_t m = ext.size();
+  for (size_t q = 0; q < m; ++q) {
+    const double a = ext[q], b = q + 1 < m ? ext[q + 1] : ext[0] + kTwoPi;
+    const double fa = f(a), fb = f(b);
+    if (std::fabs(fa) <= tol || std::fabs(fb) <= tol || fa * fb > 0.0) continue;
+    double t = std::fmod(bisect_root(f, a, b), kTwoPi);
+    if (t < 0.0 || t >= kTwoPi) t = 0.0;
+    r.push_back(t);
+  }
+  std::sort(r.begin(), r.end());
+  r.erase(std::unique(r.begin(), r.end()), r.end());
+  out.insert(out.end(), r.begin(), r.end());
 }
 
 // crossings of hole i with hole j: bracket sign changes of j's level function
@@ -301,12 +371,14 @@ LevelGeom build_geometry(const Problem& P, int n) {
   for (int e = 0; e < nh; ++e) {
     const Hole& H = P.holes[e];
     double hx = std::hypot(H.r1 * H.co, H.r2 * H.si), hy = std::hypot(H.r1 * H.si, H.r2 * H.co);
+    if (H.kind == 1) hx = hy = H.r1 + H.r2;
     std::vector<double> ts;
     int i0 = std::max(0, (int)std::floor((H.cx - hx - P.x0) / h));
     int i1 = std::min(n, (int)std::ceil((H.cx + hx - P.x0) / h));
     for (int i = i0; i <= i1; ++i) {
       std::vector<double> r;
-      trig_roots(H.co * H.r1, -H.si * H.r2, P.x0 + i * h - H.cx, r);
+      if (H.kind == 1) flower_line_roots(H, 0, P.x0 + i * h, r);
+      else trig_roots(H.co * H.r1, -H.si * H.r2, P.x0 + i * h - H.cx, r);
       for (double t : r) {
         double x, y;
         H.at(t, x, y);
@@ -318,7 +390,8 @@ LevelGeom build_geometry(const Problem& P, int n) {
     int j1 = std::min(n, (int)std::ceil((H.cy + hy - P.y0) / h));
     for (int j = j0; j <= j1; ++j) {
       std::vector<double> r;
-      trig_roots(H.si * H.r1, H.co * H.r2, P.y0 + j * h - H.cy, r);
+      if (H.kind == 1) flower_line_roots(H, 1, P.y0 + j * h, r);
+      else trig_roots(H.si * H.r1, H.co * H.r2, P.y0 + j * h - H.cy, r);
       for (double t : r) {
         double x, y;
         H.at(t, x, y);

@@ -2,6 +2,7 @@
 // classification and fits (Sec. 4), block-smoother and bottom factorisations
 // (Sec. 5).  Everything here runs once per domain in cc_setup.
 #pragma once
+#include <algorithm>
 #include <array>
 #include <cstdint>
 #include <map>
@@ -21,12 +22,17 @@ struct SetupError : std::runtime_error {
   SetupError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
+// A hole: kind 0 the ellipse c + R(th) (r1 cos t, r2 sin t); kind 1 the
+// flower c + (r1 + r2 cos(petals t)) (cos t, sin t) (Sec. 6.2).
 struct Hole {
   double cx, cy, r1, r2, th, co, si;
+  int kind = 0;
+  int petals = 0;
   // point and derivative at parameter t (counter-clockwise)
   void at(double t, double& x, double& y) const;
   void dat(double t, double& dx, double& dy) const;
   double level(double x, double y) const;   // < 0 inside
+  double halfwidth() const { return kind == 1 ? r1 - r2 : std::min(r1, r2); }
 };
 
 struct Bc { int type; double a1, a2; };

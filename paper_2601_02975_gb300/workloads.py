@@ -127,6 +127,67 @@ class Separable:
         return out
 
 
+class Pointwise:
+    """A smooth function given pointwise with its gradient (for manufactured
+    solutions that are not sums of separable products).  Averages over cells
+    and faces use 10-point Gauss-Legendre rules per direction: for the smooth
+    functions used here on cells of size h <= 1/32 they are exact to rounding."""
+
+    _G, _W = np.polynomial.legendre.leggauss(10)
+
+    def __init__(self, f, fx=None, fy=None):
+        self.f, self.fx, self.fy = f, fx, fy
+
+    def __call__(self, x, y):
+        return self.f(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+
+    def dx(self) -> "Pointwise":
+        return Pointwise(self.fx)
+
+    def dy(self) -> "Pointwise":
+        return Pointwise(self.fy)
+
+    def rect_avg(self, x0, x1, y0, y1):
+        x0, x1, y0, y1 = np.broadcast_arrays(*(np.asarray(v, dtype=np.float64) for v in (x0, x1, y0, y1)))
+        g, w = self._G, 0.5 * self._W
+        xs = 0.5 * (x0 + x1)[..., None, None] + 0.5 * (x1 - x0)[..., None, None] * g[:, None]
+        ys = 0.5 * (y0 + y1)[..., None, None] + 0.5 * (y1 - y0)[..., None, None] * g[None, :]
+        return np.einsum("...ab,a,b->...", self(xs, ys), w, w)
+
+    def xseg_avg(self, x0, x1, y):
+        x0, x1, y = np.broadcast_arrays(*(np.asarray(v, dtype=np.float64) for v in (x0, x1, y)))
+        g, w = self._G, 0.5 * self._W
+        xs = 0.5 * (x0 + x1)[..., None] + 0.5 * (x1 - x0)[..., None] * g
+        return np.einsum("...a,a->...", self(xs, y[..., None]), w)
+
+    def yseg_avg(self, x, y0, y1):
+        x, y0, y1 = np.broadcast_arrays(*(np.asarray(v, dtype=np.float64) for v in (x, y0, y1)))
+        g, w = self._G, 0.5 * self._W
+        ys = 0.5 * (y0 + y1)[..., None] + 0.5 * (y1 - y0)[..., None] * g
+        return np.einsum("...a,a->...", self(x[..., None], ys), w)
+
+
+def u_flower() -> Pointwise:
+    """u = r^4 cos(3 theta) = r (x^3 - 3 x y^2) about the origin (Sec. 6.2)."""
+    def f(x, y):
+        return np.hypot(x, y) * (x ** 3 - 3 * x * y ** 2)
+
+    def fx(x, y):
+        r = np.hypot(x, y)
+        return x / r * (x ** 3 - 3 * x * y ** 2) + r * (3 * x ** 2 - 3 * y ** 2)
+
+    def fy(x, y):
+        r = np.hypot(x, y)
+        return y / r * (x ** 3 - 3 * x * y ** 2) - 6 * r * x * y
+
+    return Pointwise(f, fx, fy)
+
+
+def f_flower() -> Pointwise:
+    """Laplacian of u_flower: (16 - 9) r^2 cos(3 theta) = 7 (x^3 - 3 x y^2) / r."""
+    return Pointwise(lambda x, y: 7.0 * (x ** 3 - 3 * x * y ** 2) / np.hypot(x, y))
+
+
 def apply_L(u: Separable, a: float, b: float, c: float) -> Separable:
     """f = a u_xx + b u_xy + c u_yy, exact (Eq. 1.1)."""
     return (u.dx().dx().scaled(a) + u.dx().dy().scaled(b)
@@ -191,6 +252,18 @@ class Ellipse:
 
 
 @dataclass(frozen=True)
+class Flower:
+    """The hole bounded by the closed curve r = r0 + amp cos(k theta) in polar
+    coordinates about (cx, cy) (Sec. 6.2): the domain keeps
+    r > r0 + amp cos(k theta).  Requires 0 < amp < r0 and an integer k >= 1."""
+    cx: float
+    cy: float
+    r0: float
+    amp: float
+    k: int
+
+
+@dataclass(frozen=True)
 class BC:
     kind: int = DIRICHLET
     alpha1: float = 1.0
@@ -209,7 +282,7 @@ class Domain:
     y0: float = 0.0
     x1: float = 1.0
     y1: float = 1.0
-    holes: List[Ellipse] = field(default_factory=list)
+    holes: List[object] = field(default_factory=list)    # Ellipse or Flower
     box_bc: Tuple[BC, BC, BC, BC] = (BC(), BC(), BC(), BC())
     hole_bc: List[BC] = field(default_factory=list)
 
@@ -319,6 +392,17 @@ def problem_four_disks(kind: int = DIRICHLET) -> Problem:
     dom = Domain(holes=disks, hole_bc=[bc] * 4)
     return Problem("four_disks_" + ("D" if kind == DIRICHLET else "N"), dom, 1.0, 0.0, 1.0, u,
                    apply_L(u, 1.0, 0.0, 1.0))
+
+
+def problem_flower(kind: int = NEUMANN) -> Problem:
+    """Sec. 6.2, a square minus a flower: Poisson's equation on
+    (-0.5, 0.5)^2 minus the flower r <= 0.25 + 0.05 cos(6 theta) about the
+    origin, u = r^4 cos(3 theta), Dirichlet on the square and `kind` on the
+    flower (Neumann in the paper); the paper uses eps = 0.02."""
+    u = u_flower()
+    bc = BC(NEUMANN, 0.0, 1.0) if kind == NEUMANN else BC(DIRICHLET, 1.0, 0.0)
+    dom = Domain(x0=-0.5, y0=-0.5, x1=0.5, y1=0.5, holes=[Flower(0.0, 0.0, 0.25, 0.05, 6)], hole_bc=[bc])
+    return Problem("flower", dom, 1.0, 0.0, 1.0, u, f_flower())
 
 
 def _boundary_points(e: Ellipse, m: int = 720):

@@ -620,3 +620,52 @@ def test_krylov_solve_on_the_disk_is_deterministic():
     res = solve_batch([H, C], [_t(f)] * 2, [_t(g)] * 2, us, [1e-10] * 2)
     assert all(x.status == 0 for x in res)
     assert torch.equal(us[0], u) and torch.equal(us[1], u)
+
+
+@pytest.mark.slow
+def test_flower_parity_and_errors():
+    """The square minus a flower of Sec. 6.2 (a polar curve, Poisson, Dirichlet
+    on the square, Neumann on the flower, eps = 0.02) at h = 1/160: the GPU's
+    right-hand side equals the oracle's to 1e-12, three FP64 W-cycles match
+    its iterates to 1e-11, and the FP64 and mixed solves to 1e-12 have L-inf,
+    L1 and L2 errors within 1.1x of the oracle's direct solve of the same
+    system and within 2.5x of the printed Table 4."""
+    n, mc = 160, 20
+    P = W.problem_flower()
+    O = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, eps=0.02, min_coarse=mc)
+    d = O.levels[0]
+    lev = d.lev
+    bo = _oracle_rhs(O, P)
+    ue_o = D.cell_averages(lev, P.u)
+    ud = spl.spsolve(d.A.tocsc(), bo.ravel()).reshape(n, n)
+
+    def norms(u):
+        e = np.abs(u - ue_o)
+        e[~lev.present] = 0.0
+        return np.array([e.max(), (e * lev.vol).sum(), math.sqrt((e * e * lev.vol).sum())])
+
+    want = norms(ud)
+    printed = {int(r[0]): [float(v) for v in r[1:]] for r in _golden_rows("flower_errors.txt")}[n]
+    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                              default_options(min_coarse_n=mc, eps=0.02, cycle=2))
+    assert H.info.n_levels == O.nl
+    _, _, _, b = _gpu_rhs(H, P)
+    assert np.abs(_np(b, n) - bo).max() <= 1e-12 * np.abs(bo).max()
+    u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    uo = np.zeros((n, n))
+    for k in range(3):
+        H.cycle(u, b)
+        uo = M.cycle(O, 0, uo, bo, 3, 3, 2)
+        err = np.abs(_np(u, n) - uo).max() / np.abs(uo).max()
+        assert err < 1e-11, (k, err)
+    for prec in (0, 1):
+        Hs = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                   default_options(min_coarse_n=mc, eps=0.02, cycle=2, precision=prec))
+        f, g, _ = I.problem_inputs(Hs, P)
+        us = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+        r = Hs.solve(_t(f), _t(g), us, 1e-12)
+        assert r.status == 0 and r.rel_res < 1e-12, (prec, r.status, r.rel_res)
+        got = norms(_np(us, n))
+        assert np.all(got <= 1.1 * want + 1e-15), (prec, got, want)
+        for gv, pv in zip(got, printed):
+            assert pv / 2.5 < gv < pv * 2.5, (prec, got, printed)

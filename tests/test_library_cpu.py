@@ -238,3 +238,28 @@ def test_coarse_level_tables_match_oracle(lib, name, n, mc):
             want = np.array(list(d.betas[k]))
             assert np.abs(beta[r, :15] - want).max() < 1e-11 * np.abs(want).max(), (l, k)
     H.close()
+
+
+@pytest.mark.parametrize("n", [40, 80])
+def test_flower_tables_match_oracle(lib, n):
+    """The flower of Sec. 6.2 (a polar curve, eps = 0.02): the library's cell
+    types, volumes, lattices and fit coefficients equal the oracle's,
+    including at the tips and valleys that lie on grid lines (touched, not
+    crossed)."""
+    P = W.problem_flower()
+    H = _host(P, n, min_coarse_n=n, eps=0.02)
+    lev = G.build_level(P.dom, n, 0.02)
+    d = D.discretize(lev, P.a, P.b, P.c)
+    typ, kind, vol = H.cell_types()
+    np.testing.assert_array_equal(kind, d.kind)
+    np.testing.assert_array_equal(typ, lev.ctype)
+    assert np.abs(vol - lev.vol).max() < 1e-15
+    _, lat, beta = H.level_tables(0)
+    plg = sorted(d.lattices)
+    assert len(plg) == len(lat)
+    for r, k in enumerate(plg):
+        np.testing.assert_array_equal(lat[r], d.lattices[k])
+        want = np.array(list(d.betas[k]))
+        assert np.abs(beta[r, :15] - want).max() < 1e-11 * np.abs(want).max()
+    assert H.info.n_bd == len(d.bd_cells)
+    H.close()
