@@ -2,7 +2,8 @@
  * ccmg.h - C ABI of the GB300 cut-cell multigrid library.
  *
  * The library solves  a u_xx + b u_xy + c u_yy = f  (b^2 < 4ac) on a square
- * box minus a union of holes (ellipses, or a flower-shaped polar curve), with Dirichlet, Neumann or Robin data
+ * box minus a union of holes (ellipses, a flower-shaped polar curve, or the
+ * outside of a rotated rectangle), with Dirichlet, Neumann or Robin data
  * N u = g on every boundary curve (Sec. 1, Eq. 1.1-1.2), by the fourth-order
  * cut-cell finite-volume discretisation (Sec. 3-4) and the cut-cell geometric
  * multigrid solver (Sec. 5).  The unknowns are cell averages <u>_i over the
@@ -57,7 +58,7 @@ typedef enum {
   CC_ERR_BUSY = 9             /* the request is still in flight (cc_poll) */
 } cc_status;
 
-enum { CC_HOLE_ELLIPSE = 0, CC_HOLE_FLOWER = 1 };
+enum { CC_HOLE_ELLIPSE = 0, CC_HOLE_FLOWER = 1, CC_HOLE_OUTSIDE_RECT = 2 };
 enum { CC_BC_DIRICHLET = 0, CC_BC_NEUMANN = 1, CC_BC_ROBIN = 2 };
 enum { CC_CYCLE_V = 1, CC_CYCLE_W = 2, CC_CYCLE_FMG = 3 };
 enum { CC_PREC_FP64 = 0, CC_PREC_MIXED = 1 };
@@ -66,7 +67,11 @@ enum { CC_SMOOTHER_JACOBI = 0, CC_SMOOTHER_MCGS = 1 };
 /* A hole.  kind CC_HOLE_ELLIPSE: centre (cx, cy), semi-axes r1, r2, rotation
  * theta (rad).  kind CC_HOLE_FLOWER (Sec. 6.2): the region
  * r <= r1 + r2 cos(theta * phi) in polar coordinates (r, phi) about (cx, cy),
- * with 0 < r2 < r1 and theta the number of petals (an integer >= 1). */
+ * with 0 < r2 < r1 and theta the number of petals (an integer >= 1).
+ * kind CC_HOLE_OUTSIDE_RECT: everything outside the rectangle with corner
+ * (cx, cy) and sides r1 (direction theta) and r2 (direction theta + pi/2),
+ * so that the domain is that rectangle (Sec. 6.1, the rotated square); it
+ * must lie inside the box and be the only hole. */
 typedef struct { int kind; double cx, cy, r1, r2, theta; } cc_hole;
 
 /* The domain: the square [x0,x1] x [y0,y1] minus the union of the holes.

@@ -33,7 +33,7 @@ from typing import Dict, List, Tuple
 
 import numpy as np
 
-from paper_2601_02975_gb300.workloads import Domain, Ellipse, Flower
+from paper_2601_02975_gb300.workloads import Domain, Ellipse, Flower, OutsideRect
 
 EMPTY, REGULAR, IRREGULAR = 0, 1, 2
 
@@ -198,14 +198,101 @@ class FlowerCurve:
         return e.cx - R, e.cx + R, e.cy - R, e.cy + R
 
 
+class RectCurve:
+    """The boundary of the hole outside a rectangle (workloads.OutsideRect):
+    the rectangle's sides, with the parameter t increasing clockwise around
+    the rectangle (each side a quarter of [0, 2 pi)), so that, as for the
+    other holes, the domain lies to the left of the curve followed from high
+    to low t.  The corners are kinks: the arcs are split there
+    (breakpoints()).  A grid line through a corner crosses there when the two
+    sides at the corner lie on its two sides, and touches it otherwise."""
+
+    TOL = 1e-13
+
+    def __init__(self, e: OutsideRect):
+        self.e = e
+        c, s = math.cos(e.theta), math.sin(e.theta)
+        v = [(e.cx, e.cy), (e.cx + e.w * c, e.cy + e.w * s),
+             (e.cx + e.w * c - e.hgt * s, e.cy + e.w * s + e.hgt * c), (e.cx - e.hgt * s, e.cy + e.hgt * c)]
+        self.ccw = v                            # counter-clockwise corners
+        self.cw = [v[0], v[3], v[2], v[1]]      # the order of increasing t
+
+    def point(self, t):
+        t = np.asarray(t, dtype=np.float64)
+        tm = np.mod(t, 2 * math.pi)
+        k = np.minimum((tm // (math.pi / 2)).astype(int), 3)
+        tau = (tm - k * (math.pi / 2)) / (math.pi / 2)
+        W = np.array(self.cw + [self.cw[0]])
+        x = W[k, 0] + tau * (W[k + 1, 0] - W[k, 0])
+        y = W[k, 1] + tau * (W[k + 1, 1] - W[k, 1])
+        return x, y
+
+    def deriv(self, t):
+        t = np.asarray(t, dtype=np.float64)
+        tm = np.mod(t, 2 * math.pi)
+        k = np.minimum((tm // (math.pi / 2)).astype(int), 3)
+        W = np.array(self.cw + [self.cw[0]])
+        return (W[k + 1, 0] - W[k, 0]) / (math.pi / 2), (W[k + 1, 1] - W[k, 1]) / (math.pi / 2)
+
+    def level(self, x, y):
+        """The distance inside the rectangle to its nearest side line (the
+        smallest inward-normal distance): positive inside the rectangle,
+        negative in the hole."""
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        out = None
+        for i in range(4):
+            (ax, ay), (bx, by) = self.ccw[i], self.ccw[(i + 1) % 4]
+            L = math.hypot(bx - ax, by - ay)
+            d = (-(by - ay) * (x - ax) + (bx - ax) * (y - ay)) / L
+            out = d if out is None else np.minimum(out, d)
+        return out
+
+    def breakpoints(self):
+        return [k * (math.pi / 2) for k in range(4)]
+
+    def _cross(self, axis, X):
+        W = self.cw
+        out = []
+        for k in range(4):
+            f0 = W[k][axis] - X
+            fp = W[(k - 1) % 4][axis] - X
+            f1 = W[(k + 1) % 4][axis] - X
+            if abs(f0) <= self.TOL:
+                if fp * f1 < 0.0 and abs(fp) > self.TOL and abs(f1) > self.TOL:
+                    out.append(k * (math.pi / 2))
+                continue
+            if abs(f1) <= self.TOL or f0 * f1 > 0.0:
+                continue
+            out.append(k * (math.pi / 2) + (math.pi / 2) * f0 / (f0 - f1))
+        return sorted(out)
+
+    def cross_x(self, X):
+        return self._cross(0, X)
+
+    def cross_y(self, Y):
+        return self._cross(1, Y)
+
+    def bbox(self):
+        xs = [p[0] for p in self.ccw]
+        ys = [p[1] for p in self.ccw]
+        return min(xs), max(xs), min(ys), max(ys)
+
+
 def make_curve(e):
     """The oracle's curve for a hole of the workload."""
-    return FlowerCurve(e) if isinstance(e, Flower) else Curve(e)
+    if isinstance(e, Flower):
+        return FlowerCurve(e)
+    if isinstance(e, OutsideRect):
+        return RectCurve(e)
+    return Curve(e)
 
 
 def hole_halfwidth(e) -> float:
     """Half the smallest width of a hole: the smaller semi-axis of an ellipse,
     the smallest radius r0 - amp of a flower."""
+    if isinstance(e, OutsideRect):
+        return math.inf          # the hole is the outside: no coarse-level width limit
     return e.r0 - e.amp if isinstance(e, Flower) else min(e.r1, e.r2)
 
 
@@ -396,6 +483,8 @@ def build_level(dom: Domain, n: int, eps: float) -> Level:
         for ej, c2 in enumerate(curves):
             if ej != ei:
                 ts.extend(_curve_crossings(c, c2))
+        if hasattr(c, "breakpoints"):
+            ts.extend(c.breakpoints())
         ts = sorted(set(ts))
         if not ts:
             segs = [(2 * math.pi, 0.0)]

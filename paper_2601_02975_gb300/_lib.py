@@ -170,8 +170,10 @@ class Hierarchy:
                  options: Optional[cc_options] = None, stream=None):
         holes = (cc_hole * max(1, len(dom.holes)))()
         for k, e in enumerate(dom.holes):
-            if hasattr(e, "petals") or hasattr(e, "amp"):     # a flower (workloads.Flower)
+            if hasattr(e, "amp"):                             # a flower (workloads.Flower)
                 holes[k] = cc_hole(1, e.cx, e.cy, e.r0, e.amp, float(e.k))
+            elif hasattr(e, "hgt"):                           # workloads.OutsideRect
+                holes[k] = cc_hole(2, e.cx, e.cy, e.w, e.hgt, e.theta)
             else:
                 holes[k] = cc_hole(0, e.cx, e.cy, e.r1, e.r2, e.theta)
         d = cc_domain(dom.x0, dom.y0, dom.x1, dom.y1, len(dom.holes), holes)

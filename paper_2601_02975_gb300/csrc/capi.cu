@@ -1950,7 +1950,8 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   P.a = a; P.b = b; P.c = c; P.eps = o.eps;
   for (int k = 0; k < dom->n_holes; ++k) {
     const cc_hole& hh = dom->holes[k];
-    if (!(hh.r1 > 0 && hh.r2 > 0) || (hh.kind != CC_HOLE_ELLIPSE && hh.kind != CC_HOLE_FLOWER)) {
+    if (!(hh.r1 > 0 && hh.r2 > 0) ||
+        (hh.kind != CC_HOLE_ELLIPSE && hh.kind != CC_HOLE_FLOWER && hh.kind != CC_HOLE_OUTSIDE_RECT)) {
       delete H;
       return CC_ERR_ARG;
     }

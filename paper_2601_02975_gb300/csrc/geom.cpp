@@ -29,7 +29,37 @@
 
 namespace ccmg {
 
+const double kTwoPi = 6.283185307179586476925286766559;
+
+void Hole::corners_cw(double vx[4], double vy[4]) const {
+  // counter-clockwise: c, c + r1 e, c + r1 e + r2 e', c + r2 e'; clockwise
+  // from c: c, c + r2 e', c + r1 e + r2 e', c + r1 e
+  vx[0] = cx;                       vy[0] = cy;
+  vx[1] = cx - r2 * si;             vy[1] = cy + r2 * co;
+  vx[2] = cx + r1 * co - r2 * si;   vy[2] = cy + r1 * si + r2 * co;
+  vx[3] = cx + r1 * co;             vy[3] = cy + r1 * si;
+}
+
+// side k of a kind-2 hole at parameter t: the corner index and the fraction
+static void rect_side(double t, int& k, double& tau) {
+  const double q = kTwoPi / 4;
+  double tm = std::fmod(t, kTwoPi);
+  if (tm < 0) tm += kTwoPi;
+  k = std::min(3, (int)std::floor(tm / q));
+  tau = (tm - k * q) / q;
+}
+
 void Hole::at(double t, double& x, double& y) const {
+  if (kind == 2) {
+    double vx[4], vy[4], tau;
+    int k;
+    corners_cw(vx, vy);
+    rect_side(t, k, tau);
+    const int k1 = (k + 1) % 4;
+    x = vx[k] + tau * (vx[k1] - vx[k]);
+    y = vy[k] + tau * (vy[k1] - vy[k]);
+    return;
+  }
   double ct = std::cos(t), st = std::sin(t);
   if (kind == 1) {
     const double r = r1 + r2 * std::cos(petals * t);
@@ -41,6 +71,16 @@ void Hole::at(double t, double& x, double& y) const {
   y = cy + si * r1 * ct + co * r2 * st;
 }
 void Hole::dat(double t, double& dx, double& dy) const {
+  if (kind == 2) {
+    double vx[4], vy[4], tau;
+    int k;
+    corners_cw(vx, vy);
+    rect_side(t, k, tau);
+    const int k1 = (k + 1) % 4;
+    dx = (vx[k1] - vx[k]) / (kTwoPi / 4);
+    dy = (vy[k1] - vy[k]) / (kTwoPi / 4);
+    return;
+  }
   double ct = std::cos(t), st = std::sin(t);
   if (kind == 1) {
     const double r = r1 + r2 * std::cos(petals * t), dr = -r2 * petals * std::sin(petals * t);
@@ -52,6 +92,21 @@ void Hole::dat(double t, double& dx, double& dy) const {
   dy = -si * r1 * st + co * r2 * ct;
 }
 double Hole::level(double x, double y) const {
+  if (kind == 2) {
+    // the smallest inward-normal distance to the rectangle's side lines:
+    // positive inside the rectangle, negative in the hole
+    double vx[4], vy[4];
+    corners_cw(vx, vy);
+    double out = 0;
+    for (int i = 0; i < 4; ++i) {
+      // counter-clockwise side from corner a to corner b
+      const int a = (4 - i) % 4, b = (3 - i + 4) % 4;
+      const double ex = vx[b] - vx[a], ey = vy[b] - vy[a], L = std::hypot(ex, ey);
+      const double d = (-ey * (x - vx[a]) + ex * (y - vy[a])) / L;
+      out = i == 0 ? d : std::min(out, d);
+    }
+    return out;
+  }
   double dx = x - cx, dy = y - cy;
   if (kind == 1) return std::hypot(dx, dy) - (r1 + r2 * std::cos(petals * std::atan2(dy, dx)));
   double u = co * dx + si * dy, v = -si * dx + co * dy;
@@ -94,7 +149,6 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
 
 namespace {
 
-const double kTwoPi = 6.283185307179586476925286766559;
 
 struct Rules {
   std::vector<double> sx, sw, ax, aw, ix, iw;
@@ -220,6 +274,26 @@ void flower_line_roots(const Hole& H, int axis, double c, std::vector<double>& o
   std::sort(r.begin(), r.end());
   r.erase(std::unique(r.begin(), r.end()), r.end());
   out.insert(out.end(), r.begin(), r.end());
+}
+
+// Crossings of a kind-2 hole's sides with the grid line x = c (axis 0) or
+// y = c (axis 1): one per side whose ends lie strictly on the two sides of
+// the line; a corner on the line (within 1e-13) is a crossing when its two
+// sides leave to the two sides of the line, and is only touched otherwise.
+void rect_line_roots(const Hole& H, int axis, double c, std::vector<double>& out) {
+  const double tol = 1e-13, q = kTwoPi / 4;
+  double vx[4], vy[4];
+  H.corners_cw(vx, vy);
+  const double* v = axis == 0 ? vx : vy;
+  for (int k = 0; k < 4; ++k) {
+    const double f0 = v[k] - c, fp = v[(k + 3) % 4] - c, f1 = v[(k + 1) % 4] - c;
+    if (std::fabs(f0) <= tol) {
+      if (fp * f1 < 0.0 && std::fabs(fp) > tol && std::fabs(f1) > tol) out.push_back(k * q);
+      continue;
+    }
+    if (std::fabs(f1) <= tol || f0 * f1 > 0.0) continue;
+    out.push_back(k * q + q * f0 / (f0 - f1));
+  }
 }
 
 // crossings of hole i with hole j: bracket sign changes of j's level function
@@ -371,13 +445,25 @@ LevelGeom build_geometry(const Problem& P, int n) {
   for (int e = 0; e < nh; ++e) {
     const Hole& H = P.holes[e];
     double hx = std::hypot(H.r1 * H.co, H.r2 * H.si), hy = std::hypot(H.r1 * H.si, H.r2 * H.co);
-    if (H.kind == 1) hx = hy = H.r1 + H.r2;
+    double bx0 = H.cx - hx, bx1 = H.cx + hx, by0 = H.cy - hy, by1 = H.cy + hy;   // bounding box
+    if (H.kind == 1) {
+      bx0 = H.cx - H.r1 - H.r2; bx1 = H.cx + H.r1 + H.r2;
+      by0 = H.cy - H.r1 - H.r2; by1 = H.cy + H.r1 + H.r2;
+    } else if (H.kind == 2) {
+      double vx[4], vy[4];
+      H.corners_cw(vx, vy);
+      bx0 = *std::min_element(vx, vx + 4); bx1 = *std::max_element(vx, vx + 4);
+      by0 = *std::min_element(vy, vy + 4); by1 = *std::max_element(vy, vy + 4);
+    }
     std::vector<double> ts;
-    int i0 = std::max(0, (int)std::floor((H.cx - hx - P.x0) / h));
-    int i1 = std::min(n, (int)std::ceil((H.cx + hx - P.x0) / h));
+    if (H.kind == 2)   // the corners are kinks: arcs end there
+      for (int k = 0; k < 4; ++k) ts.push_back(k * kTwoPi / 4);
+    int i0 = std::max(0, (int)std::floor((bx0 - P.x0) / h));
+    int i1 = std::min(n, (int)std::ceil((bx1 - P.x0) / h));
     for (int i = i0; i <= i1; ++i) {
       std::vector<double> r;
-      if (H.kind == 1) flower_line_roots(H, 0, P.x0 + i * h, r);
+      if (H.kind == 2) rect_line_roots(H, 0, P.x0 + i * h, r);
+      else if (H.kind == 1) flower_line_roots(H, 0, P.x0 + i * h, r);
       else trig_roots(H.co * H.r1, -H.si * H.r2, P.x0 + i * h - H.cx, r);
       for (double t : r) {
         double x, y;
@@ -386,11 +472,12 @@ LevelGeom build_geometry(const Problem& P, int n) {
         vline[i].push_back(y);
       }
     }
-    int j0 = std::max(0, (int)std::floor((H.cy - hy - P.y0) / h));
-    int j1 = std::min(n, (int)std::ceil((H.cy + hy - P.y0) / h));
+    int j0 = std::max(0, (int)std::floor((by0 - P.y0) / h));
+    int j1 = std::min(n, (int)std::ceil((by1 - P.y0) / h));
     for (int j = j0; j <= j1; ++j) {
       std::vector<double> r;
-      if (H.kind == 1) flower_line_roots(H, 1, P.y0 + j * h, r);
+      if (H.kind == 2) rect_line_roots(H, 1, P.y0 + j * h, r);
+      else if (H.kind == 1) flower_line_roots(H, 1, P.y0 + j * h, r);
       else trig_roots(H.si * H.r1, H.co * H.r2, P.y0 + j * h - H.cy, r);
       for (double t : r) {
         double x, y;

@@ -23,16 +23,23 @@ struct SetupError : std::runtime_error {
 };
 
 // A hole: kind 0 the ellipse c + R(th) (r1 cos t, r2 sin t); kind 1 the
-// flower c + (r1 + r2 cos(petals t)) (cos t, sin t) (Sec. 6.2).
+// flower c + (r1 + r2 cos(petals t)) (cos t, sin t) (Sec. 6.2); kind 2
+// everything outside the rectangle with corner c and sides r1 (direction th)
+// and r2 (direction th + pi/2), whose sides are the curve, followed
+// clockwise around the rectangle as t grows (a quarter of [0, 2pi) each), so
+// that the domain is on the left from high to low t as for the other holes.
 struct Hole {
   double cx, cy, r1, r2, th, co, si;
   int kind = 0;
   int petals = 0;
-  // point and derivative at parameter t (counter-clockwise)
+  // point and derivative at parameter t
   void at(double t, double& x, double& y) const;
   void dat(double t, double& dx, double& dy) const;
-  double level(double x, double y) const;   // < 0 inside
-  double halfwidth() const { return kind == 1 ? r1 - r2 : std::min(r1, r2); }
+  double level(double x, double y) const;   // < 0 inside the hole
+  double halfwidth() const {
+    return kind == 2 ? 1e300 : kind == 1 ? r1 - r2 : std::min(r1, r2);
+  }
+  void corners_cw(double vx[4], double vy[4]) const;   // kind 2, in the order of t
 };
 
 struct Bc { int type; double a1, a2; };

@@ -264,6 +264,19 @@ class Flower:
 
 
 @dataclass(frozen=True)
+class OutsideRect:
+    """The hole that is everything outside the rectangle with corner (cx, cy)
+    and sides w (along the direction theta) and hgt (along theta + pi/2):
+    with it the domain is the (rotated) rectangle, cut from the box.  The
+    rectangle must lie inside the box."""
+    cx: float
+    cy: float
+    w: float
+    hgt: float
+    theta: float
+
+
+@dataclass(frozen=True)
 class BC:
     kind: int = DIRICHLET
     alpha1: float = 1.0
@@ -282,7 +295,7 @@ class Domain:
     y0: float = 0.0
     x1: float = 1.0
     y1: float = 1.0
-    holes: List[object] = field(default_factory=list)    # Ellipse or Flower
+    holes: List[object] = field(default_factory=list)    # Ellipse, Flower or OutsideRect
     box_bc: Tuple[BC, BC, BC, BC] = (BC(), BC(), BC(), BC())
     hole_bc: List[BC] = field(default_factory=list)
 
@@ -403,6 +416,42 @@ def problem_flower(kind: int = NEUMANN) -> Problem:
     bc = BC(NEUMANN, 0.0, 1.0) if kind == NEUMANN else BC(DIRICHLET, 1.0, 0.0)
     dom = Domain(x0=-0.5, y0=-0.5, x1=0.5, y1=0.5, holes=[Flower(0.0, 0.0, 0.25, 0.05, 6)], hole_bc=[bc])
     return Problem("flower", dom, 1.0, 0.0, 1.0, u, f_flower())
+
+
+def problem_rotated_square() -> Problem:
+    """Sec. 6.1, the rotated square: Omega_r is (0,1)^2 rotated about the
+    origin by pi/6, (a, b, c) = (5, -2 sqrt 3, 7) / 4, u the solution
+    sin(4 x) cos(3 y) of the unit-square case rotated by pi/6, Dirichlet data.
+    The computational box is [-0.625, 0.875] x [-0.125, 1.375] (side 1.5, so
+    that h = 1/64 .. 1/512 divide it and Omega_r lies inside)."""
+    th = math.pi / 6
+    c, s = math.cos(th), math.sin(th)
+
+    def back(x, y):            # rotate (x, y) by -pi/6
+        return c * x + s * y, -s * x + c * y
+
+    def u(x, y):
+        xp, yp = back(x, y)
+        return np.sin(4 * xp) * np.cos(3 * yp)
+
+    def ux(x, y):
+        xp, yp = back(x, y)
+        gx, gy = 4 * np.cos(4 * xp) * np.cos(3 * yp), -3 * np.sin(4 * xp) * np.sin(3 * yp)
+        return c * gx - s * gy
+
+    def uy(x, y):
+        xp, yp = back(x, y)
+        gx, gy = 4 * np.cos(4 * xp) * np.cos(3 * yp), -3 * np.sin(4 * xp) * np.sin(3 * yp)
+        return s * gx + c * gy
+
+    def f(x, y):
+        xp, yp = back(x, y)
+        return -34.0 * np.sin(4 * xp) * np.cos(3 * yp)
+
+    dom = Domain(x0=-0.625, y0=-0.125, x1=0.875, y1=1.375,
+                 holes=[OutsideRect(0.0, 0.0, 1.0, 1.0, th)], hole_bc=[BC()])
+    return Problem("rotated_square", dom, 1.25, -math.sqrt(3.0) / 2.0, 1.75, Pointwise(u, ux, uy),
+                   Pointwise(f))
 
 
 def _boundary_points(e: Ellipse, m: int = 720):

@@ -263,3 +263,28 @@ def test_flower_tables_match_oracle(lib, n):
         assert np.abs(beta[r, :15] - want).max() < 1e-11 * np.abs(want).max()
     assert H.info.n_bd == len(d.bd_cells)
     H.close()
+
+
+@pytest.mark.parametrize("hinv", [64, 128])
+def test_rotated_square_tables_match_oracle(lib, hinv):
+    """The rotated square of Sec. 6.1 (the hole outside a rotated rectangle,
+    corners on grid lines): the library's cell types, volumes, lattices and
+    fit coefficients equal the oracle's."""
+    P = W.problem_rotated_square()
+    n = int(1.5 * hinv)
+    H = _host(P, n, min_coarse_n=n)
+    lev = G.build_level(P.dom, n, 0.1)
+    d = D.discretize(lev, P.a, P.b, P.c)
+    typ, kind, vol = H.cell_types()
+    np.testing.assert_array_equal(kind, d.kind)
+    np.testing.assert_array_equal(typ, lev.ctype)
+    assert np.abs(vol - lev.vol).max() < 1e-15
+    _, lat, beta = H.level_tables(0)
+    plg = sorted(d.lattices)
+    assert len(plg) == len(lat)
+    for r, k in enumerate(plg):
+        np.testing.assert_array_equal(lat[r], d.lattices[k])
+        want = np.array(list(d.betas[k]))
+        assert np.abs(beta[r, :15] - want).max() < 1e-11 * np.abs(want).max()
+    assert H.info.n_bd == len(d.bd_cells)
+    H.close()

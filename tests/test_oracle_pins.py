@@ -757,3 +757,52 @@ def test_flower_two_grid_spectral_radius():
             assert round(w, 3) == float(want), (nu1, nu2, w)
         else:
             assert 0.9 * float(want) < w <= float(want) + 1e-3, (nu1, nu2, w)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 6.1, the rotated square: the cross-derivative term and PLG rows on a
+# boundary that is not aligned with the grid
+# ---------------------------------------------------------------------------
+def _rotated_norms(hinv):
+    P = W.problem_rotated_square()
+    n = int(round(1.5 * hinv))          # the box has side 1.5
+    lev = G.build_level(P.dom, n, 0.1)
+    assert lev.resolved
+    assert abs(lev.vol.sum() - 1.0) < 1e-12      # the area of Omega_r
+    d = D.discretize(lev, P.a, P.b, P.c)
+    b = D.rhs(d, D.cell_averages(lev, P.f), D.boundary_data(d, P.u))
+    u = spl.spsolve(d.A.tocsc(), b.ravel()).reshape(n, n)
+    e = np.abs(u - D.cell_averages(lev, P.u))
+    e[~lev.present] = 0.0
+    return np.array([e.max(), (e * lev.vol).sum(), math.sqrt((e * e * lev.vol).sum())])
+
+
+def test_rotated_square_error_norms():
+    """Table 3, lower half: at h = 1/128 the oracle's L-inf, L1 and L2 errors
+    on Omega_r are within 5 % of the printed 8.85e-9, 2.95e-9, 3.72e-9
+    (8.64e-9, 2.94e-9, 3.67e-9); at h = 1/64 the L1 and L2 errors are within
+    15 % (5.07e-8, 6.37e-8) and the L-inf error within 10x (9.2e-7 against
+    1.35e-7: one cell of a coarse lattice); fourth order in L1 and L2."""
+    printed = {int(r[0]): np.array([float(v) for v in r[1:]]) for r in _golden("table3_rotated_square.txt")}
+    e64, e128 = _rotated_norms(64), _rotated_norms(128)
+    assert np.all(np.abs(e128 / printed[128] - 1.0) < 0.05), (e128, printed[128])
+    assert np.all(np.abs(e64[1:] / printed[64][1:] - 1.0) < 0.15), (e64, printed[64])
+    assert printed[64][0] / 10 < e64[0] < printed[64][0] * 10
+    rate = np.log2(e64[1:] / e128[1:])
+    assert np.all(rate > 3.9), rate
+
+
+def test_rotated_square_two_grid_spectral_radius():
+    """Table 2, rotated-square row, at h = 1/64 (two grids): the oracle's
+    spectral radii of TG (Eq. 5.12) are the printed ones to within one unit
+    in the third digit (1.109 / 0.744 / 0.523 / 0.421 / 0.275 against
+    1.110 / 0.745 / 0.523 / 0.421 / 0.275)."""
+    P = W.problem_rotated_square()
+    n = 96
+    H = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=n // 2)
+    assert H.nl == 2
+    for nu1, nu2, want in _golden("table2_rotated_square.txt"):
+        op = M.two_grid_operator(H, int(nu1), int(nu2))
+        v0 = np.random.default_rng(0).standard_normal(n * n)
+        w = abs(eigs(op, k=1, which="LM", return_eigenvectors=False, tol=1e-9, maxiter=20000, v0=v0)[0])
+        assert abs(w - float(want)) <= 1.5e-3, (nu1, nu2, w)
