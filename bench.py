@@ -77,6 +77,9 @@ def _args():
                     help="grids of the ellipse-union measurement (none: skip)")
     ap.add_argument("--hbm-n", type=int, default=4096,
                     help="grid of the HBM-bound sweep measurement (0: skip)")
+    ap.add_argument("--setup", type=int, default=1,
+                    help="also time the setup with its per-cell steps on the device and on host "
+                         "threads (0: skip)")
     ap.add_argument("--mcgs", type=int, default=1,
                     help="also time the headline problem with the multicolour smoother (0: skip)")
     ap.add_argument("--batch", type=int, default=8,
@@ -411,6 +414,7 @@ def run_ours(a):
     ellipse = run_ellipse_union(a, dev) if a.ellipse_union else None
     random_domains = run_random_domains(a, dev) if a.random_domains > 0 else None
     mcgs = run_mcgs(a, dev) if a.mcgs else None
+    setup = run_setup(a, dev) if a.setup else None
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -442,6 +446,7 @@ def run_ours(a):
         "ellipse_union": ellipse,
         "random_domains": random_domains,
         "multicolour_smoother": mcgs,
+        "setup": setup,
         "fp64_solve": {"ms": fp64_ms, "dof_per_s": dof / (fp64_ms / 1e3), "cycles": r64.cycles,
                        "max_error_vs_exact": err64, "steps": a.steps, "warmup": a.warmup,
                        "timing": "CUDA events around each solve, L2 flushed between steps, as the "
@@ -584,6 +589,40 @@ def run_ellipse_union(a, dev):
             H.close()
         out[str(n)] = row
     cache_clear()
+    return out
+
+
+def run_setup(a, dev):
+    """Setup time of the headline disk problem (1024^2) and of the 4096^2
+    ellipse union, with the per-cell steps (classification, Def. 4.1 kinds,
+    lattices, fits, curve-order samples) as CUDA kernels and on host threads;
+    the two must give the same tables, bit for bit (checked on the finest
+    level).  Wall clock around cc_setup; the split comes from cc_info."""
+    import numpy as np
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from paper_2601_02975_gb300 import workloads as W
+    out = {"host_threads": os.cpu_count(), "cpu_model": _cpu_model()}
+    for name, P, n in (("disk_1024", _problem(), a.n), ("ellipses0_4096", W.problem_ellipses(0), 4096)):
+        row = {}
+        tabs = []
+        for d, key in ((1, "device"), (0, "host")):
+            t = time.perf_counter()
+            H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                      default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=1,
+                                                      w_depth=W_DEPTH, nu1=NU, nu2=NU, device_setup=d))
+            wall = time.perf_counter() - t
+            info = H.info
+            row[key] = {"s": wall, "tables_s": info.setup_tables_seconds,
+                        "other_s": info.setup_seconds - info.setup_tables_seconds,
+                        "kernel_ms": info.setup_kernel_ms}
+            _, lat, beta = H.level_tables(0)
+            tabs.append((H.cell_types()[1].copy(), lat.copy(), beta.view(np.uint64).copy(),
+                         H.level_block(0).copy()))
+            row["plg_cells"] = int(info.n_plg)
+            H.close()
+        row["tables_equal"] = all(np.array_equal(x, y) for x, y in zip(*tabs))
+        row["tables_speedup"] = row["host"]["tables_s"] / row["device"]["tables_s"]
+        out[name] = row
     return out
 
 

@@ -140,6 +140,13 @@ typedef struct {
                           two-grid rate of 2 + 2 sweeps is then about that of the
                           Jacobi smoother's 3 + 3), and omega 1 diverges on this
                           fourth-order stencil */
+  int device_setup;    /* 1 (default): the per-cell steps of the setup run as FP64
+                          CUDA kernels, one thread per cell: the classification of
+                          the cells no curve crosses (Sec. 3.1), the kinds of Def.
+                          4.1, the poised lattices (Def. 4.3), the fits (Eq. 4.14,
+                          4.17-4.18) and the curve-order samples of Def. 5.1; the
+                          tables are bitwise those of the host path.  0: the same
+                          steps on host threads.  Ignored with host_only */
 } cc_options;
 
 /* Sizes of a hierarchy. */
@@ -160,6 +167,13 @@ typedef struct {
   int block_chunks[32];/* how that block is solved: 0 with its dense inverse in one launch
                           (up to 1024 cells), else the number of chunks of the two-launch
                           chunked form (one CTA per chunk) */
+  double setup_seconds;   /* wall time of the cc_setup call that built the tables
+                             (0 for a clone or a cached setup) */
+  double setup_tables_seconds; /* of which the per-level tables of Sec. 3-4: cut cells,
+                             merging, kinds, lattices, fits, block order and rows (the
+                             rest: the factorisations of the block smoother and the
+                             bottom solve, and the uploads) */
+  double setup_kernel_ms; /* device time of the setup kernels (device_setup) */
 } cc_info;
 
 /* Outcome of a solve. */
@@ -399,6 +413,14 @@ cc_status cc_smooth_noalloc(cc_handle h, int level, double* d_u, const double* d
  */
 cc_status cc_level_tables(cc_handle h, int level, uint8_t* h_kind, int* h_lattice,
                           double* h_beta, int* n_plg);
+
+/*
+ * cc_level_block: copy the cells of level l's exactly solved block (Eq. 5.8:
+ * the PLG cells, and with b != 0 the SFV cells within 4 cells of a box
+ * corner) in the solve order of Def. 5.1 to host memory (h_cells[m], may
+ * be NULL); *m receives the count.
+ */
+cc_status cc_level_block(cc_handle h, int level, int* h_cells, int* m);
 
 /* Kernels that cc_kernel_timing can time. */
 enum { CC_TIME_OFF = 0, CC_TIME_FINE_SWEEP = 1, CC_TIME_BLOCK = 2, CC_TIME_FINE_BLOCK = 3 };

@@ -62,6 +62,13 @@ def build(verbose: bool = False, force: bool = False) -> str:
                  "-Xcompiler", "-ffp-contract=off",
                  "-Xptxas", "-v" if verbose else "-O3",
                  "-c", os.path.join(CSRC, "capi.cu"), "-o", obj] + inc)
+    # the device setup steps: no fused multiply-adds, so they round like the host
+    obj = os.path.join(BUILD, "setup_dev.cu.o")
+    objs.append(obj)
+    jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
+                 "-Xcompiler", "-ffp-contract=off", "--fmad=false",
+                 "-Xptxas", "-v" if verbose else "-O3",
+                 "-c", os.path.join(CSRC, "setup_dev.cu"), "-o", obj] + inc)
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose:

@@ -42,7 +42,7 @@ class cc_options(C.Structure):
                 ("max_cycles", C.c_int), ("use_graphs", C.c_int), ("host_only", C.c_int),
                 ("fmg_cycle", C.c_int), ("w_depth", C.c_int), ("serve_slots", C.c_int),
                 ("cache", C.c_int), ("hole_cells", C.c_double), ("krylov", C.c_int),
-                ("smoother", C.c_int)]
+                ("smoother", C.c_int), ("device_setup", C.c_int)]
 
 
 class cc_info(C.Structure):
@@ -50,7 +50,9 @@ class cc_info(C.Structure):
                 ("n_g", C.c_int), ("n_plg", C.c_int), ("n_block", C.c_int),
                 ("device_bytes", C.c_int64), ("level_n", C.c_int * 32),
                 ("block_error", C.c_double), ("bottom_error", C.c_double),
-                ("block_m", C.c_int * 32), ("block_chunks", C.c_int * 32)]
+                ("block_m", C.c_int * 32), ("block_chunks", C.c_int * 32),
+                ("setup_seconds", C.c_double), ("setup_tables_seconds", C.c_double),
+                ("setup_kernel_ms", C.c_double)]
 
 
 class cc_result(C.Structure):
@@ -99,6 +101,7 @@ _SIGS = {
     "cc_prolong_add": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "cc_cycle": (C.c_int, [_P, _P, _P, _P]),
     "cc_level_tables": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(C.c_int)]),
+    "cc_level_block": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int)]),
     "cc_kernel_timing": (C.c_int, [_P, C.c_int]),
     "cc_kernel_timing_read": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -258,6 +261,14 @@ class Hierarchy:
         _check(lib().cc_level_tables(self.h, level, _hptr(kind), _hptr(lat), _hptr(beta),
                                      C.byref(m)), "cc_level_tables")
         return kind.reshape(n, n), lat[:m.value], beta[:m.value]
+
+    def level_block(self, level: int) -> np.ndarray:
+        """Cells of the level's exactly solved block, in solve order."""
+        m = C.c_int()
+        _check(lib().cc_level_block(self.h, level, None, C.byref(m)), "cc_level_block")
+        out = np.zeros(max(1, m.value), np.int32)
+        _check(lib().cc_level_block(self.h, level, _hptr(out), C.byref(m)), "cc_level_block")
+        return out[:m.value]
 
     # --- solves ------------------------------------------------------------
     def solve(self, f, g, u, tol: float, stream=None) -> cc_result:

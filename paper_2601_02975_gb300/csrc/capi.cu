@@ -706,6 +706,9 @@ struct cc_hierarchy {
   double* bottom_inv = nullptr;   // column-major FP64
   double bottom_error = 0;
   int nc_bottom = 0;
+  double setup_seconds = 0;       // wall time of the cc_setup that built the tables
+  double setup_tables_seconds = 0;  // of which discretize (all levels)
+  double setup_kernel_ms = 0;     // device time of its setup kernels
   // finest-level extras
   double* f_rhs = nullptr;        // b of the finest level (FP64)
   double* r64 = nullptr;          // FP64 residual
@@ -1881,6 +1884,7 @@ void cc_default_options(cc_options* o) {
   o->hole_cells = 2.0;
   o->krylov = 0;
   o->smoother = CC_SMOOTHER_JACOBI;
+  o->device_setup = 1;
 }
 
 const char* cc_last_error_string(void) { return t_last_error; }
@@ -1943,6 +1947,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       return st;
     }
   }
+  const double t_setup0 = now_s();
   cc_hierarchy* H = new cc_hierarchy();
   H->opt = o;
   Problem& P = H->P;
@@ -1969,9 +1974,11 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     P.bc.push_back({bc[k].type, bc[k].alpha1, bc[k].alpha2});
   }
   const bool dev = !o.host_only;
+  std::unique_ptr<SetupDevice> sdev;
   try {
     if (dev) {
       CK(cudaGetDevice(&H->device));
+      if (o.device_setup) sdev = std::make_unique<SetupDevice>((void*)s);
       pdl_setup_device();
       chunk_smem_attributes();
       // norm words: [0] the max-norm of a residual, [1] the fault word of
@@ -1992,7 +1999,9 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       }
       LevelDisc D;
       try {
-        D = discretize(P, nl);
+        const double t_d = now_s();
+        D = discretize(P, nl, sdev.get());
+        H->setup_tables_seconds += now_s() - t_d;
         if (!D.geom.resolved) throw SetupError(2, D.geom.reason);
       } catch (SetupError& e) {
         if (H->lv.empty()) throw;
@@ -2144,10 +2153,18 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     CK(cudaStreamCreateWithFlags(&H->gstream, cudaStreamNonBlocking));
     CK(cudaStreamSynchronize(s));
   done:;
+    if (sdev) H->setup_kernel_ms = sdev->kernel_ms;
+    sdev.reset();
   } catch (SetupError& e) {
     cc_status st = from_setup(e.code);
+    sdev.reset();
     destroy_hierarchy(H);
     return st;
+  } catch (DeviceError& e) {
+    snprintf(t_last_error, sizeof(t_last_error), "%s", e.what());
+    sdev.reset();
+    destroy_hierarchy(H);
+    return e.err == (int)cudaErrorMemoryAllocation ? CC_ERR_NO_MEMORY : CC_ERR_CUDA;
   } catch (CudaError& e) {
     destroy_hierarchy(H);
     return e.e == cudaErrorMemoryAllocation ? CC_ERR_NO_MEMORY : CC_ERR_CUDA;
@@ -2155,6 +2172,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     destroy_hierarchy(H);
     return CC_ERR_NO_MEMORY;
   }
+  H->setup_seconds = now_s() - t_setup0;
   if (!key.empty()) {
     // the cache keeps a clone of its own, so destroying H leaves it valid
     cc_hierarchy* T = nullptr;
@@ -2195,6 +2213,17 @@ cc_status cc_query(cc_handle H, cc_info* out) {
     out->block_chunks[l] = H->lv[l]->plan().dense ? 0 : H->lv[l]->plan().nch;
   }
   out->bottom_error = H->bottom_error;
+  out->setup_seconds = H->setup_seconds;
+  out->setup_tables_seconds = H->setup_tables_seconds;
+  out->setup_kernel_ms = H->setup_kernel_ms;
+  return CC_OK;
+}
+
+cc_status cc_level_block(cc_handle H, int level, int* h_cells, int* m) {
+  if (!H || !m || level < 0 || level >= (int)H->lv.size()) return CC_ERR_ARG;
+  const std::vector<int>& b = H->lv[level]->disc().block;
+  *m = (int)b.size();
+  if (h_cells) std::copy(b.begin(), b.end(), h_cells);
   return CC_OK;
 }
 

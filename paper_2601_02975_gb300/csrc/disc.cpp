@@ -49,9 +49,6 @@ namespace {
 const double kLap[5] = {-1, 16, -30, 16, -1};
 const double kGrad[5] = {1, -8, 0, 8, -1};
 const double kExt[2][5] = {{5, -10, 10, -5, 1}, {15, -40, 45, -24, 5}};
-const int kRadius = 6;       // largest search box (13 x 13)
-const int kRadiusFirst = 4;  // first search box (9 x 9)
-const int kCutPenalty = 2;
 
 void ghost_coefs(const Bc& bc, double h, double out[2][5]) {
   double a1 = 1.0, a2 = 0.0;
@@ -77,98 +74,6 @@ inline int inward(int n, int w, int t, int q) {
     case 2: return (n - 1 - q) * n + t;     // north
     default: return t * n + q;              // west
   }
-}
-
-// --- small dense linear algebra ---------------------------------------------
-// Solve A x = b (n x n, row-major) by Gaussian elimination with partial pivoting.
-bool lu_solve(std::vector<double> A, std::vector<double>& b, int n) {
-  for (int c = 0; c < n; ++c) {
-    int p = c;
-    for (int r = c + 1; r < n; ++r)
-      if (std::fabs(A[r * n + c]) > std::fabs(A[p * n + c])) p = r;
-    if (A[p * n + c] == 0.0) return false;
-    if (p != c) {
-      for (int k = 0; k < n; ++k) std::swap(A[p * n + k], A[c * n + k]);
-      std::swap(b[p], b[c]);
-    }
-    for (int r = c + 1; r < n; ++r) {
-      double l = A[r * n + c] / A[c * n + c];
-      if (l == 0.0) continue;
-      for (int k = c; k < n; ++k) A[r * n + k] -= l * A[c * n + k];
-      b[r] -= l * b[c];
-    }
-  }
-  for (int r = n - 1; r >= 0; --r) {
-    double s = b[r];
-    for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * b[k];
-    b[r] = s / A[r * n + r];
-  }
-  return true;
-}
-
-// Minimum 2-norm solution of B x = rhs, B (m x n) with m < n of full row
-// rank, by Householder QR of B^T: B^T = Q R, x = Q (R^-T rhs).
-bool min_norm(const std::vector<double>& B, const std::vector<double>& rhs, int m, int n,
-              std::vector<double>& x) {
-  // T = B^T, n x m, column-major copy for the reflections
-  std::vector<double> T((size_t)n * m);
-  for (int r = 0; r < m; ++r)
-    for (int c = 0; c < n; ++c) T[(size_t)r * n + c] = B[(size_t)r * n + c];  // column r of T
-  std::vector<std::vector<double>> V(m);
-  std::vector<double> Rdiag(m);
-  for (int k = 0; k < m; ++k) {
-    double* col = &T[(size_t)k * n];
-    double nrm = 0;
-    for (int i = k; i < n; ++i) nrm += col[i] * col[i];
-    nrm = std::sqrt(nrm);
-    if (nrm == 0.0) return false;
-    double alpha = col[k] > 0 ? -nrm : nrm;
-    std::vector<double> v(n, 0.0);
-    for (int i = k; i < n; ++i) v[i] = col[i];
-    v[k] -= alpha;
-    double vn = 0;
-    for (int i = k; i < n; ++i) vn += v[i] * v[i];
-    for (int j = k; j < m; ++j) {
-      double* cj = &T[(size_t)j * n];
-      double s = 0;
-      for (int i = k; i < n; ++i) s += v[i] * cj[i];
-      s = 2.0 * s / vn;
-      for (int i = k; i < n; ++i) cj[i] -= s * v[i];
-    }
-    V[k] = v;
-    Rdiag[k] = T[(size_t)k * n + k];
-  }
-  // R^T y = rhs (forward), R(i, j) = T[j*n + i] for i <= j
-  std::vector<double> y(m);
-  for (int i = 0; i < m; ++i) {
-    double s = rhs[i];
-    for (int j = 0; j < i; ++j) s -= T[(size_t)i * n + j] * y[j];
-    if (T[(size_t)i * n + i] == 0.0) return false;
-    y[i] = s / T[(size_t)i * n + i];
-  }
-  // x = Q [y; 0] = H_0 H_1 ... H_{m-1} [y; 0]
-  x.assign(n, 0.0);
-  for (int i = 0; i < m; ++i) x[i] = y[i];
-  for (int k = m - 1; k >= 0; --k) {
-    const std::vector<double>& v = V[k];
-    double vn = 0, s = 0;
-    for (int i = k; i < n; ++i) { vn += v[i] * v[i]; s += v[i] * x[i]; }
-    s = 2.0 * s / vn;
-    for (int i = k; i < n; ++i) x[i] -= s * v[i];
-  }
-  return true;
-}
-
-// basis monomials of total degree <= 4
-struct Mono { int p, q; };
-const std::vector<Mono>& basis() {
-  static std::vector<Mono> b = [] {
-    std::vector<Mono> v;
-    for (int d = 0; d <= 4; ++d)
-      for (int p = d; p >= 0; --p) v.push_back({p, d - p});
-    return v;
-  }();
-  return b;
 }
 
 }  // namespace
@@ -220,14 +125,14 @@ void LevelDisc::row(int k, std::map<int, double>& arow, std::map<int, double>* n
         if (m1 && m2) add(i + m1, j + m2, b * kGrad[m1 + 2] * kGrad[m2 + 2] / (144.0 * h2));
 }
 
-LevelDisc discretize(const Problem& P, int n) {
+LevelDisc discretize(const Problem& P, int n, SetupDevice* dev) {
   LevelDisc D;
   D.P = &P;
   D.n = n;
   D.a = P.a;
   D.b = P.b;
   D.c = P.c;
-  D.geom = build_geometry(P, n);
+  D.geom = build_geometry(P, n, dev);
   const LevelGeom& G = D.geom;
   D.h = G.h;
   const double h = G.h;
@@ -242,247 +147,86 @@ LevelDisc discretize(const Problem& P, int n) {
       D.ext[w][t] = ok;
     }
   }
-  auto ghost_ok = [&](int ii, int jj) {
-    bool ox = ii < 0 || ii >= n, oy = jj < 0 || jj >= n;
-    if (ox && oy) {
-      if (n < 5) return false;
-      int wx = ii < 0 ? 3 : 1, wy = jj < 0 ? 0 : 2;
-      for (int q = 0; q < 5; ++q) {
-        if (!D.ext[wx][jj < 0 ? q : n - 1 - q]) return false;
-        if (!D.ext[wy][ii < 0 ? q : n - 1 - q]) return false;
-      }
-      return true;
-    }
-    if (ii >= n) return (bool)D.ext[1][jj];
-    if (ii < 0) return (bool)D.ext[3][jj];
-    if (jj >= n) return (bool)D.ext[2][ii];
-    return (bool)D.ext[0][ii];
-  };
   // --- Def. 4.1 ------------------------------------------------------------
+  std::vector<uint8_t> extf((size_t)4 * n, 0);
+  for (int w = 0; w < 4; ++w)
+    for (int t = 0; t < n; ++t) extf[(size_t)w * n + t] = D.ext[w][t];
+  const bool cross = P.b != 0.0;
   D.kind.assign((size_t)n * n, K_EMPTY);
-  for (int j = 0; j < n; ++j)
-    for (int i = 0; i < n; ++i) {
-      int k = j * n + i;
-      if (G.type[k] == CT_EMPTY) continue;
-      bool sfv = G.type[k] == CT_FULL;
-      for (int dj = -2; dj <= 2 && sfv; ++dj)
-        for (int di = -2; di <= 2 && sfv; ++di) {
-          if (P.b == 0.0 && di && dj) continue;
-          int ii = i + di, jj = j + dj;
-          if (ii >= 0 && jj >= 0 && ii < n && jj < n) sfv = G.type[jj * n + ii] == CT_FULL;
-          else sfv = ghost_ok(ii, jj);
-        }
-      D.kind[k] = sfv ? K_SFV : K_PLG;
-    }
+  if (dev) {
+    dev->kinds(n, cross, G.type.data(), extf.data(), D.kind.data());
+  } else {
+    parallel_rows(n, [&](int j) {
+      for (int k = j * n; k < (j + 1) * n; ++k)
+        D.kind[k] = cell::kind_of(G.type.data(), extf.data(), n, cross, k);
+    });
+  }
   // --- PLG cells: lattice and fit --------------------------------------------
   for (int k = 0; k < n * n; ++k)
     if (D.kind[k] == K_PLG) D.plg.push_back(k);
-  const auto& B = basis();
-  // the fits are independent: computed on all host cores into per-cell slots,
-  // then appended in PLG order (the result does not depend on the threads)
-  struct PlgOut {
-    std::array<int, 15> lat{};
-    std::array<double, 16> bt{};
-    bool withb = false;
-    int err = 0;
-    const char* msg = "";
-  };
-  std::vector<PlgOut> outs(D.plg.size());
-  auto fit_one = [&](size_t pr) {
-    const int k = D.plg[pr];
-    PlgOut& O = outs[pr];
-    const int i0 = k % n, j0 = k / n;
-    // lattice: dynamic programme over lines
-    struct Cand { int cost; int orient; std::vector<int> key; std::vector<int> cells; bool ok = false; };
-    Cand best;
-    for (int R = kRadiusFirst; R <= kRadius && !best.ok; ++R)
-    for (int orient = 0; orient < 2; ++orient) {
-      std::vector<std::vector<int>> avail(2 * kRadius + 1);
-      // cost of the cell at offset (u, v): u^2 + v^2, plus kCutPenalty for a
-      // cut cell other than the cell itself (its centroid is off the line)
-      int cost[2 * kRadius + 1][2 * kRadius + 1];
-      for (int v = -R; v <= R; ++v) {
-        auto& us = avail[v + kRadius];
-        for (int u = -R; u <= R; ++u) {
-          int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
-          int ii = i0 + di, jj = j0 + dj;
-          if (ii >= 0 && jj >= 0 && ii < n && jj < n && G.type[jj * n + ii] != CT_EMPTY) {
-            us.push_back(u);
-            bool cut = G.type[jj * n + ii] == CT_CUT && (di != 0 || dj != 0);
-            cost[v + kRadius][u + kRadius] = u * u + v * v + (cut ? kCutPenalty : 0);
-          }
-        }
-        const int* cv = cost[v + kRadius];
-        std::sort(us.begin(), us.end(), [&](int x, int y) {
-          int cx = cv[x + kRadius], cy = cv[y + kRadius];
-          return cx != cy ? cx < cy : x < y;
-        });
-      }
-      const int counts[5] = {5, 4, 3, 2, 1};
-      struct St { bool have = false; int cost = 0; std::vector<int> key; std::vector<int> asg; };
-      std::vector<St> nxt(32), cur(32);
-      nxt[31].have = true;
-      nxt[31].asg.assign(2 * kRadius + 1, 0);
-      for (int v = R; v >= -R; --v) {
-        const auto& us = avail[v + kRadius];
-        for (int mask = 0; mask < 32; ++mask) {
-          St bestS;
-          auto consider = [&](int cost, std::vector<int> key, std::vector<int> asg) {
-            if (!bestS.have || cost < bestS.cost || (cost == bestS.cost && key < bestS.key)) {
-              bestS.have = true;
-              bestS.cost = cost;
-              bestS.key = std::move(key);
-              bestS.asg = std::move(asg);
-            }
-          };
-          if (nxt[mask].have) {
-            std::vector<int> key{0};
-            key.insert(key.end(), nxt[mask].key.begin(), nxt[mask].key.end());
-            consider(nxt[mask].cost, key, nxt[mask].asg);
-          }
-          for (int bit = 0; bit < 5; ++bit) {
-            int cnt = counts[bit];
-            if ((mask >> bit) & 1 || (int)us.size() < cnt) continue;
-            int m2 = mask | (1 << bit);
-            if (!nxt[m2].have) continue;
-            int rc = 0;
-            for (int q = 0; q < cnt; ++q) rc += cost[v + kRadius][us[q] + kRadius];
-            std::vector<int> key{-cnt};
-            key.insert(key.end(), nxt[m2].key.begin(), nxt[m2].key.end());
-            std::vector<int> asg = nxt[m2].asg;
-            asg[v + kRadius] = cnt;
-            consider(nxt[m2].cost + rc, key, asg);
-          }
-          cur[mask] = bestS;
-        }
-        std::swap(nxt, cur);
-      }
-      if (!nxt[0].have) continue;
-      if (!best.ok || nxt[0].cost < best.cost) {
-        best.ok = true;
-        best.cost = nxt[0].cost;
-        best.orient = orient;
-        best.cells.clear();
-        for (int v = -R; v <= R; ++v) {
-          int cnt = nxt[0].asg[v + kRadius];
-          for (int q = 0; q < cnt; ++q) {
-            int u = avail[v + kRadius][q];
-            int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
-            best.cells.push_back((j0 + dj) * n + (i0 + di));
-          }
-        }
-      }
+  const size_t np = D.plg.size();
+  const int npi = (int)np;
+  std::vector<int> lat(np * 15);
+  std::vector<uint8_t> ok(np, 0);
+  if (dev) {
+    if (np) dev->lattices(n, D.plg, lat.data(), ok.data());
+  } else {
+    parallel_rows(npi, [&](int r) {
+      ok[r] = cell::plg_lattice(G.type.data(), n, D.plg[r], &lat[(size_t)15 * r]);
+    }, 16);
+  }
+  for (size_t r = 0; r < np; ++r)
+    if (!ok[r]) throw SetupError(3, "no poised lattice for a PLG cell");
+  // boundary nodes of the cut PLG cells, the moments of the cut cells, and
+  // (alpha1, alpha2) of each condition
+  std::vector<BNode> bnode;
+  std::vector<int> bptr(np + 1, 0);
+  for (size_t r = 0; r < np; ++r) {
+    if (G.type[D.plg[r]] == CT_CUT) {
+      std::vector<BNode> bn = boundary_nodes(P, G, D.plg[r]);
+      bnode.insert(bnode.end(), bn.begin(), bn.end());
     }
-    if (!best.ok || best.cells.size() != 15) {
-      O.err = 3;
-      O.msg = "no poised lattice for a PLG cell";
-      return;
+    bptr[r + 1] = (int)bnode.size();
+  }
+  std::vector<double> a12;
+  for (const Bc& bc : P.bc) {
+    a12.push_back(bc.type == BC_D ? 1.0 : bc.type == BC_N ? 0.0 : bc.a1);
+    a12.push_back(bc.type == BC_D ? 0.0 : bc.type == BC_N ? 1.0 : bc.a2);
+  }
+  std::vector<double> beta(np * 16);
+  if (dev) {
+    std::vector<int> cut_cells;
+    std::vector<double> cut_mom;
+    for (const auto& kv : G.cut) {
+      cut_cells.push_back(kv.first);
+      cut_mom.insert(cut_mom.end(), kv.second.mom, kv.second.mom + kMoments);
     }
-    std::sort(best.cells.begin(), best.cells.end());
-    std::array<int, 15> lat;
-    std::copy(best.cells.begin(), best.cells.end(), lat.begin());
-    O.lat = lat;
-    // --- fit: rows basis functions, columns lattice cells (+ boundary) -------
-    bool withb = false;
-    std::vector<BNode> bn;
-    if (G.type[k] == CT_CUT) {
-      bn = boundary_nodes(P, G, k);
-      withb = !bn.empty();
-    }
-    const int nc = withb ? 16 : 15;
-    std::vector<double> M((size_t)15 * nc, 0.0), rhs(15, 0.0);
-    for (int c = 0; c < 15; ++c) {
-      int kj = lat[c];
-      double m0[kMoments], ms[kMoments];
-      G.moments(kj, m0);
-      shift_moments(m0, (kj % n) - i0, (kj / n) - j0, ms);
-      for (int r = 0; r < 15; ++r) M[(size_t)r * nc + c] = ms[midx(B[r].p, B[r].q)] / ms[0];
-    }
-    {
-      double mi[kMoments];
-      G.moments(k, mi);
-      auto avg = [&](int p, int q) { return mi[midx(p, q)] / mi[0]; };
-      for (int r = 0; r < 15; ++r) {
-        int p = B[r].p, q = B[r].q;
-        double v = 0;
-        if (p >= 2) v += P.a * p * (p - 1) * avg(p - 2, q);
-        if (p >= 1 && q >= 1) v += P.b * p * q * avg(p - 1, q - 1);
-        if (q >= 2) v += P.c * q * (q - 1) * avg(p, q - 2);
-        rhs[r] = v / (h * h);
-      }
-    }
-    std::array<double, 16> bt{};
-    if (withb) {
-      double px = G.x0 + (i0 + 0.5) * h, py = G.y0 + (j0 + 0.5) * h, ws = 0;
-      std::vector<double> col(15, 0.0);
-      for (const BNode& nd : bn) {
-        const Bc& bc = P.bc[nd.bc];
-        double a1 = bc.type == BC_D ? 1.0 : bc.type == BC_N ? 0.0 : bc.a1;
-        double a2 = bc.type == BC_D ? 0.0 : bc.type == BC_N ? 1.0 : bc.a2;
-        double X = (nd.x - px) / h, Y = (nd.y - py) / h;
-        for (int r = 0; r < 15; ++r) {
-          int p = B[r].p, q = B[r].q;
-          double phi = std::pow(X, p) * std::pow(Y, q);
-          double gx = p ? p * std::pow(X, p - 1) * std::pow(Y, q) / h : 0.0;
-          double gy = q ? q * std::pow(X, p) * std::pow(Y, q - 1) / h : 0.0;
-          col[r] += nd.w * (a1 * phi + a2 * (gx * nd.nx + gy * nd.ny));
-        }
-        ws += nd.w;
-      }
-      for (int r = 0; r < 15; ++r) M[(size_t)r * nc + 15] = col[r] / ws;
-      // weighted minimum norm (Eq. 4.17-4.18): beta = W^1/2 pinv(M W^1/2) rhs
-      double sw[16];
-      for (int c = 0; c < 15; ++c) {
-        int kj = lat[c];
-        double d = std::hypot((double)(kj % n - i0), (double)(kj / n - j0));
-        sw[c] = 1.0 / std::sqrt(std::max(d, 0.5));
-      }
-      sw[15] = 1.0 / std::sqrt(0.5);
-      std::vector<double> Ms(M);
-      for (int r = 0; r < 15; ++r)
-        for (int c = 0; c < 16; ++c) Ms[(size_t)r * 16 + c] *= sw[c];
-      std::vector<double> g;
-      if (!min_norm(Ms, rhs, 15, 16, g)) {
-        O.err = 3;
-        O.msg = "singular PLG fit";
-        return;
-      }
-      for (int c = 0; c < 16; ++c) bt[c] = sw[c] * g[c];
-      O.withb = true;
+    if (np)
+      dev->fits(n, h, G.x0, G.y0, P.a, P.b, P.c, D.plg, lat.data(), cut_cells, cut_mom, bnode,
+                bptr, a12, beta.data(), ok.data());
+  } else {
+    auto mom = [&](int kj, double* o) { G.moments(kj, o); };
+    parallel_rows(npi, [&](int r) {
+      const int nb = bptr[r + 1] - bptr[r];
+      ok[r] = cell::plg_fit(D.plg[r], n, h, P.a, P.b, P.c, &lat[(size_t)15 * r], mom,
+                            nb ? &bnode[bptr[r]] : nullptr, nb, a12.data(), G.x0, G.y0,
+                            &beta[(size_t)16 * r]);
+    }, 16);
+  }
+  for (size_t r = 0; r < np; ++r) {
+    if (!ok[r]) throw SetupError(3, "singular PLG fit");
+    std::array<int, 15> la;
+    std::copy(&lat[15 * r], &lat[15 * r] + 15, la.begin());
+    D.lattice.push_back(la);
+    if (bptr[r + 1] > bptr[r]) {
+      D.bd_of_plg.push_back((int)D.bd_cells.size());
+      D.bd_cells.push_back(D.plg[r]);
     } else {
-      std::vector<double> x(rhs);
-      if (!lu_solve(M, x, 15)) {
-        O.err = 3;
-        O.msg = "singular PLG fit";
-        return;
-      }
-      for (int c = 0; c < 15; ++c) bt[c] = x[c];
-      bt[15] = 0.0;
+      D.bd_of_plg.push_back(-1);
     }
-    O.bt = bt;
-  };
-  {
-    const size_t np = D.plg.size();
-    unsigned T = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
-    if (np < 256) T = 1;
-    std::vector<std::thread> pool;
-    for (unsigned t = 1; t < T; ++t)
-      pool.emplace_back([&, t] {
-        for (size_t r = t; r < np; r += T) fit_one(r);
-      });
-    for (size_t r = 0; r < np; r += T) fit_one(r);
-    for (auto& th : pool) th.join();
-    for (size_t r = 0; r < np; ++r) {
-      if (outs[r].err) throw SetupError(outs[r].err, outs[r].msg);
-      D.lattice.push_back(outs[r].lat);
-      if (outs[r].withb) {
-        D.bd_of_plg.push_back((int)D.bd_cells.size());
-        D.bd_cells.push_back(D.plg[r]);
-      } else {
-        D.bd_of_plg.push_back(-1);
-      }
-      D.beta.push_back(outs[r].bt);
-    }
+    std::array<double, 16> bt;
+    std::copy(&beta[16 * r], &beta[16 * r] + 16, bt.begin());
+    D.beta.push_back(bt);
   }
   // --- block of the smoother: PLG cells + corner blocks when b != 0 --------
   std::vector<int> blk(D.plg);
@@ -517,28 +261,51 @@ LevelDisc discretize(const Problem& P, int n) {
       int r = root(e);
       gx[r] += P.holes[e].cx; gy[r] += P.holes[e].cy; gn[r] += 1;
     }
+    // the nearest of 1024 samples of each curve to each block cell's centre
+    const int nsm = cell::kCurveSamples;
+    const int m = (int)blk.size();
+    std::vector<double> sx((size_t)nh * nsm), sy((size_t)nh * nsm), cx(m), cy(m);
+    for (int e = 0; e < nh; ++e)
+      for (int s = 0; s < nsm; ++s)
+        P.holes[e].at(6.283185307179586 * s / nsm, sx[(size_t)e * nsm + s], sy[(size_t)e * nsm + s]);
+    for (int r = 0; r < m; ++r) {
+      cx[r] = G.x0 + (blk[r] % n + 0.5) * h;
+      cy[r] = G.y0 + (blk[r] / n + 0.5) * h;
+    }
+    std::vector<int> near((size_t)m * nh);
+    std::vector<double> near_d2((size_t)m * nh);
+    if (nh && m) {
+      if (dev) {
+        dev->nearest(sx.data(), sy.data(), nh, nsm, cx.data(), cy.data(), m, near.data(),
+                     near_d2.data());
+      } else {
+        parallel_rows(m, [&](int r) {
+          for (int e = 0; e < nh; ++e)
+            near[(size_t)r * nh + e] = cell::nearest_sample(&sx[(size_t)e * nsm], &sy[(size_t)e * nsm],
+                                                            nsm, cx[r], cy[r], &near_d2[(size_t)r * nh + e]);
+        }, 16);
+      }
+    }
     const double L = P.x1 - P.x0;
     std::vector<std::tuple<int, double, int>> keys;
-    for (int k : blk) {
-      double x = G.x0 + (k % n + 0.5) * h, y = G.y0 + (k / n + 0.5) * h;
+    for (int r = 0; r < m; ++r) {
+      const int k = blk[r];
+      const double x = cx[r], y = cy[r];
       double d[4] = {y - P.y0, P.x1 - x, P.y1 - y, x - P.x0};
       int side = (int)(std::min_element(d, d + 4) - d);
       double s_box[4] = {x - P.x0, L + y - P.y0, 2 * L + P.x1 - x, 3 * L + P.y1 - y};
       double bestd = d[side], bests = s_box[side];
       int bestg = 0;
       for (int e = 0; e < nh; ++e) {
-        const int nsm = 1024;
-        for (int s = 0; s < nsm; ++s) {
-          double hx, hy;
-          P.holes[e].at(6.283185307179586 * s / nsm, hx, hy);
-          double dd = std::hypot(hx - x, hy - y);
-          if (dd < bestd) {
-            int r = root(e);
-            bestd = dd;
-            bestg = 1 + r;
-            double ang = std::atan2(hy - gy[r] / gn[r], hx - gx[r] / gn[r]);
-            bests = ang < 0 ? ang + 6.283185307179586 : ang;
-          }
+        const double dd = std::sqrt(near_d2[(size_t)r * nh + e]);
+        if (dd < bestd) {
+          const int s = near[(size_t)r * nh + e];
+          const double hx = sx[(size_t)e * nsm + s], hy = sy[(size_t)e * nsm + s];
+          int rt = root(e);
+          bestd = dd;
+          bestg = 1 + rt;
+          double ang = std::atan2(hy - gy[rt] / gn[rt], hx - gx[rt] / gn[rt]);
+          bests = ang < 0 ? ang + 6.283185307179586 : ang;
         }
       }
       keys.emplace_back(bestg, bests, k);

@@ -31,15 +31,6 @@ namespace ccmg {
 
 const double kTwoPi = 6.283185307179586476925286766559;
 
-void Hole::corners_cw(double vx[4], double vy[4]) const {
-  // counter-clockwise: c, c + r1 e, c + r1 e + r2 e', c + r2 e'; clockwise
-  // from c: c, c + r2 e', c + r1 e + r2 e', c + r1 e
-  vx[0] = cx;                       vy[0] = cy;
-  vx[1] = cx - r2 * si;             vy[1] = cy + r2 * co;
-  vx[2] = cx + r1 * co - r2 * si;   vy[2] = cy + r1 * si + r2 * co;
-  vx[3] = cx + r1 * co;             vy[3] = cy + r1 * si;
-}
-
 // side k of a kind-2 hole at parameter t: the corner index and the fraction
 static void rect_side(double t, int& k, double& tau) {
   const double q = kTwoPi / 4;
@@ -91,28 +82,6 @@ void Hole::dat(double t, double& dx, double& dy) const {
   dx = -co * r1 * st - si * r2 * ct;
   dy = -si * r1 * st + co * r2 * ct;
 }
-double Hole::level(double x, double y) const {
-  if (kind == 2) {
-    // the smallest inward-normal distance to the rectangle's side lines:
-    // positive inside the rectangle, negative in the hole
-    double vx[4], vy[4];
-    corners_cw(vx, vy);
-    double out = 0;
-    for (int i = 0; i < 4; ++i) {
-      // counter-clockwise side from corner a to corner b
-      const int a = (4 - i) % 4, b = (3 - i + 4) % 4;
-      const double ex = vx[b] - vx[a], ey = vy[b] - vy[a], L = std::hypot(ex, ey);
-      const double d = (-ey * (x - vx[a]) + ex * (y - vy[a])) / L;
-      out = i == 0 ? d : std::min(out, d);
-    }
-    return out;
-  }
-  double dx = x - cx, dy = y - cy;
-  if (kind == 1) return std::hypot(dx, dy) - (r1 + r2 * std::cos(petals * std::atan2(dy, dx)));
-  double u = co * dx + si * dy, v = -si * dx + co * dy;
-  return (u / r1) * (u / r1) + (v / r2) * (v / r2) - 1.0;
-}
-
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
   w.assign(n, 0.0);
@@ -377,29 +346,7 @@ void count_loops(const Problem& P, const std::vector<Piece>& pcs, double px, dou
 }  // namespace
 
 void shift_moments(const double in[kMoments], double dx, double dy, double out[kMoments]) {
-  // binomial coefficients, built once (thread-safe static initialisation)
-  struct Binom {
-    double c[7][7] = {};
-    Binom() {
-      for (int n = 0; n < 7; ++n) {
-        c[n][0] = c[n][n] = 1;
-        for (int k = 1; k < n; ++k) c[n][k] = c[n - 1][k - 1] + c[n - 1][k];
-      }
-    }
-  };
-  static const Binom binom;
-  const auto& C = binom.c;
-  double px[7], py[7];
-  px[0] = py[0] = 1;
-  for (int k = 1; k < 7; ++k) { px[k] = px[k - 1] * dx; py[k] = py[k - 1] * dy; }
-  for (int d = 0; d <= 6; ++d)
-    for (int q = 0; q <= d; ++q) {
-      int p = d - q;
-      double s = 0;
-      for (int a = 0; a <= p; ++a)
-        for (int b = 0; b <= q; ++b) s += C[p][a] * C[q][b] * px[p - a] * py[q - b] * in[midx(a, b)];
-      out[midx(p, q)] = s;
-    }
+  cell::shift_moments(in, dx, dy, out);
 }
 
 void LevelGeom::moments(int k, double out[kMoments]) const {
@@ -408,14 +355,7 @@ void LevelGeom::moments(int k, double out[kMoments]) const {
     std::copy(it->second.mom, it->second.mom + kMoments, out);
     return;
   }
-  // full unit cell about its centre: (1/(p+1)) (1/2)^p for even p, 0 odd
-  for (int d = 0; d <= 6; ++d)
-    for (int q = 0; q <= d; ++q) {
-      int p = d - q;
-      double mp = (p % 2) ? 0.0 : std::pow(0.5, p) / (p + 1);
-      double mq = (q % 2) ? 0.0 : std::pow(0.5, q) / (q + 1);
-      out[midx(p, q)] = mp * mq;
-    }
+  cell::full_moments(out);
 }
 
 static std::vector<Piece> full_faces(const LevelGeom& G, int i, int j) {
@@ -429,7 +369,7 @@ static std::vector<Piece> full_faces(const LevelGeom& G, int i, int j) {
   return v;
 }
 
-LevelGeom build_geometry(const Problem& P, int n) {
+LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
   LevelGeom G;
   G.n = n;
   G.x0 = P.x0;
@@ -517,18 +457,29 @@ LevelGeom build_geometry(const Problem& P, int n) {
     }
   }
 
+  // the cells no curve crosses: full or empty by their centre
   G.type.assign((size_t)n * n, CT_EMPTY);
   G.vol.assign((size_t)n * n, 0.0);
-  for (int j = 0; j < n; ++j)
-    for (int i = 0; i < n; ++i) {
-      int k = j * n + i;
-      if (arcs.count(k)) continue;
-      double xc = P.x0 + (i + 0.5) * h, yc = P.y0 + (j + 0.5) * h;
-      if (outside_all(P, xc, yc)) {
-        G.type[k] = CT_FULL;
-        G.vol[k] = h * h;
-      }
+  {
+    std::vector<uint8_t> crossed((size_t)n * n, 0);
+    for (auto& kv : arcs) crossed[kv.first] = 1;
+    if (dev) {
+      dev->classify(P, n, h, crossed.data(), G.type.data());
+    } else {
+      parallel_rows(n, [&](int j) {
+        for (int i = 0; i < n; ++i) {
+          const int k = j * n + i;
+          if (crossed[k]) continue;
+          const double xc = P.x0 + (i + 0.5) * h, yc = P.y0 + (j + 0.5) * h;
+          if (cell::outside_all(P.holes.data(), (int)P.holes.size(), xc, yc)) G.type[k] = CT_FULL;
+        }
+      });
     }
+    parallel_rows(n, [&](int j) {
+      for (int k = j * n; k < (j + 1) * n; ++k)
+        if (G.type[k] == CT_FULL) G.vol[k] = h * h;
+    });
+  }
   for (auto& kv : arcs) {
     int k = kv.first, j = k / n, i = k % n;
     double xl = P.x0 + i * h, xr = xl + h, yb = P.y0 + j * h, yt = yb + h;

@@ -8,8 +8,11 @@
 #include <map>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
+
+#include "setup_cell.h"
 
 namespace ccmg {
 
@@ -22,27 +25,32 @@ struct SetupError : std::runtime_error {
   SetupError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
-// A hole: kind 0 the ellipse c + R(th) (r1 cos t, r2 sin t); kind 1 the
-// flower c + (r1 + r2 cos(petals t)) (cos t, sin t) (Sec. 6.2); kind 2
-// everything outside the rectangle with corner c and sides r1 (direction th)
-// and r2 (direction th + pi/2), whose sides are the curve, followed
-// clockwise around the rectangle as t grows (a quarter of [0, 2pi) each), so
-// that the domain is on the left from high to low t as for the other holes.
-struct Hole {
-  double cx, cy, r1, r2, th, co, si;
-  int kind = 0;
-  int petals = 0;
-  // point and derivative at parameter t
-  void at(double t, double& x, double& y) const;
-  void dat(double t, double& dx, double& dy) const;
-  double level(double x, double y) const;   // < 0 inside the hole
-  double halfwidth() const {
-    return kind == 2 ? 1e300 : kind == 1 ? r1 - r2 : std::min(r1, r2);
-  }
-  void corners_cw(double vx[4], double vy[4]) const;   // kind 2, in the order of t
+// a failed CUDA call of the device setup steps (err: the cudaError_t value)
+struct DeviceError : std::runtime_error {
+  int err;
+  DeviceError(int e, const std::string& m) : std::runtime_error(m), err(e) {}
 };
 
 struct Bc { int type; double a1, a2; };
+
+// f(j) for every j in [0, n), on up to 32 host threads in interleaved
+// order; f must write only its own outputs
+template <class F>
+void parallel_rows(int n, F&& f, int min_per_thread = 64) {
+  unsigned T = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+  if (n < (int)T * min_per_thread) T = std::max(1, n / min_per_thread);
+  if (T <= 1) {
+    for (int j = 0; j < n; ++j) f(j);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (unsigned t = 1; t < T; ++t)
+    pool.emplace_back([&, t] {
+      for (int j = (int)t; j < n; j += (int)T) f(j);
+    });
+  for (int j = 0; j < n; j += (int)T) f(j);
+  for (auto& th : pool) th.join();
+}
 
 struct Problem {
   double x0, y0, x1, y1;
@@ -64,8 +72,6 @@ struct Piece {           // oriented boundary piece of a cut cell
   int bc;                 // index into Problem::bc, -1 for interior faces
 };
 
-struct BNode { double x, y, nx, ny, w; int bc; };
-
 struct Cut {
   std::vector<Piece> pieces;
   double mom[kMoments];   // integral of X^p Y^q dX dY, X = (x - px)/h, about the own centre
@@ -84,7 +90,13 @@ struct LevelGeom {
   void moments(int k, double out[kMoments]) const;
 };
 
-LevelGeom build_geometry(const Problem& P, int n);
+// The per-cell steps of the setup (classification of the cells no curve
+// crosses, Def. 4.1 kinds, lattices, fits, curve-order samples) run on the
+// device when a SetupDevice is given (setup_dev.cu), else on host threads;
+// both run the functions of setup_cell.h and give the same tables.
+class SetupDevice;
+
+LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev = nullptr);
 
 // boundary quadrature of cut cell k (nodes on pieces with bc >= 0)
 std::vector<BNode> boundary_nodes(const Problem& P, const LevelGeom& G, int k);
@@ -133,6 +145,42 @@ struct LevelDisc {
   const Problem* P = nullptr;
 };
 
-LevelDisc discretize(const Problem& P, int n);
+LevelDisc discretize(const Problem& P, int n, SetupDevice* dev = nullptr);
+
+// Device execution of the per-cell setup steps (setup_dev.cu): FP64 CUDA
+// kernels, one thread per cell, on the given stream; every call is
+// synchronous (its results are in host memory on return).  A failed CUDA
+// call throws DeviceError with its error text.
+class SetupDevice {
+ public:
+  explicit SetupDevice(void* stream);
+  ~SetupDevice();
+  SetupDevice(const SetupDevice&) = delete;
+  SetupDevice& operator=(const SetupDevice&) = delete;
+  // type[k] = CT_FULL if crossed[k] == 0 and the cell's centre lies
+  // outside every hole, else CT_EMPTY
+  void classify(const Problem& P, int n, double h, const uint8_t* crossed, uint8_t* type);
+  // Def. 4.1 kind of every cell; keeps the type map on the device for the
+  // calls below
+  void kinds(int n, bool cross, const uint8_t* type, const uint8_t* ext, uint8_t* kind);
+  // lattice of each cell of plg (15 ints each); ok[r] = 0 where none exists
+  void lattices(int n, const std::vector<int>& plg, int* lat, uint8_t* ok);
+  // fits of the cells of plg with the lattices lat: cut cells (sorted) and
+  // their moments, boundary nodes of plg cell r in bnode[bptr[r], bptr[r+1])
+  void fits(int n, double h, double x0, double y0, double a, double b, double c,
+            const std::vector<int>& plg, const int* lat, const std::vector<int>& cut_cells,
+            const std::vector<double>& cut_mom, const std::vector<BNode>& bnode,
+            const std::vector<int>& bptr, const std::vector<double>& a12, double* beta,
+            uint8_t* ok);
+  // for each of m points and each of nh curves (ns samples each, sx/sy
+  // nh * ns): the nearest sample and its squared distance (m * nh each)
+  void nearest(const double* sx, const double* sy, int nh, int ns, const double* px,
+               const double* py, int m, int* idx, double* d2);
+  double kernel_ms = 0;   // device time of the kernels so far
+
+ private:
+  struct Impl;
+  Impl* p_;
+};
 
 }  // namespace ccmg

@@ -1,0 +1,474 @@
+// Per-cell steps of the setup, written once for the host and the device.
+//
+// Each function here computes the table entries of ONE cell from read-only
+// inputs: the classification of a control volume (Sec. 3.1), its kind
+// (Def. 4.1), the poised lattice of a PLG cell (Def. 4.3, the reading of the
+// lattice rule stated in disc.cpp), its fit (Eq. 4.14, or the weighted
+// minimum norm of Eq. 4.17-4.18), and the nearest sample of a boundary curve
+// that orders the exactly solved block (Def. 5.1).  disc.cpp runs them on
+// host threads; setup_dev.cu runs them as CUDA kernels, one thread per cell.
+//
+// Both builds evaluate the same expressions in the same order with IEEE
+// double operations only (+ - * / and sqrt, all correctly rounded; no
+// contraction into fused multiply-adds: the host compiler gets
+// -ffp-contract=off and the device translation unit --fmad=false), so the
+// two give the same bits.  The one exception is the level function of the
+// flower and rectangle holes (hypot, atan2, cos), used only to classify
+// cells that no curve crosses: their centres lie at least h/2 from the
+// curve, so the sign cannot differ.
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define CC_HD __host__ __device__
+#else
+#define CC_HD
+#endif
+// keep the device code of the long fixed-count loops rolled (compile time)
+#ifdef __CUDA_ARCH__
+#define CC_ROLLED _Pragma("unroll 1")
+#else
+#define CC_ROLLED
+#endif
+
+namespace ccmg {
+
+// A hole: kind 0 the ellipse c + R(th) (r1 cos t, r2 sin t); kind 1 the
+// flower c + (r1 + r2 cos(petals t)) (cos t, sin t) (Sec. 6.2); kind 2
+// everything outside the rectangle with corner c and sides r1 (direction th)
+// and r2 (direction th + pi/2), whose sides are the curve, followed
+// clockwise around the rectangle as t grows (a quarter of [0, 2pi) each), so
+// that the domain is on the left from high to low t as for the other holes.
+struct Hole {
+  double cx, cy, r1, r2, th, co, si;
+  int kind = 0;
+  int petals = 0;
+  // point and derivative at parameter t (host)
+  void at(double t, double& x, double& y) const;
+  void dat(double t, double& dx, double& dy) const;
+  CC_HD double halfwidth() const {
+    return kind == 2 ? 1e300 : kind == 1 ? r1 - r2 : (r1 < r2 ? r1 : r2);
+  }
+  // kind 2, in the order of t
+  CC_HD void corners_cw(double vx[4], double vy[4]) const {
+    // counter-clockwise: c, c + r1 e, c + r1 e + r2 e', c + r2 e'; clockwise
+    // from c: c, c + r2 e', c + r1 e + r2 e', c + r1 e
+    vx[0] = cx;                       vy[0] = cy;
+    vx[1] = cx - r2 * si;             vy[1] = cy + r2 * co;
+    vx[2] = cx + r1 * co - r2 * si;   vy[2] = cy + r1 * si + r2 * co;
+    vx[3] = cx + r1 * co;             vy[3] = cy + r1 * si;
+  }
+  // < 0 inside the hole
+  CC_HD double level(double x, double y) const {
+    if (kind == 2) {
+      // the smallest inward-normal distance to the rectangle's side lines:
+      // positive inside the rectangle, negative in the hole
+      double vx[4], vy[4];
+      corners_cw(vx, vy);
+      double out = 0;
+      for (int i = 0; i < 4; ++i) {
+        // counter-clockwise side from corner a to corner b
+        const int a = (4 - i) % 4, b = (3 - i + 4) % 4;
+        const double ex = vx[b] - vx[a], ey = vy[b] - vy[a], L = hypot(ex, ey);
+        const double d = (-ey * (x - vx[a]) + ex * (y - vy[a])) / L;
+        out = (i == 0 || d < out) ? d : out;
+      }
+      return out;
+    }
+    double dx = x - cx, dy = y - cy;
+    if (kind == 1) return hypot(dx, dy) - (r1 + r2 * cos(petals * atan2(dy, dx)));
+    double u = co * dx + si * dy, v = -si * dx + co * dy;
+    return (u / r1) * (u / r1) + (v / r2) * (v / r2) - 1.0;
+  }
+};
+
+// A quadrature node on the boundary of a cut cell: position, outward unit
+// normal, weight |ds|, boundary condition index.
+struct BNode { double x, y, nx, ny, w; int bc; };
+
+namespace cell {
+
+enum : uint8_t { T_EMPTY = 0, T_FULL = 1, T_CUT = 2 };   // LevelGeom::type
+enum : uint8_t { K_EMPTY_ = 0, K_SFV_ = 1, K_PLG_ = 2 };  // LevelDisc::kind
+
+constexpr int kNM = 28;            // moments x^p y^q, p + q <= 6
+constexpr int kLatR = 6;           // largest lattice search box: 13 x 13
+constexpr int kLatR0 = 4;          // first search box: 9 x 9
+constexpr int kLatW = 2 * kLatR + 1;
+constexpr int kCutPenalty = 2;     // extra cost of a cut cell in a lattice
+constexpr int kCurveSamples = 1024;
+
+CC_HD inline int mi(int p, int q) { int d = p + q; return d * (d + 1) / 2 + q; }
+
+CC_HD inline double ipow(double x, int p) {
+  double r = 1.0;
+  for (int k = 0; k < p; ++k) r *= x;
+  return r;
+}
+
+// --- classification of a control volume no curve crosses (Sec. 3.1) --------
+CC_HD inline bool outside_all(const Hole* holes, int nh, double x, double y) {
+  for (int e = 0; e < nh; ++e)
+    if (holes[e].level(x, y) <= 0.0) return false;
+  return true;
+}
+
+// --- Def. 4.1: SFV if the cell is full and every cell of its stencil (5
+// points per direction; the 5 x 5 box when b != 0) is full or a usable
+// ghost; ext[w * n + t] flags the extendable wall positions of wall w.
+CC_HD inline bool ghost_ok(const uint8_t* ext, int n, int ii, int jj) {
+  const bool ox = ii < 0 || ii >= n, oy = jj < 0 || jj >= n;
+  if (ox && oy) {
+    if (n < 5) return false;
+    const int wx = ii < 0 ? 3 : 1, wy = jj < 0 ? 0 : 2;
+    for (int q = 0; q < 5; ++q) {
+      if (!ext[wx * n + (jj < 0 ? q : n - 1 - q)]) return false;
+      if (!ext[wy * n + (ii < 0 ? q : n - 1 - q)]) return false;
+    }
+    return true;
+  }
+  if (ii >= n) return ext[1 * n + jj] != 0;
+  if (ii < 0) return ext[3 * n + jj] != 0;
+  if (jj >= n) return ext[2 * n + ii] != 0;
+  return ext[0 * n + ii] != 0;
+}
+
+CC_HD inline uint8_t kind_of(const uint8_t* type, const uint8_t* ext, int n, bool cross, int k) {
+  if (type[k] == T_EMPTY) return K_EMPTY_;
+  const int i = k % n, j = k / n;
+  bool sfv = type[k] == T_FULL;
+  for (int dj = -2; dj <= 2 && sfv; ++dj)
+    for (int di = -2; di <= 2 && sfv; ++di) {
+      if (!cross && di && dj) continue;
+      const int ii = i + di, jj = j + dj;
+      if (ii >= 0 && jj >= 0 && ii < n && jj < n) sfv = type[jj * n + ii] == T_FULL;
+      else sfv = ghost_ok(ext, n, ii, jj);
+    }
+  return sfv ? K_SFV_ : K_PLG_;
+}
+
+// --- the poised lattice of PLG cell k -----------------------------------------
+// Five grid lines (rows, or else columns) of the search box carry 5, 4, 3, 2
+// and 1 present cells; a cell at offset (u, v) costs u^2 + v^2, plus
+// kCutPenalty for a cut cell other than k; each line takes its cheapest
+// cells (ties: smaller u); the lines and counts minimise the total cost,
+// ties to the lexicographically larger count vector from the lowest line up;
+// rows before columns on equal cost; the 9 x 9 box first, then 11 x 11 and
+// 13 x 13 where a smaller one holds no such set.  out: the 15 cells, sorted.
+CC_HD inline bool plg_lattice(const uint8_t* type, int n, int k, int out[15]) {
+  const int i0 = k % n, j0 = k / n;
+  struct St { int cost; int8_t have; int8_t asg[kLatW]; };
+  bool found = false;
+  int best_cost = 0;
+  CC_ROLLED
+  for (int R = kLatR0; R <= kLatR && !found; ++R)
+    for (int orient = 0; orient < 2; ++orient) {
+      int8_t avail[kLatW][kLatW];
+      int8_t navail[kLatW];
+      int16_t cost[kLatW][kLatW];
+      for (int v = -R; v <= R; ++v) {
+        const int vi = v + kLatR;
+        int na = 0;
+        for (int u = -R; u <= R; ++u) {
+          const int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
+          const int ii = i0 + di, jj = j0 + dj;
+          if (ii >= 0 && jj >= 0 && ii < n && jj < n && type[jj * n + ii] != T_EMPTY) {
+            const bool cut = type[jj * n + ii] == T_CUT && (di != 0 || dj != 0);
+            cost[vi][u + kLatR] = (int16_t)(u * u + v * v + (cut ? kCutPenalty : 0));
+            // insertion by (cost, u); u grows, so equal costs keep their order
+            int p = na++;
+            while (p > 0 && cost[vi][avail[vi][p - 1] + kLatR] > cost[vi][u + kLatR]) {
+              avail[vi][p] = avail[vi][p - 1];
+              --p;
+            }
+            avail[vi][p] = (int8_t)u;
+          }
+        }
+        navail[vi] = (int8_t)na;
+      }
+      St nxt[32], cur[32];
+      for (int m = 0; m < 32; ++m) {
+        nxt[m].have = 0;
+        nxt[m].cost = 0;
+        for (int q = 0; q < kLatW; ++q) nxt[m].asg[q] = 0;
+      }
+      nxt[31].have = 1;
+      CC_ROLLED
+      for (int v = R; v >= -R; --v) {
+        const int vi = v + kLatR;
+        CC_ROLLED
+        for (int mask = 0; mask < 32; ++mask) {
+          St& b = cur[mask];
+          b.have = 0;
+          // candidate (cost c, count cn on line v, the rest from state s)
+          auto consider = [&](int c, int cn, const St& s) {
+            bool better = !b.have || c < b.cost;
+            if (b.have && c == b.cost) {
+              // keys: (-count of line v, -count of line v+1, ...), smaller wins
+              int cmp = 0;
+              for (int w = vi; w < kLatW && cmp == 0; ++w) {
+                const int ka = -(w == vi ? cn : s.asg[w]), kb = -b.asg[w];
+                cmp = ka < kb ? -1 : ka > kb ? 1 : 0;
+              }
+              better = cmp < 0;
+            }
+            if (better) {
+              b.have = 1;
+              b.cost = c;
+              for (int w = 0; w < kLatW; ++w) b.asg[w] = s.asg[w];
+              b.asg[vi] = (int8_t)cn;
+            }
+          };
+          if (nxt[mask].have) consider(nxt[mask].cost, 0, nxt[mask]);
+          for (int bit = 0; bit < 5; ++bit) {
+            const int cnt = 5 - bit;
+            if (((mask >> bit) & 1) || navail[vi] < cnt) continue;
+            const int m2 = mask | (1 << bit);
+            if (!nxt[m2].have) continue;
+            int rc = 0;
+            for (int q = 0; q < cnt; ++q) rc += cost[vi][avail[vi][q] + kLatR];
+            consider(nxt[m2].cost + rc, cnt, nxt[m2]);
+          }
+        }
+        for (int m = 0; m < 32; ++m) nxt[m] = cur[m];
+      }
+      if (!nxt[0].have) continue;
+      if (!found || nxt[0].cost < best_cost) {
+        found = true;
+        best_cost = nxt[0].cost;
+        int c = 0;
+        for (int v = -R; v <= R; ++v) {
+          const int vi = v + kLatR, cnt = nxt[0].asg[vi];
+          for (int q = 0; q < cnt; ++q) {
+            const int u = avail[vi][q];
+            const int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
+            out[c++] = (j0 + dj) * n + (i0 + di);
+          }
+        }
+      }
+    }
+  if (!found) return false;
+  for (int a = 1; a < 15; ++a) {
+    const int x = out[a];
+    int p = a;
+    while (p > 0 && out[p - 1] > x) { out[p] = out[p - 1]; --p; }
+    out[p] = x;
+  }
+  return true;
+}
+
+// --- moments ---------------------------------------------------------------
+// moments of the full unit cell about its centre: (1/2)^p / (p + 1) for even
+// p (0 for odd), times the same in q
+CC_HD inline void full_moments(double out[kNM]) {
+  for (int d = 0; d <= 6; ++d)
+    for (int q = 0; q <= d; ++q) {
+      const int p = d - q;
+      const double mp = (p % 2) ? 0.0 : ipow(0.5, p) / (p + 1);
+      const double mq = (q % 2) ? 0.0 : ipow(0.5, q) / (q + 1);
+      out[mi(p, q)] = mp * mq;
+    }
+}
+
+// scaled moments about the centre p moved to p - (dx, dy) h
+CC_HD inline void shift_moments(const double in[kNM], double dx, double dy, double out[kNM]) {
+  double C[7][7];
+  for (int a = 0; a < 7; ++a) {
+    for (int b = 0; b < 7; ++b) C[a][b] = 0.0;
+    C[a][0] = C[a][a] = 1.0;
+    for (int b = 1; b < a; ++b) C[a][b] = C[a - 1][b - 1] + C[a - 1][b];
+  }
+  double px[7], py[7];
+  px[0] = py[0] = 1;
+  for (int k = 1; k < 7; ++k) { px[k] = px[k - 1] * dx; py[k] = py[k - 1] * dy; }
+  CC_ROLLED
+  for (int d = 0; d <= 6; ++d)
+    for (int q = 0; q <= d; ++q) {
+      const int p = d - q;
+      double s = 0;
+      for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= q; ++b) s += C[p][a] * C[q][b] * px[p - a] * py[q - b] * in[mi(a, b)];
+      out[mi(p, q)] = s;
+    }
+}
+
+// --- small dense solves ----------------------------------------------------
+// A x = b, A 15 x 15 row-major (overwritten), Gaussian elimination with
+// partial pivoting; b becomes x.  false if a pivot is zero.
+CC_HD inline bool lu_solve15(double* A, double* b) {
+  const int n = 15;
+  CC_ROLLED
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r * n + c]) > fabs(A[p * n + c])) p = r;
+    if (A[p * n + c] == 0.0) return false;
+    if (p != c) {
+      for (int k = 0; k < n; ++k) { double t = A[p * n + k]; A[p * n + k] = A[c * n + k]; A[c * n + k] = t; }
+      double t = b[p]; b[p] = b[c]; b[c] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const double l = A[r * n + c] / A[c * n + c];
+      if (l == 0.0) continue;
+      for (int k = c; k < n; ++k) A[r * n + k] -= l * A[c * n + k];
+      b[r] -= l * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * b[k];
+    b[r] = s / A[r * n + r];
+  }
+  return true;
+}
+
+// Minimum 2-norm solution x[16] of B x = rhs, B 15 x 16 row-major of full
+// row rank: Householder QR of B^T = Q R, then x = Q (R^-T rhs).
+CC_HD inline bool min_norm15x16(const double* B, const double* rhs, double* x) {
+  const int m = 15, n = 16;
+  double T[15][16];     // T[r] = column r of B^T = row r of B
+  double V[15][16];
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < n; ++c) T[r][c] = B[r * n + c];
+  CC_ROLLED
+  for (int k = 0; k < m; ++k) {
+    double nrm = 0;
+    for (int i = k; i < n; ++i) nrm += T[k][i] * T[k][i];
+    nrm = sqrt(nrm);
+    if (nrm == 0.0) return false;
+    const double alpha = T[k][k] > 0 ? -nrm : nrm;
+    for (int i = 0; i < n; ++i) V[k][i] = i >= k ? T[k][i] : 0.0;
+    V[k][k] -= alpha;
+    double vn = 0;
+    for (int i = k; i < n; ++i) vn += V[k][i] * V[k][i];
+    for (int j = k; j < m; ++j) {
+      double s = 0;
+      for (int i = k; i < n; ++i) s += V[k][i] * T[j][i];
+      s = 2.0 * s / vn;
+      for (int i = k; i < n; ++i) T[j][i] -= s * V[k][i];
+    }
+  }
+  // R^T y = rhs (forward), R(i, j) = T[j][i] for i <= j
+  double y[15];
+  for (int i = 0; i < m; ++i) {
+    double s = rhs[i];
+    for (int j = 0; j < i; ++j) s -= T[i][j] * y[j];
+    if (T[i][i] == 0.0) return false;
+    y[i] = s / T[i][i];
+  }
+  // x = Q [y; 0] = H_0 H_1 ... H_14 [y; 0]
+  for (int i = 0; i < n; ++i) x[i] = i < m ? y[i] : 0.0;
+  CC_ROLLED
+  for (int k = m - 1; k >= 0; --k) {
+    double vn = 0, s = 0;
+    for (int i = k; i < n; ++i) { vn += V[k][i] * V[k][i]; s += V[k][i] * x[i]; }
+    s = 2.0 * s / vn;
+    for (int i = k; i < n; ++i) x[i] -= s * V[k][i];
+  }
+  return true;
+}
+
+// --- the fit of PLG cell k (Sec. 4.2) -----------------------------------------
+// Columns: the 15 lattice cells (their scaled moments about k's centre give
+// the cell averages of the 15 monomials of degree <= 4), plus, for a cut cell
+// with boundary data, the averaged boundary functional alpha1 phi + alpha2
+// dphi/dn over its boundary nodes.  Rows: the monomials, degree by degree,
+// x^d first.  rhs: <L phi>_k.  Square system: Eq. 4.14; with the boundary
+// column: the weighted minimum norm of Eq. 4.17-4.18 with weights
+// w = max(|offset|, 1/2) (1/2 for the boundary column), computed as
+// beta = W^1/2 pinv(M W^1/2) rhs.  mom(kj, out) gives the scaled moments of
+// cell kj about its own centre; a12[2 bc + 0/1] = (alpha1, alpha2) of
+// condition bc.  beta[15] is 0 without boundary data.  false if singular.
+template <class Mom>
+CC_HD inline bool plg_fit(int k, int n, double h, double a, double b, double c, const int lat[15],
+                          const Mom& mom, const BNode* bn, int nb, const double* a12,
+                          double x0, double y0, double beta[16]) {
+  const int i0 = k % n, j0 = k / n;
+  const bool withb = nb > 0;
+  const int nc = withb ? 16 : 15;
+  double M[15 * 16], rhs[15];
+  CC_ROLLED
+  for (int col = 0; col < 15; ++col) {
+    const int kj = lat[col];
+    double m0[kNM], ms[kNM];
+    mom(kj, m0);
+    shift_moments(m0, (double)((kj % n) - i0), (double)((kj / n) - j0), ms);
+    int r = 0;
+    for (int d = 0; d <= 4; ++d)
+      for (int p = d; p >= 0; --p, ++r) M[r * nc + col] = ms[mi(p, d - p)] / ms[0];
+  }
+  {
+    double m[kNM];
+    mom(k, m);
+    int r = 0;
+    for (int d = 0; d <= 4; ++d)
+      for (int p = d; p >= 0; --p, ++r) {
+        const int q = d - p;
+        double v = 0;
+        if (p >= 2) v += a * p * (p - 1) * (m[mi(p - 2, q)] / m[0]);
+        if (p >= 1 && q >= 1) v += b * p * q * (m[mi(p - 1, q - 1)] / m[0]);
+        if (q >= 2) v += c * q * (q - 1) * (m[mi(p, q - 2)] / m[0]);
+        rhs[r] = v / (h * h);
+      }
+  }
+  if (!withb) {
+    if (!lu_solve15(M, rhs)) return false;
+    for (int col = 0; col < 15; ++col) beta[col] = rhs[col];
+    beta[15] = 0.0;
+    return true;
+  }
+  const double px = x0 + (i0 + 0.5) * h, py = y0 + (j0 + 0.5) * h;
+  double colb[15], ws = 0;
+  for (int r = 0; r < 15; ++r) colb[r] = 0.0;
+  CC_ROLLED
+  for (int s = 0; s < nb; ++s) {
+    const BNode& nd = bn[s];
+    const double a1 = a12[2 * nd.bc], a2 = a12[2 * nd.bc + 1];
+    const double X = (nd.x - px) / h, Y = (nd.y - py) / h;
+    int r = 0;
+    for (int d = 0; d <= 4; ++d)
+      for (int p = d; p >= 0; --p, ++r) {
+        const int q = d - p;
+        const double phi = ipow(X, p) * ipow(Y, q);
+        const double gx = p ? p * ipow(X, p - 1) * ipow(Y, q) / h : 0.0;
+        const double gy = q ? q * ipow(X, p) * ipow(Y, q - 1) / h : 0.0;
+        colb[r] += nd.w * (a1 * phi + a2 * (gx * nd.nx + gy * nd.ny));
+      }
+    ws += nd.w;
+  }
+  for (int r = 0; r < 15; ++r) M[r * 16 + 15] = colb[r] / ws;
+  double sw[16];
+  for (int col = 0; col < 15; ++col) {
+    const int kj = lat[col];
+    const int di = kj % n - i0, dj = kj / n - j0;
+    const double d = sqrt((double)(di * di + dj * dj));
+    sw[col] = 1.0 / sqrt(d > 0.5 ? d : 0.5);
+  }
+  sw[15] = 1.0 / sqrt(0.5);
+  for (int r = 0; r < 15; ++r)
+    for (int col = 0; col < 16; ++col) M[r * 16 + col] *= sw[col];
+  double g[16];
+  if (!min_norm15x16(M, rhs, g)) return false;
+  for (int col = 0; col < 16; ++col) beta[col] = sw[col] * g[col];
+  return true;
+}
+
+// --- Def. 5.1 ordering: the nearest of ns samples (sx, sy) of one curve to
+// (x, y), by squared distance (ties: the first); returns its index and
+// writes the squared distance
+CC_HD inline int nearest_sample(const double* sx, const double* sy, int ns, double x, double y,
+                                double* d2out) {
+  int best = 0;
+  double bd = 0;
+  for (int s = 0; s < ns; ++s) {
+    const double dx = sx[s] - x, dy = sy[s] - y;
+    const double d2 = dx * dx + dy * dy;
+    if (s == 0 || d2 < bd) { bd = d2; best = s; }
+  }
+  *d2out = bd;
+  return best;
+}
+
+}  // namespace cell
+}  // namespace ccmg

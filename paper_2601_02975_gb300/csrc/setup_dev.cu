@@ -1,0 +1,297 @@
+// The per-cell steps of the setup as FP64 CUDA kernels (Sec. 3.1, Def. 4.1,
+// Def. 4.3, Eq. 4.14 and 4.17-4.18, Def. 5.1), one thread per cell, running
+// the functions of setup_cell.h.  This translation unit is compiled with
+// --fmad=false so that its products and sums round exactly as the host's
+// (-ffp-contract=off): the tables it builds are the host's, bit for bit.
+//
+// The host keeps the steps that walk curves or depend on earlier cells: the
+// crossings of the grid lines, the cut cells' boundary pieces and moments,
+// the merging of Alg. 1 (sequential by definition), the boundary quadrature
+// nodes, the rows of A and N, and the factorisations of the block smoother.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "setup.h"
+
+namespace ccmg {
+
+namespace {
+
+void check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    throw DeviceError((int)e, buf);
+  }
+}
+#define SCK(x) check((x), #x)
+
+__global__ void k_classify(const Hole* __restrict__ holes, int nh, int n, double x0, double y0,
+                           double h, const uint8_t* __restrict__ crossed, uint8_t* __restrict__ type) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(k % n), j = (int)(k / n);
+    uint8_t t = cell::T_EMPTY;
+    if (!crossed[k]) {
+      const double xc = x0 + (i + 0.5) * h, yc = y0 + (j + 0.5) * h;
+      if (cell::outside_all(holes, nh, xc, yc)) t = cell::T_FULL;
+    }
+    type[k] = t;
+  }
+}
+
+__global__ void k_kinds(const uint8_t* __restrict__ type, const uint8_t* __restrict__ ext, int n,
+                        int cross, uint8_t* __restrict__ kind) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn;
+       k += (int64_t)gridDim.x * blockDim.x)
+    kind[k] = cell::kind_of(type, ext, n, cross != 0, (int)k);
+}
+
+__global__ void k_lattice(const uint8_t* __restrict__ type, int n, const int* __restrict__ plg,
+                          int np, int* __restrict__ lat, uint8_t* __restrict__ ok) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= np) return;
+  int out[15];
+  const bool f = cell::plg_lattice(type, n, plg[r], out);
+  for (int q = 0; q < 15; ++q) lat[(int64_t)15 * r + q] = f ? out[q] : -1;
+  ok[r] = f;
+}
+
+// scaled moments of cell kj about its own centre: the cut cells' from the
+// table (cut_cells sorted), the full cell's otherwise
+struct DevMoments {
+  const int* cells;
+  const double* mom;
+  int ncut;
+  __device__ void operator()(int kj, double* out) const {
+    int lo = 0, hi = ncut;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (cells[mid] < kj) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < ncut && cells[lo] == kj) {
+      for (int q = 0; q < cell::kNM; ++q) out[q] = mom[(int64_t)cell::kNM * lo + q];
+    } else {
+      cell::full_moments(out);
+    }
+  }
+};
+
+struct FitArgs {
+  int n, np;
+  double h, x0, y0, a, b, c;
+  const int* plg;
+  const int* lat;
+  DevMoments mom;
+  const BNode* bnode;
+  const int* bptr;
+  const double* a12;
+  double* beta;
+  uint8_t* ok;
+};
+
+__global__ void __launch_bounds__(64) k_fit(FitArgs A) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= A.np) return;
+  int lat[15];
+  for (int q = 0; q < 15; ++q) lat[q] = A.lat[(int64_t)15 * r + q];
+  const int b0 = A.bptr[r], nb = A.bptr[r + 1] - b0;
+  double beta[16];
+  const bool f = cell::plg_fit(A.plg[r], A.n, A.h, A.a, A.b, A.c, lat, A.mom,
+                               nb ? A.bnode + b0 : nullptr, nb, A.a12, A.x0, A.y0, beta);
+  for (int q = 0; q < 16; ++q) A.beta[(int64_t)16 * r + q] = f ? beta[q] : 0.0;
+  A.ok[r] = f;
+}
+
+__global__ void k_nearest(const double* __restrict__ sx, const double* __restrict__ sy, int nh,
+                          int ns, const double* __restrict__ px, const double* __restrict__ py,
+                          int m, int* __restrict__ idx, double* __restrict__ d2) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * nh) return;
+  const int r = (int)(t / nh), e = (int)(t % nh);
+  double d;
+  idx[t] = cell::nearest_sample(sx + (int64_t)e * ns, sy + (int64_t)e * ns, ns, px[r], py[r], &d);
+  d2[t] = d;
+}
+
+int grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// the stream, timing events and the type map of the level being built
+struct SetupDevice::Impl {
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  uint8_t* type = nullptr;      // the type map of the current level
+  size_t type_cap = 0;
+  int type_n = 0;
+  // a scratch allocation for the duration of one call
+  struct Scratch {
+    Impl* I;
+    std::vector<void*> ps;
+    template <class T> T* get(size_t count) {
+      void* p = nullptr;
+      SCK(cudaMalloc(&p, count * sizeof(T) + 16));
+      ps.push_back(p);
+      return static_cast<T*>(p);
+    }
+    template <class T> T* put(const T* h, size_t count) {
+      T* d = get<T>(count);
+      if (count) SCK(cudaMemcpyAsync(d, h, count * sizeof(T), cudaMemcpyHostToDevice, I->s));
+      return d;
+    }
+    ~Scratch() {
+      cudaStreamSynchronize(I->s);
+      for (void* p : ps) cudaFree(p);
+    }
+  };
+  void ensure_type(size_t nn) {
+    if (type_cap >= nn) return;
+    if (type) cudaFree(type);
+    type = nullptr;
+    SCK(cudaMalloc(&type, nn));
+    type_cap = nn;
+  }
+  void begin() { SCK(cudaEventRecord(e0, s)); }
+  void end(double& ms) {
+    SCK(cudaEventRecord(e1, s));
+    SCK(cudaGetLastError());
+    SCK(cudaEventSynchronize(e1));
+    float t = 0;
+    SCK(cudaEventElapsedTime(&t, e0, e1));
+    ms += t;
+  }
+};
+
+SetupDevice::SetupDevice(void* stream) : p_(new Impl) {
+  p_->s = (cudaStream_t)stream;
+  try {
+    SCK(cudaEventCreate(&p_->e0));
+    SCK(cudaEventCreate(&p_->e1));
+  } catch (...) {
+    if (p_->e0) cudaEventDestroy(p_->e0);
+    delete p_;
+    throw;
+  }
+}
+
+SetupDevice::~SetupDevice() {
+  cudaStreamSynchronize(p_->s);
+  if (p_->type) cudaFree(p_->type);
+  cudaEventDestroy(p_->e0);
+  cudaEventDestroy(p_->e1);
+  delete p_;
+}
+
+void SetupDevice::classify(const Problem& P, int n, double h, const uint8_t* crossed, uint8_t* type) {
+  Impl& I = *p_;
+  Impl::Scratch S{&I, {}};
+  const size_t nn = (size_t)n * n;
+  const int nh = (int)P.holes.size();
+  const Hole* dh = S.put(P.holes.data(), (size_t)nh);
+  const uint8_t* dc = S.put(crossed, nn);
+  uint8_t* dt = S.get<uint8_t>(nn);
+  I.begin();
+  k_classify<<<grid_for((int64_t)nn, 256), 256, 0, I.s>>>(dh, nh, n, P.x0, P.y0, h, dc, dt);
+  I.end(kernel_ms);
+  SCK(cudaMemcpyAsync(type, dt, nn, cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaStreamSynchronize(I.s));
+}
+
+void SetupDevice::kinds(int n, bool cross, const uint8_t* type, const uint8_t* ext, uint8_t* kind) {
+  Impl& I = *p_;
+  Impl::Scratch S{&I, {}};
+  const size_t nn = (size_t)n * n;
+  I.ensure_type(nn);
+  I.type_n = n;
+  SCK(cudaMemcpyAsync(I.type, type, nn, cudaMemcpyHostToDevice, I.s));
+  const uint8_t* de = S.put(ext, (size_t)4 * n);
+  uint8_t* dk = S.get<uint8_t>(nn);
+  I.begin();
+  k_kinds<<<grid_for((int64_t)nn, 256), 256, 0, I.s>>>(I.type, de, n, cross ? 1 : 0, dk);
+  I.end(kernel_ms);
+  SCK(cudaMemcpyAsync(kind, dk, nn, cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaStreamSynchronize(I.s));
+}
+
+void SetupDevice::lattices(int n, const std::vector<int>& plg, int* lat, uint8_t* ok) {
+  Impl& I = *p_;
+  if (I.type_n != n) throw DeviceError(1, "lattices: no type map of this level on the device");
+  Impl::Scratch S{&I, {}};
+  const int np = (int)plg.size();
+  const int* dp = S.put(plg.data(), (size_t)np);
+  int* dl = S.get<int>((size_t)15 * np);
+  uint8_t* dok = S.get<uint8_t>((size_t)np);
+  I.begin();
+  k_lattice<<<(np + 127) / 128, 128, 0, I.s>>>(I.type, n, dp, np, dl, dok);
+  I.end(kernel_ms);
+  SCK(cudaMemcpyAsync(lat, dl, (size_t)15 * np * sizeof(int), cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaMemcpyAsync(ok, dok, (size_t)np, cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaStreamSynchronize(I.s));
+}
+
+void SetupDevice::fits(int n, double h, double x0, double y0, double a, double b, double c,
+                       const std::vector<int>& plg, const int* lat, const std::vector<int>& cut_cells,
+                       const std::vector<double>& cut_mom, const std::vector<BNode>& bnode,
+                       const std::vector<int>& bptr, const std::vector<double>& a12, double* beta,
+                       uint8_t* ok) {
+  Impl& I = *p_;
+  Impl::Scratch S{&I, {}};
+  const int np = (int)plg.size();
+  FitArgs A;
+  A.n = n;
+  A.np = np;
+  A.h = h;
+  A.x0 = x0;
+  A.y0 = y0;
+  A.a = a;
+  A.b = b;
+  A.c = c;
+  A.plg = S.put(plg.data(), (size_t)np);
+  A.lat = S.put(lat, (size_t)15 * np);
+  A.mom.cells = S.put(cut_cells.data(), cut_cells.size());
+  A.mom.mom = S.put(cut_mom.data(), cut_mom.size());
+  A.mom.ncut = (int)cut_cells.size();
+  A.bnode = S.put(bnode.data(), bnode.size());
+  A.bptr = S.put(bptr.data(), bptr.size());
+  A.a12 = S.put(a12.data(), a12.size());
+  A.beta = S.get<double>((size_t)16 * np);
+  A.ok = S.get<uint8_t>((size_t)np);
+  I.begin();
+  k_fit<<<(np + 63) / 64, 64, 0, I.s>>>(A);
+  I.end(kernel_ms);
+  SCK(cudaMemcpyAsync(beta, A.beta, (size_t)16 * np * sizeof(double), cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaMemcpyAsync(ok, A.ok, (size_t)np, cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaStreamSynchronize(I.s));
+}
+
+void SetupDevice::nearest(const double* sx, const double* sy, int nh, int ns, const double* px,
+                          const double* py, int m, int* idx, double* d2) {
+  Impl& I = *p_;
+  Impl::Scratch S{&I, {}};
+  const size_t nt = (size_t)m * nh;
+  const double* dsx = S.put(sx, (size_t)nh * ns);
+  const double* dsy = S.put(sy, (size_t)nh * ns);
+  const double* dpx = S.put(px, (size_t)m);
+  const double* dpy = S.put(py, (size_t)m);
+  int* di = S.get<int>(nt);
+  double* dd = S.get<double>(nt);
+  I.begin();
+  k_nearest<<<(int)((nt + 127) / 128), 128, 0, I.s>>>(dsx, dsy, nh, ns, dpx, dpy, m, di, dd);
+  I.end(kernel_ms);
+  SCK(cudaMemcpyAsync(idx, di, nt * sizeof(int), cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaMemcpyAsync(d2, dd, nt * sizeof(double), cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaStreamSynchronize(I.s));
+}
+
+}  // namespace ccmg
