@@ -313,22 +313,35 @@ LevelDisc discretize(const Problem& P, int n, SetupDevice* dev) {
     std::sort(keys.begin(), keys.end());
     for (auto& t : keys) D.block.push_back(std::get<2>(t));
   }
-  std::map<int, double> ar, nr;
-  for (int k : D.block) {
-    D.row(k, ar, nullptr);
-    D.block_rows.push(ar);
+  // rows of A for the block cells and of N: built on host threads, stored
+  // in cell order
+  {
+    const int mb = (int)D.block.size();
+    std::vector<std::map<int, double>> br(mb);
+    parallel_rows(mb, [&](int r) { D.row(D.block[r], br[r], nullptr); }, 16);
+    for (const auto& row : br) D.block_rows.push(row);
   }
-  for (int k = 0; k < n * n; ++k) {
-    if (D.kind[k] == K_EMPTY) continue;
+  {
     // only PLG rows (boundary datum) and the rows of cells within two cells
     // of a box wall (ghost data) have terms in N
-    const int i = k % n, j = k / n;
-    if (D.kind[k] != K_PLG && i >= 2 && j >= 2 && i < n - 2 && j < n - 2) continue;
-    D.row(k, ar, &nr);
-    if (!nr.empty()) {
-      D.nrows.push(nr);
-      D.nrow_cell.push_back(k);
+    std::vector<int> cells;
+    for (int k = 0; k < n * n; ++k) {
+      if (D.kind[k] == K_EMPTY) continue;
+      const int i = k % n, j = k / n;
+      if (D.kind[k] != K_PLG && i >= 2 && j >= 2 && i < n - 2 && j < n - 2) continue;
+      cells.push_back(k);
     }
+    const int nc = (int)cells.size();
+    std::vector<std::map<int, double>> nr(nc);
+    parallel_rows(nc, [&](int r) {
+      std::map<int, double> ar;
+      D.row(cells[r], ar, &nr[r]);
+    }, 16);
+    for (int r = 0; r < nc; ++r)
+      if (!nr[r].empty()) {
+        D.nrows.push(nr[r]);
+        D.nrow_cell.push_back(cells[r]);
+      }
   }
   return D;
 }

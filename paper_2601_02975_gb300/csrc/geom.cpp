@@ -29,59 +29,6 @@
 
 namespace ccmg {
 
-const double kTwoPi = 6.283185307179586476925286766559;
-
-// side k of a kind-2 hole at parameter t: the corner index and the fraction
-static void rect_side(double t, int& k, double& tau) {
-  const double q = kTwoPi / 4;
-  double tm = std::fmod(t, kTwoPi);
-  if (tm < 0) tm += kTwoPi;
-  k = std::min(3, (int)std::floor(tm / q));
-  tau = (tm - k * q) / q;
-}
-
-void Hole::at(double t, double& x, double& y) const {
-  if (kind == 2) {
-    double vx[4], vy[4], tau;
-    int k;
-    corners_cw(vx, vy);
-    rect_side(t, k, tau);
-    const int k1 = (k + 1) % 4;
-    x = vx[k] + tau * (vx[k1] - vx[k]);
-    y = vy[k] + tau * (vy[k1] - vy[k]);
-    return;
-  }
-  double ct = std::cos(t), st = std::sin(t);
-  if (kind == 1) {
-    const double r = r1 + r2 * std::cos(petals * t);
-    x = cx + r * ct;
-    y = cy + r * st;
-    return;
-  }
-  x = cx + co * r1 * ct - si * r2 * st;
-  y = cy + si * r1 * ct + co * r2 * st;
-}
-void Hole::dat(double t, double& dx, double& dy) const {
-  if (kind == 2) {
-    double vx[4], vy[4], tau;
-    int k;
-    corners_cw(vx, vy);
-    rect_side(t, k, tau);
-    const int k1 = (k + 1) % 4;
-    dx = (vx[k1] - vx[k]) / (kTwoPi / 4);
-    dy = (vy[k1] - vy[k]) / (kTwoPi / 4);
-    return;
-  }
-  double ct = std::cos(t), st = std::sin(t);
-  if (kind == 1) {
-    const double r = r1 + r2 * std::cos(petals * t), dr = -r2 * petals * std::sin(petals * t);
-    dx = dr * ct - r * st;
-    dy = dr * st + r * ct;
-    return;
-  }
-  dx = -co * r1 * st - si * r2 * ct;
-  dy = -si * r1 * st + co * r2 * ct;
-}
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
   w.assign(n, 0.0);
@@ -121,10 +68,15 @@ namespace {
 
 struct Rules {
   std::vector<double> sx, sw, ax, aw, ix, iw;
+  Rules510 r510;
   Rules() {
     gauss_legendre(5, sx, sw);
     gauss_legendre(10, ax, aw);
     gauss_legendre(6, ix, iw);
+    std::copy(sx.begin(), sx.end(), r510.sx);
+    std::copy(sw.begin(), sw.end(), r510.sw);
+    std::copy(ax.begin(), ax.end(), r510.ax);
+    std::copy(aw.begin(), aw.end(), r510.aw);
   }
 };
 const Rules& rules() {
@@ -132,48 +84,16 @@ const Rules& rules() {
   return r;
 }
 
+
 // Quadrature points along a piece: position and the vector weight (dx, dy).
 template <class F>
 void walk(const Problem& P, const Piece& pc, F&& fn) {
-  const Rules& R = rules();
-  if (!pc.arc) {
-    for (size_t q = 0; q < R.sx.size(); ++q) {
-      double tau = 0.5 * (R.sx[q] + 1.0), wt = 0.5 * R.sw[q];
-      fn(pc.xa + tau * (pc.xb - pc.xa), pc.ya + tau * (pc.yb - pc.ya), (pc.xb - pc.xa) * wt,
-         (pc.yb - pc.ya) * wt);
-    }
-    return;
-  }
-  const Hole& H = P.holes[pc.hole];
-  int nsub = std::max(1, (int)std::ceil(std::fabs(pc.tb - pc.ta) / 0.25));
-  for (int s = 0; s < nsub; ++s) {
-    double s0 = pc.ta + (pc.tb - pc.ta) * s / nsub, s1 = pc.ta + (pc.tb - pc.ta) * (s + 1) / nsub;
-    for (size_t q = 0; q < R.ax.size(); ++q) {
-      double t = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * R.ax[q];
-      double wt = 0.5 * (s1 - s0) * R.aw[q];
-      double x, y, dx, dy;
-      H.at(t, x, y);
-      H.dat(t, dx, dy);
-      fn(x, y, dx * wt, dy * wt);
-    }
-  }
+  cell::walk_piece(P.holes.data(), pc, rules().r510, fn);
 }
 
 void piece_moments(const Problem& P, const Piece& pc, double px, double py, double h,
                    double m[kMoments]) {
-  walk(P, pc, [&](double x, double y, double, double dy) {
-    double X = (x - px) / h, Y = (y - py) / h, dY = dy / h;
-    double xp[8], yq[7];
-    xp[0] = 1;
-    yq[0] = 1;
-    for (int k = 1; k < 8; ++k) xp[k] = xp[k - 1] * X;
-    for (int k = 1; k < 7; ++k) yq[k] = yq[k - 1] * Y;
-    for (int d = 0; d <= 6; ++d)
-      for (int q = 0; q <= d; ++q) {
-        int p = d - q;
-        m[midx(p, q)] += xp[p + 1] * yq[q] * dY / (p + 1);
-      }
-  });
+  cell::piece_moments(P.holes.data(), pc, px, py, h, rules().r510, m);
 }
 
 // parameters t in [0, 2pi) with A cos t + B sin t = C
@@ -480,6 +400,10 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
         if (G.type[k] == CT_FULL) G.vol[k] = h * h;
     });
   }
+  // the cut cells: boundary pieces and components here, moments below
+  std::vector<int> ccell;
+  std::vector<Cut> ccut;
+  std::vector<double> cpx, cpy;
   for (auto& kv : arcs) {
     int k = kv.first, j = k / n, i = k % n;
     double xl = P.x0 + i * h, xr = xl + h, yb = P.y0 + j * h, yt = yb + h;
@@ -528,24 +452,56 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
       G.reason = "cell (" + std::to_string(i) + "," + std::to_string(j) + ") has " +
                  std::to_string(n_out) + " components";
     }
-    std::fill(C.mom, C.mom + kMoments, 0.0);
-    for (auto& pc : C.pieces) piece_moments(P, pc, px, py, h, C.mom);
-    if (C.mom[0] <= 0) continue;   // empty
-    G.type[k] = CT_CUT;
-    G.vol[k] = C.mom[0] * h * h;
-    G.cut[k] = C;
+    ccell.push_back(k);
+    ccut.push_back(std::move(C));
+    cpx.push_back(px);
+    cpy.push_back(py);
+  }
+  {
+    const int nc = (int)ccell.size();
+    std::vector<double> mom((size_t)nc * kMoments, 0.0);
+    if (dev && nc) {
+      std::vector<Piece> pcs;
+      std::vector<int> ptr(1, 0);
+      for (const Cut& C : ccut) {
+        pcs.insert(pcs.end(), C.pieces.begin(), C.pieces.end());
+        ptr.push_back((int)pcs.size());
+      }
+      dev->moments(P, h, ccell, pcs, ptr, cpx, cpy, quad_rules(), mom.data());
+    } else {
+      parallel_rows(nc, [&](int r) {
+        for (const Piece& pc : ccut[r].pieces)
+          cell::piece_moments(P.holes.data(), pc, cpx[r], cpy[r], h, quad_rules(), &mom[(size_t)r * kMoments]);
+      }, 16);
+    }
+    for (int r = 0; r < nc; ++r) {
+      Cut& C = ccut[r];
+      std::copy(&mom[(size_t)r * kMoments], &mom[(size_t)r * kMoments] + kMoments, C.mom);
+      if (C.mom[0] <= 0) continue;   // empty
+      const int k = ccell[r];
+      G.type[k] = CT_CUT;
+      G.vol[k] = C.mom[0] * h * h;
+      G.cut[k] = std::move(C);
+    }
   }
 
   // ---- Alg. 1, merging of small cells -----------------------------------------
   G.owner.assign((size_t)n * n, -1);
-  for (int k = 0; k < n * n; ++k)
-    if (G.type[k] != CT_EMPTY) G.owner[k] = k;
+  parallel_rows(n, [&](int j) {
+    for (int k = j * n; k < (j + 1) * n; ++k)
+      if (G.type[k] != CT_EMPTY) G.owner[k] = k;
+  });
   std::function<int(int)> root = [&](int k) {
     while (G.owner[k] != k) k = G.owner[k];
     return k;
   };
   const double h2 = h * h;
-  for (int k = 0; k < n * n; ++k) {
+  // only cut cells can be small (a full cell has volume h^2), and merging
+  // only grows cells: visiting the cut cells in index order is the row-major
+  // pass over all cells
+  std::vector<int> small_cand;
+  for (const auto& kv : G.cut) small_cand.push_back(kv.first);
+  for (int k : small_cand) {
     if (G.type[k] == CT_EMPTY || G.vol[k] >= P.eps * h2) continue;
     int i = k % n, j = k / n;
     const bool* face = G.cut.count(k) ? G.cut[k].face : nullptr;
@@ -598,8 +554,13 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
     G.type[best] = CT_CUT;
     G.owner[k] = best;
   }
-  for (int k = 0; k < n * n; ++k)
-    if (G.owner[k] >= 0) G.owner[k] = root(k);
+  {
+    std::vector<int> own(G.owner.size());
+    parallel_rows(n, [&](int j) {
+      for (int k = j * n; k < (j + 1) * n; ++k) own[k] = G.owner[k] >= 0 ? root(k) : -1;
+    });
+    G.owner.swap(own);
+  }
   return G;
 }
 
@@ -636,5 +597,7 @@ std::vector<std::array<double, 3>> volume_nodes(const Problem& P, const LevelGeo
   }
   return out;
 }
+
+const Rules510& quad_rules() { return rules().r510; }
 
 }  // namespace ccmg

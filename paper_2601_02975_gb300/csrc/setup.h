@@ -64,14 +64,6 @@ struct Problem {
 constexpr int kMoments = 28;
 inline int midx(int p, int q) { int d = p + q; return d * (d + 1) / 2 + q; }
 
-struct Piece {           // oriented boundary piece of a cut cell
-  bool arc;
-  double xa, ya, xb, yb;  // end points (start, end)
-  int hole;               // arcs
-  double ta, tb;          // arcs: parameter from ta to tb (tb < ta)
-  int bc;                 // index into Problem::bc, -1 for interior faces
-};
-
 struct Cut {
   std::vector<Piece> pieces;
   double mom[kMoments];   // integral of X^p Y^q dX dY, X = (x - px)/h, about the own centre
@@ -108,6 +100,8 @@ void shift_moments(const double in[kMoments], double dx, double dy, double out[k
 
 // Gauss-Legendre rule on [-1, 1]
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+// the rules of the cut-cell quadrature (straight pieces, sub-arcs)
+const Rules510& quad_rules();
 
 // ---------------------------------------------------------------------------
 struct SparseRows {            // CSR
@@ -160,6 +154,12 @@ class SetupDevice {
   // type[k] = CT_FULL if crossed[k] == 0 and the cell's centre lies
   // outside every hole, else CT_EMPTY
   void classify(const Problem& P, int n, double h, const uint8_t* crossed, uint8_t* type);
+  // scaled moments (28 each) of cut cells cells[r] about (px[r], py[r])
+  // from their boundary pieces pieces[ptr[r], ptr[r+1]) (Green's theorem)
+  void moments(const Problem& P, double h, const std::vector<int>& cells,
+               const std::vector<Piece>& pieces, const std::vector<int>& ptr,
+               const std::vector<double>& px, const std::vector<double>& py, const Rules510& R,
+               double* mom);
   // Def. 4.1 kind of every cell; keeps the type map on the device for the
   // calls below
   void kinds(int n, bool cross, const uint8_t* type, const uint8_t* ext, uint8_t* kind);

@@ -1,21 +1,23 @@
 // Per-cell steps of the setup, written once for the host and the device.
 //
 // Each function here computes the table entries of ONE cell from read-only
-// inputs: the classification of a control volume (Sec. 3.1), its kind
-// (Def. 4.1), the poised lattice of a PLG cell (Def. 4.3, the reading of the
-// lattice rule stated in disc.cpp), its fit (Eq. 4.14, or the weighted
-// minimum norm of Eq. 4.17-4.18), and the nearest sample of a boundary curve
-// that orders the exactly solved block (Def. 5.1).  disc.cpp runs them on
+// inputs: the classification of a control volume (Sec. 3.1), the moments of
+// a cut cell from its boundary pieces (Sec. 4.2), its kind (Def. 4.1), the
+// poised lattice of a PLG cell (Def. 4.3, the reading of the lattice rule
+// stated in disc.cpp), its fit (Eq. 4.14, or the weighted minimum norm of
+// Eq. 4.17-4.18), and the nearest sample of a boundary curve that orders the
+// exactly solved block (Def. 5.1).  disc.cpp runs them on
 // host threads; setup_dev.cu runs them as CUDA kernels, one thread per cell.
 //
 // Both builds evaluate the same expressions in the same order with IEEE
-// double operations only (+ - * / and sqrt, all correctly rounded; no
-// contraction into fused multiply-adds: the host compiler gets
-// -ffp-contract=off and the device translation unit --fmad=false), so the
-// two give the same bits.  The one exception is the level function of the
-// flower and rectangle holes (hypot, atan2, cos), used only to classify
-// cells that no curve crosses: their centres lie at least h/2 from the
-// curve, so the sign cannot differ.
+// double operations only (+ - * / and sqrt, all correctly rounded, and rint,
+// floor, ceil, fmod, exact; no contraction into fused multiply-adds: the
+// host compiler gets -ffp-contract=off and the device translation unit
+// --fmad=false), and the curves' sines and cosines come from sin_cos below,
+// so the two give the same bits.  The one exception is the level function
+// of the flower and rectangle holes (hypot, atan2, cos), used only to
+// classify cells that no curve crosses: their centres lie at least h/2 from
+// the curve, so the sign cannot differ.
 #pragma once
 #include <cmath>
 #include <cstdint>
@@ -34,6 +36,48 @@
 
 namespace ccmg {
 
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+namespace cell {
+
+// sin t and cos t, the same bits on the host and the device.  Additive range
+// reduction (Cody and Waite): k = the integer nearest t 2/pi, r = t - k pi/2
+// with pi/2 split into P1 + P2 + P3, P1 and P2 of 30 significant bits so that
+// k P1 and k P2 are exact for |k| < 2^23; then the Taylor series of sin and
+// cos about 0 on |r| <= pi/4 (to r^17 and r^18: the first omitted terms are
+// below 1e-19), and the quadrant k mod 4.
+CC_HD inline void sin_cos(double t, double* s, double* c) {
+  const double P1 = 1.5707963276654482, P2 = -8.705515692000731e-10, P3 = -3.50343439808993e-19;
+  const double k = rint(t * 0.6366197723675814);
+  const double r = ((t - k * P1) - k * P2) - k * P3;
+  const double r2 = r * r;
+  const double sr = r + r * r2 * (-0.16666666666666666 + r2 * (0.008333333333333333 +
+                    r2 * (-0.0001984126984126984 + r2 * (2.7557319223985893e-06 +
+                    r2 * (-2.505210838544172e-08 + r2 * (1.6059043836821613e-10 +
+                    r2 * (-7.647163731819816e-13 + r2 * 2.8114572543455206e-15)))))));
+  const double cr = 1.0 + r2 * (-0.5 + r2 * (0.041666666666666664 + r2 * (-0.001388888888888889 +
+                    r2 * (2.48015873015873e-05 + r2 * (-2.755731922398589e-07 +
+                    r2 * (2.08767569878681e-09 + r2 * (-1.1470745597729725e-11 +
+                    r2 * 4.779477332387385e-14)))))));
+  const long long q = ((long long)k % 4 + 4) % 4;
+  if (q == 0) { *s = sr; *c = cr; }
+  else if (q == 1) { *s = cr; *c = -sr; }
+  else if (q == 2) { *s = -sr; *c = -cr; }
+  else { *s = -cr; *c = sr; }
+}
+
+// side k of a kind-2 hole at parameter t: the corner index and the fraction
+CC_HD inline void rect_side(double t, int& k, double& tau) {
+  const double q = kTwoPi / 4;
+  double tm = fmod(t, kTwoPi);
+  if (tm < 0) tm += kTwoPi;
+  k = (int)floor(tm / q);
+  if (k > 3) k = 3;
+  tau = (tm - k * q) / q;
+}
+
+}  // namespace cell
+
 // A hole: kind 0 the ellipse c + R(th) (r1 cos t, r2 sin t); kind 1 the
 // flower c + (r1 + r2 cos(petals t)) (cos t, sin t) (Sec. 6.2); kind 2
 // everything outside the rectangle with corner c and sides r1 (direction th)
@@ -44,9 +88,55 @@ struct Hole {
   double cx, cy, r1, r2, th, co, si;
   int kind = 0;
   int petals = 0;
-  // point and derivative at parameter t (host)
-  void at(double t, double& x, double& y) const;
-  void dat(double t, double& dx, double& dy) const;
+  // point and derivative at parameter t
+  CC_HD void at(double t, double& x, double& y) const {
+    if (kind == 2) {
+      double vx[4], vy[4], tau;
+      int k;
+      corners_cw(vx, vy);
+      cell::rect_side(t, k, tau);
+      const int k1 = (k + 1) % 4;
+      x = vx[k] + tau * (vx[k1] - vx[k]);
+      y = vy[k] + tau * (vy[k1] - vy[k]);
+      return;
+    }
+    double st, ct;
+    cell::sin_cos(t, &st, &ct);
+    if (kind == 1) {
+      double sp, cp;
+      cell::sin_cos(petals * t, &sp, &cp);
+      const double r = r1 + r2 * cp;
+      x = cx + r * ct;
+      y = cy + r * st;
+      return;
+    }
+    x = cx + co * r1 * ct - si * r2 * st;
+    y = cy + si * r1 * ct + co * r2 * st;
+  }
+  CC_HD void dat(double t, double& dx, double& dy) const {
+    if (kind == 2) {
+      double vx[4], vy[4], tau;
+      int k;
+      corners_cw(vx, vy);
+      cell::rect_side(t, k, tau);
+      const int k1 = (k + 1) % 4;
+      dx = (vx[k1] - vx[k]) / (kTwoPi / 4);
+      dy = (vy[k1] - vy[k]) / (kTwoPi / 4);
+      return;
+    }
+    double st, ct;
+    cell::sin_cos(t, &st, &ct);
+    if (kind == 1) {
+      double sp, cp;
+      cell::sin_cos(petals * t, &sp, &cp);
+      const double r = r1 + r2 * cp, dr = -r2 * petals * sp;
+      dx = dr * ct - r * st;
+      dy = dr * st + r * ct;
+      return;
+    }
+    dx = -co * r1 * st - si * r2 * ct;
+    dy = -si * r1 * st + co * r2 * ct;
+  }
   CC_HD double halfwidth() const {
     return kind == 2 ? 1e300 : kind == 1 ? r1 - r2 : (r1 < r2 ? r1 : r2);
   }
@@ -86,6 +176,20 @@ struct Hole {
 // A quadrature node on the boundary of a cut cell: position, outward unit
 // normal, weight |ds|, boundary condition index.
 struct BNode { double x, y, nx, ny, w; int bc; };
+
+// An oriented boundary piece of a cut cell: a straight piece of a face, or an
+// arc of a hole from parameter ta down to tb.
+struct Piece {
+  bool arc;
+  double xa, ya, xb, yb;  // end points (start, end)
+  int hole;               // arcs
+  double ta, tb;          // arcs: parameter from ta to tb (tb < ta)
+  int bc;                 // index into Problem::bc, -1 for interior faces
+};
+
+// Gauss-Legendre rules on [-1, 1]: 5 points for straight pieces, 10 for each
+// sub-arc of at most 0.25 rad
+struct Rules510 { double sx[5], sw[5], ax[10], aw[10]; };
 
 namespace cell {
 
@@ -452,6 +556,55 @@ CC_HD inline bool plg_fit(int k, int n, double h, double a, double b, double c, 
   if (!min_norm15x16(M, rhs, g)) return false;
   for (int col = 0; col < 16; ++col) beta[col] = sw[col] * g[col];
   return true;
+}
+
+// --- moments of a cut cell (Sec. 4.2) -----------------------------------------
+// Quadrature points along a piece: fn(x, y, dx w, dy w) for each node.
+template <class F>
+CC_HD inline void walk_piece(const Hole* holes, const Piece& pc, const Rules510& R, F&& fn) {
+  if (!pc.arc) {
+    for (int q = 0; q < 5; ++q) {
+      const double tau = 0.5 * (R.sx[q] + 1.0), wt = 0.5 * R.sw[q];
+      fn(pc.xa + tau * (pc.xb - pc.xa), pc.ya + tau * (pc.yb - pc.ya), (pc.xb - pc.xa) * wt,
+         (pc.yb - pc.ya) * wt);
+    }
+    return;
+  }
+  const Hole& H = holes[pc.hole];
+  int nsub = (int)ceil(fabs(pc.tb - pc.ta) / 0.25);
+  if (nsub < 1) nsub = 1;
+  CC_ROLLED
+  for (int s = 0; s < nsub; ++s) {
+    const double s0 = pc.ta + (pc.tb - pc.ta) * s / nsub, s1 = pc.ta + (pc.tb - pc.ta) * (s + 1) / nsub;
+    for (int q = 0; q < 10; ++q) {
+      const double t = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * R.ax[q];
+      const double wt = 0.5 * (s1 - s0) * R.aw[q];
+      double x, y, dx, dy;
+      H.at(t, x, y);
+      H.dat(t, dx, dy);
+      fn(x, y, dx * wt, dy * wt);
+    }
+  }
+}
+
+// adds the scaled moments integral X^p Y^q dX dY (X = (x - px)/h, Y the
+// same) of the piece's contribution by Green's theorem: the contour
+// integral of X^(p+1) Y^q / (p+1) dY
+CC_HD inline void piece_moments(const Hole* holes, const Piece& pc, double px, double py, double h,
+                                const Rules510& R, double m[kNM]) {
+  walk_piece(holes, pc, R, [&](double x, double y, double, double dy) {
+    const double X = (x - px) / h, Y = (y - py) / h, dY = dy / h;
+    double xp[8], yq[7];
+    xp[0] = 1;
+    yq[0] = 1;
+    for (int k = 1; k < 8; ++k) xp[k] = xp[k - 1] * X;
+    for (int k = 1; k < 7; ++k) yq[k] = yq[k - 1] * Y;
+    for (int d = 0; d <= 6; ++d)
+      for (int q = 0; q <= d; ++q) {
+        const int p = d - q;
+        m[mi(p, q)] += xp[p + 1] * yq[q] * dY / (p + 1);
+      }
+  });
 }
 
 // --- Def. 5.1 ordering: the nearest of ns samples (sx, sy) of one curve to

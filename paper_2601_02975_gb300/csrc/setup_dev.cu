@@ -1,12 +1,12 @@
-// The per-cell steps of the setup as FP64 CUDA kernels (Sec. 3.1, Def. 4.1,
-// Def. 4.3, Eq. 4.14 and 4.17-4.18, Def. 5.1), one thread per cell, running
-// the functions of setup_cell.h.  This translation unit is compiled with
+// The per-cell steps of the setup as FP64 CUDA kernels (Sec. 3.1, the
+// moments of Sec. 4.2, Def. 4.1, Def. 4.3, Eq. 4.14 and 4.17-4.18, Def.
+// 5.1), one thread per cell, running the functions of setup_cell.h.  This translation unit is compiled with
 // --fmad=false so that its products and sums round exactly as the host's
 // (-ffp-contract=off): the tables it builds are the host's, bit for bit.
 //
-// The host keeps the steps that walk curves or depend on earlier cells: the
-// crossings of the grid lines, the cut cells' boundary pieces and moments,
-// the merging of Alg. 1 (sequential by definition), the boundary quadrature
+// The host keeps the steps that search curves or depend on earlier cells:
+// the crossings of the grid lines and the cut cells' boundary pieces, the
+// merging of Alg. 1 (sequential by definition), the boundary quadrature
 // nodes, the rows of A and N, and the factorisations of the block smoother.
 #include <cuda_runtime.h>
 
@@ -42,6 +42,18 @@ __global__ void k_classify(const Hole* __restrict__ holes, int nh, int n, double
     }
     type[k] = t;
   }
+}
+
+__global__ void k_cut_moments(const Hole* __restrict__ holes, int nc, double h,
+                              const Piece* __restrict__ pieces, const int* __restrict__ ptr,
+                              const double* __restrict__ px, const double* __restrict__ py,
+                              Rules510 R, double* __restrict__ mom) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nc) return;
+  double m[cell::kNM];
+  for (int q = 0; q < cell::kNM; ++q) m[q] = 0.0;
+  for (int s = ptr[r]; s < ptr[r + 1]; ++s) cell::piece_moments(holes, pieces[s], px[r], py[r], h, R, m);
+  for (int q = 0; q < cell::kNM; ++q) mom[(int64_t)cell::kNM * r + q] = m[q];
 }
 
 __global__ void k_kinds(const uint8_t* __restrict__ type, const uint8_t* __restrict__ ext, int n,
@@ -205,6 +217,26 @@ void SetupDevice::classify(const Problem& P, int n, double h, const uint8_t* cro
   k_classify<<<grid_for((int64_t)nn, 256), 256, 0, I.s>>>(dh, nh, n, P.x0, P.y0, h, dc, dt);
   I.end(kernel_ms);
   SCK(cudaMemcpyAsync(type, dt, nn, cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaStreamSynchronize(I.s));
+}
+
+void SetupDevice::moments(const Problem& P, double h, const std::vector<int>& cells,
+                          const std::vector<Piece>& pieces, const std::vector<int>& ptr,
+                          const std::vector<double>& px, const std::vector<double>& py,
+                          const Rules510& R, double* mom) {
+  Impl& I = *p_;
+  Impl::Scratch S{&I, {}};
+  const int nc = (int)cells.size();
+  const Hole* dh = S.put(P.holes.data(), P.holes.size());
+  const Piece* dp = S.put(pieces.data(), pieces.size());
+  const int* dptr = S.put(ptr.data(), ptr.size());
+  const double* dx = S.put(px.data(), px.size());
+  const double* dy = S.put(py.data(), py.size());
+  double* dm = S.get<double>((size_t)cell::kNM * nc);
+  I.begin();
+  k_cut_moments<<<(nc + 63) / 64, 64, 0, I.s>>>(dh, nc, h, dp, dptr, dx, dy, R, dm);
+  I.end(kernel_ms);
+  SCK(cudaMemcpyAsync(mom, dm, (size_t)cell::kNM * nc * sizeof(double), cudaMemcpyDeviceToHost, I.s));
   SCK(cudaStreamSynchronize(I.s));
 }
 
