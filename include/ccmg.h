@@ -147,6 +147,15 @@ typedef struct {
                           4.17-4.18) and the curve-order samples of Def. 5.1; the
                           tables are bitwise those of the host path.  0: the same
                           steps on host threads.  Ignored with host_only */
+  int device_loop;     /* 1 (default): the iterations of a cc_solve or cc_solve_host
+                          run inside one CUDA graph launch: a conditional WHILE node
+                          repeats the iteration (cycle and FP64 residual) while a
+                          one-thread kernel finds the relative residual above tol, so
+                          the host waits once per solve; same results as 0.  0: the
+                          host reads the residual after every iteration.  The host
+                          loop is also used with use_graphs = 0, krylov, cc_kernel_timing
+                          on, and for cc_solve_batch and cc_submit, where concurrent
+                          solves overlap better under it */
 } cc_options;
 
 /* Sizes of a hierarchy. */

@@ -42,7 +42,7 @@ class cc_options(C.Structure):
                 ("max_cycles", C.c_int), ("use_graphs", C.c_int), ("host_only", C.c_int),
                 ("fmg_cycle", C.c_int), ("w_depth", C.c_int), ("serve_slots", C.c_int),
                 ("cache", C.c_int), ("hole_cells", C.c_double), ("krylov", C.c_int),
-                ("smoother", C.c_int), ("device_setup", C.c_int)]
+                ("smoother", C.c_int), ("device_setup", C.c_int), ("device_loop", C.c_int)]
 
 
 class cc_info(C.Structure):

@@ -1039,12 +1039,143 @@ struct ChunkSmem {
   __host__ __device__ size_t p2_bytes(int w) const { return (size_t)p2_total() * w + (size_t)(ns4 + 4) * 4; }
 };
 
-// Launch 1, one CTA per chunk: stage [inv(A_cc); V_c], gather t of the
-// chunk's rows, then z = inv(A_cc) t_I and the contributions q = V_c t_I.
-// Everything that comes from setup (the staged stage, the row's gather
-// terms, its slot, the output index of each product row) is read before
-// the wait on the previous kernel; after it, one batch of independent loads
-// of b and u.
+// Phase 1 of the chunked solve, one CTA per chunk: gather t of the chunk's
+// rows, then z = inv(A_cc) t_I and the contributions q = V_c t_I, with
+// [inv(A_cc); V_c] staged in shared memory.  Everything that comes from
+// setup (the row's gather terms, its slot, the output index of each product
+// row) is read by p1_load, before the wait on the previous kernel; after it,
+// one batch of independent loads of b and u.
+template <class T>
+struct P1Pre {
+  bool on;
+  int cell, sl, si, t0, t1;
+  int col[kGatherMax];
+  T val[kGatherMax];
+  int oi[2];
+};
+
+template <class T>
+__device__ __forceinline__ void p1_load(const BlockDev& B, const ChunkDev& C, P1Pre<T>& r) {
+  const int tid = threadIdx.x;
+  r.on = tid < C.p1 - C.p0;
+  const int p = C.p0 + tid;
+  r.cell = 0; r.sl = 0; r.si = -1; r.t0 = 0; r.t1 = 0;
+  const T* gval = static_cast<const T*>(B.gval);
+  if (r.on) {
+    r.cell = B.cell[p];
+    r.sl = B.slot[p];
+    r.si = B.sidx[p];
+    r.t0 = B.tptr[p];
+    r.t1 = B.tptr[p + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < kGatherMax; ++k) {
+    const bool use = r.on && k < B.gk;
+    const size_t e = (size_t)k * B.m + p;
+    r.col[k] = use ? B.gcol[e] : 0;
+    r.val[k] = use ? gval[e] : T(0);
+  }
+  // output index of product rows tid and tid + kChunkThreads: interior rows
+  // go to z at their block position, V_c rows to their contribution slot
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int q = tid + k * kChunkThreads;
+    r.oi[k] = q < C.ni ? B.ipos[C.ipos_off + q] : q < C.ni + C.nv ? B.vslot[C.v_off + q - C.ni] : -1;
+  }
+}
+
+// after the wait: false (nothing written but the gathered t) if the staged
+// copy did not arrive
+template <class T>
+__device__ __forceinline__ bool p1_run(const BlockDev& B, const ChunkSmem& L, const ChunkDev& C,
+                                       const P1Pre<T>& r, const T* __restrict__ b,
+                                       const T* __restrict__ u, T* sm, uint64_t* bar) {
+  const int tid = threadIdx.x;
+  T* tl = sm + L.p1_tl();
+  if (r.on) {
+    T acc = b[r.cell];
+#pragma unroll
+    for (int k = 0; k < kGatherMax; ++k)
+      if (k < B.gk) acc -= r.val[k] * u[r.col[k]];
+    const T* tval = static_cast<const T*>(B.tval);
+    for (int k = r.t0; k < r.t1; ++k) acc -= tval[k] * u[B.tcol[k]];
+    tl[r.sl] = acc;
+    if (r.si >= 0) static_cast<T*>(B.tS)[r.si] = acc;
+  }
+  if (!stage_ready(B.stage1 != 0, bar, B.fault)) return false;
+  const T* M = B.stage1 ? sm : static_cast<const T*>(B.blob) + C.b1;
+  T* y = sm + L.p1_y();
+  cta_gemv_cm<T>(M, C.ni + C.nv, C.ni + C.nv, C.ni, tl, sm + L.p1_part(), y);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int q = tid + k * kChunkThreads;
+    if (r.oi[k] < 0) continue;
+    if (q < C.ni) static_cast<T*>(B.z)[r.oi[k]] = y[q];
+    else static_cast<T*>(B.q)[r.oi[k]] = y[q];
+  }
+  return true;
+}
+
+// Phase 2, one CTA per chunk: with the held rows of inv(S) (row-major) and
+// W_c (column-major) staged, form the interface right-hand side t_S - the
+// sum of contributions (each interface's in chunk order), x = inv(S) rows
+// times it, then x_I = z - W_c x_S, and write the interior and own
+// interface rows (with their merged-away cells).  p2_load reads the setup
+// data (the interface pointers into shared memory, this thread's rows and
+// their destinations); after the wait, t_S, the contributions and z come in
+// one batch of independent loads.
+struct P2Pre {
+  bool hi, ho;
+  int pi, ro, wr;
+  BlockDst di, dob;
+};
+
+__device__ __forceinline__ void p2_load(const BlockDev& B, const ChunkDev& C, int* qp, P2Pre& r) {
+  const int tid = threadIdx.x;
+  for (int k = tid; k <= B.ns; k += blockDim.x) qp[k] = B.qptr[k];
+  r.hi = tid < C.ni;
+  r.ho = tid < C.nown;
+  r.pi = r.hi ? B.ipos[C.ipos_off + tid] : 0;
+  r.ro = r.ho ? B.orow[C.o_off + tid] : 0;
+  r.wr = tid < C.nw ? B.wrow[C.w_off + tid] : 0;
+  if (r.hi) r.di.load(B, r.pi);
+  if (r.ho) r.dob.load(B, B.opos[C.o_off + tid]);
+}
+
+template <class T>
+__device__ __forceinline__ void p2_run(const BlockDev& B, const ChunkSmem& L, const ChunkDev& C,
+                                       const P2Pre& r, const int* qp, T* __restrict__ u, T* sm,
+                                       uint64_t* bar) {
+  const int tid = threadIdx.x;
+  T* ys = sm + L.p2_ys();
+  T* qs = sm + L.p2_q();
+  const T* tS = static_cast<const T*>(B.tS);
+  const T* q = static_cast<const T*>(B.q);
+  for (int k = tid; k < B.ns; k += blockDim.x) ys[k] = tS[k];
+  for (int j = tid; j < B.nslots; j += blockDim.x) qs[j] = q[j];
+  const T zi = r.hi ? static_cast<const T*>(B.z)[r.pi] : T(0);
+  __syncthreads();
+  for (int k = tid; k < B.ns; k += blockDim.x) {
+    T acc = ys[k];
+    for (int j = qp[k]; j < qp[k + 1]; ++j) acc -= qs[j];
+    ys[k] = acc;
+  }
+  if (!stage_ready(B.stage2 != 0, bar, B.fault)) return;
+  const T* S = B.stage2 ? sm : static_cast<const T*>(B.blob) + C.b2;
+  const T* W = S + (size_t)C.nr * B.ns;
+  T* xr = sm + L.p2_xr();
+  T* xw = sm + L.p2_xw();
+  T* part = sm + L.p2_part();
+  T* y = sm + L.p2_y();
+  cta_gemv_rm<T>(S, C.nr, B.ns, B.ns, ys, xr);
+  if (tid < C.nw) xw[tid] = xr[r.wr];
+  __syncthreads();
+  cta_gemv_cm<T>(W, C.ni, C.ni, C.nw, xw, part, y);
+  if (r.hi) r.di.write(B, u, zi - y[tid]);
+  if (r.ho) r.dob.write(B, u, xr[r.ro]);
+}
+
+// Launch 1: phase 1.
 template <class T>
 __global__ void __launch_bounds__(kChunkThreads) k_block_p1(BlockDev B, ChunkSmem L,
                                                           const T* __restrict__ b,
@@ -1053,71 +1184,16 @@ __global__ void __launch_bounds__(kChunkThreads) k_block_p1(BlockDev B, ChunkSme
   __shared__ __align__(8) uint64_t bar;
   T* sm = reinterpret_cast<T*>(smem_f4);
   const ChunkDev C = B.ch[blockIdx.x];
-  const int tid = threadIdx.x;
-  if (B.stage1 && tid == 0)
+  if (B.stage1 && threadIdx.x == 0)
     bulk_stage(sm, static_cast<const T*>(B.blob) + C.b1, (unsigned)(C.b1n * sizeof(T)), &bar);
-  const bool on = tid < C.p1 - C.p0;
-  const int p = C.p0 + tid;
-  int cell = 0, sl = 0, si = -1, t0 = 0, t1 = 0;
-  int col[kGatherMax];
-  T val[kGatherMax];
-  const T* gval = static_cast<const T*>(B.gval);
-  if (on) {
-    cell = B.cell[p];
-    sl = B.slot[p];
-    si = B.sidx[p];
-    t0 = B.tptr[p];
-    t1 = B.tptr[p + 1];
-  }
-#pragma unroll
-  for (int k = 0; k < kGatherMax; ++k) {
-    const bool use = on && k < B.gk;
-    const size_t e = (size_t)k * B.m + p;
-    col[k] = use ? B.gcol[e] : 0;
-    val[k] = use ? gval[e] : T(0);
-  }
-  // output index of product rows tid and tid + kChunkThreads: interior rows
-  // go to z at their block position, V_c rows to their contribution slot
-  int oi[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int r = tid + k * kChunkThreads;
-    oi[k] = r < C.ni ? B.ipos[C.ipos_off + r] : r < C.ni + C.nv ? B.vslot[C.v_off + r - C.ni] : -1;
-  }
+  P1Pre<T> r;
+  p1_load<T>(B, C, r);
   pdl_enter();
-  T* tl = sm + L.p1_tl();
-  if (on) {
-    T acc = b[cell];
-#pragma unroll
-    for (int k = 0; k < kGatherMax; ++k)
-      if (k < B.gk) acc -= val[k] * u[col[k]];
-    const T* tval = static_cast<const T*>(B.tval);
-    for (int k = t0; k < t1; ++k) acc -= tval[k] * u[B.tcol[k]];
-    tl[sl] = acc;
-    if (si >= 0) static_cast<T*>(B.tS)[si] = acc;
-  }
-  if (!stage_ready(B.stage1 != 0, &bar, B.fault)) { pdl_exit(); return; }
-  const T* M = B.stage1 ? sm : static_cast<const T*>(B.blob) + C.b1;
-  T* y = sm + L.p1_y();
-  cta_gemv_cm<T>(M, C.ni + C.nv, C.ni + C.nv, C.ni, tl, sm + L.p1_part(), y);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int r = tid + k * kChunkThreads;
-    if (oi[k] < 0) continue;
-    if (r < C.ni) static_cast<T*>(B.z)[oi[k]] = y[r];
-    else static_cast<T*>(B.q)[oi[k]] = y[r];
-  }
+  p1_run<T>(B, L, C, r, b, u, sm, &bar);
   pdl_exit();
 }
 
-// Launch 2, one CTA per chunk: stage the held rows of inv(S) (row-major) and
-// W_c (column-major), form the
-// interface right-hand side t_S - sum of contributions (each interface's in
-// chunk order), x = inv(S) rows times it, then x_I = z - W_c x_S, and write
-// the interior and own interface rows (with their merged-away cells).  The
-// interface pointers, this thread's rows and their destinations are setup
-// data, read before the wait; after it, t_S, the contributions and z come
-// in one batch of independent loads.
+// Launch 2: phase 2.
 template <class T>
 __global__ void __launch_bounds__(kChunkThreads) k_block_p2(BlockDev B, ChunkSmem L,
                                                           T* __restrict__ u) {
@@ -1126,45 +1202,12 @@ __global__ void __launch_bounds__(kChunkThreads) k_block_p2(BlockDev B, ChunkSme
   T* sm = reinterpret_cast<T*>(smem_f4);
   int* qp = reinterpret_cast<int*>(sm + L.p2_total());
   const ChunkDev C = B.ch[blockIdx.x];
-  const int tid = threadIdx.x;
-  if (B.stage2 && tid == 0)
+  if (B.stage2 && threadIdx.x == 0)
     bulk_stage(sm, static_cast<const T*>(B.blob) + C.b2, (unsigned)(C.b2n * sizeof(T)), &bar);
-  for (int k = tid; k <= B.ns; k += blockDim.x) qp[k] = B.qptr[k];
-  // this thread's interior row (tid < ni) and own interface row (tid < nown)
-  const bool hi = tid < C.ni, ho = tid < C.nown;
-  const int pi = hi ? B.ipos[C.ipos_off + tid] : 0;
-  const int ro = ho ? B.orow[C.o_off + tid] : 0;
-  const int wr = tid < C.nw ? B.wrow[C.w_off + tid] : 0;
-  BlockDst di, dob;
-  if (hi) di.load(B, pi);
-  if (ho) dob.load(B, B.opos[C.o_off + tid]);
+  P2Pre r;
+  p2_load(B, C, qp, r);
   pdl_enter();
-  T* ys = sm + L.p2_ys();
-  T* qs = sm + L.p2_q();
-  const T* tS = static_cast<const T*>(B.tS);
-  const T* q = static_cast<const T*>(B.q);
-  for (int k = tid; k < B.ns; k += blockDim.x) ys[k] = tS[k];
-  for (int j = tid; j < B.nslots; j += blockDim.x) qs[j] = q[j];
-  const T zi = hi ? static_cast<const T*>(B.z)[pi] : T(0);
-  __syncthreads();
-  for (int k = tid; k < B.ns; k += blockDim.x) {
-    T acc = ys[k];
-    for (int j = qp[k]; j < qp[k + 1]; ++j) acc -= qs[j];
-    ys[k] = acc;
-  }
-  if (!stage_ready(B.stage2 != 0, &bar, B.fault)) { pdl_exit(); return; }
-  const T* S = B.stage2 ? sm : static_cast<const T*>(B.blob) + C.b2;
-  const T* W = S + (size_t)C.nr * B.ns;
-  T* xr = sm + L.p2_xr();
-  T* xw = sm + L.p2_xw();
-  T* part = sm + L.p2_part();
-  T* y = sm + L.p2_y();
-  cta_gemv_rm<T>(S, C.nr, B.ns, B.ns, ys, xr);
-  if (tid < C.nw) xw[tid] = xr[wr];
-  __syncthreads();
-  cta_gemv_cm<T>(W, C.ni, C.ni, C.nw, xw, part, y);
-  if (hi) di.write(B, u, zi - y[tid]);
-  if (ho) dob.write(B, u, xr[ro]);
+  p2_run<T>(B, L, C, r, qp, u, sm, &bar);
   pdl_exit();
 }
 
@@ -1391,6 +1434,59 @@ __global__ void k_widen_masked(const T* __restrict__ e, const uint8_t* __restric
   pdl_enter();
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < nn) z[k] = cls[k] == C_EMPTY ? 0.0 : (double)e[k];
+}
+
+// The convergence test of a solve on the device (Alg. 3's outer iteration,
+// stopping on the relative max-norm residual): the state the host keeps in
+// its own loop otherwise, updated by one thread from the max-norm word the
+// residual kernels leave in norm[0] (and the bounded-wait fault word in
+// norm[1]).
+struct LoopState {
+  double bn, first, rel, tol;
+  int it, max_cycles, status, pad;
+};
+
+__global__ void k_loop_init(LoopState* st, double tol, int max_cycles) {
+  st->bn = 1.0;
+  st->first = -1.0;
+  st->rel = 0.0;
+  st->tol = tol;
+  st->it = 0;
+  st->max_cycles = max_cycles;
+  st->status = CC_ERR_NOT_CONVERGED;
+  st->pad = 0;
+}
+
+// mode 0: norm[0] holds |b|_inf; mode 1: the residual of the initial guess;
+// mode 2: the residual after one more iteration.  Modes 1 and 2 set the
+// loop's condition: 1 to run another iteration.
+__global__ void k_loop_step(LoopState* st, const unsigned long long* __restrict__ norm, int mode,
+                            cudaGraphConditionalHandle cond) {
+  pdl_enter();
+  const double v = __longlong_as_double((long long)norm[0]);
+  if (mode == 0) {
+    st->bn = v == 0.0 ? 1.0 : v;
+    pdl_exit();
+    return;
+  }
+  unsigned int more = 0;
+  const double rel = v / st->bn;
+  if (mode == 2) ++st->it;
+  st->rel = rel;
+  if (mode == 1) st->first = rel;
+  if (norm[1] != 0) {
+    st->status = CC_ERR_TIMEOUT;
+  } else if (rel < st->tol) {
+    st->status = CC_OK;
+  } else if (mode == 2 && (!isfinite(rel) || (st->first > 0 && rel > 1e3 * st->first))) {
+    st->status = CC_ERR_DIVERGED;
+  } else if (st->it >= st->max_cycles) {
+    st->status = CC_ERR_NOT_CONVERGED;
+  } else {
+    more = 1;
+  }
+  cudaGraphSetConditional(cond, more);
+  pdl_exit();
 }
 
 __global__ void k_absmax(const double* __restrict__ x, int64_t nn, unsigned long long* out) {
