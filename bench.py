@@ -77,6 +77,14 @@ def _args():
                     help="grids of the ellipse-union measurement (none: skip)")
     ap.add_argument("--hbm-n", type=int, default=4096,
                     help="grid of the HBM-bound sweep measurement (0: skip)")
+    ap.add_argument("--serve-full", type=int, default=0, metavar="N",
+                    help="run the full serving workload with N requests per rate (10000 as specified; "
+                         "0: skip, the default, as it takes about a quarter of an hour)")
+    ap.add_argument("--serve-domains", type=int, default=64)
+    ap.add_argument("--serve-full-rates", default="100,300,1000,3000,5000")
+    ap.add_argument("--plain", type=int, default=1,
+                    help="also run the plain-method cases: Poisson 64^2 (and 1024^2, 4096^2) V(3,3), "
+                         "the disk refinement sweep 128^2..1024^2, the Table 8 rates (0: skip)")
     ap.add_argument("--setup", type=int, default=1,
                     help="also time the setup with its per-cell steps on the device and on host "
                          "threads (0: skip)")
@@ -415,6 +423,10 @@ def run_ours(a):
     random_domains = run_random_domains(a, dev) if a.random_domains > 0 else None
     mcgs = run_mcgs(a, dev) if a.mcgs else None
     setup = run_setup(a, dev) if a.setup else None
+    serving_full = run_serving_full(a, dev) if a.serve_full > 0 else None
+    plain = run_plain_poisson(a, dev) if a.plain else None
+    refine = run_refinement_sweep(a, dev) if a.plain else None
+    table8 = run_table8(a, dev) if a.plain else None
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -447,6 +459,10 @@ def run_ours(a):
         "random_domains": random_domains,
         "multicolour_smoother": mcgs,
         "setup": setup,
+        "serving_full": serving_full,
+        "plain_poisson": plain,
+        "refinement_sweep": refine,
+        "table8_rates": table8,
         "fp64_solve": {"ms": fp64_ms, "dof_per_s": dof / (fp64_ms / 1e3), "cycles": r64.cycles,
                        "max_error_vs_exact": err64, "steps": a.steps, "warmup": a.warmup,
                        "timing": "CUDA events around each solve, L2 flushed between steps, as the "
@@ -589,6 +605,150 @@ def run_ellipse_union(a, dev):
             H.close()
         out[str(n)] = row
     cache_clear()
+    return out
+
+
+def _event_solve(H, ft, gt, u, tol, reps=3):
+    """min over reps of CUDA-event time of H.solve from u = 0 (after one
+    untimed solve); returns (ms, result)."""
+    import torch
+    u.zero_()
+    H.solve(ft, gt, u, tol)
+    best, r = None, None
+    for _ in range(reps):
+        u.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = H.solve(ft, gt, u, tol)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best, r
+
+
+def _inputs(H, P, dev):
+    import torch
+    from paper_2601_02975_gb300 import inputs as I
+    f, g, ue = I.problem_inputs(H, P)
+    ft = torch.tensor(f.ravel(), dtype=torch.float64, device=dev)
+    gt = torch.tensor(g, dtype=torch.float64, device=dev)
+    return ft, gt, ue
+
+
+def run_plain_poisson(a, dev):
+    """The plain-method case: Poisson on the unit square, u = sin(pi x)
+    sin(pi y), Dirichlet, FP64 V(3,3) cycles to the coarsest level 4^2 (the
+    paper's cycle) until the relative residual is below 1e-10, at 64^2;
+    then the same problem at 1024^2 and 4096^2 for throughput, with the
+    headline's cycle (W(4,4), gamma = 2 on the finest level, coarsest 32^2),
+    FP64 and mixed."""
+    import numpy as np
+    import torch
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from paper_2601_02975_gb300 import workloads as W
+    P = W.problem_poisson_square()
+    out = {"workload": "Poisson, unit square, u = sin(pi x) sin(pi y), Dirichlet, tol 1e-10 "
+                       "(1e-8 at 4096^2: the Dirichlet data are 0, so |b| = |f| ~ 2 pi^2 and the "
+                       "relative residual of the FP64 iterate cannot fall below ~1.5e-9 there)"}
+    runs = [(64, "fp64_V33", dict(min_coarse_n=4, cycle=1, precision=0, nu1=3, nu2=3))]
+    for n in (1024, 4096):
+        for prec, name in ((0, "fp64_W44"), (1, "mixed_W44")):
+            runs.append((n, name, dict(min_coarse_n=MIN_COARSE, cycle=2, precision=prec,
+                                       w_depth=W_DEPTH, nu1=NU, nu2=NU)))
+    for n, name, opt in runs:
+        H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n, default_options(max_cycles=100, **opt))
+        ft, gt, ue = _inputs(H, P, dev)
+        u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+        tol = 1e-8 if n >= 4096 else 1e-10
+        ms, r = _event_solve(H, ft, gt, u, tol)
+        err = float(np.abs(u.cpu().numpy().reshape(n, n) - ue).max())
+        out.setdefault(str(n), {})[name] = {"tol": tol,
+            "ms": ms, "dof_per_s": n * n / (ms / 1e3), "cycles": r.cycles,
+            "rate_per_cycle": r.rel_res ** (1.0 / max(1, r.cycles)), "max_error_vs_exact": err,
+            "status": r.status, "levels": [H.info.level_n[l] for l in range(H.info.n_levels)]}
+        H.close()
+    return out
+
+
+def run_refinement_sweep(a, dev):
+    """The plain method on the irregular domain: the headline disk problem in
+    FP64 (W(4,4), gamma = 2 on the finest level) to 1e-13 at 128^2 ... 1024^2,
+    the max-norm and L1 errors against the exact cell averages and the
+    observed order log2(e(2h)/e(h))."""
+    import numpy as np
+    import torch
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    P = _problem()
+    rows = []
+    for n in (128, 256, 512, 1024):
+        H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                  default_options(min_coarse_n=MIN_COARSE if n > 128 else 16, cycle=2,
+                                                  precision=0, w_depth=W_DEPTH, nu1=NU, nu2=NU,
+                                                  max_cycles=80))
+        ft, gt, ue = _inputs(H, P, dev)
+        present = H.cell_types()[0] != 0
+        u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+        ms, r = _event_solve(H, ft, gt, u, TOL)
+        e = np.abs(u.cpu().numpy().reshape(n, n) - ue)[present]
+        rows.append({"n": n, "dof": int(H.info.n_dof), "ms": ms, "dof_per_s": H.info.n_dof / (ms / 1e3),
+                     "cycles": r.cycles, "rel_res": r.rel_res, "linf": float(e.max()),
+                     "l1": float(e.sum()) / (n * n)})
+        H.close()
+    for k in range(1, len(rows)):
+        rows[k]["order_linf"] = math.log2(rows[k - 1]["linf"] / rows[k]["linf"])
+        rows[k]["order_l1"] = math.log2(rows[k - 1]["l1"] / rows[k]["l1"])
+    return {"workload": "disk domain, (a,b,c)=(1,0.5,2), Dirichlet box + Neumann circle, "
+                        "u = exp(x)cos(2y), FP64, tol 1e-13", "rows": rows}
+
+
+# printed averaged residual-reduction rates (Table 8): V and FMG cycles at
+# (nu1, nu2) = (2,1), (2,2), (3,3); the panda rows are out of scope
+TABLE8 = {
+    "unit_square": {"V": (0.858, 0.410, 0.330), "FMG": (0.672, 0.246, 0.131)},
+    "rotated_square": {"V": (0.474, 0.266, 0.216), "FMG": (0.376, 0.162, 0.103)},
+    "flower": {"V": (0.384, 0.318, 0.221), "FMG": (0.296, 0.207, 0.108)},
+    "four_disks_D": {"V": (0.298, 0.236, 0.161), "FMG": (0.292, 0.120, 0.063)},
+    "four_disks_N": {"V": (0.373, 0.336, 0.279), "FMG": (0.347, 0.208, 0.135)},
+}
+
+
+def run_table8(a, dev):
+    """Averaged residual-reduction rates (rel. residual ^ (1 / cycles), from
+    u = 0 to 1e-10) of FP64 V-cycles and FMG cycles (Alg. 3 with V) at
+    (nu1, nu2) = (2,1), (2,2), (3,3) on the paper's domains at h = 1/256
+    (384 cells across the rotated square's box of side 1.5), beside the
+    printed values.  The paper does not state the depth of its cycles; these go
+    down to the coarsest level the holes allow (at least 8^2)."""
+    import torch
+    from paper_2601_02975_gb300 import Hierarchy, default_options
+    from paper_2601_02975_gb300 import workloads as W
+    probs = {"unit_square": (W.problem_table3(), 256, {"min_coarse_n": 64}),
+             "rotated_square": (W.problem_rotated_square(), 384, {"min_coarse_n": 48}),
+             "flower": (W.problem_flower(), 256, {"eps": 0.02, "min_coarse_n": 64}),
+             "four_disks_D": (W.problem_four_disks(W.DIRICHLET), 256, {"eps": 0.08, "min_coarse_n": 64}),
+             "four_disks_N": (W.problem_four_disks(W.NEUMANN), 256, {"eps": 0.08, "min_coarse_n": 64})}
+    out = {"note": "ours / printed; FP64; three levels (the paper's depth is not stated); NaN: diverged"}
+    for key, (P, n, extra) in probs.items():
+        row = {}
+        for cyc, cname in ((1, "V"), (3, "FMG")):
+            vals = []
+            for (nu1, nu2) in ((2, 1), (2, 2), (3, 3)):
+                H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                          default_options(cycle=cyc, precision=0, nu1=nu1, nu2=nu2,
+                                                          max_cycles=200, **extra))
+                ft, gt, _ = _inputs(H, P, dev)
+                u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+                try:
+                    r = H.solve(ft, gt, u, 1e-10)
+                    rate = r.rel_res ** (1.0 / max(1, r.cycles))
+                except Exception as e:   # a diverging cycle is reported as such
+                    rate = float("nan")
+                vals.append(rate)
+                H.close()
+            row[cname] = {"ours": vals, "printed": list(TABLE8[key][cname])}
+        out[key] = row
     return out
 
 
@@ -761,6 +921,127 @@ def run_random_domains(a, dev):
 
 SERVE_SIZES = (128, 256, 512, 1024)
 SERVE_WEIGHTS = (0.5 / 3, 0.5 / 3, 0.5 / 3, 0.3)   # the request mix without its 2048^2/4096^2 share
+
+
+SERVE_FULL_SIZES = (128, 256, 512, 1024, 2048, 4096)
+SERVE_FULL_WEIGHTS = (0.5 / 3, 0.5 / 3, 0.5 / 3, 0.30, 0.15, 0.05)
+
+
+def run_serving_full(a, dev):
+    """The serving workload at its specified size: a Poisson-arrival stream
+    of a.serve_full requests per rate through cc_submit / cc_poll, sizes
+    128^2..4096^2 (50 % spread over 128^2-512^2, 30 % 1024^2, 15 % 2048^2,
+    5 % 4096^2), each on one of a.serve_domains cached ellipse-union domains
+    (seeds 0.., the 2048^2/4096^2 workload's family, set up before the
+    stream, 2 slots per handle, clones within a 150 GB cc_serve_budget).
+    Each request's f is its domain's manufactured f plus a random multiple of
+    one of 8 random-Fourier fields (16 x 16 modes, coefficients N(0,
+    1/(p^2+q^2))); tol 1e-10 (1e-9 at 4096^2, near where the FP64 cycles
+    stop reducing the residual on some of these domains).  The client keeps at most 20 GB of request
+    buffers on the device: a request that arrives beyond that waits on the
+    host, and its latency counts from its arrival.  Mixed precision at every
+    rate, FP64 at the lowest and the highest; p50 / p99 latency (arrival to
+    completion) and DOF/s."""
+    import numpy as np
+    import torch
+    from paper_2601_02975_gb300 import Hierarchy, default_options, serve_budget
+    from paper_2601_02975_gb300 import inputs as I
+    from paper_2601_02975_gb300 import workloads as W
+    rng = np.random.default_rng(23)
+    rates = [float(x) for x in a.serve_full_rates.split(",")]
+    serve_budget(150 * (1 << 30))
+    w = np.array(SERVE_FULL_WEIGHTS) / sum(SERVE_FULL_WEIGHTS)
+    pert = {}
+    for n in SERVE_FULL_SIZES:
+        x = (np.arange(n) + 0.5) / n
+        S = np.array([np.sin(p * np.pi * x) for p in range(1, 17)])
+        fields = []
+        for _ in range(8):
+            C = rng.standard_normal((16, 16)) / np.sqrt(np.add.outer(np.arange(1, 17) ** 2, np.arange(1, 17) ** 2))
+            fields.append(torch.tensor((S.T @ C @ S).ravel(), dtype=torch.float64, device=dev))
+        pert[n] = fields
+    out = {"requests_per_rate": a.serve_full,
+           "workload": "ellipse-union domains (seeds), sizes 128^2..4096^2 at 50/30/15/5 %, Poisson "
+                       "arrivals, per-request random-Fourier f, tol 1e-10 (1e-9 at 4096^2), 2 slots per handle, 150 GB "
+                       "clone budget, at most 20 GB of request buffers in flight"}
+    cap_bytes = 20 * (1 << 30)
+    for prec, name in ((1, "mixed"), (0, "fp64")):
+        t0 = time.perf_counter()
+        hs, base, rejected = {}, {}, []
+        for d in range(a.serve_domains):
+            P = W.problem_ellipses(d)
+            for n in SERVE_FULL_SIZES:
+                try:
+                    H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
+                                              default_options(min_coarse_n=MIN_COARSE, cycle=2, precision=prec,
+                                                              max_cycles=60, w_depth=W_DEPTH, nu1=NU, nu2=NU,
+                                                              serve_slots=2))
+                except Exception as e:   # a domain the setup rejects at this size
+                    rejected.append((d, n, str(e)[-60:]))
+                    continue
+                f, g, _ = I.problem_inputs(H, P)
+                hs[(d, n)] = H
+                base[(d, n)] = (torch.tensor(f.ravel(), dtype=torch.float64, device=dev),
+                                torch.tensor(g, dtype=torch.float64, device=dev), int(H.info.n_dof))
+        ok = sorted({d for (d, n) in hs if all((d, m) in hs for m in SERVE_FULL_SIZES)})
+        out.setdefault("setup", {})[name] = {"s": time.perf_counter() - t0, "domains": len(ok),
+                                             "rejected": len(rejected), "examples": rejected[:4]}
+        for (d, n), H in hs.items():   # warm-up: graphs, first clone
+            fb, gb, _ = base[(d, n)]
+            u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+            rid = H.submit(fb, gb, u, 1e-9 if n >= 4096 else 1e-10)
+            while Hierarchy.poll(rid)[0] == 9:
+                time.sleep(0.0005)
+        torch.cuda.synchronize()
+        for rate in rates:
+            if prec == 0 and rate not in (rates[0], rates[-1]):
+                continue
+            nreq = a.serve_full
+            sz = rng.choice(len(SERVE_FULL_SIZES), size=nreq, p=w)
+            dm = rng.choice(ok, size=nreq)
+            arrive = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+            scale = rng.standard_normal(nreq) * 20.0
+            which = rng.integers(0, 8, size=nreq)
+            pending, lat, dof_done, fails, held, late = {}, [], 0, {}, 0, 0
+            t_start = time.monotonic()
+            k = 0
+            while k < nreq or pending:
+                now = time.monotonic() - t_start
+                while k < nreq and now >= arrive[k]:
+                    n = SERVE_FULL_SIZES[sz[k]]
+                    if held + 16 * n * n > cap_bytes:
+                        break
+                    d = int(dm[k])
+                    fb, gb, ndof = base[(d, n)]
+                    f = torch.add(fb, pert[n][which[k]], alpha=float(scale[k]))
+                    u = torch.zeros(n * n, dtype=torch.float64, device=dev)
+                    torch.cuda.current_stream(dev).synchronize()
+                    late += now - arrive[k] > 0.001
+                    rid = hs[(d, n)].submit(f, gb, u, 1e-9 if n >= 4096 else 1e-10)
+                    pending[rid] = (n, ndof, t_start + arrive[k], f, u)
+                    held += 16 * n * n
+                    k += 1
+                for rid in list(pending):
+                    st, r = Hierarchy.poll(rid)
+                    if st == 9:
+                        continue
+                    n, ndof, t_arr, _, _ = pending.pop(rid)
+                    held -= 16 * n * n
+                    if st != 0:
+                        fails[f"{n}:{st}"] = fails.get(f"{n}:{st}", 0) + 1
+                    lat.append(r.t_done - t_arr)
+                    dof_done += ndof
+                time.sleep(0.0002)
+            wall = time.monotonic() - t_start
+            lat = np.sort(np.array(lat)) * 1e3
+            out.setdefault(f"{rate:g}", {})[name] = {
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "dof_per_s": dof_done / wall, "wall_s": wall, "failed": fails,
+                "submitted_late": int(late)}
+        for H in hs.values():
+            H.close()
+        torch.cuda.synchronize()
+    return out
 
 
 def run_serving(a, dev):
