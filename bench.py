@@ -228,7 +228,7 @@ def aggregate(dof_per_rank: float, ms_per_step_max: float, world: int) -> float:
 
 
 def _problem():
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     return W.problem_disk()
 
 
@@ -525,7 +525,7 @@ def hbm_sweep(a, dev, peak, src):
     import torch
     from paper_2601_02975_gb300 import Hierarchy, default_options
     from paper_2601_02975_gb300 import inputs as I
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     P = W.problem_poisson_square()
     n = a.hbm_n
     H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
@@ -561,7 +561,7 @@ def run_ellipse_union(a, dev):
     import torch
     from paper_2601_02975_gb300 import Hierarchy, cache_clear, default_options
     from paper_2601_02975_gb300 import inputs as I
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     P = W.problem_ellipses(0)
     out = {"workload": "unit square minus ellipse union seed 0, Robin (1, 0.5), (a,b,c)=(1.5,-0.8,1), "
                        "u = sin(3x) exp(y), tol 1e-10"}
@@ -647,7 +647,7 @@ def run_plain_poisson(a, dev):
     import numpy as np
     import torch
     from paper_2601_02975_gb300 import Hierarchy, default_options
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     P = W.problem_poisson_square()
     out = {"workload": "Poisson, unit square, u = sin(pi x) sin(pi y), Dirichlet, tol 1e-10 "
                        "(1e-8 at 4096^2: the Dirichlet data are 0, so |b| = |f| ~ 2 pi^2 and the "
@@ -723,7 +723,7 @@ def run_table8(a, dev):
     down to the coarsest level the holes allow (at least 8^2)."""
     import torch
     from paper_2601_02975_gb300 import Hierarchy, default_options
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     probs = {"unit_square": (W.problem_table3(), 256, {"min_coarse_n": 64}),
              "rotated_square": (W.problem_rotated_square(), 384, {"min_coarse_n": 48}),
              "flower": (W.problem_flower(), 256, {"eps": 0.02, "min_coarse_n": 64}),
@@ -760,7 +760,7 @@ def run_setup(a, dev):
     level).  Wall clock around cc_setup; the split comes from cc_info."""
     import numpy as np
     from paper_2601_02975_gb300 import Hierarchy, default_options
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     out = {"host_threads": os.cpu_count(), "cpu_model": _cpu_model()}
     for name, P, n in (("disk_1024", _problem(), a.n), ("ellipses0_4096", W.problem_ellipses(0), 4096)):
         row = {}
@@ -843,7 +843,7 @@ def run_random_domains(a, dev):
     import torch
     from paper_2601_02975_gb300 import CCError, Hierarchy, cache_clear, default_options, solve_batch
     from paper_2601_02975_gb300 import inputs as I
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     hs, fs, gs, dofs, sizes, skipped, probs = [], [], [], [], [], [], []
     t = time.perf_counter()
     for k in range(a.random_domains):
@@ -946,7 +946,7 @@ def run_serving_full(a, dev):
     import torch
     from paper_2601_02975_gb300 import Hierarchy, default_options, serve_budget
     from paper_2601_02975_gb300 import inputs as I
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     rng = np.random.default_rng(23)
     rates = [float(x) for x in a.serve_full_rates.split(",")]
     serve_budget(150 * (1 << 30))
@@ -1223,7 +1223,7 @@ def run_profile_sweep(a):
     import __graft_entry__
     from paper_2601_02975_gb300 import Hierarchy, default_options
     from paper_2601_02975_gb300 import inputs as I
-    from paper_2601_02975_gb300 import workloads as W
+    import workloads as W
     __graft_entry__.build()
     P = W.problem_poisson_square()
     n = a.profile_sweep

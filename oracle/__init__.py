@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call,
 link or execute this package: only `tests/`, `__graft_entry__.smoke()` and
 the `cpu_baseline` / `--impl reference` legs of `bench.py` use it.  It shares
 no code, tables or constants with the CUDA library; the one module both
-sides use is `paper_2601_02975_gb300.workloads` (seeded inputs only).
+sides use is the top-level `workloads` (seeded inputs only), which belongs
+to neither.
 
 Modules
   ghost       ghost-cell averages at grid-aligned walls (Sec. 4.1)

@@ -26,7 +26,7 @@ from typing import Dict, List, Tuple
 import numpy as np
 import scipy.sparse as sp
 
-from paper_2601_02975_gb300.workloads import (BC, DIRICHLET, NEUMANN, ROBIN,
+from workloads import (BC, DIRICHLET, NEUMANN, ROBIN,
                                                Domain, Separable)
 from . import geometry as G
 from .ghost import extrapolation_coefficients, ghost_coefficients
@@ -507,7 +507,7 @@ def cell_averages(lev: G.Level, fun) -> np.ndarray:
     8-point Gauss-Legendre; the lower limit p_x is the centre of the control
     volume, which keeps F of order h and avoids cancellation on small cells.
     """
-    from paper_2601_02975_gb300.workloads import Separable, regular_cell_averages
+    from workloads import Separable, regular_cell_averages
     n, h = lev.n, lev.h
     if isinstance(fun, Separable):
         out = regular_cell_averages(fun, lev.dom, n)
@@ -537,7 +537,7 @@ def cell_averages(lev: G.Level, fun) -> np.ndarray:
 
 def boundary_data(disc: Disc, u) -> np.ndarray:
     """g = [4 n wall face averages (S, E, N, W)] + [<<N u>>_i per boundary cell]."""
-    from paper_2601_02975_gb300.workloads import bc_value, wall_face_data
+    from workloads import bc_value, wall_face_data
     lev = disc.lev
     g = [wall_face_data(u, lev.dom, lev.n)]
     tail = np.zeros(len(disc.bd_cells))

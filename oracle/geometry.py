@@ -33,7 +33,7 @@ from typing import Dict, List, Tuple
 
 import numpy as np
 
-from paper_2601_02975_gb300.workloads import Domain, Ellipse, Flower, OutsideRect
+from workloads import Domain, Ellipse, Flower, OutsideRect
 
 EMPTY, REGULAR, IRREGULAR = 0, 1, 2
 

@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from paper_2601_02975_gb300.workloads import DIRICHLET, NEUMANN, ROBIN
+from workloads import DIRICHLET, NEUMANN, ROBIN
 
 
 def _avg_monomial(q: int, s0: float, s1: float) -> float:

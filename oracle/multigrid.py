@@ -33,7 +33,7 @@ from typing import List, Optional
 import numpy as np
 import scipy.sparse as sp
 
-from paper_2601_02975_gb300.workloads import Domain
+from workloads import Domain
 from . import discretize as D
 from . import geometry as G
 

@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import workloads as W
+import workloads as W
 
 
 def _bc_of(dom: W.Domain, idx: int) -> W.BC:

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 import __graft_entry__  # noqa: E402
 from paper_2601_02975_gb300 import Hierarchy, default_options, lib  # noqa: E402
 from paper_2601_02975_gb300 import inputs as I  # noqa: E402
-from paper_2601_02975_gb300 import workloads as W  # noqa: E402
+import workloads as W  # noqa: E402
 from paper_2601_02975_gb300._lib import cc_result  # noqa: E402
 
 DEV = "cuda:0"

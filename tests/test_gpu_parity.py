@@ -22,7 +22,7 @@ from oracle import discretize as D  # noqa: E402
 from oracle import multigrid as M  # noqa: E402
 from paper_2601_02975_gb300 import CCError, Hierarchy, default_options  # noqa: E402
 from paper_2601_02975_gb300 import inputs as I  # noqa: E402
-from paper_2601_02975_gb300 import workloads as W  # noqa: E402
+import workloads as W  # noqa: E402
 
 DEV = "cuda:0"
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")

@@ -18,7 +18,7 @@ import __graft_entry__  # noqa: E402
 from oracle import discretize as D  # noqa: E402
 from oracle import geometry as G  # noqa: E402
 from paper_2601_02975_gb300 import Hierarchy, default_options  # noqa: E402
-from paper_2601_02975_gb300 import workloads as W  # noqa: E402
+import workloads as W  # noqa: E402
 
 DEV = "cuda:0"
 

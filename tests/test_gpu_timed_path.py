@@ -30,7 +30,7 @@ from oracle import geometry as G  # noqa: E402
 from oracle import multigrid as M  # noqa: E402
 from paper_2601_02975_gb300 import Hierarchy, default_options  # noqa: E402
 from paper_2601_02975_gb300 import inputs as I  # noqa: E402
-from paper_2601_02975_gb300 import workloads as W  # noqa: E402
+import workloads as W  # noqa: E402
 
 DEV = "cuda:0"
 

@@ -10,7 +10,7 @@ import pytest
 import __graft_entry__
 from oracle import discretize as D
 from oracle import geometry as G
-from paper_2601_02975_gb300 import workloads as W
+import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 

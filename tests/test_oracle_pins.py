@@ -18,7 +18,7 @@ from oracle import discretize as D
 from oracle import geometry as G
 from oracle import multigrid as M
 from oracle.ghost import extrapolation_coefficients, ghost_coefficients
-from paper_2601_02975_gb300 import workloads as W
+import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 

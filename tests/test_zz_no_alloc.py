@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 import __graft_entry__  # noqa: E402
 from paper_2601_02975_gb300 import CCError, Hierarchy, default_options  # noqa: E402
-from paper_2601_02975_gb300 import workloads as W  # noqa: E402
+import workloads as W  # noqa: E402
 
 DEV = "cuda:0"
 

@@ -1,7 +1,8 @@
 """Seeded synthetic inputs: manufactured solutions, domains and right-hand sides.
 
-This module is shared by the tests, the benchmark and the oracle harness.  It
-holds no arithmetic of the method itself (no discretisation, no geometry
+This module is shared by the tests, the benchmark, the oracle and the
+library's input helper (paper_2601_02975_gb300/inputs.py), and belongs to
+none of them.  It holds no arithmetic of the method itself (no discretisation, no geometry
 clipping, no cycles): only closed-form functions, their exact derivatives and
 their exact averages over axis-aligned rectangles and segments, plus seeded
 random domain and right-hand-side generators.
