@@ -81,6 +81,9 @@ def _args():
                     help="run the full serving workload with N requests per rate (10000 as specified; "
                          "0: skip, the default, as it takes about a quarter of an hour)")
     ap.add_argument("--serve-domains", type=int, default=64)
+    ap.add_argument("--serve-full-fp64", type=int, default=3000,
+                    help="requests per rate of the FP64 arm of --serve-full (it runs at about a sixth "
+                         "of the mixed arm's rate)")
     ap.add_argument("--serve-full-rates", default="100,300,1000,3000,5000")
     ap.add_argument("--plain", type=int, default=1,
                     help="also run the plain-method cases: Poisson 64^2 (and 1024^2, 4096^2) V(3,3), "
@@ -442,7 +445,10 @@ def run_ours(a):
                    "cycle": f"W({NU},{NU}), gamma = 2 on the {W_DEPTH} finest level(s)",
                    "levels": [H.info.level_n[l] for l in range(H.info.n_levels)],
                    "precision": "mixed", "tol": TOL, "l2": "flushed between steps (512 MB write)",
-                   "parallelism": f"replicas x{world}", "cycles_per_solve": cycles[-1]},
+                   "parallelism": f"replicas x{world}", "cycles_per_solve": cycles[-1],
+                   "autotuned": {"sweep_ctas": [H.info.sweep_ctas[l] for l in range(H.info.n_levels)],
+                                 "block_chunk_rows": [H.info.block_chunk_rows[l]
+                                                      for l in range(H.info.n_levels)]}},
         "e2e": {"value": e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * (2 * n * n + H.info.n_g),
                 "d2h_bytes_per_step": 8 * n * n},
         "gpu_launches": kernels,
@@ -939,9 +945,11 @@ def run_serving_full(a, dev):
     1/(p^2+q^2))); tol 1e-10 (1e-9 at 4096^2, near where the FP64 cycles
     stop reducing the residual on some of these domains).  The client keeps at most 20 GB of request
     buffers on the device: a request that arrives beyond that waits on the
-    host, and its latency counts from its arrival.  Mixed precision at every
-    rate, FP64 at the lowest and the highest; p50 / p99 latency (arrival to
-    completion) and DOF/s."""
+    host, and its latency counts from its arrival.  Domains whose validation
+    request fails at some size are not served.  Mixed precision at every
+    rate, FP64 (a.serve_full_fp64 requests) at the lowest and the highest;
+    p50 / p99 latency (arrival to completion) and DOF/s of the solved
+    requests."""
     import numpy as np
     import torch
     from paper_2601_02975_gb300 import Hierarchy, default_options, serve_budget
@@ -983,20 +991,32 @@ def run_serving_full(a, dev):
                 hs[(d, n)] = H
                 base[(d, n)] = (torch.tensor(f.ravel(), dtype=torch.float64, device=dev),
                                 torch.tensor(g, dtype=torch.float64, device=dev), int(H.info.n_dof))
-        ok = sorted({d for (d, n) in hs if all((d, m) in hs for m in SERVE_FULL_SIZES)})
-        out.setdefault("setup", {})[name] = {"s": time.perf_counter() - t0, "domains": len(ok),
-                                             "rejected": len(rejected), "examples": rejected[:4]}
-        for (d, n), H in hs.items():   # warm-up: graphs, first clone
+        ok = {d for (d, n) in hs if all((d, m) in hs for m in SERVE_FULL_SIZES)}
+        # warm-up and validation: one request per handle (graphs, first clone);
+        # a domain whose cycle fails at some size (diverges, or stalls above
+        # the tolerance in 60 cycles) is not served
+        bad = set()
+        for (d, n), H in hs.items():
             fb, gb, _ = base[(d, n)]
             u = torch.zeros(n * n, dtype=torch.float64, device=dev)
             rid = H.submit(fb, gb, u, 1e-9 if n >= 4096 else 1e-10)
-            while Hierarchy.poll(rid)[0] == 9:
+            while True:
+                st, _ = Hierarchy.poll(rid)
+                if st != 9:
+                    break
                 time.sleep(0.0005)
+            if st != 0:
+                bad.add(d)
         torch.cuda.synchronize()
+        ok = sorted(ok - bad)
+        out.setdefault("setup", {})[name] = {"s": time.perf_counter() - t0, "domains_served": len(ok),
+                                             "pairs_rejected_at_setup": len(rejected),
+                                             "domains_failing_validation": sorted(bad),
+                                             "examples": rejected[:4]}
         for rate in rates:
             if prec == 0 and rate not in (rates[0], rates[-1]):
                 continue
-            nreq = a.serve_full
+            nreq = a.serve_full if prec == 1 else min(a.serve_full, a.serve_full_fp64)
             sz = rng.choice(len(SERVE_FULL_SIZES), size=nreq, p=w)
             dm = rng.choice(ok, size=nreq)
             arrive = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
@@ -1027,14 +1047,16 @@ def run_serving_full(a, dev):
                         continue
                     n, ndof, t_arr, _, _ = pending.pop(rid)
                     held -= 16 * n * n
+                    lat.append(r.t_done - t_arr)
                     if st != 0:
                         fails[f"{n}:{st}"] = fails.get(f"{n}:{st}", 0) + 1
-                    lat.append(r.t_done - t_arr)
-                    dof_done += ndof
+                    else:
+                        dof_done += ndof
                 time.sleep(0.0002)
             wall = time.monotonic() - t_start
             lat = np.sort(np.array(lat)) * 1e3
             out.setdefault(f"{rate:g}", {})[name] = {
+                "requests": nreq,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "dof_per_s": dof_done / wall, "wall_s": wall, "failed": fails,
                 "submitted_late": int(late)}

@@ -156,6 +156,16 @@ typedef struct {
                           loop is also used with use_graphs = 0, krylov, cc_kernel_timing
                           on, and for cc_solve_batch and cc_submit, where concurrent
                           solves overlap better under it */
+  int autotune;        /* 1 (default): cc_setup times candidate launch shapes on the
+                          device and keeps the fastest: the CTA count of the streamed
+                          FP32 sweep of each level of 256^2 and more (every multiple of
+                          the SM count up to the occupancy limit, and one CTA per tile;
+                          the sweep's result does not depend on it), remembered per
+                          device and grid size for the process; and the chunk size of
+                          each chunked exact block of up to 8192 cells, among the three
+                          cheapest by the shared-memory cost model that solve to
+                          rounding accuracy (20 timed FP32 solves each).  0: the cost
+                          model's choices */
 } cc_options;
 
 /* Sizes of a hierarchy. */
@@ -183,6 +193,8 @@ typedef struct {
                              rest: the factorisations of the block smoother and the
                              bottom solve, and the uploads) */
   double setup_kernel_ms; /* device time of the setup kernels (device_setup) */
+  int sweep_ctas[32];     /* CTAs of each level's streamed FP32 sweep (0: not streamed) */
+  int block_chunk_rows[32]; /* rows per chunk of each chunked exact block (0: dense or none) */
 } cc_info;
 
 /* Outcome of a solve. */

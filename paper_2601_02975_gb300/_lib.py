@@ -42,7 +42,8 @@ class cc_options(C.Structure):
                 ("max_cycles", C.c_int), ("use_graphs", C.c_int), ("host_only", C.c_int),
                 ("fmg_cycle", C.c_int), ("w_depth", C.c_int), ("serve_slots", C.c_int),
                 ("cache", C.c_int), ("hole_cells", C.c_double), ("krylov", C.c_int),
-                ("smoother", C.c_int), ("device_setup", C.c_int), ("device_loop", C.c_int)]
+                ("smoother", C.c_int), ("device_setup", C.c_int), ("device_loop", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class cc_info(C.Structure):
@@ -52,7 +53,8 @@ class cc_info(C.Structure):
                 ("block_error", C.c_double), ("bottom_error", C.c_double),
                 ("block_m", C.c_int * 32), ("block_chunks", C.c_int * 32),
                 ("setup_seconds", C.c_double), ("setup_tables_seconds", C.c_double),
-                ("setup_kernel_ms", C.c_double)]
+                ("setup_kernel_ms", C.c_double), ("sweep_ctas", C.c_int * 32),
+                ("block_chunk_rows", C.c_int * 32)]
 
 
 class cc_result(C.Structure):

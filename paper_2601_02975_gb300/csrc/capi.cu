@@ -563,11 +563,19 @@ ChunkSmem chunk_smem(const BlockPlan& B, int w, int& stage1, int& stage2) {
   return L;
 }
 
-BlockPlan plan_block(const LevelDisc& D) {
+std::vector<BlockPlan> plan_block_candidates(const LevelDisc& D, int k);
+
+BlockPlan plan_block(const LevelDisc& D) { return std::move(plan_block_candidates(D, 1)[0]); }
+
+// The exact block of level D as dense or chunked plans: the dense inverse
+// for small blocks; else the chunk shapes in the order of the cost model,
+// keeping the first k that solve to rounding accuracy (backward error below
+// 1e-13 on a fixed vector), or the most accurate one if none does.
+std::vector<BlockPlan> plan_block_candidates(const LevelDisc& D, int k) {
   BlockPlan B;
   const int m = (int)D.block.size();
   B.m = m;
-  if (m == 0) return B;
+  if (m == 0) return std::vector<BlockPlan>(1, B);
   B.cell = D.block;
   std::unordered_map<int, int> pos;
   for (int p = 0; p < m; ++p) pos[D.block[p]] = p;
@@ -595,7 +603,9 @@ BlockPlan plan_block(const LevelDisc& D) {
     B.ainv.swap(A);
     B.dense = true;
     B.error = block_plan_error(B, Abb);
-    return B;
+    std::vector<BlockPlan> one;
+    one.push_back(std::move(B));
+    return one;
   }
   // chunk sizes by the largest per-CTA stage; keep the cheapest whose
   // backward error on a fixed vector is at the level of rounding
@@ -608,6 +618,7 @@ BlockPlan plan_block(const LevelDisc& D) {
   std::sort(shapes.begin(), shapes.end(), [](const ChunkShape& a, const ChunkShape& b) { return a.cost < b.cost; });
   BlockPlan best;
   bool have = false;
+  std::vector<BlockPlan> good;
   for (const ChunkShape& S : shapes) {
     BlockPlan P = B;
     try {
@@ -616,11 +627,18 @@ BlockPlan plan_block(const LevelDisc& D) {
       continue;
     }
     P.error = block_plan_error(P, Abb);
+    if (P.error < 1e-13) {
+      good.push_back(std::move(P));
+      if ((int)good.size() >= k) break;
+      continue;
+    }
     if (!have || P.error < best.error) { best = std::move(P); have = true; }
-    if (best.error < 1e-13) break;
   }
+  if (!good.empty()) return good;
   if (!have) throw SetupError(3, "singular block of the smoother");
-  return best;
+  std::vector<BlockPlan> one;
+  one.push_back(std::move(best));
+  return one;
 }
 // ---------------------------------------------------------------------------
 // device memory
@@ -668,6 +686,7 @@ struct BlockDevSet {
 struct Level {
   int n = 0;
   int64_t nn = 0;
+  int sweep_grid = 0;        // CTAs of the streamed FP32 sweep (0: one wave at full occupancy)
   StencilParams sp;          // FP64 stencil data
   StencilP<float> spf;       // the same in FP32
   uint8_t* cls = nullptr;
@@ -976,12 +995,12 @@ void launch_sweep(Level& L, const T* in, T* out, const T* b, const T* ec, bool z
   if constexpr (std::is_same<T, float>::value) {
     if (L.n >= 256 && L.n % 32 == 0) {
       const int nt = (L.n / TX) * (L.n / WY);
+      const int g = L.sweep_grid > 0 ? L.sweep_grid
+                                     : std::min(nt, L.sp.cross ? sweep_p_blocks<true>() : sweep_p_blocks<false>());
       if (L.sp.cross)
-        pdl_launch(k_sweep_p<true>, std::min(nt, sweep_p_blocks<true>()), TX * TY, 0, s, in, out, b, L.cls,
-                   ec, P, (int)zero);
+        pdl_launch(k_sweep_p<true>, g, TX * TY, 0, s, in, out, b, L.cls, ec, P, (int)zero);
       else
-        pdl_launch(k_sweep_p<false>, std::min(nt, sweep_p_blocks<false>()), TX * TY, 0, s, in, out, b,
-                   L.cls, ec, P, (int)zero);
+        pdl_launch(k_sweep_p<false>, g, TX * TY, 0, s, in, out, b, L.cls, ec, P, (int)zero);
       return;
     }
   }
@@ -1973,6 +1992,96 @@ void destroy_hierarchy(cc_hierarchy* H) {
 }  // namespace
 
 // ============================================================================
+// ---- launch shapes timed on the device (cc_options.autotune) ----------------
+const int kTuneMaxM = 8192;     // largest exact block whose chunk size is timed
+
+// device milliseconds of `reps` runs of f() on s, after 3 untimed runs
+template <class F>
+float time_launches(cudaStream_t s, int reps, F&& f) {
+  struct Ev {
+    cudaEvent_t e = nullptr;
+    ~Ev() { if (e) cudaEventDestroy(e); }
+  } e0, e1;
+  CK(cudaEventCreate(&e0.e));
+  CK(cudaEventCreate(&e1.e));
+  for (int i = 0; i < 3; ++i) f();
+  CK(cudaEventRecord(e0.e, s));
+  for (int i = 0; i < reps; ++i) f();
+  CK(cudaEventRecord(e1.e, s));
+  CK(cudaEventSynchronize(e1.e));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0.e, e1.e));
+  return ms;
+}
+
+// the fastest of candidate plans of one exact block: each is uploaded to a
+// temporary pool and timed over 20 FP32 solves on zero vectors
+int tune_block_plan(std::vector<BlockPlan>& cand, int64_t nn, cudaStream_t s, unsigned int* fault) {
+  if (cand.size() < 2) return 0;
+  Pool tmp;
+  float* u = tmp.alloc<float>(nn);
+  float* b = tmp.alloc<float>(nn);
+  CK(cudaMemsetAsync(u, 0, nn * sizeof(float), s));
+  CK(cudaMemsetAsync(b, 0, nn * sizeof(float), s));
+  int best = 0;
+  float best_ms = 0;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    BlockDev d = upload_block<float>(tmp, cand[i], s);
+    alloc_block_work<float>(tmp, cand[i], d, fault);
+    int s1, s2;
+    const ChunkSmem sm = chunk_smem(cand[i], (int)sizeof(float), s1, s2);
+    const float ms = time_launches(s, 20, [&] { launch_block<float>(cand[i], d, sm, u, (const float*)b, s); });
+    if (i == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = (int)i;
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  return best;
+}
+
+// CTAs of the streamed FP32 sweep of level L: every multiple of the SM count
+// up to the occupancy limit, and one CTA per tile, each timed over 20
+// sweeps; remembered per (device, grid size, cross term) for the process
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_sweep_tune;
+
+int tune_sweep(Level& L, int device, cudaStream_t s) {
+  const bool cross = L.sp.cross != 0;
+  const auto key = std::make_tuple(device, L.n, cross ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_sweep_tune.find(key);
+    if (it != g_sweep_tune.end()) return it->second;
+  }
+  const int nt = (L.n / TX) * (L.n / WY);
+  int sms = 0, occ = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  if (cross) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_p<true>, TX * TY, 0));
+  else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_p<false>, TX * TY, 0));
+  std::vector<int> grids;
+  for (int k = 1; k <= std::max(1, occ); ++k) grids.push_back(std::min(nt, sms * k));
+  grids.push_back(nt);
+  std::sort(grids.begin(), grids.end());
+  grids.erase(std::unique(grids.begin(), grids.end()), grids.end());
+  int best = 0;
+  float best_ms = 0;
+  for (int g : grids) {
+    L.sweep_grid = g;
+    const float ms = time_launches(s, 20, [&] {
+      launch_sweep<float>(L, (const float*)L.u32[0], L.u32[1], (const float*)L.b32, (const float*)nullptr,
+                          false, s);
+    });
+    if (best == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = g;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_sweep_tune[key] = best;
+  return best;
+}
+
 extern "C" {
 
 void cc_default_options(cc_options* o) {
@@ -1996,6 +2105,7 @@ void cc_default_options(cc_options* o) {
   o->smoother = CC_SMOOTHER_JACOBI;
   o->device_setup = 1;
   o->device_loop = 1;
+  o->autotune = 1;
 }
 
 const char* cc_last_error_string(void) { return t_last_error; }
@@ -2134,24 +2244,34 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       L.disc().P = &H->P;
       L.sp = make_stencil(D, o.omega);
       L.spf = stencil_as<float>(L.sp);
-      L.plan() = plan_block(D);
-      {
-        // merged-away control volumes take their owner's value (Eq. 5.11)
+      // merged-away control volumes take their owner's value (Eq. 5.11)
+      auto attach_aliases = [&](BlockPlan& B) {
         std::unordered_map<int, int> pos;
-        for (int p = 0; p < L.plan().m; ++p) pos[L.plan().cell[p]] = p;
-        std::vector<std::vector<int>> al(L.plan().m);
+        for (int p = 0; p < B.m; ++p) pos[B.cell[p]] = p;
+        std::vector<std::vector<int>> al(B.m);
         for (int64_t k = 0; l > 0 && k < L.nn; ++k)
           if (D.geom.type[k] == CT_EMPTY && D.geom.owner[k] >= 0 && D.geom.owner[k] != k) {
             auto it = pos.find(D.geom.owner[k]);
             if (it == pos.end()) throw SetupError(3, "a merged cell is not in the exact block");
             al[it->second].push_back((int)k);
           }
-        L.plan().alias_ptr.assign(1, 0);
-        L.plan().alias_cell.clear();
+        B.alias_ptr.assign(1, 0);
+        B.alias_cell.clear();
         for (auto& v : al) {
-          L.plan().alias_cell.insert(L.plan().alias_cell.end(), v.begin(), v.end());
-          L.plan().alias_ptr.push_back((int)L.plan().alias_cell.size());
+          B.alias_cell.insert(B.alias_cell.end(), v.begin(), v.end());
+          B.alias_ptr.push_back((int)B.alias_cell.size());
         }
+      };
+      const int mblk = (int)D.block.size();
+      if (dev && o.autotune && l + 1 < H->lv.size() && mblk > kDenseMax && mblk <= kTuneMaxM) {
+        // chunk size: the fastest of the cost model's three cheapest plans
+        std::vector<BlockPlan> cand = plan_block_candidates(D, 3);
+        for (BlockPlan& B : cand) attach_aliases(B);
+        const int pick = tune_block_plan(cand, L.nn, s, reinterpret_cast<unsigned int*>(H->d_norm + 1));
+        L.plan() = std::move(cand[pick]);
+      } else {
+        L.plan() = plan_block(D);
+        attach_aliases(L.plan());
       }
       if (!dev) continue;
       std::vector<uint8_t> cls(L.nn, C_EMPTY);
@@ -2169,6 +2289,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       L.b32 = H->pool->alloc<float>(L.nn);
       CK(cudaMemsetAsync(L.b64, 0, L.nn * sizeof(double), s));
       CK(cudaMemsetAsync(L.b32, 0, L.nn * sizeof(float), s));
+      if (o.autotune && L.n >= 256 && L.n % 32 == 0) L.sweep_grid = tune_sweep(L, H->device, s);
       if (l + 1 < H->lv.size()) {
         unsigned int* fault = reinterpret_cast<unsigned int*>(H->d_norm + 1);
         L.blk.d64 = upload_block<double>(*H->pool, L.plan(), s);
@@ -2324,6 +2445,14 @@ cc_status cc_query(cc_handle H, cc_info* out) {
     out->block_chunks[l] = H->lv[l]->plan().dense ? 0 : H->lv[l]->plan().nch;
   }
   out->bottom_error = H->bottom_error;
+  for (size_t l = 0; l < H->lv.size() && l < 32; ++l) {
+    const Level& L = *H->lv[l];
+    out->sweep_ctas[l] = L.sweep_grid;
+    if (!H->opt.host_only && L.n >= 256 && L.n % 32 == 0 && L.sweep_grid == 0)
+      out->sweep_ctas[l] = std::min((L.n / TX) * (L.n / WY),
+                                    L.sp.cross ? sweep_p_blocks<true>() : sweep_p_blocks<false>());
+    out->block_chunk_rows[l] = (L.plan().m && !L.plan().dense) ? L.plan().s : 0;
+  }
   out->setup_seconds = H->setup_seconds;
   out->setup_tables_seconds = H->setup_tables_seconds;
   out->setup_kernel_ms = H->setup_kernel_ms;
