@@ -115,9 +115,13 @@ def run_profile(a):
     __graft_entry__.build()
     P = _problem()
     n = a.n
+    # the host loop: every iteration is an ordinary graph launch, whose kernel
+    # nodes ncu profiles one by one (the kernels are those of the loop graph,
+    # without its one-thread convergence kernels)
     H = Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
                               default_options(min_coarse_n=a.min_coarse, cycle=2, precision=1,
-                                              max_cycles=60, w_depth=W_DEPTH, nu1=NU, nu2=NU))
+                                              max_cycles=60, w_depth=W_DEPTH, nu1=NU, nu2=NU,
+                                              device_loop=0))
     f, g, _ = I.problem_inputs(H, P)
     ft = torch.tensor(f.ravel(), dtype=torch.float64, device="cuda")
     gt = torch.tensor(g, dtype=torch.float64, device="cuda")
