@@ -806,3 +806,105 @@ def test_rotated_square_two_grid_spectral_radius():
         v0 = np.random.default_rng(0).standard_normal(n * n)
         w = abs(eigs(op, k=1, which="LM", return_eigenvectors=False, tol=1e-6, maxiter=20000, v0=v0)[0])
         assert abs(w - float(want)) <= 1.5e-3, (nu1, nu2, w)
+
+
+# ---------------------------------------------------------------------------
+# PLG fits and lattices against independent computations
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["disk", "ellipses0"])
+def test_boundary_fits_are_the_closed_form_of_lemma_4_4(name):
+    """For every PLG cell with boundary data, beta is the minimiser of
+    ||beta||_{W^-1} under M beta = phi with W^-1 = diag(w), w_k = max(|j_k -
+    i|, 1/2), w_b = 1/2 (Eq. 4.17-4.18): equal to the closed form W M^T (M W
+    M^T)^-1 phi of Lemma 4.4, computed here by a normal-equations solve (the
+    oracle uses a scaled least-squares solve), and no null-space move of M
+    makes the W^-1 norm smaller."""
+    P = W.problem_disk() if name == "disk" else W.problem_ellipses(0)
+    n = 64
+    lev = G.build_level(P.dom, n, 0.1)
+    d = D.discretize(lev, P.a, P.b, P.c)
+    rng = np.random.default_rng(9)
+    checked = 0
+    for k in d.bd_cells:
+        lat = d.lattices[k]
+        j0, i0 = divmod(k, n)
+        M = np.column_stack([D.sample_column(lev, k, kj) for kj in lat] + [D._boundary_column(lev, k)])
+        phi = D._L_column(lev, k, P.a, P.b, P.c)
+        w = np.array([max(math.hypot(kj % n - i0, kj // n - j0), 0.5) for kj in lat] + [0.5])
+        Wd = 1.0 / w
+        want = Wd * (M.T @ np.linalg.solve((M * Wd[None, :]) @ M.T, phi))
+        got = np.array(list(d.betas[k]) + [d.Nmat[k, 4 * n + d.bd_cells.index(k)]])
+        assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max(), k
+        # minimality: any null-space direction z of M increases the W^-1 norm
+        ns = np.linalg.svd(M)[2][M.shape[0]:]
+        base = np.sum(w * want ** 2)
+        for z in ns:
+            for t in (1e-3, -1e-3):
+                cand = want + t * np.abs(want).max() * z
+                assert np.sum(w * cand ** 2) > base
+        checked += 1
+        if checked >= 40:
+            break
+    assert checked >= 20
+
+
+def _lattice_cost(lev, ki, cells, orient):
+    n = lev.n
+    j0, i0 = divmod(ki, n)
+    tot = 0
+    for kj in cells:
+        jj, ii = divmod(kj, n)
+        cut = lev.ctype[jj, ii] != G.REGULAR and kj != ki
+        tot += (ii - i0) ** 2 + (jj - j0) ** 2 + (D.CUT_PENALTY if cut else 0)
+    return tot
+
+
+@pytest.mark.parametrize("name", ["disk", "flower"])
+def test_lattice_is_the_cheapest_five_line_set_by_brute_force(name):
+    """The lattice rule (R4, a reading of Def. 4.3) restated as an exhaustive
+    search: over both orientations and every assignment of the counts
+    5, 4, 3, 2, 1 to distinct lines of the 9 x 9 box, each line taking its
+    cheapest present cells, the least total cost.  The oracle's dynamic
+    programme must reach that cost, with five lines of those counts."""
+    from itertools import permutations
+    if name == "disk":
+        P, eps = W.problem_disk(), 0.1
+    else:
+        P, eps = W.problem_flower(), 0.02
+    n = 64
+    lev = G.build_level(P.dom, n, eps)
+    d = D.discretize(lev, P.a, P.b, P.c)
+    plg = sorted(d.lattices)[::max(1, len(d.lattices) // 25)]
+    R = D.PLG_RADIUS
+    for ki in plg:
+        j0, i0 = divmod(ki, n)
+        best = None
+        for orient in (0, 1):
+            lines = {}
+            for v in range(-R, R + 1):
+                cs = []
+                for u in range(-R, R + 1):
+                    di, dj = (u, v) if orient == 0 else (v, u)
+                    i, j = i0 + di, j0 + dj
+                    if 0 <= i < n and 0 <= j < n and lev.present[j, i]:
+                        cut = lev.ctype[j, i] != G.REGULAR and (di, dj) != (0, 0)
+                        cs.append(u * u + v * v + (D.CUT_PENALTY if cut else 0))
+                lines[v] = sorted(cs)
+            for pick in permutations(range(-R, R + 1), 5):
+                if any(len(lines[v]) < c for v, c in zip(pick, (5, 4, 3, 2, 1))):
+                    continue
+                cost = sum(sum(lines[v][:c]) for v, c in zip(pick, (5, 4, 3, 2, 1)))
+                best = cost if best is None else min(best, cost)
+        lat = d.lattices[ki]
+        if best is None:      # no lattice in the 9 x 9 box: the oracle searched a larger one
+            continue
+        rows = sorted(collections_counter(kj // n for kj in lat).values())
+        cols = sorted(collections_counter(kj % n for kj in lat).values())
+        orient = 0 if rows == [1, 2, 3, 4, 5] else 1
+        assert rows == [1, 2, 3, 4, 5] or cols == [1, 2, 3, 4, 5], ki
+        assert _lattice_cost(lev, ki, lat, orient) == best, ki
+
+
+def collections_counter(it):
+    from collections import Counter
+    return Counter(it)
