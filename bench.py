@@ -53,10 +53,10 @@ KRYLOV_MAX_CYCLES = 400
 # DRAM bytes per timed interval (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture (cold caches), keyed like cc_kernel_timing's kernels:
 # k_sweep_p per 1024^2 launch (profiles/k_sweep_p_poisson4096_disk1024.md);
-# the finest-level block solve of the 1024^2 disk, k_block_p1 + k_block_p2
-# (profiles/block_solve_p1p2_disk1024.md); the all-level block solves were
-# not captured as one unit
-TRAFFIC = {1: 9.46e6, 2: None, 3: 2.424e6 + 2.471e6}
+# the finest-level block solve of the 1024^2 disk with its autotuned chunk
+# size, k_block_p1 + k_block_p2 (profiles/block_solve_p1p2_disk1024.md); the
+# all-level block solves were not captured as one unit
+TRAFFIC = {1: 9.46e6, 2: None, 3: 2.727e6 + 1.758e6}
 
 
 def _args():
@@ -136,7 +136,9 @@ def run_profile(a):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"profile": "one solve", "n": n, "status": r.status, "cycles": r.cycles,
-                      "kernels": r.kernels, "rel_res": r.rel_res}))
+                      "kernels": r.kernels, "rel_res": r.rel_res,
+                      "sweep_ctas": [H.info.sweep_ctas[l] for l in range(H.info.n_levels)],
+                      "block_chunk_rows": [H.info.block_chunk_rows[l] for l in range(H.info.n_levels)]}))
 
 
 def _peaks():
