@@ -273,35 +273,63 @@ def choose_lattice(lev: G.Level, ki: int) -> List[int]:
 
 
 def _lattice_in_box(lev: G.Level, ki: int, radius: int):
-    n = lev.n
-    j0, i0 = divmod(ki, n)
     best = None
     for orient in (0, 1):             # 0: lines of constant dj; 1: of constant di
-        avail: Dict[int, List[int]] = {}
-        cost: Dict[Tuple[int, int], int] = {}
-        for v in range(-radius, radius + 1):
-            us = []
-            for u in range(-radius, radius + 1):
-                di, dj = (u, v) if orient == 0 else (v, u)
-                i, j = i0 + di, j0 + dj
-                if 0 <= i < n and 0 <= j < n and lev.present[j, i]:
-                    us.append(u)
-                    cut = lev.ctype[j, i] != G.REGULAR and (di, dj) != (0, 0)
-                    cost[(u, v)] = u * u + v * v + (CUT_PENALTY if cut else 0)
-            us.sort(key=lambda u: (cost[(u, v)], u))
-            avail[v] = us
-        r = _best_rows(avail, cost, radius)
+        r = _lattice_in_box_orient(lev, ki, radius, orient)
         if r is None:
             continue
         cand = (r[0], orient, r[1])
         if best is None or cand < best[0]:
-            cells = []
-            for v, cnt in sorted(r[2].items()):
-                for u in avail[v][:cnt]:
-                    di, dj = (u, v) if orient == 0 else (v, u)
-                    cells.append((j0 + dj) * n + (i0 + di))
-            best = (cand, sorted(cells))
+            best = (cand, r[2])
     return None if best is None else best[1]
+
+
+def _lattice_in_box_orient(lev: G.Level, ki: int, radius: int, orient: int):
+    """The cheapest lattice of the box of this radius on lines of one
+    orientation: (cost, tie key, sorted cells), or None."""
+    n = lev.n
+    j0, i0 = divmod(ki, n)
+    avail: Dict[int, List[int]] = {}
+    cost: Dict[Tuple[int, int], int] = {}
+    for v in range(-radius, radius + 1):
+        us = []
+        for u in range(-radius, radius + 1):
+            di, dj = (u, v) if orient == 0 else (v, u)
+            i, j = i0 + di, j0 + dj
+            if 0 <= i < n and 0 <= j < n and lev.present[j, i]:
+                us.append(u)
+                cut = lev.ctype[j, i] != G.REGULAR and (di, dj) != (0, 0)
+                cost[(u, v)] = u * u + v * v + (CUT_PENALTY if cut else 0)
+        us.sort(key=lambda u: (cost[(u, v)], u))
+        avail[v] = us
+    r = _best_rows(avail, cost, radius)
+    if r is None:
+        return None
+    cells = []
+    for v, cnt in sorted(r[2].items()):
+        for u in avail[v][:cnt]:
+            di, dj = (u, v) if orient == 0 else (v, u)
+            cells.append((j0 + dj) * n + (i0 + di))
+    return r[0], r[1], sorted(cells)
+
+
+def lattice_candidates(lev: G.Level, ki: int) -> List[List[int]]:
+    """The alternatives to the chosen lattice (R29): the cheapest lattice of
+    each box (9 x 9, 11 x 11, 13 x 13) and orientation (rows, then columns),
+    in that order."""
+    out = []
+    for radius in range(PLG_RADIUS, PLG_RADIUS_MAX + 1):
+        for orient in (0, 1):
+            r = _lattice_in_box_orient(lev, ki, radius, orient)
+            if r is not None:
+                out.append(r[2])
+    return out
+
+
+def row_diagonal(ki: int, lattice: List[int], beta) -> float:
+    """The coefficient of cell ki in its own PLG row (0 if ki is not in its
+    lattice)."""
+    return float(beta[lattice.index(ki)]) if ki in lattice else 0.0
 
 
 def fit_beta(lev: G.Level, ki: int, lattice: List[int], a, b, c, with_boundary: bool):
@@ -447,6 +475,19 @@ def discretize(lev: G.Level, a: float, b: float, c: float) -> Disc:
         lat = choose_lattice(lev, k)
         withb = k in bd_index
         beta, beta_b = fit_beta(lev, k, lat, a, b, c, withb)
+        if row_diagonal(k, lat, beta) >= 0.0:
+            # R29: a row whose own coefficient is not negative takes the first
+            # alternative lattice whose fit gives a negative one, if any
+            for alt in lattice_candidates(lev, k):
+                if alt == lat:
+                    continue
+                try:
+                    beta2, beta_b2 = fit_beta(lev, k, alt, a, b, c, withb)
+                except np.linalg.LinAlgError:
+                    continue
+                if row_diagonal(k, alt, beta2) < 0.0:
+                    lat, beta, beta_b = alt, beta2, beta_b2
+                    break
         lattices[k] = lat
         betas[k] = beta
         for kj, bv in zip(lat, beta):

@@ -213,6 +213,40 @@ LevelDisc discretize(const Problem& P, int n, SetupDevice* dev) {
                             &beta[(size_t)16 * r]);
     }, 16);
   }
+  // a row whose own coefficient is not negative takes the first alternative
+  // lattice (the cheapest of each box, 9 x 9 to 13 x 13, rows then columns)
+  // whose fit gives a negative one, if any; on host threads for both paths
+  {
+    auto mom = [&](int kj, double* o) { G.moments(kj, o); };
+    parallel_rows(npi, [&](int r) {
+      if (!ok[r]) return;
+      const int k = D.plg[r];
+      auto diag = [k](const int* la, const double* be) {
+        for (int q = 0; q < 15; ++q)
+          if (la[q] == k) return be[q];
+        return 0.0;
+      };
+      int* la = &lat[(size_t)15 * r];
+      double* be = &beta[(size_t)16 * r];
+      if (diag(la, be) < 0.0) return;
+      const int nb = bptr[r + 1] - bptr[r];
+      for (int R = cell::kLatR0; R <= cell::kLatR; ++R)
+        for (int orient = 0; orient < 2; ++orient) {
+          int alt[15], cost = 0;
+          if (!cell::plg_lattice_box(G.type.data(), n, k, R, orient, alt, &cost)) continue;
+          if (std::equal(alt, alt + 15, la)) continue;
+          double b2[16];
+          if (!cell::plg_fit(k, n, h, P.a, P.b, P.c, alt, mom, nb ? &bnode[bptr[r]] : nullptr, nb,
+                             a12.data(), G.x0, G.y0, b2))
+            continue;
+          if (diag(alt, b2) < 0.0) {
+            std::copy(alt, alt + 15, la);
+            std::copy(b2, b2 + 16, be);
+            return;
+          }
+        }
+    }, 16);
+  }
   for (size_t r = 0; r < np; ++r) {
     if (!ok[r]) throw SetupError(3, "singular PLG fit");
     std::array<int, 15> la;

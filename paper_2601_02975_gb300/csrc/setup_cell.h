@@ -260,99 +260,92 @@ CC_HD inline uint8_t kind_of(const uint8_t* type, const uint8_t* ext, int n, boo
 // ties to the lexicographically larger count vector from the lowest line up;
 // rows before columns on equal cost; the 9 x 9 box first, then 11 x 11 and
 // 13 x 13 where a smaller one holds no such set.  out: the 15 cells, sorted.
-CC_HD inline bool plg_lattice(const uint8_t* type, int n, int k, int out[15]) {
+// The cheapest lattice of the box of half-width R on lines of one orientation
+// (0: rows, 1: columns), sorted; its cost in *cost_out; false if none.
+CC_HD inline bool plg_lattice_box(const uint8_t* type, int n, int k, int R, int orient, int out[15],
+                                   int* cost_out) {
   const int i0 = k % n, j0 = k / n;
   struct St { int cost; int8_t have; int8_t asg[kLatW]; };
-  bool found = false;
-  int best_cost = 0;
-  CC_ROLLED
-  for (int R = kLatR0; R <= kLatR && !found; ++R)
-    for (int orient = 0; orient < 2; ++orient) {
-      int8_t avail[kLatW][kLatW];
-      int8_t navail[kLatW];
-      int16_t cost[kLatW][kLatW];
-      for (int v = -R; v <= R; ++v) {
-        const int vi = v + kLatR;
-        int na = 0;
-        for (int u = -R; u <= R; ++u) {
-          const int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
-          const int ii = i0 + di, jj = j0 + dj;
-          if (ii >= 0 && jj >= 0 && ii < n && jj < n && type[jj * n + ii] != T_EMPTY) {
-            const bool cut = type[jj * n + ii] == T_CUT && (di != 0 || dj != 0);
-            cost[vi][u + kLatR] = (int16_t)(u * u + v * v + (cut ? kCutPenalty : 0));
-            // insertion by (cost, u); u grows, so equal costs keep their order
-            int p = na++;
-            while (p > 0 && cost[vi][avail[vi][p - 1] + kLatR] > cost[vi][u + kLatR]) {
-              avail[vi][p] = avail[vi][p - 1];
-              --p;
-            }
-            avail[vi][p] = (int8_t)u;
-          }
+  int8_t avail[kLatW][kLatW];
+  int8_t navail[kLatW];
+  int16_t cost[kLatW][kLatW];
+  for (int v = -R; v <= R; ++v) {
+    const int vi = v + kLatR;
+    int na = 0;
+    for (int u = -R; u <= R; ++u) {
+      const int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
+      const int ii = i0 + di, jj = j0 + dj;
+      if (ii >= 0 && jj >= 0 && ii < n && jj < n && type[jj * n + ii] != T_EMPTY) {
+        const bool cut = type[jj * n + ii] == T_CUT && (di != 0 || dj != 0);
+        cost[vi][u + kLatR] = (int16_t)(u * u + v * v + (cut ? kCutPenalty : 0));
+        // insertion by (cost, u); u grows, so equal costs keep their order
+        int p = na++;
+        while (p > 0 && cost[vi][avail[vi][p - 1] + kLatR] > cost[vi][u + kLatR]) {
+          avail[vi][p] = avail[vi][p - 1];
+          --p;
         }
-        navail[vi] = (int8_t)na;
-      }
-      St nxt[32], cur[32];
-      for (int m = 0; m < 32; ++m) {
-        nxt[m].have = 0;
-        nxt[m].cost = 0;
-        for (int q = 0; q < kLatW; ++q) nxt[m].asg[q] = 0;
-      }
-      nxt[31].have = 1;
-      CC_ROLLED
-      for (int v = R; v >= -R; --v) {
-        const int vi = v + kLatR;
-        CC_ROLLED
-        for (int mask = 0; mask < 32; ++mask) {
-          St& b = cur[mask];
-          b.have = 0;
-          // candidate (cost c, count cn on line v, the rest from state s)
-          auto consider = [&](int c, int cn, const St& s) {
-            bool better = !b.have || c < b.cost;
-            if (b.have && c == b.cost) {
-              // keys: (-count of line v, -count of line v+1, ...), smaller wins
-              int cmp = 0;
-              for (int w = vi; w < kLatW && cmp == 0; ++w) {
-                const int ka = -(w == vi ? cn : s.asg[w]), kb = -b.asg[w];
-                cmp = ka < kb ? -1 : ka > kb ? 1 : 0;
-              }
-              better = cmp < 0;
-            }
-            if (better) {
-              b.have = 1;
-              b.cost = c;
-              for (int w = 0; w < kLatW; ++w) b.asg[w] = s.asg[w];
-              b.asg[vi] = (int8_t)cn;
-            }
-          };
-          if (nxt[mask].have) consider(nxt[mask].cost, 0, nxt[mask]);
-          for (int bit = 0; bit < 5; ++bit) {
-            const int cnt = 5 - bit;
-            if (((mask >> bit) & 1) || navail[vi] < cnt) continue;
-            const int m2 = mask | (1 << bit);
-            if (!nxt[m2].have) continue;
-            int rc = 0;
-            for (int q = 0; q < cnt; ++q) rc += cost[vi][avail[vi][q] + kLatR];
-            consider(nxt[m2].cost + rc, cnt, nxt[m2]);
-          }
-        }
-        for (int m = 0; m < 32; ++m) nxt[m] = cur[m];
-      }
-      if (!nxt[0].have) continue;
-      if (!found || nxt[0].cost < best_cost) {
-        found = true;
-        best_cost = nxt[0].cost;
-        int c = 0;
-        for (int v = -R; v <= R; ++v) {
-          const int vi = v + kLatR, cnt = nxt[0].asg[vi];
-          for (int q = 0; q < cnt; ++q) {
-            const int u = avail[vi][q];
-            const int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
-            out[c++] = (j0 + dj) * n + (i0 + di);
-          }
-        }
+        avail[vi][p] = (int8_t)u;
       }
     }
-  if (!found) return false;
+    navail[vi] = (int8_t)na;
+  }
+  St nxt[32], cur[32];
+  for (int m = 0; m < 32; ++m) {
+    nxt[m].have = 0;
+    nxt[m].cost = 0;
+    for (int q = 0; q < kLatW; ++q) nxt[m].asg[q] = 0;
+  }
+  nxt[31].have = 1;
+  CC_ROLLED
+  for (int v = R; v >= -R; --v) {
+    const int vi = v + kLatR;
+    CC_ROLLED
+    for (int mask = 0; mask < 32; ++mask) {
+      St& b = cur[mask];
+      b.have = 0;
+      // candidate (cost c, count cn on line v, the rest from state s)
+      auto consider = [&](int c, int cn, const St& s) {
+        bool better = !b.have || c < b.cost;
+        if (b.have && c == b.cost) {
+          // keys: (-count of line v, -count of line v+1, ...), smaller wins
+          int cmp = 0;
+          for (int w = vi; w < kLatW && cmp == 0; ++w) {
+            const int ka = -(w == vi ? cn : s.asg[w]), kb = -b.asg[w];
+            cmp = ka < kb ? -1 : ka > kb ? 1 : 0;
+          }
+          better = cmp < 0;
+        }
+        if (better) {
+          b.have = 1;
+          b.cost = c;
+          for (int w = 0; w < kLatW; ++w) b.asg[w] = s.asg[w];
+          b.asg[vi] = (int8_t)cn;
+        }
+      };
+      if (nxt[mask].have) consider(nxt[mask].cost, 0, nxt[mask]);
+      for (int bit = 0; bit < 5; ++bit) {
+        const int cnt = 5 - bit;
+        if (((mask >> bit) & 1) || navail[vi] < cnt) continue;
+        const int m2 = mask | (1 << bit);
+        if (!nxt[m2].have) continue;
+        int rc = 0;
+        for (int q = 0; q < cnt; ++q) rc += cost[vi][avail[vi][q] + kLatR];
+        consider(nxt[m2].cost + rc, cnt, nxt[m2]);
+      }
+    }
+    for (int m = 0; m < 32; ++m) nxt[m] = cur[m];
+  }
+  if (!nxt[0].have) return false;
+  *cost_out = nxt[0].cost;
+  int c = 0;
+  for (int v = -R; v <= R; ++v) {
+    const int vi = v + kLatR, cnt = nxt[0].asg[vi];
+    for (int q = 0; q < cnt; ++q) {
+      const int u = avail[vi][q];
+      const int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
+      out[c++] = (j0 + dj) * n + (i0 + di);
+    }
+  }
   for (int a = 1; a < 15; ++a) {
     const int x = out[a];
     int p = a;
@@ -360,6 +353,25 @@ CC_HD inline bool plg_lattice(const uint8_t* type, int n, int k, int out[15]) {
     out[p] = x;
   }
   return true;
+}
+
+// The rule's lattice: the 9 x 9 box first, then 11 x 11 and 13 x 13 where a
+// smaller one holds no such set; rows before columns on equal cost.
+CC_HD inline bool plg_lattice(const uint8_t* type, int n, int k, int out[15]) {
+  bool found = false;
+  int best_cost = 0;
+  CC_ROLLED
+  for (int R = kLatR0; R <= kLatR && !found; ++R)
+    for (int orient = 0; orient < 2; ++orient) {
+      int tmp[15], c = 0;
+      if (!plg_lattice_box(type, n, k, R, orient, tmp, &c)) continue;
+      if (!found || c < best_cost) {
+        found = true;
+        best_cost = c;
+        for (int q = 0; q < 15; ++q) out[q] = tmp[q];
+      }
+    }
+  return found;
 }
 
 // --- moments ---------------------------------------------------------------

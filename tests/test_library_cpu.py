@@ -210,18 +210,23 @@ def test_default_options_match_the_header(lib):
 
 
 @pytest.mark.parametrize("name,n,mc", [("disk", 128, 16), ("four_disks_D", 128, 16),
-                                       ("batch8", 256, 32)])
+                                       ("batch8", 256, 32), ("ellipses30", 256, 32)])
 def test_coarse_level_tables_match_oracle(lib, name, n, mc):
     """Every level of the hierarchy (Eq. 5.9: each coarse level discretised
     on its own grid) has the same cell kinds, lattices and PLG coefficients
     in the library and in the oracle, and both stop coarsening at the same
     level.  Problem 8 of the batch workload is the one whose coarsest level
-    has PLG rows with a positive diagonal: both sides build the same rows."""
+    has PLG rows with a positive diagonal that no alternative lattice mends:
+    both sides build the same rows.  Ellipse union 30 has such rows on its
+    64^2 and 32^2 levels that alternative lattices do mend (R29): both sides
+    pick the same alternatives."""
     from oracle import multigrid as M
     if name == "disk":
         P = W.problem_disk()
     elif name == "four_disks_D":
         P = W.problem_four_disks(W.DIRICHLET)
+    elif name == "ellipses30":
+        P = W.problem_ellipses(30)
     else:
         P, n2 = W.problem_batch(8)
         assert n2 == n
