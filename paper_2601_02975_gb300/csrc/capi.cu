@@ -1994,6 +1994,7 @@ void destroy_hierarchy(cc_hierarchy* H) {
 // ============================================================================
 // ---- launch shapes timed on the device (cc_options.autotune) ----------------
 const int kTuneMaxM = 8192;     // largest exact block whose chunk size is timed
+const int kTuneCandidates = 3;  // chunk shapes timed per block (the cheapest by the cost model)
 
 // device milliseconds of `reps` runs of f() on s, after 3 untimed runs
 template <class F>
@@ -2264,8 +2265,8 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
       };
       const int mblk = (int)D.block.size();
       if (dev && o.autotune && l + 1 < H->lv.size() && mblk > kDenseMax && mblk <= kTuneMaxM) {
-        // chunk size: the fastest of the cost model's three cheapest plans
-        std::vector<BlockPlan> cand = plan_block_candidates(D, 3);
+        // chunk size: the fastest of the cost model's cheapest plans
+        std::vector<BlockPlan> cand = plan_block_candidates(D, kTuneCandidates);
         for (BlockPlan& B : cand) attach_aliases(B);
         const int pick = tune_block_plan(cand, L.nn, s, reinterpret_cast<unsigned int*>(H->d_norm + 1));
         L.plan() = std::move(cand[pick]);
