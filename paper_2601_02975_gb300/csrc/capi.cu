@@ -113,43 +113,44 @@ struct HostBarrier {
 // host threads; every element sees the same operations in the same order as
 // with one thread, so the result does not depend on the thread count.
 bool invert(std::vector<double>& A, int n) {
-  std::vector<double> I((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  // [A | I] Gauss-Jordan with the identity half stored by pivot step: column
+  // j of J holds column cols[j] of I, the identity column of the row chosen as
+  // pivot j.  Before its step a row's own identity entry is implicit, and
+  // every other entry outside the first c + 1 columns is an exact zero, so
+  // step c updates columns c.. of A and 0..c of J only.
+  std::vector<double> J((size_t)n * n, 0.0);
+  std::vector<int> orig(n), cols(n);
+  for (int i = 0; i < n; ++i) orig[i] = i;
   double amax = 0;
   for (double v : A) amax = std::max(amax, std::fabs(v));
-  // pivot search, row swap and scaling of pivot row c; false if singular
   auto pivot = [&](int c) {
     int p = c;
     for (int r = c + 1; r < n; ++r)
       if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)p * n + c])) p = r;
     if (!(std::fabs(A[(size_t)p * n + c]) > 1e-14 * amax)) return false;
     if (p != c) {
-      for (int k = 0; k < n; ++k) {
-        std::swap(A[(size_t)p * n + k], A[(size_t)c * n + k]);
-        std::swap(I[(size_t)p * n + k], I[(size_t)c * n + k]);
-      }
+      for (int k = c; k < n; ++k) std::swap(A[(size_t)p * n + k], A[(size_t)c * n + k]);
+      for (int k = 0; k < c; ++k) std::swap(J[(size_t)p * n + k], J[(size_t)c * n + k]);
+      std::swap(orig[p], orig[c]);
     }
+    cols[c] = orig[c];
+    J[(size_t)c * n + c] = 1.0;
     double d = 1.0 / A[(size_t)c * n + c];
-    for (int k = 0; k < n; ++k) {
-      A[(size_t)c * n + k] *= d;
-      I[(size_t)c * n + k] *= d;
-    }
+    for (int k = c; k < n; ++k) A[(size_t)c * n + k] *= d;
+    for (int k = 0; k <= c; ++k) J[(size_t)c * n + k] *= d;
     return true;
   };
-  // elimination of column c from rows [r0, r1) other than c
   auto eliminate = [&](int c, int r0, int r1) {
     const double* ac = &A[(size_t)c * n];
-    const double* ic = &I[(size_t)c * n];
+    const double* jc = &J[(size_t)c * n];
     for (int r = r0; r < r1; ++r) {
       if (r == c) continue;
       double* ar = &A[(size_t)r * n];
-      double* ir = &I[(size_t)r * n];
+      double* jr = &J[(size_t)r * n];
       const double l = ar[c];
       if (l == 0.0) continue;
-      for (int k = 0; k < n; ++k) {
-        ar[k] -= l * ac[k];
-        ir[k] -= l * ic[k];
-      }
+      for (int k = c; k < n; ++k) ar[k] -= l * ac[k];
+      for (int k = 0; k <= c; ++k) jr[k] -= l * jc[k];
     }
   };
   unsigned T = 1;
@@ -178,9 +179,11 @@ bool invert(std::vector<double>& A, int n) {
     for (auto& th : pool) th.join();
     if (singular) return false;
   }
-  A.swap(I);
+  for (int r = 0; r < n; ++r)
+    for (int j = 0; j < n; ++j) A[(size_t)r * n + cols[j]] = J[(size_t)r * n + j];
   return true;
 }
+
 
 // row-major n x m -> column-major
 std::vector<double> to_cm(const std::vector<double>& A, int rows, int cols) {
