@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -398,7 +399,11 @@ ChunkShape chunk_shape(const std::vector<std::map<int, double>>& Abb, int s) {
 
 // Numbers of the chunked solve for shape S (FP64): chunk inverses, V_c, W_c,
 // the interface Schur complement and its inverse, laid out per chunk.
-void build_chunked(BlockPlan& B, const std::vector<std::map<int, double>>& Abb, const ChunkShape& S) {
+// a dense inversion: the host's, or the device's (bitwise the same)
+using Inverter = std::function<bool(std::vector<double>&, int)>;
+
+void build_chunked(BlockPlan& B, const std::vector<std::map<int, double>>& Abb, const ChunkShape& S,
+                   const Inverter* inv = nullptr) {
   const int m = B.m, ns = S.ns, nch = S.nch;
   B.s = S.s;
   B.nch = nch;
@@ -492,7 +497,8 @@ void build_chunked(BlockPlan& B, const std::vector<std::map<int, double>>& Abb, 
         for (int j = 0; j < nw; ++j) Sm[(size_t)i * ns + S.sout[c][j]] -= a * wr[j];
       }
   }
-  if (ns && !invert(Sm, ns)) throw SetupError(3, "singular interface Schur complement");
+  if (ns && !(inv ? (*inv)(Sm, ns) : invert(Sm, ns)))
+    throw SetupError(3, "singular interface Schur complement");
   // per-chunk tables and the two stages
   for (int c = 0; c < nch; ++c) {
     ChunkDev& C = B.ch[c];
@@ -566,15 +572,17 @@ ChunkSmem chunk_smem(const BlockPlan& B, int w, int& stage1, int& stage2) {
   return L;
 }
 
-std::vector<BlockPlan> plan_block_candidates(const LevelDisc& D, int k);
+std::vector<BlockPlan> plan_block_candidates(const LevelDisc& D, int k, const Inverter* inv = nullptr);
 
-BlockPlan plan_block(const LevelDisc& D) { return std::move(plan_block_candidates(D, 1)[0]); }
+BlockPlan plan_block(const LevelDisc& D, const Inverter* inv = nullptr) {
+  return std::move(plan_block_candidates(D, 1, inv)[0]);
+}
 
 // The exact block of level D as dense or chunked plans: the dense inverse
 // for small blocks; else the chunk shapes in the order of the cost model,
 // keeping the first k that solve to rounding accuracy (backward error below
 // 1e-13 on a fixed vector), or the most accurate one if none does.
-std::vector<BlockPlan> plan_block_candidates(const LevelDisc& D, int k) {
+std::vector<BlockPlan> plan_block_candidates(const LevelDisc& D, int k, const Inverter* inv) {
   BlockPlan B;
   const int m = (int)D.block.size();
   B.m = m;
@@ -602,7 +610,7 @@ std::vector<BlockPlan> plan_block_candidates(const LevelDisc& D, int k) {
     std::vector<double> A((size_t)m * m, 0.0);
     for (int p = 0; p < m; ++p)
       for (auto& kv : Abb[p]) A[(size_t)p * m + kv.first] += kv.second;
-    if (!invert(A, m)) throw SetupError(3, "singular block of the smoother");
+    if (!(inv ? (*inv)(A, m) : invert(A, m))) throw SetupError(3, "singular block of the smoother");
     B.ainv.swap(A);
     B.dense = true;
     B.error = block_plan_error(B, Abb);
@@ -625,7 +633,7 @@ std::vector<BlockPlan> plan_block_candidates(const LevelDisc& D, int k) {
   for (const ChunkShape& S : shapes) {
     BlockPlan P = B;
     try {
-      build_chunked(P, Abb, S);
+      build_chunked(P, Abb, S, inv);
     } catch (SetupError&) {
       continue;
     }
@@ -2266,15 +2274,20 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
           B.alias_ptr.push_back((int)B.alias_cell.size());
         }
       };
+      // dense inverses of 256 rows and more on the device with the setup steps
+      const Inverter dev_inv = [&](std::vector<double>& A, int n) {
+        return n >= 256 ? sdev->invert(A, n) : invert(A, n);
+      };
+      const Inverter* inv = sdev ? &dev_inv : nullptr;
       const int mblk = (int)D.block.size();
       if (dev && o.autotune && l + 1 < H->lv.size() && mblk > kDenseMax && mblk <= kTuneMaxM) {
         // chunk size: the fastest of the cost model's cheapest plans
-        std::vector<BlockPlan> cand = plan_block_candidates(D, kTuneCandidates);
+        std::vector<BlockPlan> cand = plan_block_candidates(D, kTuneCandidates, inv);
         for (BlockPlan& B : cand) attach_aliases(B);
         const int pick = tune_block_plan(cand, L.nn, s, reinterpret_cast<unsigned int*>(H->d_norm + 1));
         L.plan() = std::move(cand[pick]);
       } else {
-        L.plan() = plan_block(D);
+        L.plan() = plan_block(D, inv);
         attach_aliases(L.plan());
       }
       if (!dev) continue;
@@ -2340,7 +2353,8 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
           A[(size_t)k * nc + own] = -1.0;
       }
       std::vector<double> A0(A);
-      if (!invert(A, nc)) throw SetupError(3, "singular coarsest-level matrix");
+      const bool inv_ok = (sdev && nc >= 256) ? sdev->invert(A, nc) : invert(A, nc);
+      if (!inv_ok) throw SetupError(3, "singular coarsest-level matrix");
       {
         std::vector<double> t(nc), x(nc, 0.0);
         for (int k = 0; k < nc; ++k) t[k] = std::sin(1.0 + 0.7 * k) + 0.25 * std::cos(3.1 * k);

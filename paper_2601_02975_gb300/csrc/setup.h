@@ -176,6 +176,10 @@ class SetupDevice {
   // nh * ns): the nearest sample and its squared distance (m * nh each)
   void nearest(const double* sx, const double* sy, int nh, int ns, const double* px,
                const double* py, int m, int* idx, double* d2);
+  // the inverse of the n x n row-major A in place by Gauss-Jordan with
+  // partial pivoting, bitwise the host's dense inversion (the same
+  // operations in the same order per element); false if singular
+  bool invert(std::vector<double>& A, int n);
   double kernel_ms = 0;   // device time of the kernels so far
 
  private:

@@ -10,6 +10,8 @@
 // nodes, the rows of A and N, and the factorisations of the block smoother.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -130,6 +132,85 @@ __global__ void k_nearest(const double* __restrict__ sx, const double* __restric
   double d;
   idx[t] = cell::nearest_sample(sx + (int64_t)e * ns, sy + (int64_t)e * ns, ns, px[r], py[r], &d);
   d2[t] = d;
+}
+
+// Gauss-Jordan step c of [A | J] (the identity half J kept in the order of
+// the pivot steps, as the host's dense inversion keeps it): pivot search
+// (the first row of largest magnitude in column c), row swap, scaling of
+// the pivot row, and the multipliers of column c.  One CTA.
+__global__ void __launch_bounds__(1024) k_gj_pivot(double* __restrict__ A, double* __restrict__ J, int n,
+                                                  int c, double tol, int* __restrict__ orig,
+                                                  int* __restrict__ cols, double* __restrict__ lcol,
+                                                  int* __restrict__ flag) {
+  __shared__ double sv[32];
+  __shared__ int sr[32];
+  __shared__ int piv;
+  __shared__ double dinv;
+  if (*flag) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double bv = -1.0;
+  int br = n;
+  for (int r = c + tid; r < n; r += blockDim.x) {
+    const double v = fabs(A[(int64_t)r * n + c]);
+    if (v > bv) { bv = v; br = r; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+    const int orr = __shfl_down_sync(0xffffffffu, br, o);
+    if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+  }
+  if (lane == 0) { sv[warp] = bv; sr[warp] = br; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] > sv[0] || (sv[w] == sv[0] && sr[w] < sr[0])) { sv[0] = sv[w]; sr[0] = sr[w]; }
+    piv = sr[0];
+    if (!(piv < n && fabs(A[(int64_t)piv * n + c]) > tol)) *flag = 1;
+  }
+  __syncthreads();
+  if (*flag) return;
+  const int p = piv;
+  if (p != c) {
+    for (int k = c + tid; k < n; k += blockDim.x) {
+      const double t = A[(int64_t)p * n + k];
+      A[(int64_t)p * n + k] = A[(int64_t)c * n + k];
+      A[(int64_t)c * n + k] = t;
+    }
+    for (int k = tid; k < c; k += blockDim.x) {
+      const double t = J[(int64_t)p * n + k];
+      J[(int64_t)p * n + k] = J[(int64_t)c * n + k];
+      J[(int64_t)c * n + k] = t;
+    }
+    if (tid == 0) { const int t = orig[p]; orig[p] = orig[c]; orig[c] = t; }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    cols[c] = orig[c];
+    J[(int64_t)c * n + c] = 1.0;
+    dinv = 1.0 / A[(int64_t)c * n + c];
+  }
+  __syncthreads();
+  const double d = dinv;
+  for (int k = c + tid; k < n; k += blockDim.x) A[(int64_t)c * n + k] *= d;
+  for (int k = tid; k <= c; k += blockDim.x) J[(int64_t)c * n + k] *= d;
+  __syncthreads();
+  for (int r = tid; r < n; r += blockDim.x) lcol[r] = r == c ? 0.0 : A[(int64_t)r * n + c];
+}
+
+// Gauss-Jordan step c: every row r != c with a nonzero multiplier l loses l
+// times the pivot row, in columns c.. of A and 0..c of J.
+__global__ void k_gj_elim(double* __restrict__ A, double* __restrict__ J, int n, int c,
+                          const double* __restrict__ lcol, const int* __restrict__ flag) {
+  if (*flag) return;
+  const int64_t w = (int64_t)n + 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * w;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / w), t = (int)(e % w);
+    const double l = lcol[r];
+    if (r == c || l == 0.0) continue;
+    if (t <= c) J[(int64_t)r * n + t] -= l * J[(int64_t)c * n + t];
+    else A[(int64_t)r * n + (t - 1)] -= l * A[(int64_t)c * n + (t - 1)];
+  }
 }
 
 int grid_for(int64_t work, int block) {
@@ -305,6 +386,42 @@ void SetupDevice::fits(int n, double h, double x0, double y0, double a, double b
   SCK(cudaMemcpyAsync(beta, A.beta, (size_t)16 * np * sizeof(double), cudaMemcpyDeviceToHost, I.s));
   SCK(cudaMemcpyAsync(ok, A.ok, (size_t)np, cudaMemcpyDeviceToHost, I.s));
   SCK(cudaStreamSynchronize(I.s));
+}
+
+bool SetupDevice::invert(std::vector<double>& A, int n) {
+  Impl& I = *p_;
+  Impl::Scratch S{&I, {}};
+  const size_t nn = (size_t)n * n;
+  double amax = 0;
+  for (double v : A) amax = std::max(amax, std::fabs(v));
+  std::vector<int> orig(n);
+  for (int i = 0; i < n; ++i) orig[i] = i;
+  double* dA = S.put(A.data(), nn);
+  double* dJ = S.get<double>(nn);
+  SCK(cudaMemsetAsync(dJ, 0, nn * sizeof(double), I.s));
+  int* dorig = S.put(orig.data(), (size_t)n);
+  int* dcols = S.get<int>((size_t)n);
+  double* dl = S.get<double>((size_t)n);
+  int* dflag = S.get<int>(1);
+  SCK(cudaMemsetAsync(dflag, 0, sizeof(int), I.s));
+  const int g = grid_for((int64_t)n * (n + 1), 256);
+  I.begin();
+  for (int c = 0; c < n; ++c) {
+    k_gj_pivot<<<1, 1024, 0, I.s>>>(dA, dJ, n, c, 1e-14 * amax, dorig, dcols, dl, dflag);
+    k_gj_elim<<<g, 256, 0, I.s>>>(dA, dJ, n, c, dl, dflag);
+  }
+  I.end(kernel_ms);
+  int flag = 0;
+  std::vector<double> Jh(nn);
+  std::vector<int> cols(n);
+  SCK(cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaMemcpyAsync(Jh.data(), dJ, nn * sizeof(double), cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaMemcpyAsync(cols.data(), dcols, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, I.s));
+  SCK(cudaStreamSynchronize(I.s));
+  if (flag) return false;
+  for (int r = 0; r < n; ++r)
+    for (int j = 0; j < n; ++j) A[(size_t)r * n + cols[j]] = Jh[(size_t)r * n + j];
+  return true;
 }
 
 void SetupDevice::nearest(const double* sx, const double* sy, int nh, int ns, const double* px,
