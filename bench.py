@@ -846,8 +846,8 @@ def run_random_domains(a, dev):
     in FP64 refinement to 1e-10: solved one at a time, then all at once with
     one cc_solve_batch call (the DOF/s count the converged problems' DOF over
     the time of all).
-    Problems the setup rejects (a finest-grid cut cell of two components, or
-    a coarsest level too large for the dense bottom solve) are listed as
+    Problems the setup rejects (a finest-grid cut cell with a hole inside it,
+    or a coarsest level too large for the dense bottom solve) are listed as
     skipped; holes of 2-5 coarse cells can give coarsest-level cut-cell rows
     of the wrong sign and make the cycle diverge, which is reported, not
     hidden.  The same problems are then solved once more, as one batch, with

@@ -20,10 +20,12 @@ applied with the reading listed in the design notes: cells are visited once
 in row-major order (y index outer), the volume is the current one, a merge
 target is a present cell reachable through a shared face piece of positive
 length, the argmin ties go to the first neighbour in the order -x, +x, -y,
-+y.  The step of Alg. 1 for cells with several connected components is not
-exercised: a level where some cut cell has more than one component violates
-the algorithm's precondition ("h is sufficiently small to resolve the
-topology") and is reported as unresolved.
++y.  The step of Alg. 1 for cells with several connected components comes
+first: such a cell keeps its largest component, and every other component
+joins the face neighbour (through one of its own face pieces, in the order
+-x, +x, -y, +y, near-ties to the first) whose volume with it comes closest
+to h^2 (reading R30).  A cell whose components include an inner loop (a
+hole inside the cell) is reported as unresolved.
 """
 from __future__ import annotations
 
@@ -524,7 +526,8 @@ def build_level(dom: Domain, n: int, eps: float) -> Level:
     ctype[~inside_any] = REGULAR
     vol[~inside_any] = h * h
 
-    for k, arcs in arcs_by_cell.items():
+    orphans = []   # (cell, pieces) of the components a cell does not keep
+    for k, arcs in sorted(arcs_by_cell.items()):
         j, i = divmod(k, n)
         xl, xr = x0 + i * h, x0 + (i + 1) * h
         yb, yt = y0 + j * h, y0 + (j + 1) * h
@@ -563,9 +566,23 @@ def build_level(dom: Domain, n: int, eps: float) -> Level:
                         bc = 3
                     pieces.append(Piece('seg', qa, qb, bc=bc, face=f))
                     faces[f] = True
-        # chain pieces into loops to count connected components
-        nloops_out, nloops_in = _count_loops(pieces, h, curves, xl + 0.5 * h, yb + 0.5 * h)
-        if nloops_out != 1:
+        # chain pieces into loops: the connected components
+        loops = _loops(pieces, h, curves, xl + 0.5 * h, yb + 0.5 * h)
+        nloops_out = sum(1 for _, a in loops if a > 0)
+        nloops_in = len(loops) - nloops_out
+        if nloops_out >= 2 and nloops_in == 0:
+            # Alg. 1, cells of several components: keep the largest here, the
+            # others join a face neighbour below
+            big = max(range(len(loops)), key=lambda q: (loops[q][1], -q))
+            for q, (idx, _) in enumerate(loops):
+                if q != big:
+                    orphans.append((k, [pieces[t] for t in idx]))
+            pieces = [pieces[t] for t in loops[big][0]]
+            faces = [False, False, False, False]
+            for pc in pieces:
+                if pc.kind == 'seg':
+                    faces[pc.face] = True
+        elif nloops_out != 1:
             resolved = False
             reason = f"cell ({i},{j}) has {nloops_out} components"
         mom = np.zeros(len(MOMS))
@@ -584,15 +601,67 @@ def build_level(dom: Domain, n: int, eps: float) -> Level:
     present = ctype != EMPTY
     owner = np.where(present.ravel(), np.arange(n * n), -1).reshape(n, n)
     lev = Level(dom, n, h, eps, present, ctype, vol, owner, cut, resolved, reason)
+    for k, pcs in orphans:
+        if not _attach_component(lev, k, pcs, curves):
+            lev.resolved = False
+            lev.reason = f"a component of cell {divmod(k, n)[::-1]} has no neighbour"
     _merge_small(lev)
     return lev
 
 
+def _attach_component(lev: Level, k: int, pcs: List[Piece], curves) -> bool:
+    """Alg. 1, the step for cells of several components: the component of
+    cell k bounded by pcs joins the face neighbour C_j (one across a face
+    piece of the component, in the order -x, +x, -y, +y) minimising
+    |vol_j + vol_component - h^2| (scores within 1e-9 h^2 of the smallest are
+    ties, to the first); False if it touches no present neighbour."""
+    n, h = lev.n, lev.h
+    h2 = h * h
+    j, i = divmod(k, n)
+    px, py = lev.center(k)
+    mk = np.zeros(len(MOMS))
+    for p in pcs:
+        mk += piece_moments(p, curves, px, py, h)
+    vk = mk[0] * h2
+    faces = {p.face for p in pcs if p.kind == 'seg'}
+    nbrs = []
+    for f, (di, dj) in ((3, (-1, 0)), (1, (1, 0)), (0, (0, -1)), (2, (0, 1))):
+        ii, jj = i + di, j + dj
+        if f not in faces or not (0 <= ii < n and 0 <= jj < n) or not lev.present[jj, ii]:
+            continue
+        nbrs.append(jj * n + ii)
+    if not nbrs:
+        return False
+    score = [abs(lev.vol.flat[t] + vk - h2) for t in nbrs]
+    smin = min(score)
+    best = next(t for t, sc in zip(nbrs, score) if sc <= smin + 1e-9 * h2)
+    bj, bi = divmod(best, n)
+    tgt = lev.cut.get(best)
+    if tgt is None:
+        tgt = CutCell(_full_edges(lev, bi, bj), regular_moments().copy(), [True] * 4)
+        tgt.bnodes = _wall_nodes(lev, bi, bj)
+        lev.cut[best] = tgt
+    tgt.mom = tgt.mom + shift_moments(mk, i - bi, j - bj)
+    tgt.pieces = tgt.pieces + list(pcs)
+    tgt.bnodes = tgt.bnodes + _boundary_nodes(list(pcs), curves)
+    lev.vol[bj, bi] += vk
+    lev.ctype[bj, bi] = IRREGULAR
+    return True
+
+
 def _count_loops(pieces: List[Piece], h: float, curves, px, py):
     """Number of outer (positive area) and inner loops formed by the pieces."""
+    loops = _loops(pieces, h, curves, px, py)
+    n_out = sum(1 for _, a in loops if a > 0)
+    return n_out, len(loops) - n_out
+
+
+def _loops(pieces: List[Piece], h: float, curves, px, py):
+    """The closed loops formed by the pieces, each as (piece indices in
+    chaining order, scaled area), in the order of their first pieces."""
     tol = 1e-9 * h
     left = list(range(len(pieces)))
-    n_out = n_in = 0
+    out = []
     while left:
         start = left.pop(0)
         loop = [start]
@@ -615,11 +684,8 @@ def _count_loops(pieces: List[Piece], h: float, curves, px, py):
             if guard > 10000:
                 raise GeometryError("loop chaining did not terminate")
         area = sum(piece_moments(pieces[k], curves, px, py, h)[0] for k in loop)
-        if area > 0:
-            n_out += 1
-        else:
-            n_in += 1
-    return n_out, n_in
+        out.append((loop, area))
+    return out
 
 
 def _boundary_nodes(pieces: List[Piece], curves) -> list:

@@ -230,16 +230,22 @@ bool outside_all(const Problem& P, double x, double y, int skip = -1) {
   return true;
 }
 
-// number of closed loops with positive / negative area
-void count_loops(const Problem& P, const std::vector<Piece>& pcs, double px, double py, double h,
-                 int& n_out, int& n_in) {
-  n_out = n_in = 0;
+// The closed loops the pieces form (the connected components of a cut cell):
+// each as its pieces in chaining order and its scaled area, in the order of
+// their first pieces.
+struct Loop { std::vector<int> idx; double area; };
+
+std::vector<Loop> chain_loops(const Problem& P, const std::vector<Piece>& pcs, double px, double py,
+                              double h) {
+  std::vector<Loop> out;
   std::vector<char> used(pcs.size(), 0);
   const double tol = 1e-10 * h;
   for (size_t s = 0; s < pcs.size(); ++s) {
     if (used[s]) continue;
     used[s] = 1;
-    double area = 0, m[kMoments];
+    Loop L;
+    L.idx.push_back((int)s);
+    double m[kMoments];
     std::fill(m, m + kMoments, 0.0);
     piece_moments(P, pcs[s], px, py, h, m);
     double ex = pcs[s].xb, ey = pcs[s].yb;
@@ -254,13 +260,15 @@ void count_loops(const Problem& P, const std::vector<Piece>& pcs, double px, dou
       if (nxt < 0 || ++guard > 100000)
         throw SetupError(2, "cut-cell boundary pieces do not close");
       used[nxt] = 1;
+      L.idx.push_back(nxt);
       piece_moments(P, pcs[nxt], px, py, h, m);
       ex = pcs[nxt].xb;
       ey = pcs[nxt].yb;
     }
-    area = m[0];
-    if (area > 0) ++n_out; else ++n_in;
+    L.area = m[0];
+    out.push_back(std::move(L));
   }
+  return out;
 }
 
 }  // namespace
@@ -282,10 +290,10 @@ static std::vector<Piece> full_faces(const LevelGeom& G, int i, int j) {
   int n = G.n;
   double xl = G.x0 + i * G.h, xr = xl + G.h, yb = G.y0 + j * G.h, yt = yb + G.h;
   std::vector<Piece> v;
-  v.push_back({false, xl, yb, xr, yb, -1, 0, 0, j == 0 ? 0 : -1});
-  v.push_back({false, xr, yb, xr, yt, -1, 0, 0, i == n - 1 ? 1 : -1});
-  v.push_back({false, xr, yt, xl, yt, -1, 0, 0, j == n - 1 ? 2 : -1});
-  v.push_back({false, xl, yt, xl, yb, -1, 0, 0, i == 0 ? 3 : -1});
+  v.push_back({false, xl, yb, xr, yb, -1, 0, 0, j == 0 ? 0 : -1, 0});
+  v.push_back({false, xr, yb, xr, yt, -1, 0, 0, i == n - 1 ? 1 : -1, 1});
+  v.push_back({false, xr, yt, xl, yt, -1, 0, 0, j == n - 1 ? 2 : -1, 2});
+  v.push_back({false, xl, yt, xl, yb, -1, 0, 0, i == 0 ? 3 : -1, 3});
   return v;
 }
 
@@ -373,6 +381,7 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
       H.at(pc.ta, pc.xa, pc.ya);
       H.at(pc.tb, pc.xb, pc.yb);
       pc.bc = 4 + e;
+      pc.face = -1;
       arcs[jj * n + ii].push_back(pc);
     }
   }
@@ -404,6 +413,8 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
   std::vector<int> ccell;
   std::vector<Cut> ccut;
   std::vector<double> cpx, cpy;
+  struct Orphan { int k; std::vector<Piece> pcs; };
+  std::vector<Orphan> orphans;   // the components a cell does not keep
   for (auto& kv : arcs) {
     int k = kv.first, j = k / n, i = k % n;
     double xl = P.x0 + i * h, xr = xl + h, yb = P.y0 + j * h, yt = yb + h;
@@ -441,13 +452,34 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
         else { pc.ya = pts[s]; pc.yb = pts[s + 1]; pc.xa = pc.xb = ed.ax; }
         if (!outside_all(P, 0.5 * (pc.xa + pc.xb), 0.5 * (pc.ya + pc.yb))) continue;
         pc.bc = ed.bc;
+        pc.face = f;
         C.pieces.push_back(pc);
         C.face[f] = true;
       }
     }
-    int n_out, n_in;
-    count_loops(P, C.pieces, px, py, h, n_out, n_in);
-    if (n_out != 1) {
+    std::vector<Loop> loops = chain_loops(P, C.pieces, px, py, h);
+    int n_out = 0;
+    for (const Loop& L : loops) n_out += L.area > 0;
+    const int n_in = (int)loops.size() - n_out;
+    if (n_out >= 2 && n_in == 0) {
+      // Alg. 1, cells of several components: the largest stays (its pieces
+      // in chaining order), the others join a face neighbour below
+      size_t big = 0;
+      for (size_t q = 1; q < loops.size(); ++q)
+        if (loops[q].area > loops[big].area) big = q;
+      for (size_t q = 0; q < loops.size(); ++q) {
+        if (q == big) continue;
+        Orphan O{k, {}};
+        for (int t : loops[q].idx) O.pcs.push_back(C.pieces[t]);
+        orphans.push_back(std::move(O));
+      }
+      std::vector<Piece> keep;
+      for (int t : loops[big].idx) keep.push_back(C.pieces[t]);
+      C.pieces.swap(keep);
+      for (int f = 0; f < 4; ++f) C.face[f] = false;
+      for (const Piece& pc : C.pieces)
+        if (!pc.arc) C.face[pc.face] = true;
+    } else if (n_out != 1) {
       G.resolved = false;
       G.reason = "cell (" + std::to_string(i) + "," + std::to_string(j) + ") has " +
                  std::to_string(n_out) + " components";
@@ -483,6 +515,57 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
       G.vol[k] = C.mom[0] * h * h;
       G.cut[k] = std::move(C);
     }
+  }
+  // Alg. 1, the other components of a cell: each joins the face neighbour
+  // across one of its own face pieces (order -x, +x, -y, +y) whose volume
+  // with it comes closest to h^2, near-ties to the first
+  for (const Orphan& O : orphans) {
+    const int k = O.k, i = k % n, j = k / n;
+    const double px = P.x0 + (i + 0.5) * h, py = P.y0 + (j + 0.5) * h;
+    double mk[kMoments];
+    std::fill(mk, mk + kMoments, 0.0);
+    for (const Piece& pc : O.pcs) piece_moments(P, pc, px, py, h, mk);
+    const double vk = mk[0] * h * h, h2 = h * h;
+    bool on[4] = {false, false, false, false};
+    for (const Piece& pc : O.pcs)
+      if (!pc.arc) on[pc.face] = true;
+    static const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1}, fidx[4] = {3, 1, 0, 2};
+    std::vector<int> cand;
+    for (int q = 0; q < 4; ++q) {
+      const int ii = i + di[q], jj = j + dj[q];
+      if (!on[fidx[q]] || ii < 0 || jj < 0 || ii >= n || jj >= n) continue;
+      if (G.type[jj * n + ii] != CT_EMPTY) cand.push_back(jj * n + ii);
+    }
+    if (cand.empty()) {
+      G.resolved = false;
+      G.reason = "a component of cell (" + std::to_string(i) + "," + std::to_string(j) +
+                 ") has no neighbour";
+      continue;
+    }
+    double smin = 0;
+    std::vector<double> score(cand.size());
+    for (size_t q = 0; q < cand.size(); ++q) {
+      score[q] = std::fabs(G.vol[cand[q]] + vk - h2);
+      smin = q == 0 ? score[q] : std::min(smin, score[q]);
+    }
+    int best = cand[0];
+    for (size_t q = 0; q < cand.size(); ++q)
+      if (score[q] <= smin + 1e-9 * h2) { best = cand[q]; break; }
+    const int bi = best % n, bj = best / n;
+    if (!G.cut.count(best)) {
+      Cut T;
+      T.pieces = full_faces(G, bi, bj);
+      for (int f = 0; f < 4; ++f) T.face[f] = true;
+      cell::full_moments(T.mom);
+      G.cut[best] = T;
+    }
+    Cut& T = G.cut[best];
+    double sh[kMoments];
+    shift_moments(mk, i - bi, j - bj, sh);
+    for (int q = 0; q < kMoments; ++q) T.mom[q] += sh[q];
+    T.pieces.insert(T.pieces.end(), O.pcs.begin(), O.pcs.end());
+    G.vol[best] += vk;
+    G.type[best] = CT_CUT;
   }
 
   // ---- Alg. 1, merging of small cells -----------------------------------------

@@ -185,6 +185,7 @@ struct Piece {
   int hole;               // arcs
   double ta, tb;          // arcs: parameter from ta to tb (tb < ta)
   int bc;                 // index into Problem::bc, -1 for interior faces
+  int face;               // face pieces: 0 bottom, 1 right, 2 top, 3 left; arcs -1
 };
 
 // Gauss-Legendre rules on [-1, 1]: 5 points for straight pieces, 10 for each

@@ -210,7 +210,8 @@ def test_default_options_match_the_header(lib):
 
 
 @pytest.mark.parametrize("name,n,mc", [("disk", 128, 16), ("four_disks_D", 128, 16),
-                                       ("batch8", 256, 32), ("ellipses30", 256, 32)])
+                                       ("batch8", 256, 32), ("ellipses30", 256, 32),
+                                       ("batch4", 64, 8), ("ellipses15", 128, 32)])
 def test_coarse_level_tables_match_oracle(lib, name, n, mc):
     """Every level of the hierarchy (Eq. 5.9: each coarse level discretised
     on its own grid) has the same cell kinds, lattices and PLG coefficients
@@ -219,20 +220,26 @@ def test_coarse_level_tables_match_oracle(lib, name, n, mc):
     has PLG rows with a positive diagonal that no alternative lattice mends:
     both sides build the same rows.  Ellipse union 30 has such rows on its
     64^2 and 32^2 levels that alternative lattices do mend (R29): both sides
-    pick the same alternatives."""
+    pick the same alternatives.  Problem 4 of the batch and union 15 have
+    finest-level cut cells of two components (Alg. 1): both sides keep the
+    same one, move the other to the same neighbour, and build the same
+    cells, volumes and rows."""
     from oracle import multigrid as M
     if name == "disk":
         P = W.problem_disk()
     elif name == "four_disks_D":
         P = W.problem_four_disks(W.DIRICHLET)
-    elif name == "ellipses30":
-        P = W.problem_ellipses(30)
+    elif name.startswith("ellipses"):
+        P = W.problem_ellipses(int(name[8:]))
     else:
-        P, n2 = W.problem_batch(8)
+        P, n2 = W.problem_batch(int(name[5:]))
         assert n2 == n
     H = _host(P, n, min_coarse_n=mc)
     O = M.build_hierarchy(P.dom, n, P.a, P.b, P.c, min_coarse=mc)
     assert H.info.n_levels == O.nl
+    typ, _, vol = H.cell_types()
+    np.testing.assert_array_equal(typ, O.levels[0].lev.ctype)
+    assert np.abs(vol - O.levels[0].lev.vol).max() < 1e-15
     for l, d in enumerate(O.levels):
         kind, lat, beta = H.level_tables(l)
         np.testing.assert_array_equal(kind, d.kind)

@@ -317,6 +317,62 @@ def test_ellipse_area():
     assert abs(lev.vol.sum() - (1 - math.pi * e.r1 * e.r2)) < 1e-13
 
 
+def _moved_components(monkeypatch):
+    moved = []
+    attach = G._attach_component
+    monkeypatch.setattr(G, "_attach_component",
+                        lambda lev, k, pcs, cv: (moved.append(k), attach(lev, k, pcs, cv))[1])
+    return moved
+
+
+def test_components_moved_to_a_neighbour_keep_the_moments(monkeypatch):
+    """Alg. 1, cells of several components: at N = 64 some cut cells of
+    problem 4 of the batch workload hold two pieces of the domain (a narrow
+    gap between two holes), the level still resolves, and every component
+    joins some cell whole.  The area, first and second moments of the domain
+    then equal the closed forms of the unit square minus disjoint rotated
+    ellipses: a component dropped, or its moments shifted to the wrong
+    centre, fails one of them."""
+    P, n = W.problem_batch(4)
+    moved = _moved_components(monkeypatch)
+    lev = G.build_level(P.dom, n, 0.1)
+    assert moved and lev.resolved, lev.reason
+    want = {(0, 0): 1.0, (1, 0): 0.5, (0, 1): 0.5, (2, 0): 1 / 3, (1, 1): 0.25, (0, 2): 1 / 3}
+    for e in P.dom.holes:
+        a = math.pi * e.r1 * e.r2
+        c, s = math.cos(e.theta), math.sin(e.theta)
+        ixx = a / 4 * (e.r1 ** 2 * c * c + e.r2 ** 2 * s * s)
+        iyy = a / 4 * (e.r1 ** 2 * s * s + e.r2 ** 2 * c * c)
+        ixy = a / 4 * (e.r1 ** 2 - e.r2 ** 2) * c * s
+        want[(0, 0)] -= a
+        want[(1, 0)] -= a * e.cx
+        want[(0, 1)] -= a * e.cy
+        want[(2, 0)] -= a * e.cx ** 2 + ixx
+        want[(1, 1)] -= a * e.cx * e.cy + ixy
+        want[(0, 2)] -= a * e.cy ** 2 + iyy
+    assert abs(lev.vol.sum() - want[(0, 0)]) < 1e-13
+    for (p, q), v in want.items():
+        assert abs(_level_moment(lev, p, q) - v) < 1e-13, (p, q)
+
+
+def test_components_moved_in_an_overlapping_union_keep_the_moments(monkeypatch):
+    """The same step in a union of overlapping ellipses (union 15) at
+    N = 128, where it moves components; at N = 150 no cell has several.
+    The moments of the domain agree between the two grids within 1e-12 (the
+    Gauss rules on the ellipse arcs leave a few 1e-13): the moved component
+    has volume 1.7e-9, so dropping it, or shifting its moments by one cell,
+    shows."""
+    P = W.problem_ellipses(15)
+    moved = _moved_components(monkeypatch)
+    lev = G.build_level(P.dom, 128, 0.1)
+    assert moved and lev.resolved, lev.reason
+    del moved[:]
+    other = G.build_level(P.dom, 150, 0.1)
+    assert not moved
+    for p, q in ((0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)):
+        assert abs(_level_moment(lev, p, q) - _level_moment(other, p, q)) < 1e-12, (p, q)
+
+
 # ---------------------------------------------------------------------------
 # PLG rows: exactness on quartics with averages from adaptive quadrature
 # ---------------------------------------------------------------------------
