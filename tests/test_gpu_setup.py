@@ -51,11 +51,15 @@ def _problem(name):
 
 
 def _both(name, n, mc, **opt):
+    """The same problem set up on the device and on host threads.  Launch
+    shapes are not tuned: a timed choice of chunk size could differ between
+    the two and change the rounding of the block solves (tuning has its own
+    tests)."""
     P, extra = _problem(name)
     hs = []
     for dev in (1, 0):
         hs.append(Hierarchy.from_domain(P.dom, P.a, P.b, P.c, n,
-                                        default_options(min_coarse_n=mc, device_setup=dev,
+                                        default_options(min_coarse_n=mc, device_setup=dev, autotune=0,
                                                         **extra, **opt)))
     return P, extra, hs[0], hs[1]
 
