@@ -397,9 +397,11 @@ cc_status cc_cycle(cc_handle h, double* d_u, const double* d_b, cc_stream stream
  * contributions to the interface right-hand sides) live in one file-scope
  * device array of CC_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB) in the
  * library.  Every GPU that loads the library's device code holds that array
- * until the process exits.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current.
- * Make that first call before any stream capture.
+ * until the process exits.  cc_setup looks up the array's device address
+ * (cudaGetSymbolAddress) with the handle's device current and keeps it in
+ * the handle (a clone shares it), so the call itself makes no runtime query
+ * and may run inside a stream capture; a handle made after a device reset
+ * holds the address in the new context.
  *
  * All calls share the one array, and it keeps the last call's contents.
  * Each call writes every entry it reads before reading it, so nothing needs

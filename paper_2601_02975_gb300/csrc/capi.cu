@@ -726,6 +726,21 @@ struct Level {
 
 }  // namespace
 
+// Scratch of cc_smooth_noalloc: one file-scope device array per device.  Host
+// code cannot use the symbol's host-side address; cc_setup looks up the
+// device address with the handle's device current and keeps it in the handle
+// (clones share it), so a handle made after a device reset holds the address
+// in the new context, and the sweep itself makes no lookup.
+static __device__ __align__(256) double g_noalloc_scratch[CC_NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+double* noalloc_scratch() {
+  void* p = nullptr;
+  CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  return static_cast<double*>(p);
+}
+}  // namespace
+
 struct cc_hierarchy {
   Problem P;
   cc_options opt;
@@ -736,6 +751,7 @@ struct cc_hierarchy {
   double* bottom_inv = nullptr;   // column-major FP64
   double bottom_error = 0;
   int nc_bottom = 0;
+  double* noalloc = nullptr;      // the device's cc_smooth_noalloc scratch (looked up at setup)
   double setup_seconds = 0;       // wall time of the cc_setup that built the tables
   double setup_tables_seconds = 0;  // of which discretize (all levels)
   double setup_kernel_ms = 0;     // device time of its setup kernels
@@ -2211,6 +2227,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
   try {
     if (dev) {
       CK(cudaGetDevice(&H->device));
+      H->noalloc = noalloc_scratch();
       if (o.device_setup) sdev = std::make_unique<SetupDevice>((void*)s);
       pdl_setup_device();
       chunk_smem_attributes();
@@ -2555,6 +2572,7 @@ cc_status cc_clone(cc_handle S, cc_stream stream, cc_handle* out) {
     H->P = S->P;
     H->opt = S->opt;
     H->device = S->device;
+    H->noalloc = S->noalloc;
     H->tables = S->tables ? S->tables : S->pool;
     H->bottom_inv = S->bottom_inv;
     H->bottom_error = S->bottom_error;
@@ -2836,25 +2854,6 @@ cc_status cc_cycle(cc_handle H, double* u, const double* b, cc_stream st) {
 }  // extern "C"
 
 // ---- allocation-free sweep ---------------------------------------------------
-// Scratch of cc_smooth_noalloc: one file-scope device array per device.  Host
-// code cannot use the symbol's host-side address; the device address is
-// looked up once per device (with that device current) and cached.
-static __device__ __align__(256) double g_noalloc_scratch[CC_NOALLOC_SCRATCH_DOUBLES];
-
-namespace {
-std::mutex g_noalloc_mu;
-std::unordered_map<int, double*> g_noalloc_ptr;   // device -> address of the array
-
-double* noalloc_scratch(int device) {
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  auto it = g_noalloc_ptr.find(device);
-  if (it != g_noalloc_ptr.end()) return it->second;
-  void* p = nullptr;
-  CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-  g_noalloc_ptr[device] = static_cast<double*>(p);
-  return static_cast<double*>(p);
-}
-}  // namespace
 
 extern "C" {
 
@@ -2880,7 +2879,7 @@ cc_status cc_smooth_noalloc(cc_handle H, int l, double* u, const double* b, cc_s
                "available", l, (long long)need, CC_NOALLOC_SCRATCH_DOUBLES);
       return CC_ERR_ARG;
     }
-    double* scr = noalloc_scratch(dev);
+    double* scr = H->noalloc;
     double* out = scr;                      // [0, nn): Jacobi output
     BlockDev B = L.blk.d64;                 // the handle's tables, temporaries in scratch
     B.fault = nullptr;                      // nothing of the handle is written
