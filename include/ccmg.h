@@ -213,9 +213,10 @@ void cc_default_options(cc_options* opt);
 const char* cc_status_string(cc_status s);
 
 /* Text of the last error that made a call from this host thread return
- * CC_ERR_CUDA or CC_ERR_NO_MEMORY, or of a size limit that made
- * cc_smooth_noalloc return CC_ERR_ARG ("" if none); valid until the next
- * call. */
+ * CC_ERR_CUDA or CC_ERR_NO_MEMORY, of the setup step that made cc_setup
+ * reject a problem (e.g. "singular PLG fit" with CC_ERR_SINGULAR), or of
+ * a size limit that made cc_smooth_noalloc return CC_ERR_ARG ("" if none);
+ * valid until the next call that sets it. */
 const char* cc_last_error_string(void);
 
 /*

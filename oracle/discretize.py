@@ -36,6 +36,7 @@ GRAD = {-2: 1.0, -1: -8.0, 0: 0.0, 1: 8.0, 2: -1.0}          # x 1/(12 h)
 LAP = {-2: -1.0, -1: 16.0, 0: -30.0, 1: 16.0, 2: -1.0}      # x 1/(12 h^2)
 PLG_RADIUS = 4
 PLG_RADIUS_MAX = 6    # larger boxes are searched only when the 9 x 9 box has no lattice
+PLG_RADIUS_FAR = 12   # the far search, only when the 13 x 13 box has none
 EXT = extrapolation_coefficients()
 
 
@@ -254,7 +255,8 @@ def choose_lattice(lev: G.Level, ki: int) -> List[int]:
     The lattice is made of 5 distinct grid lines (rows, or else columns)
     holding 5, 4, 3, 2 and 1 present cells of the 9 x 9 box centred on the
     cell (11 x 11, then 13 x 13, where the 9 x 9 box holds none, as in thin
-    wedges at the kinks of a union of holes); such a set is poised in Pi_4 for point values (a line with 5
+    wedges at the kinks of a union of holes, and on to 25 x 25 near the tips
+    of the thinnest wedges); such a set is poised in Pi_4 for point values (a line with 5
     distinct points fixes a quartic on it, and the rest recurses on Pi_3),
     and hence for cell averages, which are an invertible map of Pi_4.  A
     cell at offset (u, v) costs u^2 + v^2, plus CUT_PENALTY if it is a cut
@@ -264,7 +266,7 @@ def choose_lattice(lev: G.Level, ki: int) -> List[int]:
     used (negative u first on a tie); among all such lattices the one of
     least total cost is taken, rows before columns on a tie.
     """
-    for radius in range(PLG_RADIUS, PLG_RADIUS_MAX + 1):
+    for radius in range(PLG_RADIUS, PLG_RADIUS_FAR + 1):
         lat = _lattice_in_box(lev, ki, radius)
         if lat is not None:
             return lat

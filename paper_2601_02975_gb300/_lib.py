@@ -133,7 +133,7 @@ def status_string(s: int) -> str:
 def _check(st: int, what: str):
     if st != CC_OK:
         msg = lib().cc_last_error_string().decode()
-        if msg and st in (CC_ERR_ARG, CC_ERR_CUDA, CC_ERR_NO_MEMORY):
+        if msg:
             what = what + " [" + msg + "]"
         raise CCError(st, what)
 

@@ -2156,6 +2156,7 @@ const char* cc_status_string(cc_status s) {
 
 cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_bc* bc, int n_bc,
                    int n, const cc_options* opt, cc_stream stream, cc_handle* out) {
+  t_last_error[0] = '\0';
   if (!out) return CC_ERR_ARG;
   *out = nullptr;
   if (!dom || !bc || n < 4 || (dom->n_holes > 0 && !dom->holes)) return CC_ERR_ARG;
@@ -2424,6 +2425,7 @@ cc_status cc_setup(const cc_domain* dom, double a, double b, double c, const cc_
     sdev.reset();
   } catch (SetupError& e) {
     cc_status st = from_setup(e.code);
+    snprintf(t_last_error, sizeof(t_last_error), "%s", e.what());
     sdev.reset();
     destroy_hierarchy(H);
     return st;

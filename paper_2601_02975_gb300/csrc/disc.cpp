@@ -175,6 +175,15 @@ LevelDisc discretize(const Problem& P, int n, SetupDevice* dev) {
       ok[r] = cell::plg_lattice(G.type.data(), n, D.plg[r], &lat[(size_t)15 * r]);
     }, 16);
   }
+  // the far search for the cells whose 13 x 13 box holds no lattice (rare:
+  // the tips of thin wedges), on host threads for both paths
+  std::vector<int> far;
+  for (size_t r = 0; r < np; ++r)
+    if (!ok[r]) far.push_back((int)r);
+  parallel_rows((int)far.size(), [&](int q) {
+    const int r = far[q];
+    ok[r] = cell::plg_lattice_far(G.type.data(), n, D.plg[r], &lat[(size_t)15 * r]);
+  }, 1);
   for (size_t r = 0; r < np; ++r)
     if (!ok[r]) throw SetupError(3, "no poised lattice for a PLG cell");
   // boundary nodes of the cut PLG cells, the moments of the cut cells, and

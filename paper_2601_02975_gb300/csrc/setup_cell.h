@@ -198,9 +198,9 @@ enum : uint8_t { T_EMPTY = 0, T_FULL = 1, T_CUT = 2 };   // LevelGeom::type
 enum : uint8_t { K_EMPTY_ = 0, K_SFV_ = 1, K_PLG_ = 2 };  // LevelDisc::kind
 
 constexpr int kNM = 28;            // moments x^p y^q, p + q <= 6
-constexpr int kLatR = 6;           // largest lattice search box: 13 x 13
+constexpr int kLatR = 6;           // largest box of the first search: 13 x 13
 constexpr int kLatR0 = 4;          // first search box: 9 x 9
-constexpr int kLatW = 2 * kLatR + 1;
+constexpr int kLatRFar = 12;       // the far search, where 13 x 13 holds no lattice: up to 25 x 25
 constexpr int kCutPenalty = 2;     // extra cost of a cut cell in a lattice
 constexpr int kCurveSamples = 1024;
 
@@ -260,28 +260,33 @@ CC_HD inline uint8_t kind_of(const uint8_t* type, const uint8_t* ext, int n, boo
 // cells (ties: smaller u); the lines and counts minimise the total cost,
 // ties to the lexicographically larger count vector from the lowest line up;
 // rows before columns on equal cost; the 9 x 9 box first, then 11 x 11 and
-// 13 x 13 where a smaller one holds no such set.  out: the 15 cells, sorted.
+// 13 x 13 where a smaller one holds no such set, and then the far search
+// (plg_lattice_far).  out: the 15 cells, sorted.
 // The cheapest lattice of the box of half-width R on lines of one orientation
-// (0: rows, 1: columns), sorted; its cost in *cost_out; false if none.
+// (0: rows, 1: columns), sorted; its cost in *cost_out; false if none.  RM
+// is the largest half-width the arrays hold (R <= RM); the result does not
+// depend on it.
+template <int RM = kLatR>
 CC_HD inline bool plg_lattice_box(const uint8_t* type, int n, int k, int R, int orient, int out[15],
                                    int* cost_out) {
+  constexpr int kLatW = 2 * RM + 1;
   const int i0 = k % n, j0 = k / n;
   struct St { int cost; int8_t have; int8_t asg[kLatW]; };
   int8_t avail[kLatW][kLatW];
   int8_t navail[kLatW];
   int16_t cost[kLatW][kLatW];
   for (int v = -R; v <= R; ++v) {
-    const int vi = v + kLatR;
+    const int vi = v + RM;
     int na = 0;
     for (int u = -R; u <= R; ++u) {
       const int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
       const int ii = i0 + di, jj = j0 + dj;
       if (ii >= 0 && jj >= 0 && ii < n && jj < n && type[jj * n + ii] != T_EMPTY) {
         const bool cut = type[jj * n + ii] == T_CUT && (di != 0 || dj != 0);
-        cost[vi][u + kLatR] = (int16_t)(u * u + v * v + (cut ? kCutPenalty : 0));
+        cost[vi][u + RM] = (int16_t)(u * u + v * v + (cut ? kCutPenalty : 0));
         // insertion by (cost, u); u grows, so equal costs keep their order
         int p = na++;
-        while (p > 0 && cost[vi][avail[vi][p - 1] + kLatR] > cost[vi][u + kLatR]) {
+        while (p > 0 && cost[vi][avail[vi][p - 1] + RM] > cost[vi][u + RM]) {
           avail[vi][p] = avail[vi][p - 1];
           --p;
         }
@@ -299,7 +304,7 @@ CC_HD inline bool plg_lattice_box(const uint8_t* type, int n, int k, int R, int 
   nxt[31].have = 1;
   CC_ROLLED
   for (int v = R; v >= -R; --v) {
-    const int vi = v + kLatR;
+    const int vi = v + RM;
     CC_ROLLED
     for (int mask = 0; mask < 32; ++mask) {
       St& b = cur[mask];
@@ -330,7 +335,7 @@ CC_HD inline bool plg_lattice_box(const uint8_t* type, int n, int k, int R, int 
         const int m2 = mask | (1 << bit);
         if (!nxt[m2].have) continue;
         int rc = 0;
-        for (int q = 0; q < cnt; ++q) rc += cost[vi][avail[vi][q] + kLatR];
+        for (int q = 0; q < cnt; ++q) rc += cost[vi][avail[vi][q] + RM];
         consider(nxt[m2].cost + rc, cnt, nxt[m2]);
       }
     }
@@ -340,7 +345,7 @@ CC_HD inline bool plg_lattice_box(const uint8_t* type, int n, int k, int R, int 
   *cost_out = nxt[0].cost;
   int c = 0;
   for (int v = -R; v <= R; ++v) {
-    const int vi = v + kLatR, cnt = nxt[0].asg[vi];
+    const int vi = v + RM, cnt = nxt[0].asg[vi];
     for (int q = 0; q < cnt; ++q) {
       const int u = avail[vi][q];
       const int di = orient == 0 ? u : v, dj = orient == 0 ? v : u;
@@ -373,6 +378,28 @@ CC_HD inline bool plg_lattice(const uint8_t* type, int n, int k, int out[15]) {
       }
     }
   return found;
+}
+
+// The far search of the rule, where the 13 x 13 box holds no lattice (a
+// cell near the tip of a thin wedge between two holes): the boxes 15 x 15 to
+// 25 x 25 in turn, rows before columns on equal cost, as above.  Host only
+// (its arrays are four times those of the first search).
+inline bool plg_lattice_far(const uint8_t* type, int n, int k, int out[15]) {
+  for (int R = kLatR + 1; R <= kLatRFar; ++R) {
+    bool found = false;
+    int best_cost = 0;
+    for (int orient = 0; orient < 2; ++orient) {
+      int tmp[15], c = 0;
+      if (!plg_lattice_box<kLatRFar>(type, n, k, R, orient, tmp, &c)) continue;
+      if (!found || c < best_cost) {
+        found = true;
+        best_cost = c;
+        for (int q = 0; q < 15; ++q) out[q] = tmp[q];
+      }
+    }
+    if (found) return true;
+  }
+  return false;
 }
 
 // --- moments ---------------------------------------------------------------

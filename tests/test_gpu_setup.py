@@ -7,7 +7,9 @@ The device kernels and the host threads run the same per-cell functions with
 IEEE operations only and no fused multiply-adds, so every table must equal
 the host path's bit for bit, on every level (union 15 and 32 include cut
 cells of two components, whose second component the host moves to a
-neighbour in both paths); the device tables are also
+neighbour in both paths; union 52 has a cell whose lattice only the host's
+far search finds, after the device's search of the 9 x 9 to 13 x 13
+boxes); the device tables are also
 compared with the oracle's directly (lattices exactly, fits to rounding).
 """
 import numpy as np
@@ -68,7 +70,8 @@ def _both(name, n, mc, **opt):
                                        ("ellipses3", 512, 64), ("four_disks", 256, 32),
                                        ("flower", 256, 32), ("rotated", 192, 24),
                                        ("box_cross", 128, 8), ("disk", 1024, 32),
-                                       ("ellipses15", 128, 32), ("ellipses32", 256, 32)])
+                                       ("ellipses15", 128, 32), ("ellipses32", 256, 32),
+                                       ("ellipses52", 256, 32)])
 def test_device_tables_equal_host_tables(name, n, mc):
     P, _, Hd, Hh = _both(name, n, mc)
     assert Hd.info.n_levels == Hh.info.n_levels

@@ -972,6 +972,63 @@ def collections_counter(it):
     return Counter(it)
 
 
+def _brute_lattice_cost(lev, ki, R):
+    """The least cost of a five-line set with counts 5, 4, 3, 2, 1 in the box
+    of half-width R around cell ki, over both orientations and every
+    assignment of the counts to distinct lines (each line taking its
+    cheapest present cells); None if the box holds no such set."""
+    from itertools import permutations
+    n = lev.n
+    j0, i0 = divmod(ki, n)
+    best = None
+    for orient in (0, 1):
+        lines = {}
+        for v in range(-R, R + 1):
+            cs = []
+            for u in range(-R, R + 1):
+                di, dj = (u, v) if orient == 0 else (v, u)
+                i, j = i0 + di, j0 + dj
+                if 0 <= i < n and 0 <= j < n and lev.present[j, i]:
+                    cut = lev.ctype[j, i] != G.REGULAR and (di, dj) != (0, 0)
+                    cs.append(u * u + v * v + (D.CUT_PENALTY if cut else 0))
+            lines[v] = sorted(cs)
+        usable = [v for v in lines if lines[v]]
+        for pick in permutations(usable, 5):
+            if any(len(lines[v]) < c for v, c in zip(pick, (5, 4, 3, 2, 1))):
+                continue
+            cost = sum(sum(lines[v][:c]) for v, c in zip(pick, (5, 4, 3, 2, 1)))
+            best = cost if best is None else min(best, cost)
+    return best
+
+
+def test_far_lattices_at_wedge_tips_are_the_cheapest_by_brute_force():
+    """Near the tip of a thin wedge between two overlapping ellipses (union
+    52 at 256^2) the 13 x 13 box holds no five-line set, and the rule's
+    search goes on to larger boxes (R4).  For every such cell the
+    exhaustive search finds no set in the 9 x 9 to 13 x 13 boxes either, the
+    oracle's lattice lies in the first larger box that holds one and has the
+    least cost there, and the cell's row has a negative own coefficient."""
+    P = W.problem_ellipses(52)
+    n = 256
+    lev = G.build_level(P.dom, n, 0.1)
+    d = D.discretize(lev, P.a, P.b, P.c)
+    far = {}
+    for ki, lat in d.lattices.items():
+        j0, i0 = divmod(ki, n)
+        ext = max(max(abs(kj % n - i0), abs(kj // n - j0)) for kj in lat)
+        if ext > D.PLG_RADIUS_MAX:
+            far[ki] = ext
+    assert far
+    for ki, ext in sorted(far.items()):
+        for R in range(D.PLG_RADIUS, ext):
+            assert _brute_lattice_cost(lev, ki, R) is None, (ki, R)
+        lat = d.lattices[ki]
+        rows = sorted(collections_counter(kj // n for kj in lat).values())
+        orient = 0 if rows == [1, 2, 3, 4, 5] else 1
+        assert _lattice_cost(lev, ki, lat, orient) == _brute_lattice_cost(lev, ki, ext), ki
+        assert D.row_diagonal(ki, lat, d.betas[ki]) < 0.0, ki
+
+
 def test_alternative_lattices_mend_a_diverging_union(monkeypatch):
     """R29 on ellipse union 30 at 128^2 (three overlapping ellipses): with the
     cheapest lattice alone, PLG rows of its 64^2 and 32^2 levels have a
