@@ -1001,6 +1001,37 @@ def _brute_lattice_cost(lev, ki, R):
     return best
 
 
+@pytest.mark.parametrize("name,n", [("disk", 64), ("disk", 128), ("four_disks", 64), ("flower", 80),
+                                    ("ellipses0", 128), ("ellipses1", 128), ("ellipses2", 128),
+                                    ("ellipses3", 128)])
+def test_plg_rows_have_the_sign_of_the_sfv_centre_weight(name, n):
+    """On the validation domains every PLG row of the finest level gives its
+    own cell a negative coefficient, the sign of the SFV centre weight
+    -5(a + c)/(2 h^2) of Eq. 4.7, of between a fifth and five times that
+    weight (measured: 0.29 to 3.04).  The lattice rule (R4) is not given by
+    the paper; this checks
+    its rows against the regular stencil rather than against itself.  It does
+    not hold everywhere: R29 lists the rows of other domains (a few per
+    level on some random unions and batch domains) that no alternative
+    lattice mends."""
+    if name == "disk":
+        P, eps = W.problem_disk(), 0.1
+    elif name == "four_disks":
+        P, eps = W.problem_four_disks(W.NEUMANN), 0.08
+    elif name == "flower":
+        P, eps = W.problem_flower(), 0.02
+    else:
+        P, eps = W.problem_ellipses(int(name[8:])), 0.1
+    lev = G.build_level(P.dom, n, eps)
+    d = D.discretize(lev, P.a, P.b, P.c)
+    centre = -5.0 * (P.a + P.c) / (2.0 * lev.h ** 2)
+    assert d.lattices
+    for k, lat in d.lattices.items():
+        own = D.row_diagonal(k, lat, d.betas[k])
+        assert own < 0.0, (k, own)
+        assert 0.2 < own / centre < 5.0, (k, own / centre)
+
+
 def test_far_lattices_at_wedge_tips_are_the_cheapest_by_brute_force():
     """Near the tip of a thin wedge between two overlapping ellipses (union
     52 at 256^2) the 13 x 13 box holds no five-line set, and the rule's
