@@ -24,8 +24,9 @@ length, the argmin ties go to the first neighbour in the order -x, +x, -y,
 first: such a cell keeps its largest component, and every other component
 joins the face neighbour (through one of its own face pieces, in the order
 -x, +x, -y, +y, near-ties to the first) whose volume with it comes closest
-to h^2 (reading R30).  A cell whose components include an inner loop (a
-hole inside the cell) is reported as unresolved.
+to h^2 (reading R30).  A cell of one component may also hold a whole hole
+(an inner loop, counted in its moments); a cell of several components that
+also holds an inner loop, or of none, is reported as unresolved.
 """
 from __future__ import annotations
 
