@@ -114,6 +114,25 @@ def test_setup_rejects_bad_arguments(lib, case):
     assert ei.value.status in (1, 2)
 
 
+def test_rejected_setup_says_which_step(lib):
+    """A problem the setup rejects names the step in cc_last_error_string and
+    in the Python error: ellipse union 58 at 2048^2 has cells near a wedge
+    tip with no five-line set up to 25 x 25 (the far search of the lattice
+    rule ends there), and union 52 at 256^2, whose cells need boxes of
+    15 x 15, sets up."""
+    from paper_2601_02975_gb300 import CCError
+    P = W.problem_ellipses(58)
+    with pytest.raises(CCError) as ei:
+        _host(P, 2048, min_coarse_n=32)
+    assert ei.value.status == 3
+    assert "no poised lattice" in str(ei.value)
+    assert lib.lib().cc_last_error_string().decode() == "no poised lattice for a PLG cell"
+    P = W.problem_ellipses(52)
+    H = _host(P, 256, min_coarse_n=32)
+    assert H.info.n_levels >= 2
+    H.close()
+
+
 def test_new_options_are_checked(lib):
     """hole_cells, serve_slots, w_depth, fmg_cycle and krylov are validated
     by cc_setup (krylov: 0..32, with a V or W cycle); cc_serve_budget rejects
