@@ -297,6 +297,24 @@ static std::vector<Piece> full_faces(const LevelGeom& G, int i, int j) {
   return v;
 }
 
+// Alg. 1's choice of a neighbour: the candidate whose volume with vol_add
+// comes closest to h^2.  Scores within 1e-9 h^2 of the smallest are ties
+// (they differ by rounding only, e.g. the mirror cells on a diagonal of a
+// disk): the first such candidate wins, so the choice does not depend on
+// rounding.
+static int closest_to_h2(const LevelGeom& G, const std::vector<int>& cand, double vol_add) {
+  const double h2 = G.h * G.h;
+  std::vector<double> score(cand.size());
+  double smin = 0;
+  for (size_t q = 0; q < cand.size(); ++q) {
+    score[q] = std::fabs(G.vol[cand[q]] + vol_add - h2);
+    smin = q == 0 ? score[q] : std::min(smin, score[q]);
+  }
+  for (size_t q = 0; q < cand.size(); ++q)
+    if (score[q] <= smin + 1e-9 * h2) return cand[q];
+  return cand[0];
+}
+
 LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
   LevelGeom G;
   G.n = n;
@@ -525,7 +543,7 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
     double mk[kMoments];
     std::fill(mk, mk + kMoments, 0.0);
     for (const Piece& pc : O.pcs) piece_moments(P, pc, px, py, h, mk);
-    const double vk = mk[0] * h * h, h2 = h * h;
+    const double vk = mk[0] * h * h;
     bool on[4] = {false, false, false, false};
     for (const Piece& pc : O.pcs)
       if (!pc.arc) on[pc.face] = true;
@@ -542,15 +560,7 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
                  ") has no neighbour";
       continue;
     }
-    double smin = 0;
-    std::vector<double> score(cand.size());
-    for (size_t q = 0; q < cand.size(); ++q) {
-      score[q] = std::fabs(G.vol[cand[q]] + vk - h2);
-      smin = q == 0 ? score[q] : std::min(smin, score[q]);
-    }
-    int best = cand[0];
-    for (size_t q = 0; q < cand.size(); ++q)
-      if (score[q] <= smin + 1e-9 * h2) { best = cand[q]; break; }
+    const int best = closest_to_h2(G, cand, vk);
     const int bi = best % n, bj = best / n;
     if (!G.cut.count(best)) {
       Cut T;
@@ -600,18 +610,7 @@ LevelGeom build_geometry(const Problem& P, int n, SetupDevice* dev) {
       if (t != k && std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
     }
     if (cand.empty()) throw SetupError(2, "a small cut cell has no neighbour to merge into");
-    // scores within 1e-9 h^2 of the smallest are ties (they differ by
-    // rounding only, e.g. the mirror cells on a diagonal of a disk): the
-    // first such neighbour wins, so the choice does not depend on rounding
-    std::vector<double> score(cand.size());
-    double smin = 0;
-    for (size_t q = 0; q < cand.size(); ++q) {
-      score[q] = std::fabs(G.vol[cand[q]] + G.vol[k] - h2);
-      smin = q == 0 ? score[q] : std::min(smin, score[q]);
-    }
-    int best = cand[0];
-    for (size_t q = 0; q < cand.size(); ++q)
-      if (score[q] <= smin + 1e-9 * h2) { best = cand[q]; break; }
+    const int best = closest_to_h2(G, cand, G.vol[k]);
     int bi = best % n, bj = best / n;
     double mk[kMoments], mt[kMoments], sh[kMoments];
     G.moments(k, mk);
