@@ -316,7 +316,8 @@ def _lattice_in_box_orient(lev: G.Level, ki: int, radius: int, orient: int):
 
 
 def lattice_candidates(lev: G.Level, ki: int) -> List[List[int]]:
-    """The alternatives to the chosen lattice (R29): the cheapest lattice of
+    """The alternatives to the chosen lattice (for a row whose own coefficient
+    is not negative): the cheapest lattice of
     each box (9 x 9, 11 x 11, 13 x 13) and orientation (rows, then columns),
     in that order."""
     out = []
@@ -478,7 +479,7 @@ def discretize(lev: G.Level, a: float, b: float, c: float) -> Disc:
         withb = k in bd_index
         beta, beta_b = fit_beta(lev, k, lat, a, b, c, withb)
         if row_diagonal(k, lat, beta) >= 0.0:
-            # R29: a row whose own coefficient is not negative takes the first
+            # a row whose own coefficient is not negative takes the first
             # alternative lattice whose fit gives a negative one, if any
             for alt in lattice_candidates(lev, k):
                 if alt == lat:

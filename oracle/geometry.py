@@ -24,7 +24,7 @@ length, the argmin ties go to the first neighbour in the order -x, +x, -y,
 first: such a cell keeps its largest component, and every other component
 joins the face neighbour (through one of its own face pieces, in the order
 -x, +x, -y, +y, near-ties to the first) whose volume with it comes closest
-to h^2 (reading R30).  A cell of one component may also hold a whole hole
+to h^2 (a reading: the paper does not say where the extra components go).  A cell of one component may also hold a whole hole
 (an inner loop, counted in its moments); a cell of several components that
 also holds an inner loop, or of none, is reported as unresolved.
 """

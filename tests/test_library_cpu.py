@@ -239,7 +239,7 @@ def test_coarse_level_tables_match_oracle(lib, name, n, mc):
     level.  Problem 8 of the batch workload is the one whose coarsest level
     has PLG rows with a positive diagonal that no alternative lattice mends:
     both sides build the same rows.  Ellipse union 30 has such rows on its
-    64^2 and 32^2 levels that alternative lattices do mend (R29): both sides
+    64^2 and 32^2 levels that alternative lattices do mend: both sides
     pick the same alternatives.  Problem 4 of the batch and union 15 have
     finest-level cut cells of two components (Alg. 1): both sides keep the
     same one, move the other to the same neighbour, and build the same

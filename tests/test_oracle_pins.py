@@ -917,7 +917,7 @@ def _lattice_cost(lev, ki, cells, orient):
 
 @pytest.mark.parametrize("name", ["disk", "flower"])
 def test_lattice_is_the_cheapest_five_line_set_by_brute_force(name):
-    """The lattice rule (R4, a reading of Def. 4.3) restated as an exhaustive
+    """The lattice rule (a reading of Def. 4.3) restated as an exhaustive
     search: over both orientations and every assignment of the counts
     5, 4, 3, 2, 1 to distinct lines of the 9 x 9 box, each line taking its
     cheapest present cells, the least total cost.  The oracle's dynamic
@@ -959,7 +959,7 @@ def test_lattice_is_the_cheapest_five_line_set_by_brute_force(name):
         orient = 0 if rows == [1, 2, 3, 4, 5] else 1
         assert rows == [1, 2, 3, 4, 5] or cols == [1, 2, 3, 4, 5], ki
         if _lattice_cost(lev, ki, lat, orient) != best:
-            # only an alternative taken by R29: the cheapest lattice's row
+            # only an alternative lattice taken for the sign: the cheapest lattice's row
             # then has a coefficient of its own cell that is not negative
             first = D.choose_lattice(lev, ki)
             beta, _ = D.fit_beta(lev, ki, first, P.a, P.b, P.c, ki in d.bd_cells)
@@ -1008,12 +1008,11 @@ def test_plg_rows_have_the_sign_of_the_sfv_centre_weight(name, n):
     """On the validation domains every PLG row of the finest level gives its
     own cell a negative coefficient, the sign of the SFV centre weight
     -5(a + c)/(2 h^2) of Eq. 4.7, of between a fifth and five times that
-    weight (measured: 0.29 to 3.04).  The lattice rule (R4) is not given by
-    the paper; this checks
-    its rows against the regular stencil rather than against itself.  It does
-    not hold everywhere: R29 lists the rows of other domains (a few per
-    level on some random unions and batch domains) that no alternative
-    lattice mends."""
+    weight (measured: 0.29 to 3.04).  The lattice rule is not given by the
+    paper; this checks its rows against the regular stencil rather than
+    against itself.  It does not hold everywhere: on some random unions and
+    batch domains a few rows per level keep a non-negative coefficient that
+    no alternative lattice mends."""
     if name == "disk":
         P, eps = W.problem_disk(), 0.1
     elif name == "four_disks":
@@ -1035,7 +1034,7 @@ def test_plg_rows_have_the_sign_of_the_sfv_centre_weight(name, n):
 def test_far_lattices_at_wedge_tips_are_the_cheapest_by_brute_force():
     """Near the tip of a thin wedge between two overlapping ellipses (union
     52 at 256^2) the 13 x 13 box holds no five-line set, and the rule's
-    search goes on to larger boxes (R4).  For every such cell the
+    search goes on to larger boxes.  For every such cell the
     exhaustive search finds no set in the 9 x 9 to 13 x 13 boxes either, the
     oracle's lattice lies in the first larger box that holds one and has the
     least cost there, and the cell's row has a negative own coefficient."""
@@ -1061,7 +1060,7 @@ def test_far_lattices_at_wedge_tips_are_the_cheapest_by_brute_force():
 
 
 def test_alternative_lattices_mend_a_diverging_union(monkeypatch):
-    """R29 on ellipse union 30 at 128^2 (three overlapping ellipses): with the
+    """Alternative lattices on ellipse union 30 at 128^2 (three overlapping ellipses): with the
     cheapest lattice alone, PLG rows of its 64^2 and 32^2 levels have a
     coefficient of their own cell that is not negative, and the W(4,4)
     iteration diverges.  With the alternatives every PLG row of every level
