@@ -40,9 +40,17 @@ def _host(P, n, **kw):
 
 @pytest.mark.parametrize("name,n", [("disk", 32), ("disk", 64), ("ellipses0", 64),
                                     ("ellipses3", 96), ("box_cross", 24), ("four_disks_N", 64),
-                                    ("ellipses0", 256)])
+                                    ("ellipses0", 256), ("waist", 48)])
 def test_setup_tables_match_oracle(lib, name, n):
-    if name == "disk":
+    """The finest level's cell types, volumes, kinds, lattices, fits and
+    boundary coefficients equal the oracle's.  "waist": two disks overlapping
+    by a sliver, whose waist splits a cell into two components (Alg. 1)."""
+    if name == "waist":
+        u = W.u_expcos()
+        dom = W.Domain(holes=[W.Ellipse(0.3, 0.507, 0.2, 0.2), W.Ellipse(0.6999, 0.507, 0.2, 0.2)],
+                       hole_bc=[W.BC(), W.BC(W.NEUMANN, 0, 1)])
+        P = W.Problem("waist", dom, 1.0, 0.3, 1.5, u, W.apply_L(u, 1.0, 0.3, 1.5))
+    elif name == "disk":
         P = W.problem_disk()
     elif name == "four_disks_N":
         P = W.problem_four_disks(W.NEUMANN)

@@ -355,6 +355,50 @@ def test_components_moved_to_a_neighbour_keep_the_moments(monkeypatch):
         assert abs(_level_moment(lev, p, q) - v) < 1e-13, (p, q)
 
 
+def _waist_domain():
+    """Two disks of radius 0.2 whose centres are 0.3999 apart: their union
+    has a waist 0.0089 high at x = 0.49995, thinner than a cell at the grids
+    below, so the cell holding it is split into the parts above and below."""
+    return W.Domain(holes=[W.Ellipse(0.3, 0.507, 0.2, 0.2), W.Ellipse(0.6999, 0.507, 0.2, 0.2)],
+                    hole_bc=[W.BC(), W.BC(W.NEUMANN, 0, 1)])
+
+
+@pytest.mark.parametrize("n", [32, 48, 64])
+def test_cell_split_by_a_waist_keeps_the_moments(monkeypatch, n):
+    """Alg. 1, cells of several components, on a union of two disks that
+    overlap by a sliver: the cells holding the waist have a part above and
+    a part below it; one part stays, the other joins a neighbour, and the
+    level resolves.  The area and the moments of the domain equal those of
+    the square minus the union: two disks minus their lens, with the
+    first moments from the union's symmetry and the second moments of the
+    lens by adaptive quadrature."""
+    dom = _waist_domain()
+    moved = _moved_components(monkeypatch)
+    lev = G.build_level(dom, n, 0.1)
+    assert moved and lev.resolved, lev.reason
+    r, c1, c2, cy = 0.2, 0.3, 0.6999, 0.507
+    d = c2 - c1
+    lens = 2 * r * r * math.acos(d / (2 * r)) - 0.5 * d * math.sqrt(4 * r * r - d * d)
+    union = 2 * math.pi * r * r - lens
+    xm = 0.5 * (c1 + c2)
+
+    def lens_int(f):
+        half = lambda x: min(math.sqrt(max(0.0, r * r - (x - c1) ** 2)), math.sqrt(max(0.0, r * r - (x - c2) ** 2)))
+        return integrate.dblquad(lambda y, x: f(x, y), c2 - r, c1 + r, lambda x: cy - half(x),
+                                 lambda x: cy + half(x), epsabs=1e-16, epsrel=1e-14)[0]
+
+    disk_xx = sum(math.pi * r * r * (c * c + r * r / 4) for c in (c1, c2))
+    disk_yy = 2 * math.pi * r * r * (cy * cy + r * r / 4)
+    disk_xy = sum(math.pi * r * r * c * cy for c in (c1, c2))
+    want = {(0, 0): 1.0 - union, (1, 0): 0.5 - union * xm, (0, 1): 0.5 - union * cy,
+            (2, 0): 1 / 3 - (disk_xx - lens_int(lambda x, y: x * x)),
+            (0, 2): 1 / 3 - (disk_yy - lens_int(lambda x, y: y * y)),
+            (1, 1): 0.25 - (disk_xy - lens_int(lambda x, y: x * y))}
+    assert abs(lev.vol.sum() - want[(0, 0)]) < 1e-13
+    for (p, q), v in want.items():
+        assert abs(_level_moment(lev, p, q) - v) < 1e-13, (p, q)
+
+
 def test_components_moved_in_an_overlapping_union_keep_the_moments(monkeypatch):
     """The same step in a union of overlapping ellipses (union 15) at
     N = 128, where it moves components; at N = 150 no cell has several.
